@@ -78,7 +78,7 @@ def _int_exp(a, x1, x2):
     h = x2 - x1
     pos = a.real >= 0
     ref = np.where(pos, x2, x1)
-    with np.errstate(invalid="ignore", divide="ignore"):
+    with np.errstate(invalid="ignore", divide="ignore", over="ignore"):
         f = np.where(pos, -np.expm1(-a * h) / a, np.expm1(a * h) / a)
     f = np.where(np.abs(a) * h < 1e-300, h, f)
     return ref, f
