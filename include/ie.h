@@ -1,0 +1,147 @@
+/*
+ * ie.h -- C ABI of the GB300 (sm_103a) Galerkin integral-equation solver.
+ *
+ * The library solves the discretised contracting integral equation of
+ * Kruglyakov & Bloshanskaya ("High-performance parallel solver for integral
+ * equations of electromagnetics based on Galerkin method"):
+ *
+ *   U_n - sum_m gamma_m K_n^m U_m = U_n^0                       eq. (slae1)
+ *   K_n^m = I + (2/V_n) sqrt(Re s_b^m Re s_b^n) B_n^m,
+ *   gamma_m = (s_a^m - s_b^m) / (s_a^m + conj s_b^m)            eq. (slae_matricies)
+ *
+ * whose matrix is A = S + R1 B R2 with S = diag(1 - gamma), R1 = -diag(2 s / V),
+ * R2 = diag(s gamma), s = sqrt(Re sigma_b) and B block-Toeplitz in x and y
+ * (eq. (matrix_convolv), (bcyl)).  B is applied with zero-padded 2-D FFTs and a
+ * per-wavenumber contraction of the symmetry-compressed blocks (Sect. 3.1, 3.3).
+ *
+ * Conventions.  SI units; time dependence exp(-i omega t); z positive downwards,
+ * the earth surface at z = 0.  Complex numbers are interleaved (re, im) pairs of
+ * double (c128) or float (c64).  A field vector for R right-hand sides is
+ * [R][3][Nz][Ny][Nx] (component x, y, z; x fastest).  Cell arrays are [Nz][Ny][Nx].
+ *
+ * Ownership.  Pointers named *_host are host memory read during the call; the
+ * library keeps no reference to them.  Pointers named *_dev are device memory on
+ * the context's device, owned by the caller, and must stay valid until the call
+ * that uses them has completed on its stream.  The context owns its coefficient
+ * tensors and workspaces and frees them in ie_destroy.
+ *
+ * Errors.  Every call returns an ie_status; nothing is thrown across the ABI.
+ * On IE_ERR_* the outputs are unspecified.  A solve that reaches its iteration
+ * cap returns IE_NOT_CONVERGED with info filled and the best iterate in u.
+ *
+ * Streams.  Calls are ordered on the context's stream (ie_ctx_stream); matvec
+ * accepts an explicit stream.  ie_setup and the solves synchronise before they
+ * return.
+ */
+#ifndef IE_GB300_H
+#define IE_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ie_ctx ie_ctx;
+
+typedef enum {
+  IE_OK = 0,
+  IE_NOT_CONVERGED = 1,  /* iteration cap reached; best iterate returned */
+  IE_BREAKDOWN = 2,      /* a Krylov vector vanished before convergence */
+  IE_ERR_ARG = -1,       /* invalid argument (null pointer, size, enum) */
+  IE_ERR_GEOMETRY = -2,  /* a cell straddles a layer interface, or Re sigma_b <= 0 in the domain */
+  IE_ERR_COEFF = -3,     /* coefficient tensor missing or inconsistent */
+  IE_ERR_OOM = -4,       /* device allocation failed */
+  IE_ERR_CUDA = -5       /* a CUDA call failed */
+} ie_status;
+
+enum { IE_C64 = 0, IE_C128 = 1 };                 /* element type of matvec vectors */
+enum { IE_FP64 = 0, IE_MIXED = 1 };              /* solve precision */
+
+/* Grid of Nx*Ny*Nz cells (eq. (bcyl)): equal lateral sizes hx, hy; z_edges_host holds
+ * the nz+1 increasing cell boundaries (m).  x0, y0 are the lateral origin (m). */
+typedef struct {
+  int nx, ny, nz;
+  double hx, hy;
+  const double *z_edges_host;
+  double x0, y0;
+} ie_grid;
+
+/* Layered background (Appendix B): n_interfaces = L values d_1..d_L (d_1 = 0, the
+ * surface); sigma_host holds L+1 complex conductivities (interleaved) for the air
+ * (layer 0), the finite layers and the basement, in S/m. */
+typedef struct {
+  int n_interfaces;
+  const double *interfaces_host;
+  const double *sigma_host;
+} ie_layers;
+
+typedef struct {
+  int restart;       /* GMRES restart length m (>= 2); 0 selects 30 */
+  int max_iter;      /* cap on inner iterations per solve; 0 selects 2000 */
+  double inner_tol;  /* mixed precision: relative tolerance of each inner c64 solve; 0 selects 1e-3 */
+  int max_outer;     /* mixed precision: cap on refinement steps; 0 selects 50 */
+} ie_options;
+
+typedef struct {
+  int outer_iters;       /* FP64 residual evaluations (refinement steps) */
+  int inner_iters;       /* total Krylov iterations */
+  double final_rel_res;  /* max over right-hand sides of ||b - A u|| / ||b|| with the c128 operator */
+  double t_solve;        /* wall time of the solve, s */
+} ie_solve_info;
+
+/* Build a context for one grid, one layered background, one anomaly and n_freq
+ * frequencies (one operator instance per frequency).
+ *   sigma_a_host : Nz*Ny*Nx complex anomaly conductivities (interleaved), cell order.
+ *   freq_host    : n_freq frequencies in Hz.
+ *   q_real_host  : n_freq compressed real-space coefficient tensors, each
+ *                  [Ny][Nx][6][Nz][Nz] complex (block order xx, yy, zz, xy, xz, yz;
+ *                  offsets i in [0,Ny), j in [0,Nx); the storage of eq. (matrix_symm)),
+ *                  i.e. the 3x3 blocks B_n^m of Appendix A.  Required.
+ *   max_rhs      : largest number of right-hand sides passed to one call (1..4).
+ * The tensors are transformed on the device (2N-periodic embedding with the
+ * parities of Lemma 2, 2-D DFT) and kept in c128 and c64. */
+ie_status ie_setup(const ie_grid *grid, const ie_layers *layers, const double *sigma_a_host, int n_freq,
+                   const double *freq_host, const double *q_real_host, int max_rhs, const ie_options *opt,
+                   ie_ctx **out);
+
+/* y = A x (transpose = 0) or y = A^T x (transpose = 1) for instance inst, with nrhs
+ * right-hand sides.  dtype selects c64 (IE_C64, the c64 coefficient copy) or c128.
+ * x_dev, y_dev: device arrays [nrhs][3][Nz][Ny][Nx] of that type; they must not
+ * alias.  stream: a cudaStream_t, or NULL for the context stream.  Asynchronous. */
+ie_status ie_matvec(ie_ctx *ctx, int inst, const void *x_dev, void *y_dev, int nrhs, int dtype, int transpose,
+                    void *stream);
+
+/* Solve A u = b for instance inst (Sect. 3.3 (ii): GMRES with classical Gram-Schmidt
+ * applied twice).  precision IE_FP64: every product with the c128 operator.
+ * IE_MIXED: iterative refinement whose residual uses the c128 operator and whose
+ * corrections come from GMRES on the c64 operator with FP64 Arnoldi vectors.
+ * Stops when ||b - A u|| <= tol ||b|| for every right-hand side.
+ * b_dev, u_dev: device c128 [nrhs][3][Nz][Ny][Nx]; if use_x0 the initial guess is
+ * read from u_dev, otherwise it is zero. */
+ie_status ie_solve(ie_ctx *ctx, int inst, const void *b_dev, void *u_dev, int nrhs, double tol, int precision,
+                   int use_x0, ie_solve_info *info);
+
+/* Solve the transposed system A^T w = b (same arguments as ie_solve).  The
+ * transpose uses the complex symmetry B^T = B of Lorentz reciprocity, so
+ * A^T = S + R2 B R1. */
+ie_status ie_adjoint_solve(ie_ctx *ctx, int inst, const void *b_dev, void *w_dev, int nrhs, double tol,
+                           int precision, int use_x0, ie_solve_info *info);
+
+/* Right-hand side U^0 of eq. (slae_matricies) for a magnetotelluric plane wave:
+ * the 1-D normal field of the background, normalised by H_y(0) = 1 (x-polarisation,
+ * pol = 0) or H_x(0) = -1 (y-polarisation, pol = 1), averaged over every cell and
+ * scaled by sqrt(Re sigma_b).  u0_dev: device c128 [3][Nz][Ny][Nx]. */
+ie_status ie_rhs_mt(ie_ctx *ctx, int inst, int pol, void *u0_dev);
+
+/* The context's CUDA stream (a cudaStream_t). */
+void *ie_ctx_stream(ie_ctx *ctx);
+
+/* Bytes of device memory held by the context. */
+long long ie_ctx_device_bytes(ie_ctx *ctx);
+
+void ie_destroy(ie_ctx *ctx);
+const char *ie_status_str(ie_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IE_GB300_H */

@@ -192,3 +192,36 @@ def gmres(apply, b, tol=1e-12, m=30, max_iter=2000, x0=None):
                 break
         x = x + Vb[:k_used].T @ y
     return x.reshape(bshape), it, hist
+
+
+def block_at(q, i, j):
+    """The 3Nz x 3Nz block B(i, j) for any signed offset from the compressed tensor
+    q [Ny][Nx][6][Nz][Nz], by the lateral parities of Lemma 2 and Lemma 1."""
+    ai, aj = abs(i), abs(j)
+    six = np.empty_like(q[0, 0])
+    for b, (px, py) in enumerate(PARITY):
+        s = (py if i < 0 else 1) * (px if j < 0 else 1)
+        six[b] = s * q[ai, aj, b]
+    return full_block(six)
+
+
+def direct_rows(model, q, x, cells):
+    """(A x) at the listed cells (z, y, x) by direct summation over every source cell;
+    returns an array [len(cells)][3].  q: compressed tensor; x: [3][Nz][Ny][Nx]."""
+    g = model.grid
+    nz, ny, nx = g.nz, g.ny, g.nx
+    gamma, s, V = diagonals(model)
+    xs = (s[:, None, None] * gamma)[None] * x                      # R2 x
+    out = []
+    for (zn, yn, xn) in cells:
+        acc = np.zeros(3, dtype=np.complex128)
+        for yy in range(ny):
+            i = yn - yy
+            for xx in range(nx):
+                j = xn - xx
+                B = block_at(q, i, j)
+                rows = B[[zn, nz + zn, 2 * nz + zn]]                  # [3][3Nz]
+                acc += rows @ xs[:, :, yy, xx].reshape(-1)
+        r1 = -(2.0 / V[zn]) * s[zn]
+        out.append((1.0 - gamma[zn, yn, xn]) * x[:, zn, yn, xn] + r1 * acc)
+    return np.array(out)

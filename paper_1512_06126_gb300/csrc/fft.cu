@@ -1,0 +1,202 @@
+// Batched FFT kernels: the strided-axis pass and the two row passes that also
+// transpose between the vector layout [cz][y][x] and the wavenumber-major
+// layout [y][kx][cz] (cz = rhs * 3Nz + component * Nz + z).
+#include "fft.cuh"
+
+#include <stdexcept>
+
+namespace ie {
+
+FftPlan make_plan(int L) {
+  FftPlan p{};
+  p.L = L;
+  p.n_stages = 0;
+  int n = L;
+  auto push = [&](int r) {
+    if (p.n_stages >= kMaxStages) throw std::runtime_error("FFT plan too long");
+    p.radix[p.n_stages++] = r;
+  };
+  while (n % 4 == 0) { push(4); n /= 4; }
+  while (n % 2 == 0) { push(2); n /= 2; }
+  for (int f = 3; n > 1; f += 2) {
+    while (n % f == 0) {
+      if (f != 3 && f != 5 && f != 7 && f != 11 && f != 13)
+        throw std::runtime_error("FFT length has a prime factor other than 2, 3, 5, 7, 11, 13");
+      push(f);
+      n /= f;
+    }
+  }
+  return p;
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kThreads) fft_axis_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
+                                                            int Lin, int Lout, long long inner, FftPlan plan,
+                                                            T scale) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int TI = fft_ti<T>();
+  const int L = plan.L;
+  C<T> *tw = reinterpret_cast<C<T> *>(smem_raw);
+  C<T> *A = tw + L;
+  C<T> *B = A + (size_t)L * TI;
+  const int tid = threadIdx.x;
+  const long long i0 = (long long)blockIdx.x * TI;
+  const long long o = blockIdx.y;
+  fill_twiddles<T>(tw, L, tid, kThreads);
+  for (int q = tid; q < L * TI; q += kThreads) {
+    const int l = q / TI, t = q % TI;
+    C<T> v = mk<T>(0, 0);
+    if (l < Lin && i0 + t < inner) v = in[(o * Lin + l) * inner + i0 + t];
+    A[l * TI + t] = v;
+  }
+  __syncthreads();
+  C<T> *res = fft_smem<T, INV>(A, B, TI, TI, tw, plan, tid, kThreads);
+  for (int q = tid; q < Lout * TI; q += kThreads) {
+    const int l = q / TI, t = q % TI;
+    if (i0 + t < inner) out[(o * Lout + l) * inner + i0 + t] = cscale(res[l * TI + t], scale);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) fft_rows_fwd_kernel(const C<T> *__restrict__ x,
+                                                                const C<T> *__restrict__ in_scale,
+                                                                C<T> *__restrict__ t1, int CZ, int Nz, int Ny,
+                                                                int Nx, FftPlan plan) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int TI = fft_ti<T>();
+  constexpr int LD = TI + 1;
+  const int L = plan.L;  // 2 Nx
+  C<T> *tw = reinterpret_cast<C<T> *>(smem_raw);
+  C<T> *A = tw + L;
+  C<T> *B = A + (size_t)L * LD;
+  const int tid = threadIdx.x;
+  const int cz0 = blockIdx.x * TI;
+  const int y = blockIdx.y;
+  fill_twiddles<T>(tw, L, tid, kThreads);
+  for (int q = tid; q < Nx * TI; q += kThreads) {
+    const int t = q / Nx, xx = q % Nx;
+    const int cz = cz0 + t;
+    C<T> v = mk<T>(0, 0);
+    if (cz < CZ) {
+      v = x[((long long)cz * Ny + y) * Nx + xx];
+      if (in_scale) v = cmul(v, in_scale[((long long)(cz % Nz) * Ny + y) * Nx + xx]);
+    }
+    A[xx * LD + t] = v;
+  }
+  for (int q = tid; q < (L - Nx) * TI; q += kThreads) {
+    const int l = Nx + q / TI, t = q % TI;
+    A[l * LD + t] = mk<T>(0, 0);
+  }
+  __syncthreads();
+  C<T> *res = fft_smem<T, false>(A, B, LD, TI, tw, plan, tid, kThreads);
+  for (int q = tid; q < L * TI; q += kThreads) {
+    const int kx = q / TI, t = q % TI;
+    if (cz0 + t < CZ) t1[((long long)y * L + kx) * CZ + cz0 + t] = res[kx * LD + t];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) fft_rows_inv_kernel(const C<T> *__restrict__ t1,
+                                                                const C<T> *__restrict__ x,
+                                                                const C<T> *__restrict__ diag,
+                                                                const C<T> *__restrict__ out_scale,
+                                                                C<T> *__restrict__ y_out, int CZ, int Nz, int Ny,
+                                                                int Nx, FftPlan plan) {
+  extern __shared__ unsigned char smem_raw[];
+  constexpr int TI = fft_ti<T>();
+  constexpr int LD = TI + 1;
+  const int L = plan.L;
+  C<T> *tw = reinterpret_cast<C<T> *>(smem_raw);
+  C<T> *A = tw + L;
+  C<T> *B = A + (size_t)L * LD;
+  const int tid = threadIdx.x;
+  const int cz0 = blockIdx.x * TI;
+  const int y = blockIdx.y;
+  fill_twiddles<T>(tw, L, tid, kThreads);
+  for (int q = tid; q < L * TI; q += kThreads) {
+    const int kx = q / TI, t = q % TI;
+    C<T> v = mk<T>(0, 0);
+    if (cz0 + t < CZ) v = t1[((long long)y * L + kx) * CZ + cz0 + t];
+    A[kx * LD + t] = v;
+  }
+  __syncthreads();
+  C<T> *res = fft_smem<T, true>(A, B, LD, TI, tw, plan, tid, kThreads);
+  for (int q = tid; q < Nx * TI; q += kThreads) {
+    const int t = q / Nx, xx = q % Nx;
+    const int cz = cz0 + t;
+    if (cz < CZ) {
+      const long long cell = ((long long)(cz % Nz) * Ny + y) * Nx + xx;
+      const long long gi = ((long long)cz * Ny + y) * Nx + xx;
+      C<T> v = cmul(res[xx * LD + t], out_scale[cell]);
+      if (diag) cfma(v, diag[cell], x[gi]);
+      y_out[gi] = v;
+    }
+  }
+}
+
+template <typename T> size_t axis_smem(int L) { return sizeof(C<T>) * ((size_t)L + 2 * (size_t)L * fft_ti<T>()); }
+template <typename T> size_t rows_smem(int L) {
+  return sizeof(C<T>) * ((size_t)L + 2 * (size_t)L * (fft_ti<T>() + 1));
+}
+
+template <typename K> void set_smem(K kern, size_t bytes) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+template <typename T, bool INV>
+void launch_fft_axis(const C<T> *in, C<T> *out, int outer, int Lin, int Lout, long long inner,
+                     const FftPlan &plan, T scale, cudaStream_t s) {
+  constexpr int TI = fft_ti<T>();
+  const size_t sm = axis_smem<T>(plan.L);
+  auto k = fft_axis_kernel<T, INV>;
+  set_smem(k, sm);
+  dim3 grid((unsigned)((inner + TI - 1) / TI), (unsigned)outer);
+  k<<<grid, kThreads, sm, s>>>(in, out, Lin, Lout, inner, plan, scale);
+}
+
+template <typename T>
+void launch_fft_rows_fwd(const C<T> *x, const C<T> *in_scale, C<T> *t1, int CZ, int Nz, int Ny, int Nx,
+                         const FftPlan &plan, cudaStream_t s) {
+  constexpr int TI = fft_ti<T>();
+  const size_t sm = rows_smem<T>(plan.L);
+  auto k = fft_rows_fwd_kernel<T>;
+  set_smem(k, sm);
+  dim3 grid((unsigned)((CZ + TI - 1) / TI), (unsigned)Ny);
+  k<<<grid, kThreads, sm, s>>>(x, in_scale, t1, CZ, Nz, Ny, Nx, plan);
+}
+
+template <typename T>
+void launch_fft_rows_inv(const C<T> *t1, const C<T> *x, const C<T> *diag, const C<T> *out_scale, C<T> *y,
+                         int CZ, int Nz, int Ny, int Nx, const FftPlan &plan, cudaStream_t s) {
+  constexpr int TI = fft_ti<T>();
+  const size_t sm = rows_smem<T>(plan.L);
+  auto k = fft_rows_inv_kernel<T>;
+  set_smem(k, sm);
+  dim3 grid((unsigned)((CZ + TI - 1) / TI), (unsigned)Ny);
+  k<<<grid, kThreads, sm, s>>>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx, plan);
+}
+
+template void launch_fft_axis<float, false>(const float2 *, float2 *, int, int, int, long long, const FftPlan &,
+                                            float, cudaStream_t);
+template void launch_fft_axis<float, true>(const float2 *, float2 *, int, int, int, long long, const FftPlan &,
+                                           float, cudaStream_t);
+template void launch_fft_axis<double, false>(const double2 *, double2 *, int, int, int, long long,
+                                             const FftPlan &, double, cudaStream_t);
+template void launch_fft_axis<double, true>(const double2 *, double2 *, int, int, int, long long, const FftPlan &,
+                                            double, cudaStream_t);
+template void launch_fft_rows_fwd<float>(const float2 *, const float2 *, float2 *, int, int, int, int,
+                                         const FftPlan &, cudaStream_t);
+template void launch_fft_rows_fwd<double>(const double2 *, const double2 *, double2 *, int, int, int, int,
+                                          const FftPlan &, cudaStream_t);
+template void launch_fft_rows_inv<float>(const float2 *, const float2 *, const float2 *, const float2 *, float2 *,
+                                         int, int, int, int, const FftPlan &, cudaStream_t);
+template void launch_fft_rows_inv<double>(const double2 *, const double2 *, const double2 *, const double2 *,
+                                          double2 *, int, int, int, int, const FftPlan &, cudaStream_t);
+
+}  // namespace ie

@@ -1,0 +1,607 @@
+// C ABI of the GB300 integral-equation solver: context, setup, the FFT matrix-vector
+// product A = S + R1 B R2 (eq. (matrix_convolv)), GMRES and the mixed-precision
+// iterative refinement.  See include/ie.h for the contract of every entry point.
+#include "../../include/ie.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "blas.cuh"
+#include "contract.cuh"
+#include "fft.cuh"
+#include "setup.cuh"
+
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr double kMu0 = 4e-7 * M_PI;
+
+struct DiagSet {  // per-cell complex scales of one precision
+  void *in_f = nullptr, *out_f = nullptr, *diag = nullptr, *in_t = nullptr, *out_t = nullptr;
+};
+
+struct Instance {
+  double freq = 0.0;
+  double2 *q64 = nullptr;
+  float2 *q32 = nullptr;
+};
+
+}  // namespace
+
+struct ie_ctx {
+  int nx = 0, ny = 0, nz = 0;
+  double hx = 0, hy = 0, x0 = 0, y0 = 0;
+  std::vector<double> ze, d;
+  std::vector<cd> sig, sigma_a;
+  std::vector<int> lay;
+  ie::FftPlan px{}, py{};
+  int max_rhs = 1;
+  int restart = 30, max_iter = 2000, max_outer = 50;
+  double inner_tol = 1e-3;
+  std::vector<Instance> inst;
+  DiagSet d64, d32;
+  cudaStream_t stream = nullptr;
+  void *t1 = nullptr, *spec = nullptr;        // FFT workspaces (sized for c128, max_rhs)
+  float2 *x32 = nullptr, *y32 = nullptr;       // c64 staging for mixed precision
+  double2 *V = nullptr, *w = nullptr, *r = nullptr, *dx = nullptr, *part = nullptr, *hdev = nullptr;
+  double *nrmpart = nullptr, *nrm = nullptr;
+  std::vector<void *> allocs;
+  long long dev_bytes = 0;
+
+  long long ncell() const { return (long long)nx * ny * nz; }
+  long long nvec() const { return 3 * ncell(); }
+};
+
+namespace {
+
+ie_status cuda_status(cudaError_t e) { return e == cudaSuccess ? IE_OK : (e == cudaErrorMemoryAllocation ? IE_ERR_OOM : IE_ERR_CUDA); }
+
+template <typename P> ie_status dalloc(ie_ctx *c, P **p, size_t bytes) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? IE_ERR_OOM : IE_ERR_CUDA;
+  }
+  c->allocs.push_back(q);
+  c->dev_bytes += (long long)bytes;
+  *p = reinterpret_cast<P *>(q);
+  return IE_OK;
+}
+
+#define IE_TRY(x)                      \
+  do {                                 \
+    ie_status _s = (x);                \
+    if (_s != IE_OK) return _s;        \
+  } while (0)
+#define IE_CUDA(x) IE_TRY(cuda_status(x))
+
+// ---------------------------------------------------------------------------
+// Geometry and diagonals
+// ---------------------------------------------------------------------------
+
+int layer_of_cell(const std::vector<double> &d, double z1, double z2) {
+  // layer m holds (d_m, d_{m+1}); layer 0 is the air above d_1
+  int ra = 0, rb = 0;
+  for (size_t k = 0; k < d.size(); ++k) {
+    if (z1 >= d[k]) ra = (int)k + 1;
+    if (z2 > d[k]) rb = (int)k + 1;
+  }
+  return ra == rb ? ra : -1;
+}
+
+template <typename T>
+ie_status upload_cplx(ie_ctx *c, const std::vector<cd> &h, void **dst) {
+  using V = ie::C<T>;
+  std::vector<V> tmp(h.size());
+  for (size_t i = 0; i < h.size(); ++i) tmp[i] = ie::mk<T>((T)h[i].real(), (T)h[i].imag());
+  V *p = nullptr;
+  IE_TRY(dalloc(c, &p, tmp.size() * sizeof(V)));
+  IE_CUDA(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(V), cudaMemcpyHostToDevice));
+  *dst = p;
+  return IE_OK;
+}
+
+ie_status build_diagonals(ie_ctx *c) {
+  const long long N = c->ncell();
+  const double norm = 1.0 / (4.0 * c->nx * c->ny);
+  std::vector<cd> in_f(N), out_f(N), diag(N), in_t(N), out_t(N);
+  for (int z = 0; z < c->nz; ++z) {
+    const cd sb = c->sig[c->lay[z]];
+    const double s = std::sqrt(sb.real());
+    const double V = c->hx * c->hy * (c->ze[z + 1] - c->ze[z]);
+    for (long long q = 0; q < (long long)c->ny * c->nx; ++q) {
+      const long long i = (long long)z * c->ny * c->nx + q;
+      const cd sa = c->sigma_a[i];
+      const cd g = (sa - sb) / (sa + std::conj(sb));
+      in_f[i] = s * g;
+      out_f[i] = -2.0 * s / V * norm;
+      diag[i] = 1.0 - g;
+      in_t[i] = -2.0 * s / V;
+      out_t[i] = s * g * norm;
+    }
+  }
+  IE_TRY(upload_cplx<double>(c, in_f, &c->d64.in_f));
+  IE_TRY(upload_cplx<double>(c, out_f, &c->d64.out_f));
+  IE_TRY(upload_cplx<double>(c, diag, &c->d64.diag));
+  IE_TRY(upload_cplx<double>(c, in_t, &c->d64.in_t));
+  IE_TRY(upload_cplx<double>(c, out_t, &c->d64.out_t));
+  IE_TRY(upload_cplx<float>(c, in_f, &c->d32.in_f));
+  IE_TRY(upload_cplx<float>(c, out_f, &c->d32.out_f));
+  IE_TRY(upload_cplx<float>(c, diag, &c->d32.diag));
+  IE_TRY(upload_cplx<float>(c, in_t, &c->d32.in_t));
+  IE_TRY(upload_cplx<float>(c, out_t, &c->d32.out_t));
+  return IE_OK;
+}
+
+// Coefficient DFT: real-space compressed tensor (host c128) -> folded spectral c128 + c64.
+ie_status build_spectral(ie_ctx *c, Instance &in, const double *q_host) {
+  const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
+  const long long NE = 6LL * Nz * Nz;
+  const long long nq = (long long)Nx * Ny * NE;
+  const long long BS = 2LL * Nz * (2 * Nz + 1);
+  const long long nf = (long long)(Nx + 1) * (Ny + 1);
+  IE_TRY(dalloc(c, &in.q64, nf * BS * sizeof(double2)));
+  IE_TRY(dalloc(c, &in.q32, nf * BS * sizeof(float2)));
+  double2 *dq = nullptr, *buf = nullptr;
+  IE_CUDA(cudaMalloc(&dq, nq * sizeof(double2)));
+  const long long plane = 4LL * Nx * Ny;
+  long long E = std::max<long long>(1, std::min<long long>(NE, (1LL << 30) / (plane * (long long)sizeof(double2))));
+  cudaError_t e = cudaMalloc(&buf, plane * E * sizeof(double2));
+  if (e != cudaSuccess) { cudaFree(dq); return cuda_status(e); }
+  e = cudaMemcpyAsync(dq, q_host, nq * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
+  for (long long e0 = 0; e == cudaSuccess && e0 < NE; e0 += E) {
+    const long long Ec = std::min(E, NE - e0);
+    ie::launch_embed(dq, buf, Nx, Ny, Nz, e0, Ec, c->stream);
+    ie::launch_fft_axis<double, false>(buf, buf, 2 * Ny, 2 * Nx, 2 * Nx, Ec, c->px, 1.0, c->stream);
+    ie::launch_fft_axis<double, false>(buf, buf, 1, 2 * Ny, 2 * Ny, 2LL * Nx * Ec, c->py, 1.0, c->stream);
+    ie::launch_pack(buf, in.q64, in.q32, Nx, Ny, Nz, e0, Ec, c->stream);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(dq);
+  cudaFree(buf);
+  return cuda_status(e);
+}
+
+// ---------------------------------------------------------------------------
+// The matrix-vector product
+// ---------------------------------------------------------------------------
+
+template <typename T> const DiagSet &diags(const ie_ctx *c);
+template <> const DiagSet &diags<double>(const ie_ctx *c) { return c->d64; }
+template <> const DiagSet &diags<float>(const ie_ctx *c) { return c->d32; }
+template <typename T> const ie::C<T> *qf(const Instance &in);
+template <> const double2 *qf<double>(const Instance &in) { return in.q64; }
+template <> const float2 *qf<float>(const Instance &in) { return in.q32; }
+
+template <typename T>
+ie_status apply(ie_ctx *c, int inst, const ie::C<T> *x, ie::C<T> *y, int R, int transpose, cudaStream_t s) {
+  using V = ie::C<T>;
+  const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
+  const int CZ = R * 3 * Nz;
+  const DiagSet &D = diags<T>(c);
+  const V *in_s = (const V *)(transpose ? D.in_t : D.in_f);
+  const V *out_s = (const V *)(transpose ? D.out_t : D.out_f);
+  const V *dg = (const V *)D.diag;
+  V *t1 = (V *)c->t1;
+  V *spec = (V *)c->spec;
+  ie::launch_fft_rows_fwd<T>(x, in_s, t1, CZ, Nz, Ny, Nx, c->px, s);
+  ie::launch_fft_axis<T, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, (T)1, s);
+  if (ie::launch_contract<T>(spec, qf<T>(c->inst[inst]), Nx, Ny, Nz, R, s) != 0) return IE_ERR_ARG;
+  ie::launch_fft_axis<T, true>(spec, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, (T)1, s);
+  ie::launch_fft_rows_inv<T>(t1, x, dg, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
+  return cuda_status(cudaGetLastError());
+}
+
+// FP64-level operator used by the Krylov solver: c128 product, or c64 product with casts.
+struct Op {
+  ie_ctx *c;
+  int inst;
+  int transpose;
+  bool single;
+  ie_status operator()(const double2 *x, double2 *y, int R) const {
+    const long long n = (long long)R * c->nvec();
+    if (!single) return apply<double>(c, inst, x, y, R, transpose, c->stream);
+    ie::launch_cast64to32(x, c->x32, n, c->stream);
+    IE_TRY(apply<float>(c, inst, c->x32, c->y32, R, transpose, c->stream));
+    ie::launch_cast32to64(c->y32, y, n, c->stream);
+    return cuda_status(cudaGetLastError());
+  }
+};
+
+// ---------------------------------------------------------------------------
+// GMRES(m), classical Gram-Schmidt applied twice, all right-hand sides in lockstep.
+// Solves op(x) = b until ||b - op x|| <= tol ||b|| for every right-hand side (the
+// Givens recurrence ends a cycle; a true residual at the next restart confirms it).
+// ---------------------------------------------------------------------------
+
+struct GmresResult {
+  int iters = 0;
+  int cycles = 0;
+  bool converged = false;
+  bool breakdown = false;
+};
+
+ie_status gmres(ie_ctx *c, const Op &op, const double2 *b, double2 *x, int R, double tol, int max_iter,
+                GmresResult *res) {
+  const long long n = c->nvec();
+  const long long nR = n * R;
+  const int m = c->restart;
+  const int ldh = m + 1;
+  cudaStream_t s = c->stream;
+  double2 *h1 = c->hdev, *h2 = c->hdev + (size_t)R * ldh, *yd = c->hdev + 2 * (size_t)R * ldh;
+  std::vector<double> bnorm(R), nrm(R);
+  ie::gmres_norm(b, c->nrmpart, c->nrm, R, n, s);
+  IE_CUDA(cudaMemcpyAsync(bnorm.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+  IE_CUDA(cudaStreamSynchronize(s));
+  std::vector<cd> Rm((size_t)R * ldh * m), g((size_t)R * ldh), sn((size_t)R * m);
+  std::vector<double> cs((size_t)R * m);
+  std::vector<double2> hh((size_t)2 * R * ldh), yv((size_t)R * ldh);
+  std::vector<int> kr(R);
+  std::vector<char> active(R);
+  res->converged = false;
+  res->breakdown = false;
+  int it = 0;
+  while (true) {
+    IE_TRY(op(x, c->w, R));
+    ie::vec_sub(b, c->w, c->w, nR, s);
+    ie::gmres_norm(c->w, c->nrmpart, c->nrm, R, n, s);
+    ie::gmres_scale(c->w, c->V, c->nrm, R, n, s);
+    IE_CUDA(cudaMemcpyAsync(nrm.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+    IE_CUDA(cudaStreamSynchronize(s));
+    int n_active = 0;
+    for (int r = 0; r < R; ++r) {
+      active[r] = nrm[r] > tol * bnorm[r];
+      n_active += active[r];
+      kr[r] = 0;
+      for (int i = 0; i < ldh; ++i) g[(size_t)r * ldh + i] = 0.0;
+      g[(size_t)r * ldh] = nrm[r];
+    }
+    if (n_active == 0) { res->converged = true; break; }
+    if (it >= max_iter) break;
+    res->cycles++;
+    int kmax = 0;
+    for (int k = 0; k < m && it < max_iter && n_active > 0; ++k) {
+      IE_TRY(op(c->V + (long long)k * nR, c->w, R));
+      ie::gmres_mdot(c->V, c->w, c->part, h1, k + 1, R, n, ldh, 0, s);
+      ie::gmres_maxpy(c->V, h1, c->w, k + 1, R, n, ldh, -1.0, s);
+      ie::gmres_mdot(c->V, c->w, c->part, h2, k + 1, R, n, ldh, 0, s);
+      ie::gmres_maxpy(c->V, h2, c->w, k + 1, R, n, ldh, -1.0, s);
+      ie::gmres_norm(c->w, c->nrmpart, c->nrm, R, n, s);
+      ie::gmres_scale(c->w, c->V + (long long)(k + 1) * nR, c->nrm, R, n, s);
+      IE_CUDA(cudaMemcpyAsync(hh.data(), h1, (size_t)2 * R * ldh * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      IE_CUDA(cudaMemcpyAsync(nrm.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+      IE_CUDA(cudaStreamSynchronize(s));
+      ++it;
+      kmax = k + 1;
+      for (int r = 0; r < R; ++r) {
+        if (!active[r]) continue;
+        cd *col = &Rm[((size_t)r * m + k) * ldh];
+        for (int i = 0; i <= k; ++i) {
+          const double2 a = hh[(size_t)r * ldh + i], bb = hh[(size_t)(R + r) * ldh + i];
+          col[i] = cd(a.x + bb.x, a.y + bb.y);
+        }
+        cd hk1 = nrm[r];
+        for (int i = 0; i < k; ++i) {
+          const double ci = cs[(size_t)r * m + i];
+          const cd si = sn[(size_t)r * m + i];
+          const cd t = ci * col[i] + si * col[i + 1];
+          col[i + 1] = -std::conj(si) * col[i] + ci * col[i + 1];
+          col[i] = t;
+        }
+        const cd a = col[k];
+        const double rho = std::sqrt(std::norm(a) + std::norm(hk1));
+        double ck;
+        cd sk;
+        if (std::abs(a) == 0.0) { ck = 0.0; sk = 1.0; }
+        else { ck = std::abs(a) / rho; sk = (a / std::abs(a)) * std::conj(hk1) / rho; }
+        col[k] = ck * a + sk * hk1;
+        cs[(size_t)r * m + k] = ck;
+        sn[(size_t)r * m + k] = sk;
+        cd *gr = &g[(size_t)r * ldh];
+        gr[k + 1] = -std::conj(sk) * gr[k];
+        gr[k] = ck * gr[k];
+        kr[r] = k + 1;
+        if (nrm[r] == 0.0) { active[r] = 0; res->breakdown = true; }
+        if (std::abs(gr[k + 1]) <= tol * bnorm[r]) active[r] = 0;
+      }
+      n_active = 0;
+      for (int r = 0; r < R; ++r) n_active += active[r];
+    }
+    // back substitution and x += V y
+    for (int r = 0; r < R; ++r) {
+      std::vector<cd> y(kr[r]);
+      for (int i = kr[r] - 1; i >= 0; --i) {
+        cd acc = g[(size_t)r * ldh + i];
+        for (int j = i + 1; j < kr[r]; ++j) acc -= Rm[((size_t)r * m + j) * ldh + i] * y[j];
+        const cd d = Rm[((size_t)r * m + i) * ldh + i];
+        y[i] = d == 0.0 ? cd(0.0) : acc / d;
+      }
+      for (int i = 0; i < ldh; ++i) {
+        const cd v = i < kr[r] ? y[i] : cd(0.0);
+        yv[(size_t)r * ldh + i] = make_double2(v.real(), v.imag());
+      }
+    }
+    IE_CUDA(cudaMemcpyAsync(yd, yv.data(), (size_t)R * ldh * sizeof(double2), cudaMemcpyHostToDevice, s));
+    ie::gmres_maxpy(c->V, yd, x, kmax, R, n, ldh, 1.0, s);
+    IE_CUDA(cudaGetLastError());
+  }
+  res->iters = it;
+  return IE_OK;
+}
+
+// max over right-hand sides of ||b - A128 u|| / ||b||; leaves the residual in c->r
+ie_status true_residual(ie_ctx *c, int inst, int transpose, const double2 *b, const double2 *u, int R,
+                        std::vector<double> &rel) {
+  const long long n = c->nvec();
+  Op op{c, inst, transpose, false};
+  IE_TRY(op(u, c->r, R));
+  ie::vec_sub(b, c->r, c->r, n * R, c->stream);
+  std::vector<double> rn(R), bn(R);
+  ie::gmres_norm(c->r, c->nrmpart, c->nrm, R, n, c->stream);
+  IE_CUDA(cudaMemcpyAsync(rn.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  ie::gmres_norm(b, c->nrmpart, c->nrm + R, R, n, c->stream);
+  IE_CUDA(cudaMemcpyAsync(bn.data(), c->nrm + R, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  rel.resize(R);
+  for (int r = 0; r < R; ++r) rel[r] = bn[r] > 0 ? rn[r] / bn[r] : rn[r];
+  return IE_OK;
+}
+
+ie_status solve_impl(ie_ctx *c, int inst, const double2 *b, double2 *u, int R, double tol, int precision,
+                     int use_x0, int transpose, ie_solve_info *info) {
+  if (!c || !b || !u || inst < 0 || inst >= (int)c->inst.size() || R < 1 || R > c->max_rhs || !(tol > 0))
+    return IE_ERR_ARG;
+  if (precision != IE_FP64 && precision != IE_MIXED) return IE_ERR_ARG;
+  const long long n = c->nvec();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!use_x0) IE_CUDA(cudaMemsetAsync(u, 0, n * R * sizeof(double2), c->stream));
+  ie_solve_info inf{};
+  bool conv = false, brk = false;
+  std::vector<double> rel;
+  if (precision == IE_FP64) {
+    GmresResult gr;
+    IE_TRY(gmres(c, Op{c, inst, transpose, false}, b, u, R, tol, c->max_iter, &gr));
+    inf.inner_iters = gr.iters;
+    inf.outer_iters = gr.cycles;
+    conv = gr.converged;
+    brk = gr.breakdown;
+  } else {
+    int inner_total = 0;
+    for (int outer = 0; outer <= c->max_outer; ++outer) {
+      IE_TRY(true_residual(c, inst, transpose, b, u, R, rel));
+      inf.outer_iters = outer + 1;
+      double worst = 0;
+      for (double v : rel) worst = std::max(worst, v);
+      if (worst <= tol) { conv = true; break; }
+      if (outer == c->max_outer || inner_total >= c->max_iter) break;
+      // inner: A64 d = r (relative tolerance inner_tol, bounded below so as not to over-solve)
+      IE_CUDA(cudaMemsetAsync(c->dx, 0, n * R * sizeof(double2), c->stream));
+      GmresResult gr;
+      const double itol = std::max(c->inner_tol, 0.5 * tol / std::max(worst, 1e-300));
+      IE_TRY(gmres(c, Op{c, inst, transpose, true}, c->r, c->dx, R, std::min(itol, 0.5), c->max_iter - inner_total,
+                   &gr));
+      inner_total += gr.iters;
+      brk = brk || gr.breakdown;
+      ie::vec_add(c->dx, u, n * R, c->stream);
+    }
+    inf.inner_iters = inner_total;
+  }
+  IE_TRY(true_residual(c, inst, transpose, b, u, R, rel));
+  double worst = 0;
+  for (double v : rel) worst = std::max(worst, v);
+  inf.final_rel_res = worst;
+  inf.t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  if (worst <= tol) return IE_OK;
+  (void)conv;
+  return brk ? IE_BREAKDOWN : IE_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// Magnetotelluric normal field (1-D plane wave), integrated over the cells.
+// E'' = kappa^2 E in each layer, kappa = sqrt(-i w mu0 sigma); E decays in the
+// basement; E and E' continuous; E'(0) = i w mu0 (H(0) = 1).  Propagated upwards
+// from the basement with the layer transfer (cosh, sinh) relations.
+// ---------------------------------------------------------------------------
+
+std::vector<cd> mt_cell_average(const ie_ctx *c, double omega) {
+  const int L = (int)c->d.size();
+  std::vector<cd> kap(L + 1), Eb(L + 1), Epb(L + 1);
+  for (int m = 0; m <= L; ++m) kap[m] = std::sqrt(cd(0.0, -omega * kMu0) * c->sig[m]);
+  cd E = 1.0, Ep = -kap[L];
+  double scale_log = 0.0;  // not needed for realistic layers; states are renormalised below
+  for (int m = L - 1; m >= 1; --m) {
+    Eb[m] = E;
+    Epb[m] = Ep;
+    const double l = c->d[m] - c->d[m - 1];
+    const cd ch = std::cosh(kap[m] * l), sh = std::sinh(kap[m] * l);
+    const cd Et = E * ch - Ep * sh / kap[m];
+    const cd Ept = -E * kap[m] * sh + Ep * ch;
+    E = Et;
+    Ep = Ept;
+  }
+  (void)scale_log;
+  const cd a = cd(0.0, omega * kMu0) / Ep;  // E'(0) = i w mu0
+  const cd EL = a;                          // E at the top of the basement before scaling was 1
+  std::vector<cd> out(c->nz);
+  for (int z = 0; z < c->nz; ++z) {
+    const int m = c->lay[z];
+    const double z1 = c->ze[z], z2 = c->ze[z + 1];
+    const cd k = kap[m];
+    cd integral;
+    if (m == L) {
+      const double dL = c->d[L - 1];
+      integral = EL * (std::exp(-k * (z1 - dL)) - std::exp(-k * (z2 - dL))) / k;
+    } else {
+      const double zb = c->d[m];
+      auto F = [&](double zz) {
+        return a * (Eb[m] * std::sinh(k * (zz - zb)) / k + Epb[m] * std::cosh(k * (zz - zb)) / (k * k));
+      };
+      integral = F(z2) - F(z1);
+    }
+    out[z] = integral / (z2 - z1);
+  }
+  return out;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+const char *ie_status_str(ie_status s) {
+  switch (s) {
+    case IE_OK: return "ok";
+    case IE_NOT_CONVERGED: return "not converged";
+    case IE_BREAKDOWN: return "Krylov breakdown";
+    case IE_ERR_ARG: return "invalid argument";
+    case IE_ERR_GEOMETRY: return "invalid geometry";
+    case IE_ERR_COEFF: return "invalid coefficient tensor";
+    case IE_ERR_OOM: return "out of device memory";
+    case IE_ERR_CUDA: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+void ie_destroy(ie_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void *p : c->allocs) cudaFree(p);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+void *ie_ctx_stream(ie_ctx *c) { return c ? (void *)c->stream : nullptr; }
+long long ie_ctx_device_bytes(ie_ctx *c) { return c ? c->dev_bytes : 0; }
+
+static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double *sigma_a, int n_freq,
+                            const double *freq, const double *q_real, int max_rhs, const ie_options *opt,
+                            ie_ctx *c) {
+  c->nx = g->nx; c->ny = g->ny; c->nz = g->nz;
+  c->hx = g->hx; c->hy = g->hy; c->x0 = g->x0; c->y0 = g->y0;
+  c->ze.assign(g->z_edges_host, g->z_edges_host + g->nz + 1);
+  for (int k = 0; k < g->nz; ++k)
+    if (!(c->ze[k + 1] > c->ze[k])) return IE_ERR_ARG;
+  c->d.assign(lay->interfaces_host, lay->interfaces_host + lay->n_interfaces);
+  for (int k = 0; k + 1 < lay->n_interfaces; ++k)
+    if (!(c->d[k + 1] > c->d[k])) return IE_ERR_ARG;
+  c->sig.resize(lay->n_interfaces + 1);
+  for (int k = 0; k <= lay->n_interfaces; ++k) c->sig[k] = cd(lay->sigma_host[2 * k], lay->sigma_host[2 * k + 1]);
+  c->lay.resize(g->nz);
+  for (int z = 0; z < g->nz; ++z) {
+    const int m = layer_of_cell(c->d, c->ze[z], c->ze[z + 1]);
+    if (m < 0) return IE_ERR_GEOMETRY;
+    if (!(c->sig[m].real() > 0.0)) return IE_ERR_GEOMETRY;
+    c->lay[z] = m;
+  }
+  const long long N = c->ncell();
+  c->sigma_a.resize(N);
+  for (long long i = 0; i < N; ++i) c->sigma_a[i] = cd(sigma_a[2 * i], sigma_a[2 * i + 1]);
+  c->max_rhs = max_rhs;
+  if (opt) {
+    if (opt->restart > 0) c->restart = opt->restart;
+    if (opt->max_iter > 0) c->max_iter = opt->max_iter;
+    if (opt->inner_tol > 0) c->inner_tol = opt->inner_tol;
+    if (opt->max_outer > 0) c->max_outer = opt->max_outer;
+  }
+  if (c->restart < 2) return IE_ERR_ARG;
+  try {
+    c->px = ie::make_plan(2 * c->nx);
+    c->py = ie::make_plan(2 * c->ny);
+  } catch (...) {
+    return IE_ERR_ARG;
+  }
+  IE_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  IE_TRY(build_diagonals(c));
+  c->inst.resize(n_freq);
+  const long long nq = (long long)c->nx * c->ny * 6LL * c->nz * c->nz;
+  for (int f = 0; f < n_freq; ++f) {
+    if (!(freq[f] > 0)) return IE_ERR_ARG;
+    c->inst[f].freq = freq[f];
+    IE_TRY(build_spectral(c, c->inst[f], q_real + 2 * nq * f));
+  }
+  // workspaces (sized for c128 and max_rhs)
+  const long long CZ = (long long)max_rhs * 3 * c->nz;
+  IE_TRY(dalloc(c, &c->t1, (size_t)c->ny * 2 * c->nx * CZ * sizeof(double2)));
+  IE_TRY(dalloc(c, &c->spec, (size_t)4 * c->ny * c->nx * CZ * sizeof(double2)));
+  const long long nv = c->nvec() * max_rhs;
+  IE_TRY(dalloc(c, &c->x32, nv * sizeof(float2)));
+  IE_TRY(dalloc(c, &c->y32, nv * sizeof(float2)));
+  IE_TRY(dalloc(c, &c->V, (size_t)(c->restart + 1) * nv * sizeof(double2)));
+  IE_TRY(dalloc(c, &c->w, nv * sizeof(double2)));
+  IE_TRY(dalloc(c, &c->r, nv * sizeof(double2)));
+  IE_TRY(dalloc(c, &c->dx, nv * sizeof(double2)));
+  IE_TRY(dalloc(c, &c->part, (size_t)max_rhs * (c->restart + 1) * ie::mdot_nb(c->nvec()) * sizeof(double2)));
+  IE_TRY(dalloc(c, &c->hdev, (size_t)3 * max_rhs * (c->restart + 1) * sizeof(double2)));
+  IE_TRY(dalloc(c, &c->nrmpart, (size_t)max_rhs * 1024 * sizeof(double)));
+  IE_TRY(dalloc(c, &c->nrm, (size_t)2 * max_rhs * sizeof(double)));
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
+ie_status ie_setup(const ie_grid *g, const ie_layers *lay, const double *sigma_a, int n_freq, const double *freq,
+                   const double *q_real, int max_rhs, const ie_options *opt, ie_ctx **out) {
+  if (!out) return IE_ERR_ARG;
+  *out = nullptr;
+  if (!g || !lay || !sigma_a || !freq || n_freq < 1 || max_rhs < 1 || max_rhs > 4) return IE_ERR_ARG;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->hx > 0) || !(g->hy > 0) || !g->z_edges_host) return IE_ERR_ARG;
+  if (lay->n_interfaces < 1 || !lay->interfaces_host || !lay->sigma_host) return IE_ERR_ARG;
+  if (!q_real) return IE_ERR_COEFF;
+  ie_ctx *c = new (std::nothrow) ie_ctx();
+  if (!c) return IE_ERR_OOM;
+  const ie_status st = setup_impl(g, lay, sigma_a, n_freq, freq, q_real, max_rhs, opt, c);
+  if (st != IE_OK) {
+    ie_destroy(c);
+    return st;
+  }
+  *out = c;
+  return IE_OK;
+}
+
+ie_status ie_matvec(ie_ctx *c, int inst, const void *x, void *y, int nrhs, int dtype, int transpose, void *stream) {
+  if (!c || !x || !y || x == y || inst < 0 || inst >= (int)c->inst.size() || nrhs < 1 || nrhs > c->max_rhs)
+    return IE_ERR_ARG;
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+  transpose = transpose ? 1 : 0;
+  if (dtype == IE_C128) return apply<double>(c, inst, (const double2 *)x, (double2 *)y, nrhs, transpose, s);
+  if (dtype == IE_C64) return apply<float>(c, inst, (const float2 *)x, (float2 *)y, nrhs, transpose, s);
+  return IE_ERR_ARG;
+}
+
+ie_status ie_solve(ie_ctx *c, int inst, const void *b, void *u, int nrhs, double tol, int precision, int use_x0,
+                   ie_solve_info *info) {
+  return solve_impl(c, inst, (const double2 *)b, (double2 *)u, nrhs, tol, precision, use_x0, 0, info);
+}
+
+ie_status ie_adjoint_solve(ie_ctx *c, int inst, const void *b, void *w, int nrhs, double tol, int precision,
+                           int use_x0, ie_solve_info *info) {
+  return solve_impl(c, inst, (const double2 *)b, (double2 *)w, nrhs, tol, precision, use_x0, 1, info);
+}
+
+ie_status ie_rhs_mt(ie_ctx *c, int inst, int pol, void *u0) {
+  if (!c || !u0 || inst < 0 || inst >= (int)c->inst.size() || (pol != 0 && pol != 1)) return IE_ERR_ARG;
+  const double omega = 2.0 * M_PI * c->inst[inst].freq;
+  const std::vector<cd> avg = mt_cell_average(c, omega);
+  const long long plane = (long long)c->nx * c->ny;
+  std::vector<double2> h((size_t)c->nvec(), make_double2(0.0, 0.0));
+  for (int z = 0; z < c->nz; ++z) {
+    const cd v = std::sqrt(c->sig[c->lay[z]].real()) * avg[z];
+    for (long long q = 0; q < plane; ++q) h[((size_t)pol * c->nz + z) * plane + q] = make_double2(v.real(), v.imag());
+  }
+  IE_CUDA(cudaMemcpyAsync(u0, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
+}  // extern "C"

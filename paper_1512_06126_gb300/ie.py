@@ -1,0 +1,164 @@
+"""ctypes binding of libie_gb300.so: the same entry points as include/ie.h.
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  Device buffers are passed as raw pointers (for instance
+``torch.Tensor.data_ptr()`` of a CUDA tensor); this module never falls back to a
+CPU path and raises if the library cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libie_gb300.so")
+
+IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN = 0, 1, 2
+IE_C64, IE_C128 = 0, 1
+IE_FP64, IE_MIXED = 0, 1
+
+EXPORTS = ("ie_setup", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_rhs_mt", "ie_ctx_stream",
+           "ie_ctx_device_bytes", "ie_destroy", "ie_status_str")
+
+
+class ie_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double),
+                ("z_edges_host", ctypes.POINTER(ctypes.c_double)),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double)]
+
+
+class ie_layers(ctypes.Structure):
+    _fields_ = [("n_interfaces", ctypes.c_int),
+                ("interfaces_host", ctypes.POINTER(ctypes.c_double)),
+                ("sigma_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class ie_options(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
+
+
+class ie_solve_info(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("final_rel_res", ctypes.c_double), ("t_solve", ctypes.c_double)]
+
+
+class IEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg}: status {status}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises OSError if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with paper_1512_06126_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, VP = ctypes.POINTER, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    lib.ie_setup.argtypes = [P(ie_grid), P(ie_layers), P(D), I, P(D), P(D), I, P(ie_options), P(VP)]
+    lib.ie_setup.restype = I
+    lib.ie_matvec.argtypes = [VP, I, VP, VP, I, I, I, VP]
+    lib.ie_matvec.restype = I
+    lib.ie_solve.argtypes = [VP, I, VP, VP, I, D, I, I, P(ie_solve_info)]
+    lib.ie_solve.restype = I
+    lib.ie_adjoint_solve.argtypes = [VP, I, VP, VP, I, D, I, I, P(ie_solve_info)]
+    lib.ie_adjoint_solve.restype = I
+    lib.ie_rhs_mt.argtypes = [VP, I, I, VP]
+    lib.ie_rhs_mt.restype = I
+    lib.ie_ctx_stream.argtypes = [VP]
+    lib.ie_ctx_stream.restype = VP
+    lib.ie_ctx_device_bytes.argtypes = [VP]
+    lib.ie_ctx_device_bytes.restype = ctypes.c_longlong
+    lib.ie_destroy.argtypes = [VP]
+    lib.ie_destroy.restype = None
+    lib.ie_status_str.argtypes = [I]
+    lib.ie_status_str.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_str(s: int) -> str:
+    return load().ie_status_str(s).decode()
+
+
+def _check(s, what, ok=(IE_OK,)):
+    if s not in ok:
+        raise IEError(s, f"{what} failed ({status_str(s)})")
+    return s
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _cplx_pairs(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
+
+
+class Context:
+    """Owns one ie_ctx.  ``q_real`` is a list (one per frequency) of compressed
+    real-space tensors [Ny][Nx][6][Nz][Nz] (complex)."""
+
+    def __init__(self, grid, layers, sigma_a, freqs, q_real, max_rhs=2, restart=30, max_iter=2000,
+                 inner_tol=1e-3, max_outer=50):
+        lib = load()
+        self._lib = lib
+        self._keep = []
+        ze = np.ascontiguousarray(np.asarray(grid.z_edges, dtype=np.float64))
+        g = ie_grid(grid.nx, grid.ny, grid.nz, grid.hx, grid.hy, _dptr(ze), 0.0, 0.0)
+        d = np.ascontiguousarray(np.asarray(layers.interfaces, dtype=np.float64))
+        sig = _cplx_pairs(layers.sigma)
+        lay = ie_layers(len(d), _dptr(d), _dptr(sig))
+        sa = _cplx_pairs(np.asarray(sigma_a).reshape(-1))
+        fr = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64))
+        q = _cplx_pairs(np.stack([np.asarray(x, dtype=np.complex128) for x in q_real]).reshape(-1))
+        opt = ie_options(restart, max_iter, inner_tol, max_outer)
+        ctx = ctypes.c_void_p()
+        s = lib.ie_setup(ctypes.byref(g), ctypes.byref(lay), _dptr(sa), len(fr), _dptr(fr), _dptr(q), max_rhs,
+                         ctypes.byref(opt), ctypes.byref(ctx))
+        _check(s, "ie_setup")
+        self.ctx = ctx
+        self.grid = grid
+        self.max_rhs = max_rhs
+        self.n_unknowns = 3 * grid.nx * grid.ny * grid.nz
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._lib.ie_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self):
+        return self._lib.ie_ctx_stream(self.ctx)
+
+    def device_bytes(self):
+        return int(self._lib.ie_ctx_device_bytes(self.ctx))
+
+    def matvec(self, inst, x_ptr, y_ptr, nrhs, dtype=IE_C128, transpose=False, stream=None):
+        s = self._lib.ie_matvec(self.ctx, inst, x_ptr, y_ptr, nrhs, dtype, int(bool(transpose)), stream)
+        _check(s, "ie_matvec")
+
+    def solve(self, inst, b_ptr, u_ptr, nrhs, tol, precision=IE_FP64, use_x0=False, adjoint=False):
+        info = ie_solve_info()
+        fn = self._lib.ie_adjoint_solve if adjoint else self._lib.ie_solve
+        s = fn(self.ctx, inst, b_ptr, u_ptr, nrhs, tol, precision, int(bool(use_x0)), ctypes.byref(info))
+        _check(s, "ie_adjoint_solve" if adjoint else "ie_solve", ok=(IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN))
+        return s, info
+
+    def rhs_mt(self, inst, pol, u0_ptr):
+        _check(self._lib.ie_rhs_mt(self.ctx, inst, pol, u0_ptr), "ie_rhs_mt")

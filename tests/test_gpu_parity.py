@@ -1,0 +1,152 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative L2 unless stated):
+* c128 matrix-vector product: 1e-12 (FFT round-off of two routes, O(eps log N)).
+* c64 product: 2e-5 (FP32 FFTs and contraction with FP32 accumulation: about
+  eps32 * (log2(4 Nx Ny) + 3 Nz) for these sizes, where eps32 = 6e-8).
+* FP64 solve at tol 1e-10: 1e-9 against dense LU (cond(A) of the small models <~ 10).
+* mixed solve at tol 1e-7: 1e-5 on U against dense LU.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import normal, operator as O
+from tests.gpu_support import lib_context, need_gpu, rel, to_dev, to_host, torch
+from tests.oracle_cache import all_offsets_cached
+
+pytestmark = pytest.mark.gpu
+
+MODELS = {
+    "c1": lambda: W.config1(),
+    "ragged": lambda: W.small_model(nx=7, ny=5, nz=3, seed=11, freq=3.0),
+    "nz1": lambda: W.small_model(nx=6, ny=6, nz=1, seed=5, freq=0.5, n_layers=1),
+}
+
+
+@pytest.fixture(scope="module", params=list(MODELS))
+def case(request):
+    need_gpu()
+    m = MODELS[request.param]()
+    qa = all_offsets_cached(m)
+    g = m.grid
+    q = qa[g.ny - 1:, g.nx - 1:]
+    B = O.dense_B(m, qa)
+    A = O.dense_matrix(m, B)
+    ctx = lib_context(m, [q], max_rhs=2)
+    yield m, q, A, ctx
+    ctx.close()
+
+
+def test_matvec_c128_and_transpose(case):
+    m, q, A, ctx = case
+    g = m.grid
+    shp = (2, 3, g.nz, g.ny, g.nx)
+    x = W.random_field(shp, 3)
+    xd = to_dev(x)
+    yd = torch.empty_like(xd)
+    for tr in (False, True):
+        ctx.matvec(0, xd.data_ptr(), yd.data_ptr(), 2, dtype=1, transpose=tr,
+                   stream=torch.cuda.current_stream().cuda_stream)
+        y = to_host(yd)
+        M = A.T if tr else A
+        for r in range(2):
+            ref = (M @ x[r].ravel()).reshape(x[r].shape)
+            assert rel(y[r], ref) <= 1e-12, (tr, r, rel(y[r], ref))
+
+
+def test_matvec_c64(case):
+    m, q, A, ctx = case
+    g = m.grid
+    x = W.random_field((1, 3, g.nz, g.ny, g.nx), 4)
+    xd = to_dev(x, torch.complex64)
+    yd = torch.empty_like(xd)
+    ctx.matvec(0, xd.data_ptr(), yd.data_ptr(), 1, dtype=0, stream=torch.cuda.current_stream().cuda_stream)
+    y = to_host(yd).astype(np.complex128)
+    ref = (A @ x[0].astype(np.complex64).astype(np.complex128).ravel()).reshape(x[0].shape)
+    assert rel(y[0], ref) <= 2e-5
+
+
+def test_rhs_mt_matches_oracle(case):
+    m, q, A, ctx = case
+    for pol, name in ((0, "x"), (1, "y")):
+        u0 = torch.empty((3, m.grid.nz, m.grid.ny, m.grid.nx), dtype=torch.complex128, device="cuda")
+        ctx.rhs_mt(0, pol, u0.data_ptr())
+        ref = normal.rhs_U0(m, m.freqs[0], name)
+        assert rel(to_host(u0), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-10, 1e-9), (1, 1e-7, 1e-5)])
+def test_solve_against_lu(case, precision, tol, bound):
+    m, q, A, ctx = case
+    g = m.grid
+    b = np.stack([normal.rhs_U0(m, m.freqs[0], "x"), normal.rhs_U0(m, m.freqs[0], "y")])
+    u_ref = np.stack([np.linalg.solve(A, b[r].ravel()).reshape(b[r].shape) for r in range(2)])
+    bd = to_dev(b)
+    ud = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), 2, tol, precision=precision)
+    assert st == 0, (st, info.final_rel_res)
+    assert info.final_rel_res <= tol
+    u = to_host(ud)
+    for r in range(2):
+        assert rel(u[r], u_ref[r]) <= bound, (r, rel(u[r], u_ref[r]))
+
+
+def test_adjoint_solve_against_lu(case):
+    m, q, A, ctx = case
+    g = m.grid
+    b = W.random_field((1, 3, g.nz, g.ny, g.nx), 9)
+    w_ref = np.linalg.solve(A.T, b[0].ravel()).reshape(b[0].shape)
+    bd = to_dev(b)
+    wd = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    st, info = ctx.solve(0, bd.data_ptr(), wd.data_ptr(), 1, 1e-10, precision=0, adjoint=True)
+    assert st == 0
+    assert rel(to_host(wd)[0], w_ref) <= 1e-9
+
+
+def test_no_anomaly_solution_is_normal_field():
+    need_gpu()
+    m0 = W.small_model(nx=5, ny=4, nz=3, seed=11, freq=3.0)
+    sb = W.background_sigma(m0.grid, m0.layers)
+    m = W.Model(m0.name, m0.grid, m0.layers, np.broadcast_to(sb[:, None, None], m0.sigma_a.shape).copy(),
+                m0.freqs, m0.pols)
+    qa = all_offsets_cached(m0)
+    q = qa[m.grid.ny - 1:, m.grid.nx - 1:]
+    ctx = lib_context(m, [q], max_rhs=1)
+    b = normal.rhs_U0(m, m.freqs[0], "x")[None]
+    bd = to_dev(b)
+    ud = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), 1, 1e-12, precision=0)
+    assert st == 0 and info.inner_iters == 0
+    assert rel(to_host(ud), b) <= 1e-15
+    ctx.close()
+
+
+def test_full_size_matvec_sampled_rows():
+    """128 x 128 x 32 (the single-solve grid) with a random coefficient tensor:
+    sampled rows of A x from direct summation in the oracle."""
+    need_gpu()
+    m = W.config2()
+    g = m.grid
+    q = W.random_compressed_q(g.ny, g.nx, g.nz, seed=21)
+    ctx = lib_context(m, [q], max_rhs=2)
+    x = W.random_field((2, 3, g.nz, g.ny, g.nx), 22)
+    xd = to_dev(x)
+    yd = torch.empty_like(xd)
+    ctx.matvec(0, xd.data_ptr(), yd.data_ptr(), 2, dtype=1, stream=torch.cuda.current_stream().cuda_stream)
+    y = to_host(yd)
+    x32 = to_dev(x, torch.complex64)
+    y32 = torch.empty_like(x32)
+    ctx.matvec(0, x32.data_ptr(), y32.data_ptr(), 2, dtype=0, stream=torch.cuda.current_stream().cuda_stream)
+    y32h = to_host(y32).astype(np.complex128)
+    cells = [(0, 0, 0), (31, 127, 127), (5, 64, 3), (17, 1, 126), (31, 0, 77)]
+    for r in range(2):
+        ref = O.direct_rows(m, q, x[r], cells)
+        got = np.array([y[r][:, c[0], c[1], c[2]] for c in cells])
+        assert rel(got, ref) <= 1e-11, rel(got, ref)
+        got32 = np.array([y32h[r][:, c[0], c[1], c[2]] for c in cells])
+        assert rel(got32, ref) <= 1e-4, rel(got32, ref)
+    ctx.close()
