@@ -138,6 +138,23 @@ void *ie_ctx_stream(ie_ctx *ctx);
 /* Bytes of device memory held by the context. */
 long long ie_ctx_device_bytes(ie_ctx *ctx);
 
+/* Profiling.  ie_profile(ctx, 1) clears earlier records and starts recording a pair
+ * of CUDA events around every launch of the wavenumber-contraction kernel (step 2
+ * of Sect. 3.3) on the stream it runs on; ie_profile(ctx, 0) stops.  ie_profile_read
+ * waits for the recorded events and returns the summed duration (ms) and the number
+ * of launches for one element type (IE_C64 or IE_C128). */
+ie_status ie_profile(ie_ctx *ctx, int enable);
+ie_status ie_profile_read(ie_ctx *ctx, int dtype, double *total_ms, long long *n_launch);
+
+/* Average duration (ms) of each of the five kernels of one matrix-vector product
+ * (row FFT, column FFT, contraction, inverse column FFT, inverse row FFT + scaling),
+ * measured with CUDA events over n_iter products on the context's workspaces
+ * (values are whatever the workspaces hold).  ms_out_host: 5 doubles. */
+ie_status ie_profile_matvec(ie_ctx *ctx, int inst, int nrhs, int dtype, int n_iter, double *ms_out_host);
+
+/* Number of kernels the library has launched in this process (all contexts). */
+long long ie_kernel_launches(void);
+
 void ie_destroy(ie_ctx *ctx);
 const char *ie_status_str(ie_status s);
 

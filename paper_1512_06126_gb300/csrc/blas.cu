@@ -178,31 +178,37 @@ int mdot_nb(long long n) { return (int)((n + kChunk - 1) / kChunk); }
 void gmres_mdot(const double2 *V, const double2 *w, double2 *part, double2 *h_out, int k1, int R, long long n, int ldh,
                 int accumulate, cudaStream_t s) {
   const int nb = mdot_nb(n);
+  count_launches(2);
   mdot_partial<<<dim3(nb, R), kT, 0, s>>>(V, w, part, k1, R, n, nb);
   mdot_final<<<dim3(k1, R), kT, 0, s>>>(part, h_out, k1, nb, ldh, accumulate);
 }
 
 void gmres_maxpy(const double2 *V, const double2 *h, double2 *w, int k1, int R, long long n, int ldh, double sign,
                  cudaStream_t s) {
+  count_launches(1);
   maxpy_kernel<<<dim3(blocks_for(n), R), kT, 0, s>>>(V, h, w, k1, R, n, ldh, sign);
 }
 
 void gmres_norm(const double2 *w, double *part, double *out, int R, long long n, cudaStream_t s) {
   int nb = mdot_nb(n);
   if (nb > 1024) nb = 1024;
+  count_launches(2);
   norm_partial<<<dim3(nb, R), kT, 0, s>>>(w, part, n, nb);
   norm_final<<<R, kT, 0, s>>>(part, out, nb);
 }
 
 void gmres_scale(const double2 *src, double2 *dst, const double *nrm, int R, long long n, cudaStream_t s) {
+  count_launches(1);
   scale_kernel<<<dim3(blocks_for(n), R), kT, 0, s>>>(src, dst, nrm, n);
 }
 
 void vec_sub(const double2 *a, const double2 *b, double2 *out, long long n, cudaStream_t s) {
+  count_launches(1);
   sub_kernel<<<blocks_for(n), kT, 0, s>>>(a, b, out, n);
 }
 
 void vec_add(const double2 *x, double2 *y, long long n, cudaStream_t s) {
+  count_launches(1);
   add_kernel<<<blocks_for(n), kT, 0, s>>>(x, y, n);
 }
 

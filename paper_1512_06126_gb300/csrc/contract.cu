@@ -122,6 +122,7 @@ void launch_t(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStr
   int threads = ((3 * Nz + 31) / 32) * 32;
   if (threads > 512) threads = 512;
   dim3 grid(Nx + 1, Ny + 1);
+  count_launches(1);
   k<<<grid, threads, sm, s>>>(spec, qf, Nx, Ny, Nz, R);
 }
 

@@ -157,6 +157,7 @@ void launch_fft_axis(const C<T> *in, C<T> *out, int outer, int Lin, int Lout, lo
   auto k = fft_axis_kernel<T, INV>;
   set_smem(k, sm);
   dim3 grid((unsigned)((inner + TI - 1) / TI), (unsigned)outer);
+  count_launches(1);
   k<<<grid, kThreads, sm, s>>>(in, out, Lin, Lout, inner, plan, scale);
 }
 
@@ -168,6 +169,7 @@ void launch_fft_rows_fwd(const C<T> *x, const C<T> *in_scale, C<T> *t1, int CZ, 
   auto k = fft_rows_fwd_kernel<T>;
   set_smem(k, sm);
   dim3 grid((unsigned)((CZ + TI - 1) / TI), (unsigned)Ny);
+  count_launches(1);
   k<<<grid, kThreads, sm, s>>>(x, in_scale, t1, CZ, Nz, Ny, Nx, plan);
 }
 
@@ -179,6 +181,7 @@ void launch_fft_rows_inv(const C<T> *t1, const C<T> *x, const C<T> *diag, const 
   auto k = fft_rows_inv_kernel<T>;
   set_smem(k, sm);
   dim3 grid((unsigned)((CZ + TI - 1) / TI), (unsigned)Ny);
+  count_launches(1);
   k<<<grid, kThreads, sm, s>>>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx, plan);
 }
 

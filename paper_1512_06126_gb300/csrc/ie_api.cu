@@ -18,6 +18,13 @@
 
 using cd = std::complex<double>;
 
+#include <atomic>
+namespace ie {
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace ie
+
 namespace {
 
 constexpr double kMu0 = 4e-7 * M_PI;
@@ -53,6 +60,10 @@ struct ie_ctx {
   double *nrmpart = nullptr, *nrm = nullptr;
   std::vector<void *> allocs;
   long long dev_bytes = 0;
+  // profiling of the contraction kernel: event pairs recorded around each launch
+  bool prof = false;
+  struct ProfRec { cudaEvent_t a, b; int dtype; };
+  std::vector<ProfRec> prof_rec;
 
   long long ncell() const { return (long long)nx * ny * nz; }
   long long nvec() const { return 3 * ncell(); }
@@ -194,7 +205,17 @@ ie_status apply(ie_ctx *c, int inst, const ie::C<T> *x, ie::C<T> *y, int R, int 
   V *spec = (V *)c->spec;
   ie::launch_fft_rows_fwd<T>(x, in_s, t1, CZ, Nz, Ny, Nx, c->px, s);
   ie::launch_fft_axis<T, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, (T)1, s);
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (c->prof) {
+    cudaEventCreate(&ea);
+    cudaEventCreate(&eb);
+    cudaEventRecord(ea, s);
+  }
   if (ie::launch_contract<T>(spec, qf<T>(c->inst[inst]), Nx, Ny, Nz, R, s) != 0) return IE_ERR_ARG;
+  if (c->prof) {
+    cudaEventRecord(eb, s);
+    c->prof_rec.push_back({ea, eb, sizeof(T) == 8 ? IE_C128 : IE_C64});
+  }
   ie::launch_fft_axis<T, true>(spec, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, (T)1, s);
   ie::launch_fft_rows_inv<T>(t1, x, dg, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
   return cuda_status(cudaGetLastError());
@@ -474,15 +495,102 @@ const char *ie_status_str(ie_status s) {
   return "unknown status";
 }
 
+static void prof_clear(ie_ctx *c);
 void ie_destroy(ie_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  prof_clear(c);
   for (void *p : c->allocs) cudaFree(p);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
 void *ie_ctx_stream(ie_ctx *c) { return c ? (void *)c->stream : nullptr; }
+
+long long ie_kernel_launches(void) { return ie::launches(); }
+
+static void prof_clear(ie_ctx *c) {
+  for (auto &r : c->prof_rec) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  c->prof_rec.clear();
+}
+
+ie_status ie_profile(ie_ctx *c, int enable) {
+  if (!c) return IE_ERR_ARG;
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  prof_clear(c);
+  c->prof = enable != 0;
+  return IE_OK;
+}
+
+ie_status ie_profile_read(ie_ctx *c, int dtype, double *total_ms, long long *n_launch) {
+  if (!c || !total_ms || !n_launch) return IE_ERR_ARG;
+  double tot = 0.0;
+  long long n = 0;
+  for (auto &r : c->prof_rec) {
+    if (r.dtype != dtype) continue;
+    IE_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    IE_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    tot += ms;
+    ++n;
+  }
+  *total_ms = tot;
+  *n_launch = n;
+  return IE_OK;
+}
+
+ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter, double *ms_out) {
+  if (!c || !ms_out || inst < 0 || inst >= (int)c->inst.size() || nrhs < 1 || nrhs > c->max_rhs || n_iter < 1)
+    return IE_ERR_ARG;
+  if (dtype != IE_C64 && dtype != IE_C128) return IE_ERR_ARG;
+  const int Nx = c->nx, Ny = c->ny, Nz = c->nz, CZ = nrhs * 3 * Nz;
+  cudaStream_t s = c->stream;
+  cudaEvent_t ev[6];
+  for (auto &e : ev) IE_CUDA(cudaEventCreate(&e));
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int it = 0; it < n_iter; ++it) {
+    if (dtype == IE_C128) {
+      const double2 *x = c->w;
+      double2 *y = c->r, *t1 = (double2 *)c->t1, *sp = (double2 *)c->spec;
+      cudaEventRecord(ev[0], s);
+      ie::launch_fft_rows_fwd<double>(x, (const double2 *)c->d64.in_f, t1, CZ, Nz, Ny, Nx, c->px, s);
+      cudaEventRecord(ev[1], s);
+      ie::launch_fft_axis<double, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0, s);
+      cudaEventRecord(ev[2], s);
+      ie::launch_contract<double>(sp, c->inst[inst].q64, Nx, Ny, Nz, nrhs, s);
+      cudaEventRecord(ev[3], s);
+      ie::launch_fft_axis<double, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0, s);
+      cudaEventRecord(ev[4], s);
+      ie::launch_fft_rows_inv<double>(t1, x, (const double2 *)c->d64.diag, (const double2 *)c->d64.out_f, y, CZ, Nz,
+                                      Ny, Nx, c->px, s);
+      cudaEventRecord(ev[5], s);
+    } else {
+      const float2 *x = c->x32;
+      float2 *y = c->y32, *t1 = (float2 *)c->t1, *sp = (float2 *)c->spec;
+      cudaEventRecord(ev[0], s);
+      ie::launch_fft_rows_fwd<float>(x, (const float2 *)c->d32.in_f, t1, CZ, Nz, Ny, Nx, c->px, s);
+      cudaEventRecord(ev[1], s);
+      ie::launch_fft_axis<float, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
+      cudaEventRecord(ev[2], s);
+      ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, s);
+      cudaEventRecord(ev[3], s);
+      ie::launch_fft_axis<float, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
+      cudaEventRecord(ev[4], s);
+      ie::launch_fft_rows_inv<float>(t1, x, (const float2 *)c->d32.diag, (const float2 *)c->d32.out_f, y, CZ, Nz, Ny,
+                                     Nx, c->px, s);
+      cudaEventRecord(ev[5], s);
+    }
+    IE_CUDA(cudaEventSynchronize(ev[5]));
+    for (int k = 0; k < 5; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      acc[k] += ms;
+    }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  for (int k = 0; k < 5; ++k) ms_out[k] = acc[k] / n_iter;
+  return cuda_status(cudaGetLastError());
+}
 long long ie_ctx_device_bytes(ie_ctx *c) { return c ? c->dev_bytes : 0; }
 
 static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double *sigma_a, int n_freq,

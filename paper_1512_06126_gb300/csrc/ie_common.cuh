@@ -30,6 +30,10 @@ template <typename V> __host__ __device__ __forceinline__ V cconj(V a) { a.y = -
 template <typename V, typename S> __host__ __device__ __forceinline__ V cscale(V a, S s) { a.x *= s; a.y *= s; return a; }
 template <typename V> __host__ __device__ __forceinline__ V cneg(V a) { a.x = -a.x; a.y = -a.y; return a; }
 
+// Count of kernels launched by the library (all launchers increment it).
+void count_launches(long long n);
+long long launches();
+
 // Maximum number of radix stages in an FFT plan.
 constexpr int kMaxStages = 20;
 

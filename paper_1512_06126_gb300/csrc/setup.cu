@@ -100,18 +100,22 @@ int grid_for(long long n) {
 
 void launch_embed(const double2 *qreal, double2 *emb, int Nx, int Ny, int Nz, long long e0, long long E,
                   cudaStream_t s) {
+  count_launches(1);
   embed_kernel<<<grid_for(4LL * Nx * Ny * E), 256, 0, s>>>(qreal, emb, Nx, Ny, Nz, e0, E);
 }
 
 void launch_pack(const double2 *spec, double2 *q64, float2 *q32, int Nx, int Ny, int Nz, long long e0, long long E,
                  cudaStream_t s) {
+  count_launches(1);
   pack_kernel<<<grid_for((long long)(Nx + 1) * (Ny + 1) * E), 256, 0, s>>>(spec, q64, q32, Nx, Ny, Nz, e0, E);
 }
 
 void launch_cast64to32(const double2 *a, float2 *b, long long n, cudaStream_t s) {
+  count_launches(1);
   cast64to32<<<grid_for(n), 256, 0, s>>>(a, b, n);
 }
 void launch_cast32to64(const float2 *a, double2 *b, long long n, cudaStream_t s) {
+  count_launches(1);
   cast32to64<<<grid_for(n), 256, 0, s>>>(a, b, n);
 }
 

@@ -20,7 +20,8 @@ IE_C64, IE_C128 = 0, 1
 IE_FP64, IE_MIXED = 0, 1
 
 EXPORTS = ("ie_setup", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_rhs_mt", "ie_ctx_stream",
-           "ie_ctx_device_bytes", "ie_destroy", "ie_status_str")
+           "ie_ctx_device_bytes", "ie_profile", "ie_profile_read", "ie_profile_matvec", "ie_kernel_launches",
+           "ie_destroy", "ie_status_str")
 
 
 class ie_grid(ctypes.Structure):
@@ -78,12 +79,24 @@ def load(path: str = LIB_PATH):
     lib.ie_ctx_stream.restype = VP
     lib.ie_ctx_device_bytes.argtypes = [VP]
     lib.ie_ctx_device_bytes.restype = ctypes.c_longlong
+    lib.ie_profile.argtypes = [VP, I]
+    lib.ie_profile.restype = I
+    lib.ie_profile_read.argtypes = [VP, I, P(D), P(ctypes.c_longlong)]
+    lib.ie_profile_read.restype = I
+    lib.ie_profile_matvec.argtypes = [VP, I, I, I, I, P(D)]
+    lib.ie_profile_matvec.restype = I
+    lib.ie_kernel_launches.argtypes = []
+    lib.ie_kernel_launches.restype = ctypes.c_longlong
     lib.ie_destroy.argtypes = [VP]
     lib.ie_destroy.restype = None
     lib.ie_status_str.argtypes = [I]
     lib.ie_status_str.restype = ctypes.c_char_p
     _lib = lib
     return lib
+
+
+def kernel_launches() -> int:
+    return int(load().ie_kernel_launches())
 
 
 def status_str(s: int) -> str:
@@ -159,6 +172,20 @@ class Context:
         s = fn(self.ctx, inst, b_ptr, u_ptr, nrhs, tol, precision, int(bool(use_x0)), ctypes.byref(info))
         _check(s, "ie_adjoint_solve" if adjoint else "ie_solve", ok=(IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN))
         return s, info
+
+    def profile(self, enable):
+        _check(self._lib.ie_profile(self.ctx, int(bool(enable))), "ie_profile")
+
+    def profile_read(self, dtype):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        _check(self._lib.ie_profile_read(self.ctx, dtype, ctypes.byref(ms), ctypes.byref(n)), "ie_profile_read")
+        return ms.value, n.value
+
+    def profile_matvec(self, inst, nrhs, dtype, n_iter):
+        out = (ctypes.c_double * 5)()
+        _check(self._lib.ie_profile_matvec(self.ctx, inst, nrhs, dtype, n_iter, out), "ie_profile_matvec")
+        return list(out)
 
     def rhs_mt(self, inst, pol, u0_ptr):
         _check(self._lib.ie_rhs_mt(self.ctx, inst, pol, u0_ptr), "ie_rhs_mt")

@@ -120,8 +120,14 @@ def test_no_anomaly_solution_is_normal_field():
     ud = torch.zeros_like(bd)
     torch.cuda.synchronize()
     st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), 1, 1e-12, precision=0)
-    assert st == 0 and info.inner_iters == 0
+    # A = I when gamma = 0: one Krylov step from the zero guess reaches U = U^0
+    assert st == 0 and info.inner_iters == 1
     assert rel(to_host(ud), b) <= 1e-15
+    # starting from U^0 itself no iteration is needed
+    ud2 = bd.clone()
+    st, info = ctx.solve(0, bd.data_ptr(), ud2.data_ptr(), 1, 1e-12, precision=0, use_x0=True)
+    assert st == 0 and info.inner_iters == 0
+    assert rel(to_host(ud2), b) == 0.0
     ctx.close()
 
 
