@@ -95,13 +95,26 @@ typedef struct {
  *   q_real_host  : n_freq compressed real-space coefficient tensors, each
  *                  [Ny][Nx][6][Nz][Nz] complex (block order xx, yy, zz, xy, xz, yz;
  *                  offsets i in [0,Ny), j in [0,Nx); the storage of eq. (matrix_symm)),
- *                  i.e. the 3x3 blocks B_n^m of Appendix A.  Required.
+ *                  i.e. the 3x3 blocks B_n^m of Appendix A; or NULL, in which case the
+ *                  library generates them on the device (ie_generate_coefficients).
  *   max_rhs      : largest number of right-hand sides passed to one call (1..4).
  * The tensors are transformed on the device (2N-periodic embedding with the
  * parities of Lemma 2, 2-D DFT) and kept in c128 and c64. */
 ie_status ie_setup(const ie_grid *grid, const ie_layers *layers, const double *sigma_a_host, int n_freq,
                    const double *freq_host, const double *q_real_host, int max_rhs, const ie_options *opt,
                    ie_ctx **out);
+
+/* Generate the compressed real-space coefficient tensor of one frequency on the device
+ * (Appendices A-C): the vertical integrals (Ver_Int) of the layered-medium fundamental
+ * functions (recursions (pq_req), amplitudes (A_rs), form (UU2)) on a master grid of
+ * lambda, uniform in ln(lambda); the lateral cell-to-cell Hankel kernels of (Hor_Int)
+ * integrated by Gauss-Legendre panels per offset and mapped onto that grid (the
+ * separable structure of the filter of Appendix C); their product; and, for cells
+ * whose footprints touch, the quasi-static part in closed form.
+ * q_dev: device c128 [Ny][Nx][6][Nz][Nz]; stream: cudaStream_t or NULL.  Synchronous.
+ * Supports up to 24 interfaces and Nz <= 256. */
+ie_status ie_generate_coefficients(const ie_grid *grid, const ie_layers *layers, double freq, void *q_dev,
+                                   void *stream);
 
 /* y = A x (transpose = 0) or y = A^T x (transpose = 1) for instance inst, with nrhs
  * right-hand sides.  dtype selects c64 (IE_C64, the c64 coefficient copy) or c128.

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "blas.cuh"
+#include "coefgen.cuh"
 #include "contract.cuh"
 #include "fft.cuh"
 #include "setup.cuh"
@@ -151,7 +152,9 @@ ie_status build_diagonals(ie_ctx *c) {
   return IE_OK;
 }
 
-// Coefficient DFT: real-space compressed tensor (host c128) -> folded spectral c128 + c64.
+// Coefficient DFT: real-space compressed tensor (c128, on the host or already on the
+// device) -> folded spectral c128 + c64.  If both pointers are null the tensor is
+// generated on the device (Appendices A-C).
 ie_status build_spectral(ie_ctx *c, Instance &in, const double *q_host) {
   const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
   const long long NE = 6LL * Nz * Nz;
@@ -162,11 +165,24 @@ ie_status build_spectral(ie_ctx *c, Instance &in, const double *q_host) {
   IE_TRY(dalloc(c, &in.q32, nf * BS * sizeof(float2)));
   double2 *dq = nullptr, *buf = nullptr;
   IE_CUDA(cudaMalloc(&dq, nq * sizeof(double2)));
+  cudaError_t e = cudaSuccess;
+  if (q_host) {
+    e = cudaMemcpyAsync(dq, q_host, nq * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
+  } else {
+    std::vector<double> sg(2 * c->sig.size());
+    for (size_t k = 0; k < c->sig.size(); ++k) { sg[2 * k] = c->sig[k].real(); sg[2 * k + 1] = c->sig[k].imag(); }
+    ie::CoefGenInput gi{c->nx, c->ny, c->nz, c->hx, c->hy, c->ze.data(), c->lay.data(), (int)c->d.size(),
+                        c->d.data(), sg.data(), in.freq};
+    const ie::CoefGenStatus gs = ie::generate_coefficients(gi, dq, c->stream);
+    if (gs != ie::CoefGenStatus::kOk) {
+      cudaFree(dq);
+      return gs == ie::CoefGenStatus::kUnsupported ? IE_ERR_ARG : IE_ERR_CUDA;
+    }
+  }
   const long long plane = 4LL * Nx * Ny;
   long long E = std::max<long long>(1, std::min<long long>(NE, (1LL << 30) / (plane * (long long)sizeof(double2))));
-  cudaError_t e = cudaMalloc(&buf, plane * E * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&buf, plane * E * sizeof(double2));
   if (e != cudaSuccess) { cudaFree(dq); return cuda_status(e); }
-  e = cudaMemcpyAsync(dq, q_host, nq * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
   for (long long e0 = 0; e == cudaSuccess && e0 < NE; e0 += E) {
     const long long Ec = std::min(E, NE - e0);
     ie::launch_embed(dq, buf, Nx, Ny, Nz, e0, Ec, c->stream);
@@ -509,6 +525,25 @@ void *ie_ctx_stream(ie_ctx *c) { return c ? (void *)c->stream : nullptr; }
 
 long long ie_kernel_launches(void) { return ie::launches(); }
 
+ie_status ie_generate_coefficients(const ie_grid *g, const ie_layers *lay, double freq, void *q_dev, void *stream) {
+  if (!g || !lay || !q_dev || !(freq > 0) || g->nx < 1 || g->ny < 1 || g->nz < 1 || !g->z_edges_host ||
+      lay->n_interfaces < 1 || !lay->interfaces_host || !lay->sigma_host)
+    return IE_ERR_ARG;
+  std::vector<double> ze(g->z_edges_host, g->z_edges_host + g->nz + 1);
+  std::vector<double> d(lay->interfaces_host, lay->interfaces_host + lay->n_interfaces);
+  std::vector<int> cl(g->nz);
+  for (int z = 0; z < g->nz; ++z) {
+    if (!(ze[z + 1] > ze[z])) return IE_ERR_ARG;
+    cl[z] = layer_of_cell(d, ze[z], ze[z + 1]);
+    if (cl[z] < 0 || !(lay->sigma_host[2 * cl[z]] > 0.0)) return IE_ERR_GEOMETRY;
+  }
+  ie::CoefGenInput gi{g->nx, g->ny, g->nz, g->hx, g->hy, ze.data(), cl.data(), lay->n_interfaces, d.data(),
+                      lay->sigma_host, freq};
+  const ie::CoefGenStatus gs = ie::generate_coefficients(gi, (double2 *)q_dev, (cudaStream_t)stream);
+  if (gs == ie::CoefGenStatus::kUnsupported) return IE_ERR_ARG;
+  return gs == ie::CoefGenStatus::kOk ? IE_OK : IE_ERR_CUDA;
+}
+
 static void prof_clear(ie_ctx *c) {
   for (auto &r : c->prof_rec) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   c->prof_rec.clear();
@@ -637,7 +672,7 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   for (int f = 0; f < n_freq; ++f) {
     if (!(freq[f] > 0)) return IE_ERR_ARG;
     c->inst[f].freq = freq[f];
-    IE_TRY(build_spectral(c, c->inst[f], q_real + 2 * nq * f));
+    IE_TRY(build_spectral(c, c->inst[f], q_real ? q_real + 2 * nq * f : nullptr));
   }
   // workspaces (sized for c128 and max_rhs)
   const long long CZ = (long long)max_rhs * 3 * c->nz;
@@ -665,7 +700,6 @@ ie_status ie_setup(const ie_grid *g, const ie_layers *lay, const double *sigma_a
   if (!g || !lay || !sigma_a || !freq || n_freq < 1 || max_rhs < 1 || max_rhs > 4) return IE_ERR_ARG;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->hx > 0) || !(g->hy > 0) || !g->z_edges_host) return IE_ERR_ARG;
   if (lay->n_interfaces < 1 || !lay->interfaces_host || !lay->sigma_host) return IE_ERR_ARG;
-  if (!q_real) return IE_ERR_COEFF;
   ie_ctx *c = new (std::nothrow) ie_ctx();
   if (!c) return IE_ERR_OOM;
   const ie_status st = setup_impl(g, lay, sigma_a, n_freq, freq, q_real, max_rhs, opt, c);

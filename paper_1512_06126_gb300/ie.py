@@ -19,7 +19,7 @@ IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN = 0, 1, 2
 IE_C64, IE_C128 = 0, 1
 IE_FP64, IE_MIXED = 0, 1
 
-EXPORTS = ("ie_setup", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_rhs_mt", "ie_ctx_stream",
+EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_rhs_mt", "ie_ctx_stream",
            "ie_ctx_device_bytes", "ie_profile", "ie_profile_read", "ie_profile_matvec", "ie_kernel_launches",
            "ie_destroy", "ie_status_str")
 
@@ -67,6 +67,8 @@ def load(path: str = LIB_PATH):
     P, I, D, VP = ctypes.POINTER, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
     lib.ie_setup.argtypes = [P(ie_grid), P(ie_layers), P(D), I, P(D), P(D), I, P(ie_options), P(VP)]
     lib.ie_setup.restype = I
+    lib.ie_generate_coefficients.argtypes = [P(ie_grid), P(ie_layers), D, VP, VP]
+    lib.ie_generate_coefficients.restype = I
     lib.ie_matvec.argtypes = [VP, I, VP, VP, I, I, I, VP]
     lib.ie_matvec.restype = I
     lib.ie_solve.argtypes = [VP, I, VP, VP, I, D, I, I, P(ie_solve_info)]
@@ -117,9 +119,28 @@ def _cplx_pairs(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
 
 
+def _grid_layers(grid, layers, keep):
+    ze = np.ascontiguousarray(np.asarray(grid.z_edges, dtype=np.float64))
+    d = np.ascontiguousarray(np.asarray(layers.interfaces, dtype=np.float64))
+    sig = _cplx_pairs(layers.sigma)
+    keep += [ze, d, sig]
+    return (ie_grid(grid.nx, grid.ny, grid.nz, grid.hx, grid.hy, _dptr(ze), 0.0, 0.0),
+            ie_layers(len(d), _dptr(d), _dptr(sig)))
+
+
+def generate_coefficients(grid, layers, freq, q_ptr, stream=None):
+    """Compressed real-space tensor [Ny][Nx][6][Nz][Nz] (c128) written to the device
+    buffer q_ptr by the library's generator."""
+    keep = []
+    g, lay = _grid_layers(grid, layers, keep)
+    _check(load().ie_generate_coefficients(ctypes.byref(g), ctypes.byref(lay), float(freq), q_ptr, stream),
+           "ie_generate_coefficients")
+
+
 class Context:
     """Owns one ie_ctx.  ``q_real`` is a list (one per frequency) of compressed
-    real-space tensors [Ny][Nx][6][Nz][Nz] (complex)."""
+    real-space tensors [Ny][Nx][6][Nz][Nz] (complex), or None to let the library
+    generate them on the device."""
 
     def __init__(self, grid, layers, sigma_a, freqs, q_real, max_rhs=2, restart=30, max_iter=2000,
                  inner_tol=1e-3, max_outer=50):
@@ -133,10 +154,14 @@ class Context:
         lay = ie_layers(len(d), _dptr(d), _dptr(sig))
         sa = _cplx_pairs(np.asarray(sigma_a).reshape(-1))
         fr = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64))
-        q = _cplx_pairs(np.stack([np.asarray(x, dtype=np.complex128) for x in q_real]).reshape(-1))
+        if q_real is None:
+            q = None
+        else:
+            q = _cplx_pairs(np.stack([np.asarray(x, dtype=np.complex128) for x in q_real]).reshape(-1))
         opt = ie_options(restart, max_iter, inner_tol, max_outer)
         ctx = ctypes.c_void_p()
-        s = lib.ie_setup(ctypes.byref(g), ctypes.byref(lay), _dptr(sa), len(fr), _dptr(fr), _dptr(q), max_rhs,
+        s = lib.ie_setup(ctypes.byref(g), ctypes.byref(lay), _dptr(sa), len(fr), _dptr(fr),
+                         None if q is None else _dptr(q), max_rhs,
                          ctypes.byref(opt), ctypes.byref(ctx))
         _check(s, "ie_setup")
         self.ctx = ctx
