@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Galerkin integral-equation solver.
+
+Workload (default): the single-solve configuration, Nx = Ny = 128, Nz = 32 cells of
+50 m (1,572,864 unknowns), 5-layer seeded background, 20 seeded anomalies of
+0.01-0.1 ohm-m, 1 Hz, both MT polarisations; coefficients generated on the
+device by the library.  One step = one mixed-precision solve (c64 FFT products
+with FP32 accumulation, FP64 Arnoldi and FP64 c128 refinement residual) of both
+polarisations to ||b - A u|| <= 1e-7 ||b||, i.e. every step of the hot path.
+
+Printed (one JSON line, rank 0):
+  value         unknowns * Krylov iterations / s over the timed steps (device-resident
+                inputs), summed over ranks (replicas) / max time
+  matvec        the IE matrix-vector product: algorithmic GB/s (coefficients once +
+                input and output vectors) of the c64 product for both polarisations
+  tts           time-to-solution at 1e-7: mixed vs plain FP64 (c128 products only)
+  roofline      the contraction kernel, timed with CUDA events during the timed steps
+  cpu_baseline  the FP64 oracle (numpy) on the host: GMRES iterations of the same grid
+  e2e           the same metric through the C ABI with host buffers (H2D of the
+                right-hand sides and D2H of the solution inside the timed region)
+
+--impl reference runs the oracle (the reference implementation of this tier) on the
+host cores for the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "IE matvec GB/s & unknowns*iters/s; GMRES time-to-solution at 1e-7, mixed vs FP64"
+UNIT = "unknowns*iters/s"
+TOL = 1e-7
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def workload(name):
+    return {"C1": W.config1, "C2": W.config2, "C4": W.config4, "C5": W.config5}[name]()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: each rank solves its own copy)
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend=backend)
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host (cpu baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(model, n_iters, seed=41):
+    """FP64 oracle GMRES iterations on the workload's grid for one right-hand side.
+
+    The coefficient values do not change the oracle's cost, so a seeded random tensor
+    of the workload's shape stands in for the generated one.  Returns (seconds spent
+    in the timed iterations, iterations)."""
+    from oracle import operator as O
+    g = model.grid
+    q = W.random_compressed_q(g.ny, g.nx, g.nz, seed=seed)
+    qt = O.full_spectrum_blocks(O.embed_spectrum(q))
+    b = W.random_field((3, g.nz, g.ny, g.nx), seed + 1)
+    t0 = time.perf_counter()
+    O.gmres(lambda v: O.fft_apply(model, qt, v), b, tol=1e-30, m=30, max_iter=n_iters)
+    return time.perf_counter() - t0, n_iters
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    model = workload(args.workload)
+    g = model.grid
+    n_unk = 3 * g.nx * g.ny * g.nz
+    for _ in range(args.warmup):
+        oracle_sample(model, 1)
+    t, it = 0.0, 0
+    for _ in range(args.steps):
+        dt, n = oracle_sample(model, 1)
+        t += dt
+        it += n
+    value = n_unk * it / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": args.workload, "grid": [g.nx, g.ny, g.nz]},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+                             "sample": "one FP64 GMRES iteration (FFT product + CGS2) of the oracle per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, ws):
+    import torch
+    from paper_1512_06126_gb300 import build, ie
+
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    model = workload(args.workload)
+    g = model.grid
+    R = 2
+    n_unk = 3 * g.nx * g.ny * g.nz
+    t0 = time.perf_counter()
+    ctx = ie.Context(g, model.layers, model.sigma_a, model.freqs[:1], None, max_rhs=R, restart=args.restart,
+                     inner_tol=args.inner_tol)
+    t_setup = time.perf_counter() - t0
+    b = torch.empty((R, 3, g.nz, g.ny, g.nx), dtype=torch.complex128, device="cuda")
+    for r in range(R):
+        ctx.rhs_mt(0, r, b[r].data_ptr())
+    u = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    ext = torch.cuda.ExternalStream(ctx.stream)
+
+    def solve(precision):
+        st, info = ctx.solve(0, b.data_ptr(), u.data_ptr(), R, TOL, precision=precision)
+        if st != ie.IE_OK:
+            raise RuntimeError(f"solve did not converge: status {st}, residual {info.final_rel_res:.2e}")
+        return info
+
+    for _ in range(args.warmup):
+        solve(ie.IE_MIXED)
+    # ---- timed region: K mixed solves, device-resident inputs ----
+    clocks = Clocks(dev)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.profile(True)
+    l0 = ie.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(ext):
+        ev0.record()
+    iters = 0
+    outer = 0
+    res = 0.0
+    for _ in range(args.steps):
+        info = solve(ie.IE_MIXED)
+        iters += info.inner_iters
+        outer += info.outer_iters
+        res = max(res, info.final_rel_res)
+    with torch.cuda.stream(ext):
+        ev1.record()
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(ws)
+    l1 = ie.kernel_launches()
+    k3_ms, k3_n = ctx.profile_read(ie.IE_C64)
+    ctx.profile(False)
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = allreduce_max(t_ms / 1e3, ws)
+    units = allreduce_sum(float(n_unk) * R * iters, ws)
+    value = units / t_max
+
+    # ---- time-to-solution: mixed (mean of the timed steps) vs plain FP64 ----
+    tts_mixed = t_ms / 1e3 / args.steps
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    info64 = solve(ie.IE_FP64)
+    torch.cuda.synchronize()
+    tts_fp64 = time.perf_counter() - t1
+
+    # ---- matvec GB/s (c64, both polarisations) ----
+    nf = (g.nx + 1) * (g.ny + 1)
+    bs = 2 * g.nz * (2 * g.nz + 1)
+    q_bytes = nf * bs * 8
+    xs = torch.randn((R, 3, g.nz, g.ny, g.nx), dtype=torch.complex64, device="cuda")
+    ys = torch.empty_like(xs)
+    sp = torch.cuda.current_stream().cuda_stream
+    for _ in range(3):
+        ctx.matvec(0, xs.data_ptr(), ys.data_ptr(), R, dtype=ie.IE_C64, stream=sp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_mv = 20
+    e0.record()
+    for _ in range(n_mv):
+        ctx.matvec(0, xs.data_ptr(), ys.data_ptr(), R, dtype=ie.IE_C64, stream=sp)
+    e1.record()
+    e1.synchronize()
+    mv_ms = e0.elapsed_time(e1) / n_mv
+    mv_bytes = q_bytes + 2 * 8 * n_unk * R
+    kern_ms = ctx.profile_matvec(0, R, ie.IE_C64, 10)
+
+    # ---- roofline of the contraction kernel (timed during the steps) ----
+    hbm_peak, sm_max, peak_src = peaks()
+    k3_avg_ms = k3_ms / max(k3_n, 1)
+    k3_bytes = q_bytes + 2 * 4 * g.nx * g.ny * 3 * g.nz * R * 8
+    k3_flops = 8.0 * 4 * g.nx * g.ny * R * 9 * g.nz * g.nz
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12            # TFLOP/s, FP32 FMA pipes at max clock
+    t_hbm = k3_bytes / (hbm_peak * 1e9)
+    t_alu = k3_flops / (fp32_peak * 1e12)
+    if t_alu > t_hbm:
+        achieved = k3_flops / (k3_avg_ms * 1e-3) / 1e12
+        roof = {"kernel": "contract (c64, 2 right-hand sides)", "bound": "alu", "achieved": achieved,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                "hbm_GBs": k3_bytes / (k3_avg_ms * 1e-3) / 1e9, "hbm_frac": k3_bytes / (k3_avg_ms * 1e-3) / 1e9 / hbm_peak,
+                "bytes_per_launch": k3_bytes, "flops_per_launch": k3_flops, "traffic": None,
+                "launches": k3_n, "avg_ms": k3_avg_ms}
+    else:
+        achieved = k3_bytes / (k3_avg_ms * 1e-3) / 1e9
+        roof = {"kernel": "contract (c64, 2 right-hand sides)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_src,
+                "bytes_per_launch": k3_bytes, "traffic": None, "launches": k3_n, "avg_ms": k3_avg_ms}
+
+    # ---- e2e: through the ABI with host buffers ----
+    bh = b.cpu().pin_memory()
+    uh = torch.empty_like(bh).pin_memory()
+    bd = torch.empty_like(b)
+    ud = torch.empty_like(b)
+    torch.cuda.synchronize()
+    e0.record()
+    it_e2e = 0
+    n_e2e = max(1, min(args.steps, 3))
+    for _ in range(n_e2e):
+        bd.copy_(bh, non_blocking=True)
+        torch.cuda.synchronize()
+        st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), R, TOL, precision=ie.IE_MIXED)
+        uh.copy_(ud, non_blocking=True)
+        it_e2e += info.inner_iters
+    e1.record()
+    e1.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3
+    e2e_value = allreduce_sum(float(n_unk) * R * it_e2e, ws) / allreduce_max(t_e2e, ws)
+
+    # ---- cpu baseline (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        t_cpu, n_cpu = oracle_sample(model, args.cpu_iters)
+        cpu = {"value": n_unk * n_cpu / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n_cpu} FP64 GMRES iterations of the numpy oracle (FFT product + CGS2), one right-hand "
+                         f"side, same grid, random coefficient tensor of the same shape; {t_cpu:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64 products, c128 refinement", "data": "synthetic",
+                "config": {"workload": f"{args.workload}: {g.nx}x{g.ny}x{g.nz} cells, {len(model.layers.sigma) - 1}"
+                                       f" layers + air, {model.freqs[0]} Hz, 2 polarisations, tol {TOL}",
+                           "unknowns": n_unk, "rhs": R, "restart": args.restart,
+                           "l2": "inputs larger than L2 (c64 coefficients %.0f MB)" % (q_bytes / 1e6),
+                           "parallelism": f"replicas x{ws}", "coefficients": "generated on the device",
+                           "setup_s": t_setup},
+                "matvec": {"GBs": mv_bytes / (mv_ms * 1e-3) / 1e9, "ms": mv_ms, "bytes": mv_bytes,
+                           "kernel_ms": {"rows_fwd": kern_ms[0], "cols_fwd": kern_ms[1], "contract": kern_ms[2],
+                                         "cols_inv": kern_ms[3], "rows_inv": kern_ms[4]}},
+                "tts": {"mixed_s": tts_mixed, "fp64_s": tts_fp64, "speedup": tts_fp64 / tts_mixed,
+                        "mixed_iters": iters / args.steps, "mixed_outer": outer / args.steps,
+                        "fp64_iters": info64.inner_iters, "final_rel_res": res},
+                "roofline": roof,
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 16),
+                        "d2h_bytes_per_step": int(b.numel() * 16)},
+                "gpu_launches": int(l1 - l0),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="C2", choices=["C1", "C2", "C4", "C5"])
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--inner-tol", type=float, default=1e-3)
+    ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, ws = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

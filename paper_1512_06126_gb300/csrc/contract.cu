@@ -13,6 +13,7 @@
 // (Lemma 2), so one CTA loads a block once and applies it to all its mirrors and
 // all right-hand sides.
 #include "contract.cuh"
+#include "contract_tma.cuh"
 
 namespace ie {
 namespace {
@@ -126,7 +127,65 @@ void launch_t(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStr
   k<<<grid, threads, sm, s>>>(spec, qf, Nx, Ny, Nz, R);
 }
 
+__device__ int g_contract_err = 0;
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int NZ, int R, int NS>
+bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, cudaStream_t s) {
+  using Cfg = ContractCfg<NZ, R, NS>;
+  if (Cfg::SMEM > 227 * 1024) return false;
+  auto k = contract_tma_kernel<NZ, R, NS>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int *err = nullptr;
+  cudaGetSymbolAddress((void **)&err, g_contract_err);
+  const int nf = (Nx + 1) * (Ny + 1);
+  const int grid = nf < num_sms() ? nf : num_sms();
+  count_launches(1);
+  k<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(spec, qf, Nx, Ny, err);
+  return true;
+}
+
+template <int NZ, int R>
+bool try_tma_stages(float2 *spec, const float2 *qf, int Nx, int Ny, cudaStream_t s) {
+  if (ContractCfg<NZ, R, 3>::SMEM <= 227 * 1024) return try_tma<NZ, R, 3>(spec, qf, Nx, Ny, s);
+  if (ContractCfg<NZ, R, 2>::SMEM <= 227 * 1024) return try_tma<NZ, R, 2>(spec, qf, Nx, Ny, s);
+  return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, s);
+}
+
+template <int R>
+bool dispatch_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, cudaStream_t s) {
+  switch (Nz) {
+    case 16: return try_tma_stages<16, R>(spec, qf, Nx, Ny, s);
+    case 24: return try_tma_stages<24, R>(spec, qf, Nx, Ny, s);
+    case 32: return try_tma_stages<32, R>(spec, qf, Nx, Ny, s);
+    case 48: return try_tma_stages<48, R>(spec, qf, Nx, Ny, s);
+    default: return false;
+  }
+}
+
 }  // namespace
+
+bool contract_tma_enabled = true;
+
+int contract_take_error() {
+  int h = 0, z = 0;
+  cudaMemcpyFromSymbol(&h, g_contract_err, sizeof(int));
+  if (h) cudaMemcpyToSymbol(g_contract_err, &z, sizeof(int));
+  return h;
+}
 
 size_t contract_smem_bytes(int Nz, int R, size_t elem) {
   return elem * ((size_t)6 * Nz * (Nz + 1) + (size_t)4 * R * 3 * Nz);
@@ -134,6 +193,12 @@ size_t contract_smem_bytes(int Nz, int R, size_t elem) {
 
 template <typename T>
 int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (contract_tma_enabled) {
+      if (R == 1 && dispatch_tma<1>(spec, qf, Nx, Ny, Nz, s)) return 0;
+      if (R == 2 && dispatch_tma<2>(spec, qf, Nx, Ny, Nz, s)) return 0;
+    }
+  }
   if (R <= 1) launch_t<T, 4>(spec, qf, Nx, Ny, Nz, R, s);
   else if (R <= 2) launch_t<T, 8>(spec, qf, Nx, Ny, Nz, R, s);
   else if (R <= 4) launch_t<T, 16>(spec, qf, Nx, Ny, Nz, R, s);

@@ -8,6 +8,11 @@ namespace ie {
 template <typename T>
 int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStream_t s);
 
+// Use the TMA-pipelined kernel where it applies (c64, Nz in {16, 24, 32, 48}, R <= 2).
+extern bool contract_tma_enabled;
+// Error code recorded by a contraction kernel since the last call (0: none); resets it.
+int contract_take_error();
+
 // Shared memory needed by the contraction CTA.
 size_t contract_smem_bytes(int Nz, int R, size_t elem);
 

@@ -156,3 +156,26 @@ def test_full_size_matvec_sampled_rows():
         got32 = np.array([y32h[r][:, c[0], c[1], c[2]] for c in cells])
         assert rel(got32, ref) <= 1e-4, rel(got32, ref)
     ctx.close()
+
+
+@pytest.mark.parametrize("shape", [(40, 24, 16), (20, 36, 24), (16, 12, 48), (24, 20, 32)])
+def test_c64_pipelined_contraction_against_c128(shape):
+    """The pipelined c64 contraction (Nz in {16, 24, 32, 48}) against the c128 path and
+    the oracle's FFT apply, on a random coefficient tensor with the physical layout."""
+    need_gpu()
+    nx, ny, nz = shape
+    m0 = W.small_model(nx=nx, ny=ny, nz=nz, seed=3, freq=1.0)
+    g = m0.grid
+    q = W.random_compressed_q(ny, nx, nz, seed=31)
+    ctx = lib_context(m0, [q], max_rhs=2)
+    qt = O.full_spectrum_blocks(O.embed_spectrum(q))
+    for R in (1, 2):
+        x = W.random_field((R, 3, nz, ny, nx), 32 + R)
+        xd = to_dev(x, torch.complex64)
+        yd = torch.empty_like(xd)
+        ctx.matvec(0, xd.data_ptr(), yd.data_ptr(), R, dtype=0, stream=torch.cuda.current_stream().cuda_stream)
+        y = to_host(yd).astype(np.complex128)
+        for r in range(R):
+            ref = O.fft_apply(m0, qt, x[r].astype(np.complex64).astype(np.complex128))
+            assert rel(y[r], ref) <= 2e-5, (shape, R, r, rel(y[r], ref))
+    ctx.close()
