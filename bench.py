@@ -152,20 +152,28 @@ class Clocks:
 # the oracle on the host (cpu baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(model, n_iters, seed=41):
+class OracleSample:
     """FP64 oracle GMRES iterations on the workload's grid for one right-hand side.
 
     The coefficient values do not change the oracle's cost, so a seeded random tensor
-    of the workload's shape stands in for the generated one.  Returns (seconds spent
-    in the timed iterations, iterations)."""
-    from oracle import operator as O
-    g = model.grid
-    q = W.random_compressed_q(g.ny, g.nx, g.nz, seed=seed)
-    qt = O.full_spectrum_blocks(O.embed_spectrum(q))
-    b = W.random_field((3, g.nz, g.ny, g.nx), seed + 1)
-    t0 = time.perf_counter()
-    O.gmres(lambda v: O.fft_apply(model, qt, v), b, tol=1e-30, m=30, max_iter=n_iters)
-    return time.perf_counter() - t0, n_iters
+    of the workload's shape stands in for the generated one.  The spectral blocks are
+    built once (setup, untimed); run(n) times n GMRES iterations."""
+
+    def __init__(self, model, seed=41):
+        from oracle import operator as O
+        self.O = O
+        self.model = model
+        g = model.grid
+        q = W.random_compressed_q(g.ny, g.nx, g.nz, seed=seed)
+        self.qt = O.full_spectrum_blocks(O.embed_spectrum(q))
+        del q
+        self.b = W.random_field((3, g.nz, g.ny, g.nx), seed + 1)
+
+    def run(self, n_iters):
+        O = self.O
+        t0 = time.perf_counter()
+        O.gmres(lambda v: O.fft_apply(self.model, self.qt, v), self.b, tol=1e-30, m=30, max_iter=n_iters)
+        return time.perf_counter() - t0, n_iters
 
 
 def run_reference(args, rank, ws):
@@ -174,11 +182,12 @@ def run_reference(args, rank, ws):
     model = workload(args.workload)
     g = model.grid
     n_unk = 3 * g.nx * g.ny * g.nz
+    sample = OracleSample(model)
     for _ in range(args.warmup):
-        oracle_sample(model, 1)
+        sample.run(1)
     t, it = 0.0, 0
     for _ in range(args.steps):
-        dt, n = oracle_sample(model, 1)
+        dt, n = sample.run(1)
         t += dt
         it += n
     value = n_unk * it / t
@@ -272,15 +281,18 @@ def run_ours(args, rank, ws):
     q_bytes = nf * bs * 8
     xs = torch.randn((R, 3, g.nz, g.ny, g.nx), dtype=torch.complex64, device="cuda")
     ys = torch.empty_like(xs)
-    sp = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    # launched on the context's stream; events recorded on that same stream
     for _ in range(3):
-        ctx.matvec(0, xs.data_ptr(), ys.data_ptr(), R, dtype=ie.IE_C64, stream=sp)
+        ctx.matvec(0, xs.data_ptr(), ys.data_ptr(), R, dtype=ie.IE_C64)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n_mv = 20
-    e0.record()
+    with torch.cuda.stream(ext):
+        e0.record()
     for _ in range(n_mv):
-        ctx.matvec(0, xs.data_ptr(), ys.data_ptr(), R, dtype=ie.IE_C64, stream=sp)
-    e1.record()
+        ctx.matvec(0, xs.data_ptr(), ys.data_ptr(), R, dtype=ie.IE_C64)
+    with torch.cuda.stream(ext):
+        e1.record()
     e1.synchronize()
     mv_ms = e0.elapsed_time(e1) / n_mv
     mv_bytes = q_bytes + 2 * 8 * n_unk * R
@@ -314,6 +326,8 @@ def run_ours(args, rank, ws):
     bd = torch.empty_like(b)
     ud = torch.empty_like(b)
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     it_e2e = 0
     n_e2e = max(1, min(args.steps, 3))
@@ -331,7 +345,7 @@ def run_ours(args, rank, ws):
     # ---- cpu baseline (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        t_cpu, n_cpu = oracle_sample(model, args.cpu_iters)
+        t_cpu, n_cpu = OracleSample(model).run(args.cpu_iters)
         cpu = {"value": n_unk * n_cpu / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n_cpu} FP64 GMRES iterations of the numpy oracle (FFT product + CGS2), one right-hand "
                          f"side, same grid, random coefficient tensor of the same shape; {t_cpu:.1f} s"}
@@ -362,6 +376,34 @@ def run_ours(args, rank, ws):
     ctx.close()
 
 
+def run_matvec_only(args):
+    """Setup plus --warmup + --steps c64 products of both polarisations (used for kernel
+    profiles of the product on its own)."""
+    import torch
+    from paper_1512_06126_gb300 import build, ie
+    build.build()
+    model = workload(args.workload)
+    g = model.grid
+    R = 2
+    ctx = ie.Context(g, model.layers, model.sigma_a, model.freqs[:1], None, max_rhs=R)
+    xs = torch.randn((R, 3, g.nz, g.ny, g.nx), dtype=torch.complex64, device="cuda")
+    ys = torch.empty_like(xs)
+    torch.cuda.synchronize()
+    ext = torch.cuda.ExternalStream(ctx.stream)
+    for _ in range(args.warmup):
+        ctx.matvec(0, xs.data_ptr(), ys.data_ptr(), R, dtype=ie.IE_C64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(ext):
+        e0.record()
+    for _ in range(args.steps):
+        ctx.matvec(0, xs.data_ptr(), ys.data_ptr(), R, dtype=ie.IE_C64)
+    with torch.cuda.stream(ext):
+        e1.record()
+    e1.synchronize()
+    print(json.dumps({"mode": "matvec", "workload": args.workload, "ms_per_product": e0.elapsed_time(e1) / args.steps}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,9 +415,12 @@ def main():
     ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", choices=["solve", "matvec"], default="solve")
     args = ap.parse_args()
     rank, ws = dist_setup()
-    if args.impl == "reference":
+    if args.mode == "matvec":
+        run_matvec_only(args)
+    elif args.impl == "reference":
         run_reference(args, rank, ws)
     else:
         run_ours(args, rank, ws)

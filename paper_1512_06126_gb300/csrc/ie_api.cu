@@ -307,11 +307,8 @@ ie_status gmres(ie_ctx *c, const Op &op, const double2 *b, double2 *x, int R, do
     int kmax = 0;
     for (int k = 0; k < m && it < max_iter && n_active > 0; ++k) {
       IE_TRY(op(c->V + (long long)k * nR, c->w, R));
-      ie::gmres_mdot(c->V, c->w, c->part, h1, k + 1, R, n, ldh, 0, s);
-      ie::gmres_maxpy(c->V, h1, c->w, k + 1, R, n, ldh, -1.0, s);
-      ie::gmres_mdot(c->V, c->w, c->part, h2, k + 1, R, n, ldh, 0, s);
-      ie::gmres_maxpy(c->V, h2, c->w, k + 1, R, n, ldh, -1.0, s);
-      ie::gmres_norm(c->w, c->nrmpart, c->nrm, R, n, s);
+      if (ie::gmres_cgs2(c->V, c->w, h1, h2, c->part, c->nrmpart, c->nrm, k + 1, R, n, ldh, s) != 0)
+        return IE_ERR_ARG;
       ie::gmres_scale(c->w, c->V + (long long)(k + 1) * nR, c->nrm, R, n, s);
       IE_CUDA(cudaMemcpyAsync(hh.data(), h1, (size_t)2 * R * ldh * sizeof(double2), cudaMemcpyDeviceToHost, s));
       IE_CUDA(cudaMemcpyAsync(nrm.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -685,9 +682,11 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   IE_TRY(dalloc(c, &c->w, nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->r, nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->dx, nv * sizeof(double2)));
-  IE_TRY(dalloc(c, &c->part, (size_t)max_rhs * (c->restart + 1) * ie::mdot_nb(c->nvec()) * sizeof(double2)));
+  if (c->restart > 31) return IE_ERR_ARG;
+  const long long nbp = std::max<long long>(ie::mdot_nb(c->nvec()), ie::cgs2_partial_blocks(c->nvec()));
+  IE_TRY(dalloc(c, &c->part, (size_t)max_rhs * (c->restart + 1) * nbp * sizeof(double2)));
   IE_TRY(dalloc(c, &c->hdev, (size_t)3 * max_rhs * (c->restart + 1) * sizeof(double2)));
-  IE_TRY(dalloc(c, &c->nrmpart, (size_t)max_rhs * 1024 * sizeof(double)));
+  IE_TRY(dalloc(c, &c->nrmpart, (size_t)max_rhs * std::max<long long>(1024, nbp) * sizeof(double)));
   IE_TRY(dalloc(c, &c->nrm, (size_t)2 * max_rhs * sizeof(double)));
   IE_CUDA(cudaStreamSynchronize(c->stream));
   return IE_OK;
