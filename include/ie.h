@@ -75,7 +75,7 @@ typedef struct {
 } ie_layers;
 
 typedef struct {
-  int restart;       /* GMRES restart length m (2..31); 0 selects 30 */
+  int restart;       /* GMRES restart length m (2..63); 0 selects 30 */
   int max_iter;      /* cap on inner iterations per solve; 0 selects 2000 */
   double inner_tol;  /* mixed precision: relative tolerance of each inner c64 solve; 0 selects 1e-3 */
   int max_outer;     /* mixed precision: cap on refinement steps; 0 selects 50 */

@@ -166,113 +166,110 @@ __global__ void add_kernel(const double2 *__restrict__ x, double2 *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Fused classical Gram-Schmidt passes (all k1 <= KMAX basis vectors per pass):
-//   cgs_dot:        part_i = sum conj(V_i) w                               (h1)
-//   cgs_sub_dot:    w -= sum_i h1_i V_i;  part_i = sum conj(V_i) w          (h2)
-//   cgs_sub_norm:   w -= sum_i h2_i V_i;  part = sum |w|^2
-// Each thread keeps KMAX complex accumulators; one block reduction per pass.
+// Classical Gram-Schmidt passes, tiled over the vector length.  A block owns a tile
+// of kTile consecutive elements of one right-hand side:
+//   MODE 0 (dot):       part_i = sum_tile conj(V_i) w
+//   MODE 1 (sub + dot): w -= sum_i h_i V_i on the tile, then part_i = sum conj(V_i) w
+//   MODE 2 (sub + norm): w -= sum_i h_i V_i on the tile, then part = sum |w|^2
+// The tile of w sits in shared memory; for the dots, (basis vector, 256-element
+// chunk) work units are spread over the warps, each lane streaming 8 elements, so a
+// block keeps many independent loads in flight with few registers.
 // ---------------------------------------------------------------------------
-template <int KMAX>
-__device__ __forceinline__ void reduce_many(double2 (&acc)[KMAX], int k1, double2 *sh, double2 *part, int R,
-                                            int nb, int r) {
-  // sh: [kT/32][KMAX]
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < KMAX; ++i) {
-    if (i < k1) {
-      double2 v = acc[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-      }
-      if (lane == 0) sh[wid * KMAX + i] = v;
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < k1; i += kT) {
-    double2 t = make_double2(0.0, 0.0);
-    for (int w2 = 0; w2 < kT / 32; ++w2) {
-      t.x += sh[w2 * KMAX + i].x;
-      t.y += sh[w2 * KMAX + i].y;
-    }
-    part[((long long)r * k1 + i) * nb + blockIdx.x] = t;
-  }
-}
+constexpr int kTileEPT = 8;
+constexpr int kTile = kT * kTileEPT;  // 2048 elements
+constexpr int kChunk256 = 256;
 
-template <int KMAX, int MODE>  // MODE 0: dot, 1: sub + dot
-__global__ void __launch_bounds__(kT) cgs_kernel(const double2 *__restrict__ V, double2 *__restrict__ w,
-                                                 const double2 *__restrict__ h, double2 *__restrict__ part, int k1,
-                                                 int R, long long n, int nb, int ldh) {
-  __shared__ double2 sh[(kT / 32) * KMAX];
-  __shared__ double2 hv[KMAX];
+template <int MODE>
+__global__ void __launch_bounds__(kT) cgs_tile_kernel(const double2 *__restrict__ V, double2 *__restrict__ w,
+                                                      const double2 *__restrict__ h, double2 *__restrict__ part,
+                                                      double *__restrict__ npart, int k1, int R, long long n, int nb,
+                                                      int ldh) {
+  __shared__ double2 xw[kTile];
+  __shared__ double red[2 * 64];
+  __shared__ double2 hs[64];
+  __shared__ double2 shn[kT / 32];
   const int r = blockIdx.y;
-  double2 acc[KMAX];
-#pragma unroll
-  for (int i = 0; i < KMAX; ++i) acc[i] = make_double2(0.0, 0.0);
-  if (MODE == 1) {
-    for (int i = threadIdx.x; i < KMAX; i += kT) hv[i] = i < k1 ? h[(long long)r * ldh + i] : make_double2(0.0, 0.0);
-    __syncthreads();
-  }
+  const long long t0 = (long long)blockIdx.x * kTile;
   const long long Rn = (long long)R * n;
-  for (long long e = blockIdx.x * (long long)kT + threadIdx.x; e < n; e += (long long)nb * kT) {
-    double2 x = w[(long long)r * n + e];
-    if (MODE == 1) {
-      const double2 *vp = V + (long long)r * n + e;
-#pragma unroll
-      for (int i = 0; i < KMAX; ++i) {
-        if (i < k1) {
-          const double2 a = __ldg(vp);
-          x.x -= hv[i].x * a.x - hv[i].y * a.y;
-          x.y -= hv[i].x * a.y + hv[i].y * a.x;
-        }
-        vp += Rn;
-      }
-      w[(long long)r * n + e] = x;
-    }
-    const double2 *vp = V + (long long)r * n + e;
-#pragma unroll
-    for (int i = 0; i < KMAX; ++i) {
-      if (i < k1) {
-        const double2 a = __ldg(vp);
-        acc[i].x = fma(a.x, x.x, acc[i].x);
-        acc[i].x = fma(a.y, x.y, acc[i].x);
-        acc[i].y = fma(a.x, x.y, acc[i].y);
-        acc[i].y = fma(-a.y, x.x, acc[i].y);
-      }
-      vp += Rn;
-    }
-  }
-  reduce_many<KMAX>(acc, k1, sh, part, R, nb, r);
-}
-
-template <int KMAX>
-__global__ void __launch_bounds__(kT) cgs_sub_norm_kernel(const double2 *__restrict__ V, double2 *__restrict__ w,
-                                                          const double2 *__restrict__ h, double *__restrict__ part,
-                                                          int k1, int R, long long n, int nb, int ldh) {
-  __shared__ double2 sh[kT / 32];
-  __shared__ double2 hv[KMAX];
-  const int r = blockIdx.y;
-  for (int i = threadIdx.x; i < KMAX; i += kT) hv[i] = i < k1 ? h[(long long)r * ldh + i] : make_double2(0.0, 0.0);
+  const int tid = threadIdx.x;
+  const double2 *Vr = V + (long long)r * n;
+  double2 *wr = w + (long long)r * n;
+  if (tid < 2 * 64) red[tid] = 0.0;
+  if (MODE != 0 && tid < k1) hs[tid] = h[(long long)r * ldh + tid];
   __syncthreads();
-  double acc = 0.0;
-  const long long Rn = (long long)R * n;
-  for (long long e = blockIdx.x * (long long)kT + threadIdx.x; e < n; e += (long long)nb * kT) {
-    double2 x = w[(long long)r * n + e];
-    const double2 *vp = V + (long long)r * n + e;
-#pragma unroll 8
+  double nacc = 0.0;
+  if (MODE == 0) {
+#pragma unroll
+    for (int j = 0; j < kTileEPT; ++j) {
+      const long long e = t0 + j * kT + tid;
+      xw[j * kT + tid] = e < n ? wr[e] : make_double2(0.0, 0.0);
+    }
+  } else {
+    double2 x[kTileEPT];
+#pragma unroll
+    for (int j = 0; j < kTileEPT; ++j) {
+      const long long e = t0 + j * kT + tid;
+      x[j] = e < n ? wr[e] : make_double2(0.0, 0.0);
+    }
     for (int i = 0; i < k1; ++i) {
-      const double2 a = __ldg(vp);
-      x.x -= hv[i].x * a.x - hv[i].y * a.y;
-      x.y -= hv[i].x * a.y + hv[i].y * a.x;
-      vp += Rn;
+      const double2 hv = hs[i];
+      const double2 *vi = Vr + (long long)i * Rn;
+#pragma unroll
+      for (int j = 0; j < kTileEPT; ++j) {
+        const long long e = t0 + j * kT + tid;
+        if (e < n) {
+          const double2 a = __ldg(vi + e);
+          x[j].x -= hv.x * a.x - hv.y * a.y;
+          x[j].y -= hv.x * a.y + hv.y * a.x;
+        }
+      }
     }
-    w[(long long)r * n + e] = x;
-    acc = fma(x.x, x.x, acc);
-    acc = fma(x.y, x.y, acc);
+#pragma unroll
+    for (int j = 0; j < kTileEPT; ++j) {
+      const long long e = t0 + j * kT + tid;
+      if (e < n) wr[e] = x[j];
+      xw[j * kT + tid] = x[j];
+      nacc = fma(x[j].x, x[j].x, nacc);
+      nacc = fma(x[j].y, x[j].y, nacc);
+    }
   }
-  const double2 sres = block_reduce(make_double2(acc, 0.0), sh);
-  if (threadIdx.x == 0) part[(long long)r * nb + blockIdx.x] = sres.x;
+  if (MODE == 2) {
+    const double2 sres = block_reduce(make_double2(nacc, 0.0), shn);
+    if (tid == 0) npart[(long long)r * nb + blockIdx.x] = sres.x;
+    return;
+  }
+  __syncthreads();
+  const int lane = tid & 31, wid = tid >> 5;
+  const int units = k1 * (kTile / kChunk256);
+  for (int u = wid; u < units; u += kT / 32) {
+    const int i = u / (kTile / kChunk256), c = u % (kTile / kChunk256);
+    const double2 *vi = Vr + (long long)i * Rn;
+    double ax = 0.0, ay = 0.0;
+#pragma unroll
+    for (int q = 0; q < kChunk256 / 32; ++q) {
+      const int le = c * kChunk256 + q * 32 + lane;
+      const long long e = t0 + le;
+      if (e < n) {
+        const double2 a = __ldg(vi + e);
+        const double2 b = xw[le];
+        ax = fma(a.x, b.x, ax);
+        ax = fma(a.y, b.y, ax);
+        ay = fma(a.x, b.y, ay);
+        ay = fma(-a.y, b.x, ay);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ax += __shfl_down_sync(0xffffffffu, ax, o);
+      ay += __shfl_down_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&red[2 * i], ax);
+      atomicAdd(&red[2 * i + 1], ay);
+    }
+  }
+  __syncthreads();
+  if (tid < k1) part[((long long)r * k1 + tid) * nb + blockIdx.x] = make_double2(red[2 * tid], red[2 * tid + 1]);
 }
 
 // out[r * ldh + i] = sum_b part[(r * k1 + i) * nb + b]
@@ -290,24 +287,7 @@ __global__ void part_sum_kernel(const double2 *__restrict__ part, double2 *__res
   if (threadIdx.x == 0) out[(long long)r * ldh + i] = t;
 }
 
-int cgs_nb(long long n) {
-  long long g = (n + kT - 1) / kT;
-  if (g > 152LL * 8) g = 152LL * 8;
-  return (int)(g < 1 ? 1 : g);
-}
-
-template <int KMAX>
-void cgs2_t(const double2 *V, double2 *w, double2 *h1, double2 *h2, double2 *part, double *npart, double *nrm,
-            int k1, int R, long long n, int ldh, cudaStream_t s) {
-  const int nb = cgs_nb(n);
-  count_launches(6);
-  cgs_kernel<KMAX, 0><<<dim3(nb, R), kT, 0, s>>>(V, w, nullptr, part, k1, R, n, nb, ldh);
-  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h1, k1, nb, ldh);
-  cgs_kernel<KMAX, 1><<<dim3(nb, R), kT, 0, s>>>(V, w, h1, part, k1, R, n, nb, ldh);
-  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h2, k1, nb, ldh);
-  cgs_sub_norm_kernel<KMAX><<<dim3(nb, R), kT, 0, s>>>(V, w, h2, npart, k1, R, n, nb, ldh);
-  norm_final<<<R, kT, 0, s>>>(npart, nrm, nb);
-}
+int cgs_nb(long long n) { return (int)((n + kTile - 1) / kTile); }
 
 int blocks_for(long long n) {
   long long g = (n + kT - 1) / kT;
@@ -343,10 +323,15 @@ void gmres_norm(const double2 *w, double *part, double *out, int R, long long n,
 
 int gmres_cgs2(const double2 *V, double2 *w, double2 *h1, double2 *h2, double2 *part, double *npart, double *nrm,
                int k1, int R, long long n, int ldh, cudaStream_t s) {
-  if (k1 <= 8) cgs2_t<8>(V, w, h1, h2, part, npart, nrm, k1, R, n, ldh, s);
-  else if (k1 <= 16) cgs2_t<16>(V, w, h1, h2, part, npart, nrm, k1, R, n, ldh, s);
-  else if (k1 <= 32) cgs2_t<32>(V, w, h1, h2, part, npart, nrm, k1, R, n, ldh, s);
-  else return -1;
+  if (k1 < 1 || k1 > 64) return -1;
+  const int nb = cgs_nb(n);
+  count_launches(6);
+  cgs_tile_kernel<0><<<dim3(nb, R), kT, 0, s>>>(V, w, nullptr, part, nullptr, k1, R, n, nb, ldh);
+  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h1, k1, nb, ldh);
+  cgs_tile_kernel<1><<<dim3(nb, R), kT, 0, s>>>(V, w, h1, part, nullptr, k1, R, n, nb, ldh);
+  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h2, k1, nb, ldh);
+  cgs_tile_kernel<2><<<dim3(nb, R), kT, 0, s>>>(V, w, h2, nullptr, npart, k1, R, n, nb, ldh);
+  norm_final<<<R, kT, 0, s>>>(npart, nrm, nb);
   return 0;
 }
 

@@ -14,7 +14,7 @@ void gmres_maxpy(const double2 *V, const double2 *h, double2 *w, int k1, int R, 
 // out[r] = ||w[r]||_2
 void gmres_norm(const double2 *w, double *part, double *out, int R, long long n, cudaStream_t s);
 // Classical Gram-Schmidt applied twice against V_0..V_{k1-1} in three fused passes:
-// h1 = V^H w; w -= V h1 and h2 = V^H w; w -= V h2 and nrm = ||w||.  k1 <= 32.
+// h1 = V^H w; w -= V h1 and h2 = V^H w; w -= V h2 and nrm = ||w||.  k1 <= 64.
 // part: R * k1 * cgs2_partial_blocks(n) complex; npart: R * cgs2_partial_blocks(n).
 int gmres_cgs2(const double2 *V, double2 *w, double2 *h1, double2 *h2, double2 *part, double *npart, double *nrm,
                int k1, int R, long long n, int ldh, cudaStream_t s);

@@ -18,90 +18,82 @@
 namespace ie {
 namespace {
 
+// Element (row, col) of the 3 Nz x 3 Nz block from its packed storage, row = alpha Nz + a,
+// col = beta Nz + b: symmetric xx, yy, zz, xy from their upper triangles, xz and yz in
+// full, zx = -xz^T and zy = -yz^T (Lemma 1).
 template <typename T>
-__device__ __forceinline__ void unpack_block(const C<T> *__restrict__ q, C<T> *sm, int Nz, int ld, int tid,
-                                             int nthr) {
-  // sm holds 6 matrices [Nz][ld]: xx, yy, zz, xy (both triangles), xz, yz
-  const int P = Nz * (Nz + 1) / 2;
-  for (int e = tid; e < 4 * P; e += nthr) {
-    const int blk = e / P;
-    int p = e - blk * P;
-    // row a of the packed upper triangle starts at a*Nz - a(a-1)/2 and has Nz - a entries
-    int a = 0;
-    int rowlen = Nz;
-    while (p >= rowlen) { p -= rowlen; ++a; --rowlen; }
-    const int b = a + p;
-    const C<T> v = q[e];
-    C<T> *m = sm + (size_t)blk * Nz * ld;
-    m[a * ld + b] = v;
-    m[b * ld + a] = v;
+__device__ __forceinline__ C<T> block_entry(const C<T> *__restrict__ q, int Nz, int P, int row, int col) {
+  const int alpha = row / Nz, a = row - alpha * Nz;
+  const int beta = col / Nz, b = col - beta * Nz;
+  const bool full = (alpha == 2) != (beta == 2);  // xz / yz / zx / zy
+  if (!full) {
+    const int kind = alpha == beta ? alpha : 3;  // xx, yy, zz on the diagonal; xy off it
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return q[(size_t)kind * P + lo * Nz - lo * (lo - 1) / 2 + (hi - lo)];
   }
-  const C<T> *qf = q + 4 * P;
-  for (int e = tid; e < 2 * Nz * Nz; e += nthr) {
-    const int blk = e / (Nz * Nz);
-    const int r = e - blk * Nz * Nz;
-    const int a = r / Nz, b = r - a * Nz;
-    sm[(size_t)(4 + blk) * Nz * ld + a * ld + b] = qf[e];
-  }
+  if (beta == 2) return q[4 * (size_t)P + (size_t)alpha * Nz * Nz + a * Nz + b];
+  return cneg(q[4 * (size_t)P + (size_t)beta * Nz * Nz + b * Nz + a]);
 }
 
+// One CTA per folded wavenumber.  The mirror vectors (with their component signs) sit
+// in shared memory as X[MAXC][3 Nz]; the block streams through a panel of PW columns
+// [3 Nz][PW + 1] (PW = 3 Nz when the whole block fits three CTAs per SM; the odd row stride keeps the
+// per-thread row reads free of bank conflicts); thread t accumulates output row t over
+// all panels in registers.
 template <typename T, int MAXC>
 __global__ void contract_kernel(C<T> *__restrict__ spec, const C<T> *__restrict__ qf, int Nx, int Ny, int Nz,
-                                int R) {
-  extern __shared__ unsigned char smem_raw[];
-  const int ld = Nz + 1;
-  C<T> *blk = reinterpret_cast<C<T> *>(smem_raw);
-  C<T> *X = blk + (size_t)6 * Nz * ld;  // [MAXC][3 Nz]
+                                int R, int PW) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n3 = 3 * Nz;
+  C<T> *X = reinterpret_cast<C<T> *>(smem_raw);  // [MAXC][3 Nz]
+  C<T> *pan = X + (size_t)MAXC * n3;              // [3 Nz][PW + 1]
+  const int ldp = PW + 1;
   const int kxb = blockIdx.x, kyb = blockIdx.y;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int n3 = 3 * Nz;
   const int CZ = R * n3;
+  const int P = Nz * (Nz + 1) / 2;
   const long long BS = 2LL * Nz * (2 * Nz + 1);
   const C<T> *q = qf + ((long long)kyb * (Nx + 1) + kxb) * BS;
-  unpack_block<T>(q, blk, Nz, ld, tid, nthr);
 
-  // mirror wavenumbers and their component signs
-  int kxs[2], kys[2];
-  int nmx = 1, nmy = 1;
-  kxs[0] = kxb;
-  kys[0] = kyb;
-  if (kxb > 0 && kxb < Nx) { kxs[1] = 2 * Nx - kxb; nmx = 2; }
-  if (kyb > 0 && kyb < Ny) { kys[1] = 2 * Ny - kyb; nmy = 2; }
+  // mirror wavenumbers and their component signs (scalars: see the pipelined kernel)
+  const int nmx = (kxb > 0 && kxb < Nx) ? 2 : 1, nmy = (kyb > 0 && kyb < Ny) ? 2 : 1;
+  const int kx1 = 2 * Nx - kxb, ky1 = 2 * Ny - kyb;
   const int ncol = nmx * nmy * R;
   for (int e = tid; e < ncol * n3; e += nthr) {
     const int col = e / n3, row = e - col * n3;
     const int m = col / R, r = col - m * R;
     const int mx = m % nmx, my = m / nmx;
     const int comp = row / Nz;
-    const long long g = ((long long)kys[my] * 2 * Nx + kxs[mx]) * CZ + r * n3 + row;
+    const long long g = ((long long)(my ? ky1 : kyb) * 2 * Nx + (mx ? kx1 : kxb)) * CZ + r * n3 + row;
     C<T> v = spec[g];
     if ((comp == 0 && mx == 1) || (comp == 1 && my == 1)) v = cneg(v);
     X[col * n3 + row] = v;
   }
-  __syncthreads();
-  const C<T> *Axx = blk, *Ayy = blk + Nz * ld, *Azz = blk + 2 * Nz * ld, *Axy = blk + 3 * Nz * ld;
-  const C<T> *Axz = blk + 4 * Nz * ld, *Ayz = blk + 5 * Nz * ld;
-  for (int row = tid; row < n3; row += nthr) {
-    const int alpha = row / Nz, a = row - alpha * Nz;
-    C<T> acc[MAXC];
+  const int row = tid;
+  C<T> acc[MAXC];
 #pragma unroll
-    for (int c = 0; c < MAXC; ++c) acc[c] = mk<T>(0, 0);
-    for (int beta = 0; beta < 3; ++beta) {
-      for (int b = 0; b < Nz; ++b) {
-        C<T> m;
-        if (alpha == 0) {
-          m = beta == 0 ? Axx[b * ld + a] : (beta == 1 ? Axy[b * ld + a] : Axz[a * ld + b]);
-        } else if (alpha == 1) {
-          m = beta == 0 ? Axy[b * ld + a] : (beta == 1 ? Ayy[b * ld + a] : Ayz[a * ld + b]);
-        } else {
-          m = beta == 0 ? cneg(Axz[b * ld + a]) : (beta == 1 ? cneg(Ayz[b * ld + a]) : Azz[b * ld + a]);
-        }
-        const C<T> *xb = X + beta * Nz + b;
+  for (int c = 0; c < MAXC; ++c) acc[c] = mk<T>(0, 0);
+  for (int c0 = 0; c0 < n3; c0 += PW) {
+    const int w = n3 - c0 < PW ? n3 - c0 : PW;
+    __syncthreads();  // previous panel consumed (first pass: X staged)
+    for (int e = tid; e < n3 * w; e += nthr) {
+      const int rr = e / w, j = e - rr * w;
+      pan[rr * ldp + j] = block_entry<T>(q, Nz, P, rr, c0 + j);
+    }
+    __syncthreads();
+    if (row < n3) {
+      const C<T> *mrow = pan + (size_t)row * ldp;
+      for (int j = 0; j < w; ++j) {
+        const C<T> m = mrow[j];
+        const C<T> *xb = X + c0 + j;
 #pragma unroll
         for (int c = 0; c < MAXC; ++c)
           if (c < ncol) cfma(acc[c], m, xb[c * n3]);
       }
     }
+  }
+  if (row < n3) {
+    const int alpha = row / Nz;
 #pragma unroll
     for (int c = 0; c < MAXC; ++c) {
       if (c < ncol) {
@@ -109,22 +101,36 @@ __global__ void contract_kernel(C<T> *__restrict__ spec, const C<T> *__restrict_
         const int mx = mm % nmx, my = mm / nmx;
         C<T> v = acc[c];
         if ((alpha == 0 && mx == 1) || (alpha == 1 && my == 1)) v = cneg(v);
-        spec[((long long)kys[my] * 2 * Nx + kxs[mx]) * CZ + r * n3 + row] = v;
+        spec[((long long)(my ? ky1 : kyb) * 2 * Nx + (mx ? kx1 : kxb)) * CZ + r * n3 + row] = v;
       }
     }
   }
 }
 
+constexpr size_t kMaxSmem = 227 * 1024;
+
 template <typename T, int MAXC>
-void launch_t(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStream_t s) {
-  const size_t sm = sizeof(C<T>) * ((size_t)6 * Nz * (Nz + 1) + (size_t)MAXC * 3 * Nz);
+int launch_t(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStream_t s) {
+  const int n3 = 3 * Nz;
+  if (n3 > 1024) return -1;
+  const size_t e = sizeof(C<T>);
+  const size_t xb = e * (size_t)MAXC * n3;
+  // widest panel that leaves room for three CTAs per SM (one stages while the others
+  // compute); else the narrowest that fits at all
+  int PW = 16;
+  for (int cand : {n3, 64, 32, 16}) {
+    if (cand > n3) continue;
+    if (xb + e * (size_t)n3 * (cand + 1) <= kMaxSmem / 3) { PW = cand; break; }
+  }
+  const size_t sm = xb + e * (size_t)n3 * (PW + 1);
+  if (sm > kMaxSmem) return -1;
   auto k = contract_kernel<T, MAXC>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  int threads = ((3 * Nz + 31) / 32) * 32;
-  if (threads > 512) threads = 512;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
+  const int threads = ((n3 + 31) / 32) * 32;
   dim3 grid(Nx + 1, Ny + 1);
   count_launches(1);
-  k<<<grid, threads, sm, s>>>(spec, qf, Nx, Ny, Nz, R);
+  k<<<grid, threads, sm, s>>>(spec, qf, Nx, Ny, Nz, R, PW);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 __device__ int g_contract_err = 0;
@@ -141,7 +147,7 @@ int num_sms() {
 }
 
 template <int NZ, int R, int NS>
-bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, cudaStream_t s) {
+bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int per_sm, cudaStream_t s) {
   using Cfg = ContractCfg<NZ, R, NS>;
   if (Cfg::SMEM > 227 * 1024) return false;
   auto k = contract_tma_kernel<NZ, R, NS>;
@@ -152,17 +158,24 @@ bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, cudaStream_t s) {
   int *err = nullptr;
   cudaGetSymbolAddress((void **)&err, g_contract_err);
   const int nf = (Nx + 1) * (Ny + 1);
-  const int grid = nf < num_sms() ? nf : num_sms();
+  const int want = per_sm * num_sms();
+  const int grid = nf < want ? nf : want;
   count_launches(1);
   k<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(spec, qf, Nx, Ny, err);
+  if (cudaPeekAtLastError() != cudaSuccess) {  // not launched: the caller falls back to the panel kernel
+    cudaGetLastError();
+    return false;
+  }
   return true;
 }
 
+// One ring slot per CTA and two CTAs per SM where they fit (the copy of the next
+// wavenumber overlaps the arithmetic of the current one, and the other CTA on the
+// SM covers the unpacking phase); otherwise one CTA per SM.
 template <int NZ, int R>
 bool try_tma_stages(float2 *spec, const float2 *qf, int Nx, int Ny, cudaStream_t s) {
-  if (ContractCfg<NZ, R, 3>::SMEM <= 227 * 1024) return try_tma<NZ, R, 3>(spec, qf, Nx, Ny, s);
-  if (ContractCfg<NZ, R, 2>::SMEM <= 227 * 1024) return try_tma<NZ, R, 2>(spec, qf, Nx, Ny, s);
-  return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, s);
+  if (2 * ContractCfg<NZ, R, 1>::SMEM <= 227 * 1024) return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, 2, s);
+  return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, 1, s);
 }
 
 template <int R>
@@ -187,10 +200,6 @@ int contract_take_error() {
   return h;
 }
 
-size_t contract_smem_bytes(int Nz, int R, size_t elem) {
-  return elem * ((size_t)6 * Nz * (Nz + 1) + (size_t)4 * R * 3 * Nz);
-}
-
 template <typename T>
 int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
@@ -199,11 +208,10 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, c
       if (R == 2 && dispatch_tma<2>(spec, qf, Nx, Ny, Nz, s)) return 0;
     }
   }
-  if (R <= 1) launch_t<T, 4>(spec, qf, Nx, Ny, Nz, R, s);
-  else if (R <= 2) launch_t<T, 8>(spec, qf, Nx, Ny, Nz, R, s);
-  else if (R <= 4) launch_t<T, 16>(spec, qf, Nx, Ny, Nz, R, s);
-  else return -1;
-  return 0;
+  if (R <= 1) return launch_t<T, 4>(spec, qf, Nx, Ny, Nz, R, s);
+  if (R <= 2) return launch_t<T, 8>(spec, qf, Nx, Ny, Nz, R, s);
+  if (R <= 4) return launch_t<T, 16>(spec, qf, Nx, Ny, Nz, R, s);
+  return -1;
 }
 
 template int launch_contract<float>(float2 *, const float2 *, int, int, int, int, cudaStream_t);

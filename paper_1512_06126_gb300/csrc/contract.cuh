@@ -4,7 +4,7 @@
 namespace ie {
 
 // Apply the folded spectral blocks in place to spec[2Ny][2Nx][R * 3Nz].
-// Returns -1 if R > 4.
+// Returns -1 if R > 4, 3 Nz > 1024 or a launch fails (nothing is applied then).
 template <typename T>
 int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStream_t s);
 
@@ -12,8 +12,5 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, c
 extern bool contract_tma_enabled;
 // Error code recorded by a contraction kernel since the last call (0: none); resets it.
 int contract_take_error();
-
-// Shared memory needed by the contraction CTA.
-size_t contract_smem_bytes(int Nz, int R, size_t elem);
 
 }  // namespace ie

@@ -57,6 +57,19 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 
 }  // namespace tma
 
+// Packed two-lane FP32 FMA of sm_100+ (fma.rn.f32x2): one instruction, two FMAs.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long pk(float lo, float hi) {
+  return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float2 upk(unsigned long long v) {
+  return make_float2(__uint_as_float((unsigned)(v & 0xffffffffu)), __uint_as_float((unsigned)(v >> 32)));
+}
+
 constexpr long long kWaitLimit = 1LL << 28;  // polls before a wait is declared failed
 enum ContractError { kContractOk = 0, kContractTimeout = 1 };
 
@@ -80,10 +93,30 @@ struct ContractCfg {
   static constexpr size_t OFF_BLK = OFF_XRAW + NSTAGE * XRAW_BYTES;
   static constexpr size_t BLK_BYTES = (size_t)6 * NZ * LD * 8;
   static constexpr size_t OFF_XS = OFF_BLK + BLK_BYTES;
-  static constexpr size_t XS_BYTES = (size_t)N3 * MAXC * 8;
+  static constexpr size_t XS_BYTES = (size_t)2 * N3 * MAXC * 8;  // X and X with re/im swapped
   static constexpr size_t OFF_TRI = OFF_XS + XS_BYTES;
   static constexpr size_t SMEM = OFF_TRI + (size_t)P * 4;
 };
+
+// Folded wavenumber w = ky_bar (Nx + 1) + kx_bar and its mirrors 2 Nx - kx_bar,
+// 2 Ny - ky_bar (present for 0 < k_bar < N).  Kept in scalars: indexing small
+// per-thread arrays by a run-time mirror number would place them in local memory.
+struct Mirrors {
+  int kx0, kx1, ky0, ky1, nmx, nmy;
+  __device__ __forceinline__ size_t pos(int mx, int my, int Nx) const {
+    return (size_t)(my ? ky1 : ky0) * 2 * Nx + (mx ? kx1 : kx0);
+  }
+};
+__device__ __forceinline__ Mirrors mirrors_of(int w, int Nx, int Ny) {
+  Mirrors m;
+  m.kx0 = w % (Nx + 1);
+  m.ky0 = w / (Nx + 1);
+  m.nmx = (m.kx0 > 0 && m.kx0 < Nx) ? 2 : 1;
+  m.nmy = (m.ky0 > 0 && m.ky0 < Ny) ? 2 : 1;
+  m.kx1 = 2 * Nx - m.kx0;
+  m.ky1 = 2 * Ny - m.ky0;
+  return m;
+}
 
 template <int NZ, int R, int NSTAGE>
 __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
@@ -112,24 +145,18 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
   }
   __syncthreads();
 
-  auto mirrors = [&](int w, int *kxs, int *kys, int &nmx, int &nmy) {
-    const int kxb = w % (Nx + 1), kyb = w / (Nx + 1);
-    kxs[0] = kxb; kys[0] = kyb; nmx = 1; nmy = 1;
-    if (kxb > 0 && kxb < Nx) { kxs[1] = 2 * Nx - kxb; nmx = 2; }
-    if (kyb > 0 && kyb < Ny) { kys[1] = 2 * Ny - kyb; nmy = 2; }
-  };
   // thread 0: issue the copies of wavenumber w into slot s
   auto issue = [&](int w, int s) {
-    int kxs[2], kys[2], nmx, nmy;
-    mirrors(w, kxs, kys, nmx, nmy);
-    const uint32_t bytes = (uint32_t)(Cfg::RAW_BYTES + (size_t)nmx * nmy * CZ * 8);
+    const Mirrors mi = mirrors_of(w, Nx, Ny);
+    const int nm = mi.nmx * mi.nmy;
+    const uint32_t bytes = (uint32_t)(Cfg::RAW_BYTES + (size_t)nm * CZ * 8);
     tma::fence_proxy_async();
     tma::mbar_expect_tx(&bar[s], bytes);
     tma::bulk_g2s(raw + (size_t)s * BS, qf + (size_t)w * BS, (uint32_t)Cfg::RAW_BYTES, &bar[s]);
-    for (int m = 0; m < nmx * nmy; ++m) {
-      const int mx = m % nmx, my = m / nmx;
-      const size_t g = ((size_t)kys[my] * 2 * Nx + kxs[mx]) * CZ;
-      tma::bulk_g2s(xraw + (size_t)s * 4 * CZ + (size_t)m * CZ, spec + g, (uint32_t)(CZ * 8), &bar[s]);
+    for (int m = 0; m < nm; ++m) {
+      const int mx = m % mi.nmx, my = m / mi.nmx;
+      tma::bulk_g2s(xraw + (size_t)s * 4 * CZ + (size_t)m * CZ, spec + mi.pos(mx, my, Nx) * CZ, (uint32_t)(CZ * 8),
+                    &bar[s]);
     }
   };
 
@@ -173,9 +200,9 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
       for (int k = 0; k < NSTAGE; ++k) tma::mbar_wait_bounded(&bar[(s + k) % NSTAGE], phase, kWaitLimit);
       return;
     }
-    int kxs[2], kys[2], nmx, nmy;
-    mirrors(w, kxs, kys, nmx, nmy);
-    const int ncol = nmx * nmy * R;
+    const Mirrors mw = mirrors_of(w, Nx, Ny);
+    const int nmx = mw.nmx;
+    const int ncol = mw.nmx * mw.nmy * R;
     // unpack the packed block of slot s
     const float2 *q = raw + (size_t)s * BS;
     for (int e = tid; e < 4 * P; e += Cfg::THREADS) {
@@ -206,6 +233,7 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
         if ((comp == 0 && mx == 1) || (comp == 1 && my == 1)) { v.x = -v.x; v.y = -v.y; }
       }
       xs[k * MAXC + col] = v;
+      xs[N3 * MAXC + k * MAXC + col] = make_float2(v.y, v.x);
     }
     __syncthreads();
     // slot s is consumed: refill it with wavenumber w + NSTAGE * gridDim.x
@@ -214,37 +242,39 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
       if (wn < nf) issue(wn, s);
     }
     if (cg * CPT < ncol) {
-      float2 acc[CPT];
+      // complex MAC acc += m x as two packed FMAs: (re, im) += (mr, mr)(xr, xi) and
+      // (re, im) += (-mi, mi)(xi, xr)
+      unsigned long long acc[CPT];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) acc[c] = make_float2(0.f, 0.f);
+      for (int c = 0; c < CPT; ++c) acc[c] = 0ull;
 #pragma unroll
       for (int beta = 0; beta < 3; ++beta) {
-        float2 tmp[CPT];
+        unsigned long long tmp[CPT];
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) tmp[c] = make_float2(0.f, 0.f);
+        for (int c = 0; c < CPT; ++c) tmp[c] = 0ull;
         const float2 *mp = bp[beta];
         const int st = bs[beta];
-        const float4 *xp = reinterpret_cast<const float4 *>(xs + (size_t)beta * NZ * MAXC + cg * CPT);
+        const ulonglong2 *xp = reinterpret_cast<const ulonglong2 *>(xs + (size_t)beta * NZ * MAXC + cg * CPT);
+        const ulonglong2 *xq = reinterpret_cast<const ulonglong2 *>(xs + (size_t)N3 * MAXC + (size_t)beta * NZ * MAXC +
+                                                                    cg * CPT);
 #pragma unroll 8
         for (int b = 0; b < NZ; ++b) {
           const float2 m = mp[b * st];
-          const float4 x01 = xp[b * (MAXC / 2)];
-          const float4 x23 = xp[b * (MAXC / 2) + 1];
-          const float2 xv[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w), make_float2(x23.x, x23.y),
-                                make_float2(x23.z, x23.w)};
-#pragma unroll
-          for (int c = 0; c < CPT; ++c) {
-            tmp[c].x = fmaf(m.x, xv[c].x, tmp[c].x);
-            tmp[c].x = fmaf(-m.y, xv[c].y, tmp[c].x);
-            tmp[c].y = fmaf(m.x, xv[c].y, tmp[c].y);
-            tmp[c].y = fmaf(m.y, xv[c].x, tmp[c].y);
-          }
+          const unsigned long long mr = pk(m.x, m.x), mi = pk(-m.y, m.y);
+          const ulonglong2 x01 = xp[b * (MAXC / 2)], x23 = xp[b * (MAXC / 2) + 1];
+          const ulonglong2 y01 = xq[b * (MAXC / 2)], y23 = xq[b * (MAXC / 2) + 1];
+          tmp[0] = ffma2(mr, x01.x, tmp[0]);
+          tmp[1] = ffma2(mr, x01.y, tmp[1]);
+          tmp[2] = ffma2(mr, x23.x, tmp[2]);
+          tmp[3] = ffma2(mr, x23.y, tmp[3]);
+          tmp[0] = ffma2(mi, y01.x, tmp[0]);
+          tmp[1] = ffma2(mi, y01.y, tmp[1]);
+          tmp[2] = ffma2(mi, y23.x, tmp[2]);
+          tmp[3] = ffma2(mi, y23.y, tmp[3]);
         }
+        const unsigned long long sgp = pk(sg[beta], sg[beta]);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-          acc[c].x = fmaf(sg[beta], tmp[c].x, acc[c].x);
-          acc[c].y = fmaf(sg[beta], tmp[c].y, acc[c].y);
-        }
+        for (int c = 0; c < CPT; ++c) acc[c] = ffma2(sgp, tmp[c], acc[c]);
       }
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
@@ -252,9 +282,9 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
         if (col < ncol) {
           const int m = col / R, r = col - m * R;
           const int mx = m % nmx, my = m / nmx;
-          float2 v = acc[c];
+          float2 v = upk(acc[c]);
           if ((alpha == 0 && mx == 1) || (alpha == 1 && my == 1)) { v.x = -v.x; v.y = -v.y; }
-          spec[((size_t)kys[my] * 2 * Nx + kxs[mx]) * CZ + r * N3 + row] = v;
+          spec[mw.pos(mx, my, Nx) * CZ + r * N3 + row] = v;
         }
       }
     }

@@ -61,9 +61,15 @@ __global__ void __launch_bounds__(kThreads) fft_axis_kernel(const C<T> *__restri
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) fft_rows_fwd_kernel(const C<T> *__restrict__ x,
-                                                                const C<T> *__restrict__ in_scale,
+template <typename T, typename TX>
+__device__ __forceinline__ C<T> to_t(C<TX> v) {
+  return mk<T>((T)v.x, (T)v.y);
+}
+
+// T: arithmetic type of the transform; TX: element type of the vectors and scales.
+template <typename T, typename TX>
+__global__ void __launch_bounds__(kThreads) fft_rows_fwd_kernel(const C<TX> *__restrict__ x,
+                                                                const C<TX> *__restrict__ in_scale,
                                                                 C<T> *__restrict__ t1, int CZ, int Nz, int Ny,
                                                                 int Nx, FftPlan plan) {
   extern __shared__ unsigned char smem_raw[];
@@ -82,8 +88,9 @@ __global__ void __launch_bounds__(kThreads) fft_rows_fwd_kernel(const C<T> *__re
     const int cz = cz0 + t;
     C<T> v = mk<T>(0, 0);
     if (cz < CZ) {
-      v = x[((long long)cz * Ny + y) * Nx + xx];
-      if (in_scale) v = cmul(v, in_scale[((long long)(cz % Nz) * Ny + y) * Nx + xx]);
+      C<TX> u = x[((long long)cz * Ny + y) * Nx + xx];
+      if (in_scale) u = cmul(u, in_scale[((long long)(cz % Nz) * Ny + y) * Nx + xx]);
+      v = to_t<T, TX>(u);
     }
     A[xx * LD + t] = v;
   }
@@ -99,12 +106,12 @@ __global__ void __launch_bounds__(kThreads) fft_rows_fwd_kernel(const C<T> *__re
   }
 }
 
-template <typename T>
+template <typename T, typename TX>
 __global__ void __launch_bounds__(kThreads) fft_rows_inv_kernel(const C<T> *__restrict__ t1,
-                                                                const C<T> *__restrict__ x,
-                                                                const C<T> *__restrict__ diag,
-                                                                const C<T> *__restrict__ out_scale,
-                                                                C<T> *__restrict__ y_out, int CZ, int Nz, int Ny,
+                                                                const C<TX> *__restrict__ x,
+                                                                const C<TX> *__restrict__ diag,
+                                                                const C<TX> *__restrict__ out_scale,
+                                                                C<TX> *__restrict__ y_out, int CZ, int Nz, int Ny,
                                                                 int Nx, FftPlan plan) {
   extern __shared__ unsigned char smem_raw[];
   constexpr int TI = fft_ti<T>();
@@ -131,7 +138,8 @@ __global__ void __launch_bounds__(kThreads) fft_rows_inv_kernel(const C<T> *__re
     if (cz < CZ) {
       const long long cell = ((long long)(cz % Nz) * Ny + y) * Nx + xx;
       const long long gi = ((long long)cz * Ny + y) * Nx + xx;
-      C<T> v = cmul(res[xx * LD + t], out_scale[cell]);
+      const C<T> r = res[xx * LD + t];
+      C<TX> v = cmul(mk<TX>((TX)r.x, (TX)r.y), out_scale[cell]);
       if (diag) cfma(v, diag[cell], x[gi]);
       y_out[gi] = v;
     }
@@ -161,24 +169,24 @@ void launch_fft_axis(const C<T> *in, C<T> *out, int outer, int Lin, int Lout, lo
   k<<<grid, kThreads, sm, s>>>(in, out, Lin, Lout, inner, plan, scale);
 }
 
-template <typename T>
-void launch_fft_rows_fwd(const C<T> *x, const C<T> *in_scale, C<T> *t1, int CZ, int Nz, int Ny, int Nx,
+template <typename T, typename TX>
+void launch_fft_rows_fwd(const C<TX> *x, const C<TX> *in_scale, C<T> *t1, int CZ, int Nz, int Ny, int Nx,
                          const FftPlan &plan, cudaStream_t s) {
   constexpr int TI = fft_ti<T>();
   const size_t sm = rows_smem<T>(plan.L);
-  auto k = fft_rows_fwd_kernel<T>;
+  auto k = fft_rows_fwd_kernel<T, TX>;
   set_smem(k, sm);
   dim3 grid((unsigned)((CZ + TI - 1) / TI), (unsigned)Ny);
   count_launches(1);
   k<<<grid, kThreads, sm, s>>>(x, in_scale, t1, CZ, Nz, Ny, Nx, plan);
 }
 
-template <typename T>
-void launch_fft_rows_inv(const C<T> *t1, const C<T> *x, const C<T> *diag, const C<T> *out_scale, C<T> *y,
+template <typename T, typename TX>
+void launch_fft_rows_inv(const C<T> *t1, const C<TX> *x, const C<TX> *diag, const C<TX> *out_scale, C<TX> *y,
                          int CZ, int Nz, int Ny, int Nx, const FftPlan &plan, cudaStream_t s) {
   constexpr int TI = fft_ti<T>();
   const size_t sm = rows_smem<T>(plan.L);
-  auto k = fft_rows_inv_kernel<T>;
+  auto k = fft_rows_inv_kernel<T, TX>;
   set_smem(k, sm);
   dim3 grid((unsigned)((CZ + TI - 1) / TI), (unsigned)Ny);
   count_launches(1);
@@ -193,13 +201,18 @@ template void launch_fft_axis<double, false>(const double2 *, double2 *, int, in
                                              const FftPlan &, double, cudaStream_t);
 template void launch_fft_axis<double, true>(const double2 *, double2 *, int, int, int, long long, const FftPlan &,
                                             double, cudaStream_t);
-template void launch_fft_rows_fwd<float>(const float2 *, const float2 *, float2 *, int, int, int, int,
-                                         const FftPlan &, cudaStream_t);
-template void launch_fft_rows_fwd<double>(const double2 *, const double2 *, double2 *, int, int, int, int,
-                                          const FftPlan &, cudaStream_t);
-template void launch_fft_rows_inv<float>(const float2 *, const float2 *, const float2 *, const float2 *, float2 *,
-                                         int, int, int, int, const FftPlan &, cudaStream_t);
-template void launch_fft_rows_inv<double>(const double2 *, const double2 *, const double2 *, const double2 *,
-                                          double2 *, int, int, int, int, const FftPlan &, cudaStream_t);
+template void launch_fft_rows_fwd<float, float>(const float2 *, const float2 *, float2 *, int, int, int, int,
+                                                const FftPlan &, cudaStream_t);
+template void launch_fft_rows_fwd<double, double>(const double2 *, const double2 *, double2 *, int, int, int, int,
+                                                  const FftPlan &, cudaStream_t);
+template void launch_fft_rows_fwd<float, double>(const double2 *, const double2 *, float2 *, int, int, int, int,
+                                                 const FftPlan &, cudaStream_t);
+template void launch_fft_rows_inv<float, float>(const float2 *, const float2 *, const float2 *, const float2 *,
+                                                float2 *, int, int, int, int, const FftPlan &, cudaStream_t);
+template void launch_fft_rows_inv<double, double>(const double2 *, const double2 *, const double2 *,
+                                                  const double2 *, double2 *, int, int, int, int, const FftPlan &,
+                                                  cudaStream_t);
+template void launch_fft_rows_inv<float, double>(const float2 *, const double2 *, const double2 *, const double2 *,
+                                                 double2 *, int, int, int, int, const FftPlan &, cudaStream_t);
 
 }  // namespace ie

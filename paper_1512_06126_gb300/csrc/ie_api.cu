@@ -227,7 +227,7 @@ ie_status apply(ie_ctx *c, int inst, const ie::C<T> *x, ie::C<T> *y, int R, int 
     cudaEventCreate(&eb);
     cudaEventRecord(ea, s);
   }
-  if (ie::launch_contract<T>(spec, qf<T>(c->inst[inst]), Nx, Ny, Nz, R, s) != 0) return IE_ERR_ARG;
+  if (ie::launch_contract<T>(spec, qf<T>(c->inst[inst]), Nx, Ny, Nz, R, s) != 0) return IE_ERR_CUDA;
   if (c->prof) {
     cudaEventRecord(eb, s);
     c->prof_rec.push_back({ea, eb, sizeof(T) == 8 ? IE_C128 : IE_C64});
@@ -237,19 +237,44 @@ ie_status apply(ie_ctx *c, int inst, const ie::C<T> *x, ie::C<T> *y, int R, int 
   return cuda_status(cudaGetLastError());
 }
 
-// FP64-level operator used by the Krylov solver: c128 product, or c64 product with casts.
+// c64 product on FP64 vectors: the row passes read and write FP64 (rounding the scaled
+// input to FP32 on load; the diagonal term and the output in FP64), the FFTs and the
+// contraction run in FP32.
+ie_status apply_mixed(ie_ctx *c, int inst, const double2 *x, double2 *y, int R, int transpose, cudaStream_t s) {
+  const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
+  const int CZ = R * 3 * Nz;
+  const DiagSet &D = c->d64;
+  const double2 *in_s = (const double2 *)(transpose ? D.in_t : D.in_f);
+  const double2 *out_s = (const double2 *)(transpose ? D.out_t : D.out_f);
+  float2 *t1 = (float2 *)c->t1;
+  float2 *spec = (float2 *)c->spec;
+  ie::launch_fft_rows_fwd<float, double>(x, in_s, t1, CZ, Nz, Ny, Nx, c->px, s);
+  ie::launch_fft_axis<float, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (c->prof) {
+    cudaEventCreate(&ea);
+    cudaEventCreate(&eb);
+    cudaEventRecord(ea, s);
+  }
+  if (ie::launch_contract<float>(spec, c->inst[inst].q32, Nx, Ny, Nz, R, s) != 0) return IE_ERR_CUDA;
+  if (c->prof) {
+    cudaEventRecord(eb, s);
+    c->prof_rec.push_back({ea, eb, IE_C64});
+  }
+  ie::launch_fft_axis<float, true>(spec, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
+  ie::launch_fft_rows_inv<float, double>(t1, x, (const double2 *)D.diag, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
+  return cuda_status(cudaGetLastError());
+}
+
+// FP64-level operator used by the Krylov solver: c128 product, or the c64 product.
 struct Op {
   ie_ctx *c;
   int inst;
   int transpose;
   bool single;
   ie_status operator()(const double2 *x, double2 *y, int R) const {
-    const long long n = (long long)R * c->nvec();
     if (!single) return apply<double>(c, inst, x, y, R, transpose, c->stream);
-    ie::launch_cast64to32(x, c->x32, n, c->stream);
-    IE_TRY(apply<float>(c, inst, c->x32, c->y32, R, transpose, c->stream));
-    ie::launch_cast32to64(c->y32, y, n, c->stream);
-    return cuda_status(cudaGetLastError());
+    return apply_mixed(c, inst, x, y, R, transpose, c->stream);
   }
 };
 
@@ -580,6 +605,7 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
   cudaEvent_t ev[6];
   for (auto &e : ev) IE_CUDA(cudaEventCreate(&e));
   double acc[5] = {0, 0, 0, 0, 0};
+  int bad = 0;
   for (int it = 0; it < n_iter; ++it) {
     if (dtype == IE_C128) {
       const double2 *x = c->w;
@@ -589,7 +615,7 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
       cudaEventRecord(ev[1], s);
       ie::launch_fft_axis<double, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0, s);
       cudaEventRecord(ev[2], s);
-      ie::launch_contract<double>(sp, c->inst[inst].q64, Nx, Ny, Nz, nrhs, s);
+      bad |= ie::launch_contract<double>(sp, c->inst[inst].q64, Nx, Ny, Nz, nrhs, s);
       cudaEventRecord(ev[3], s);
       ie::launch_fft_axis<double, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0, s);
       cudaEventRecord(ev[4], s);
@@ -604,7 +630,7 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
       cudaEventRecord(ev[1], s);
       ie::launch_fft_axis<float, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[2], s);
-      ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, s);
+      bad |= ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, s);
       cudaEventRecord(ev[3], s);
       ie::launch_fft_axis<float, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[4], s);
@@ -621,7 +647,8 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
   }
   for (auto &e : ev) cudaEventDestroy(e);
   for (int k = 0; k < 5; ++k) ms_out[k] = acc[k] / n_iter;
-  return cuda_status(cudaGetLastError());
+  const ie_status st = cuda_status(cudaGetLastError());
+  return bad ? IE_ERR_CUDA : st;
 }
 long long ie_ctx_device_bytes(ie_ctx *c) { return c ? c->dev_bytes : 0; }
 
@@ -682,7 +709,7 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   IE_TRY(dalloc(c, &c->w, nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->r, nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->dx, nv * sizeof(double2)));
-  if (c->restart > 31) return IE_ERR_ARG;
+  if (c->restart > 63) return IE_ERR_ARG;
   const long long nbp = std::max<long long>(ie::mdot_nb(c->nvec()), ie::cgs2_partial_blocks(c->nvec()));
   IE_TRY(dalloc(c, &c->part, (size_t)max_rhs * (c->restart + 1) * nbp * sizeof(double2)));
   IE_TRY(dalloc(c, &c->hdev, (size_t)3 * max_rhs * (c->restart + 1) * sizeof(double2)));

@@ -179,3 +179,65 @@ def test_c64_pipelined_contraction_against_c128(shape):
             ref = O.fft_apply(m0, qt, x[r].astype(np.complex64).astype(np.complex128))
             assert rel(y[r], ref) <= 2e-5, (shape, R, r, rel(y[r], ref))
     ctx.close()
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 32), (24, 20, 16), (20, 16, 24), (12, 10, 48)])
+def test_c64_pipelined_contraction_generated_coefficients(shape):
+    """The pipelined c64 contraction on coefficients from the device generator (the
+    physical tensor, with its large self terms) against the c128 path, and two calls
+    in a row bit-identical: a wrong or racy store in one row of one wavenumber shows
+    here even where it hides under random coefficients.  FP32 bound: the contraction
+    sums 3 Nz products and each FFT pass adds O(eps32 log N); 2e-6 leaves a margin of
+    ~40x over the measured ~4e-8."""
+    need_gpu()
+    nx, ny, nz = shape
+    m0 = W.small_model(nx=nx, ny=ny, nz=nz, seed=3, freq=1.0)
+    g = m0.grid
+    from paper_1512_06126_gb300 import build, ie
+    build.build()
+    ctx = ie.Context(g, m0.layers, m0.sigma_a, m0.freqs[:1], None, max_rhs=2)
+    s = torch.cuda.current_stream().cuda_stream
+    for R in (1, 2):
+        x = W.random_field((R, 3, nz, ny, nx), 40 + R)
+        x128 = to_dev(x.astype(np.complex64).astype(np.complex128), torch.complex128)
+        y128 = torch.empty_like(x128)
+        ctx.matvec(0, x128.data_ptr(), y128.data_ptr(), R, dtype=1, stream=s)
+        x64 = x128.to(torch.complex64)
+        y1 = torch.empty_like(x64)
+        y2 = torch.empty_like(x64)
+        ctx.matvec(0, x64.data_ptr(), y1.data_ptr(), R, dtype=0, stream=s)
+        ctx.matvec(0, x64.data_ptr(), y2.data_ptr(), R, dtype=0, stream=s)
+        torch.cuda.synchronize()
+        assert torch.equal(y1, y2), (shape, R, float((y1 - y2).abs().max()))
+        err = float((y1.to(torch.complex128) - y128).norm() / y128.norm())
+        assert err <= 2e-6, (shape, R, err)
+    ctx.close()
+
+
+@pytest.mark.parametrize("shape", [(12, 10, 48), (8, 6, 64)])
+def test_large_nz_contraction_against_oracle(shape):
+    """Nz whose full 3 Nz x 3 Nz c128 block does not fit in shared memory: the
+    panel-staged contraction (c128 always; c64 for R > 2 or Nz outside the pipelined
+    set) against the oracle's FFT apply, R = 1..3."""
+    need_gpu()
+    nx, ny, nz = shape
+    m0 = W.small_model(nx=nx, ny=ny, nz=nz, seed=5, freq=1.0)
+    q = W.random_compressed_q(ny, nx, nz, seed=33)
+    ctx = lib_context(m0, [q], max_rhs=3)
+    qt = O.full_spectrum_blocks(O.embed_spectrum(q))
+    x = W.random_field((3, 3, nz, ny, nx), 61)
+    for R in (1, 2, 3):
+        xd = to_dev(x[:R])
+        yd = torch.empty_like(xd)
+        ctx.matvec(0, xd.data_ptr(), yd.data_ptr(), R, dtype=1, stream=torch.cuda.current_stream().cuda_stream)
+        y = to_host(yd)
+        x32 = to_dev(x[:R], torch.complex64)
+        y32d = torch.empty_like(x32)
+        ctx.matvec(0, x32.data_ptr(), y32d.data_ptr(), R, dtype=0, stream=torch.cuda.current_stream().cuda_stream)
+        y32 = to_host(y32d).astype(np.complex128)
+        for r in range(R):
+            ref = O.fft_apply(m0, qt, x[r])
+            assert rel(y[r], ref) <= 1e-12, (shape, R, r, rel(y[r], ref))
+            ref32 = O.fft_apply(m0, qt, x[r].astype(np.complex64).astype(np.complex128))
+            assert rel(y32[r], ref32) <= 2e-5, (shape, R, r, rel(y32[r], ref32))
+    ctx.close()
