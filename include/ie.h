@@ -50,7 +50,8 @@ typedef enum {
   IE_ERR_GEOMETRY = -2,  /* a cell straddles a layer interface, or Re sigma_b <= 0 in the domain */
   IE_ERR_COEFF = -3,     /* coefficient tensor missing or inconsistent */
   IE_ERR_OOM = -4,       /* device allocation failed */
-  IE_ERR_CUDA = -5       /* a CUDA call failed */
+  IE_ERR_CUDA = -5,      /* a CUDA call failed */
+  IE_ERR_SCRATCH = -6    /* the problem needs more work space than ie_matvec_noalloc's fixed array */
 } ie_status;
 
 enum { IE_C64 = 0, IE_C128 = 1 };                 /* element type of matvec vectors */
@@ -103,6 +104,31 @@ typedef struct {
 ie_status ie_setup(const ie_grid *grid, const ie_layers *layers, const double *sigma_a_host, int n_freq,
                    const double *freq_host, const double *q_real_host, int max_rhs, const ie_options *opt,
                    ie_ctx **out);
+
+/* Allocation-free c64 product y = A x for callers that cannot allocate device memory
+ * (an allocator-free host policy, or a plug-in restricted to the buffers it is given):
+ * no context, no cudaMalloc/cudaFree, no allocating library call.  The paper has no
+ * counterpart; it is the same five kernels as ie_matvec with their two FFT work arrays
+ * placed in one fixed device array of 64 MiB that the library reserves on every GPU
+ * that loads it, for the life of the process.
+ *   qf_dev        : folded spectral coefficients, c64 [(Ny+1)(Nx+1)][2Nz(2Nz+1)]: for
+ *                   kx in [0, Nx], ky in [0, Ny] the DFT of the 2N-periodic embedding of
+ *                   Q, blocks xx, yy, zz, xy as packed upper triangles (row-major, a <= b)
+ *                   then xz, yz in full (the layout ie_setup builds internally).
+ *   in_scale_dev  : c64 per cell [Nz][Ny][Nx], R2 = s gamma (forward product).
+ *   out_scale_dev : c64 per cell, R1 / (4 Nx Ny) = -2 s / (V 4 Nx Ny).
+ *   diag_dev      : c64 per cell, S = 1 - gamma (may be NULL for y = R1 B R2 x).
+ *   x_dev, y_dev  : c64 [nrhs][3][Nz][Ny][Nx], must not alias; nrhs 1..4.
+ * The work space needs (6 Nx Ny) * nrhs * 3 Nz * 8 bytes; larger problems return
+ * IE_ERR_SCRATCH.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call outside any stream capture.  All calls
+ * share the array: calls whose kernels overlap on the GPU (two streams, two threads)
+ * race on it and must be serialised by the caller.  Nothing in the array needs to
+ * start at zero (each call writes everything it reads).  Asynchronous on stream
+ * (a cudaStream_t, NULL for the legacy default stream). */
+ie_status ie_matvec_noalloc(int nx, int ny, int nz, int nrhs, const void *qf_dev, const void *in_scale_dev,
+                            const void *out_scale_dev, const void *diag_dev, const void *x_dev, void *y_dev,
+                            void *stream);
 
 /* Generate the compressed real-space coefficient tensor of one frequency on the device
  * (Appendices A-C): the vertical integrals (Ver_Int) of the layered-medium fundamental

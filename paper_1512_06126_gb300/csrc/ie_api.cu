@@ -529,6 +529,7 @@ const char *ie_status_str(ie_status s) {
     case IE_ERR_COEFF: return "invalid coefficient tensor";
     case IE_ERR_OOM: return "out of device memory";
     case IE_ERR_CUDA: return "CUDA error";
+    case IE_ERR_SCRATCH: return "problem larger than the fixed work space of ie_matvec_noalloc";
   }
   return "unknown status";
 }

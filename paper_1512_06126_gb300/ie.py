@@ -16,10 +16,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libie_gb300.so")
 
 IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN = 0, 1, 2
+IE_ERR_SCRATCH = -6
 IE_C64, IE_C128 = 0, 1
 IE_FP64, IE_MIXED = 0, 1
 
-EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_rhs_mt", "ie_ctx_stream",
+EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_rhs_mt", "ie_ctx_stream",
            "ie_ctx_device_bytes", "ie_profile", "ie_profile_read", "ie_profile_matvec", "ie_kernel_launches",
            "ie_destroy", "ie_status_str")
 
@@ -69,6 +70,8 @@ def load(path: str = LIB_PATH):
     lib.ie_setup.restype = I
     lib.ie_generate_coefficients.argtypes = [P(ie_grid), P(ie_layers), D, VP, VP]
     lib.ie_generate_coefficients.restype = I
+    lib.ie_matvec_noalloc.argtypes = [I, I, I, I, VP, VP, VP, VP, VP, VP, VP]
+    lib.ie_matvec_noalloc.restype = I
     lib.ie_matvec.argtypes = [VP, I, VP, VP, I, I, I, VP]
     lib.ie_matvec.restype = I
     lib.ie_solve.argtypes = [VP, I, VP, VP, I, D, I, I, P(ie_solve_info)]
@@ -99,6 +102,13 @@ def load(path: str = LIB_PATH):
 
 def kernel_launches() -> int:
     return int(load().ie_kernel_launches())
+
+
+def matvec_noalloc(nx, ny, nz, nrhs, qf_ptr, in_scale_ptr, out_scale_ptr, diag_ptr, x_ptr, y_ptr, stream=None):
+    """Allocation-free c64 product (see ie_matvec_noalloc in include/ie.h).  Returns the
+    status code (IE_OK, or IE_ERR_SCRATCH for a problem above the fixed work space)."""
+    return load().ie_matvec_noalloc(nx, ny, nz, nrhs, qf_ptr, in_scale_ptr, out_scale_ptr, diag_ptr, x_ptr, y_ptr,
+                                    stream)
 
 
 def status_str(s: int) -> str:
