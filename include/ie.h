@@ -149,8 +149,9 @@ ie_status ie_generate_coefficients(const ie_grid *grid, const ie_layers *layers,
 ie_status ie_matvec(ie_ctx *ctx, int inst, const void *x_dev, void *y_dev, int nrhs, int dtype, int transpose,
                     void *stream);
 
-/* Solve A u = b for instance inst (Sect. 3.3 (ii): GMRES with classical Gram-Schmidt
- * applied twice).  precision IE_FP64: every product with the c128 operator.
+/* Solve A u = b for instance inst (Sect. 3.3 (ii): restarted GMRES; classical
+ * Gram-Schmidt in FP64 with a second projection wherever the first one cancels more
+ * than 15/16 of the new vector's norm).  precision IE_FP64: every product with the c128 operator.
  * IE_MIXED: iterative refinement whose residual uses the c128 operator and whose
  * corrections come from GMRES on the c64 operator with FP64 Arnoldi vectors.
  * Stops when ||b - A u|| <= tol ||b|| for every right-hand side.

@@ -1,6 +1,7 @@
-// FP64 Krylov kernels for restarted GMRES with classical Gram-Schmidt applied
-// twice (the orthogonalisation of FGMRES, Sect. 3.3 (ii) of the paper).  All
-// right-hand sides advance in lockstep; each has its own Krylov space.
+// FP64 Krylov kernels for restarted GMRES (the iterative method of Sect. 3.3 (ii)):
+// classical Gram-Schmidt with selective reorthogonalisation, norms, scaling and the
+// basis update.  All right-hand sides advance in lockstep; each has its own Krylov
+// space.
 //
 // Layout: a basis vector block is V[i][r][n] (basis index i, right-hand side r,
 // element n), so basis vector i of right-hand side r starts at V + (i*R + r)*n.
@@ -33,56 +34,6 @@ __device__ __forceinline__ double2 block_reduce(double2 v, double2 *sh) {
   }
   __syncthreads();
   return r;
-}
-
-// part[(r * k1 + i) * nb + blk] = sum over the block's chunk of conj(V_i) * w
-__global__ void __launch_bounds__(kT) mdot_partial(const double2 *__restrict__ V, const double2 *__restrict__ w,
-                                                   double2 *__restrict__ part, int k1, int R, long long n, int nb) {
-  __shared__ double2 sh[kT / 32];
-  const int r = blockIdx.y;
-  const long long base = (long long)blockIdx.x * kChunk;
-  double2 wl[kEPT];
-#pragma unroll
-  for (int e = 0; e < kEPT; ++e) {
-    const long long idx = base + e * kT + threadIdx.x;
-    wl[e] = idx < n ? w[(long long)r * n + idx] : make_double2(0.0, 0.0);
-  }
-  for (int i = 0; i < k1; ++i) {
-    const double2 *vi = V + ((long long)i * R + r) * n;
-    double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int e = 0; e < kEPT; ++e) {
-      const long long idx = base + e * kT + threadIdx.x;
-      if (idx < n) {
-        const double2 a = vi[idx];
-        acc.x = fma(a.x, wl[e].x, acc.x);
-        acc.x = fma(a.y, wl[e].y, acc.x);
-        acc.y = fma(a.x, wl[e].y, acc.y);
-        acc.y = fma(-a.y, wl[e].x, acc.y);
-      }
-    }
-    const double2 s = block_reduce(acc, sh);
-    if (threadIdx.x == 0) part[((long long)r * k1 + i) * nb + blockIdx.x] = s;
-  }
-}
-
-// out[r * ldh + i] (+)= sum_b part[(r * k1 + i) * nb + b]
-__global__ void mdot_final(const double2 *__restrict__ part, double2 *__restrict__ out, int k1, int nb, int ldh,
-                           int accumulate) {
-  __shared__ double2 sh[kT / 32];
-  const int i = blockIdx.x, r = blockIdx.y;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int b = threadIdx.x; b < nb; b += kT) {
-    const double2 v = part[((long long)r * k1 + i) * nb + b];
-    acc.x += v.x;
-    acc.y += v.y;
-  }
-  const double2 s = block_reduce(acc, sh);
-  if (threadIdx.x == 0) {
-    double2 *o = out + (long long)r * ldh + i;
-    if (accumulate) { o->x += s.x; o->y += s.y; }
-    else *o = s;
-  }
 }
 
 // w[r] -= sum_{i<k1} h[r * ldh + i] * V_i[r]   (sign = -1), or x[r] += ... (sign = +1)
@@ -166,117 +117,165 @@ __global__ void add_kernel(const double2 *__restrict__ x, double2 *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Classical Gram-Schmidt passes, tiled over the vector length.  A block owns a tile
-// of kTile consecutive elements of one right-hand side:
-//   MODE 0 (dot):       part_i = sum_tile conj(V_i) w
-//   MODE 1 (sub + dot): w -= sum_i h_i V_i on the tile, then part_i = sum conj(V_i) w
-//   MODE 2 (sub + norm): w -= sum_i h_i V_i on the tile, then part = sum |w|^2
-// The tile of w sits in shared memory; for the dots, (basis vector, 256-element
-// chunk) work units are spread over the warps, each lane streaming 8 elements, so a
-// block keeps many independent loads in flight with few registers.
+// Classical Gram-Schmidt with selective reorthogonalisation.  FP64 arithmetic sets
+// the pace here (the vector length times the basis size in complex FMAs per pass), so
+// the passes are organised to spend the FP64 pipe on multiply-adds and little else.
+// A block owns a tile of kTile consecutive elements of one right-hand side.
+//   dot pass: part_i = sum_tile conj(V_i) x  and  npart = sum_tile |x|^2
+//   sub pass: x -= sum_i h_i V_i on the tile  and  npart = sum_tile |x|^2
+// In the dot pass the tile of x sits in shared memory and warp j owns basis vectors
+// j, j + 8, ...: each lane accumulates over 64 elements of the tile before a single
+// warp reduction per (vector, tile).  With a per-right-hand-side flag the block of a
+// right-hand side whose flag is 0 returns at once.
 // ---------------------------------------------------------------------------
 constexpr int kTileEPT = 8;
 constexpr int kTile = kT * kTileEPT;  // 2048 elements
-constexpr int kChunk256 = 256;
 
-template <int MODE>
-__global__ void __launch_bounds__(kT) cgs_tile_kernel(const double2 *__restrict__ V, double2 *__restrict__ w,
-                                                      const double2 *__restrict__ h, double2 *__restrict__ part,
-                                                      double *__restrict__ npart, int k1, int R, long long n, int nb,
-                                                      int ldh) {
+__global__ void __launch_bounds__(kT) cgs_dot_kernel(const double2 *__restrict__ V, const double2 *__restrict__ x,
+                                                     double2 *__restrict__ part, double *__restrict__ npart,
+                                                     const int *__restrict__ flag, int k1, int R, long long n,
+                                                     int nb) {
   __shared__ double2 xw[kTile];
-  __shared__ double red[2 * 64];
-  __shared__ double2 hs[64];
   __shared__ double2 shn[kT / 32];
   const int r = blockIdx.y;
+  if (flag && !flag[r]) return;
   const long long t0 = (long long)blockIdx.x * kTile;
-  const long long Rn = (long long)R * n;
   const int tid = threadIdx.x;
-  const double2 *Vr = V + (long long)r * n;
-  double2 *wr = w + (long long)r * n;
-  if (tid < 2 * 64) red[tid] = 0.0;
-  if (MODE != 0 && tid < k1) hs[tid] = h[(long long)r * ldh + tid];
-  __syncthreads();
+  const double2 *xr = x + (long long)r * n;
   double nacc = 0.0;
-  if (MODE == 0) {
 #pragma unroll
-    for (int j = 0; j < kTileEPT; ++j) {
-      const long long e = t0 + j * kT + tid;
-      xw[j * kT + tid] = e < n ? wr[e] : make_double2(0.0, 0.0);
-    }
-  } else {
-    double2 x[kTileEPT];
-#pragma unroll
-    for (int j = 0; j < kTileEPT; ++j) {
-      const long long e = t0 + j * kT + tid;
-      x[j] = e < n ? wr[e] : make_double2(0.0, 0.0);
-    }
-    for (int i = 0; i < k1; ++i) {
-      const double2 hv = hs[i];
-      const double2 *vi = Vr + (long long)i * Rn;
-#pragma unroll
-      for (int j = 0; j < kTileEPT; ++j) {
-        const long long e = t0 + j * kT + tid;
-        if (e < n) {
-          const double2 a = __ldg(vi + e);
-          x[j].x -= hv.x * a.x - hv.y * a.y;
-          x[j].y -= hv.x * a.y + hv.y * a.x;
-        }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kTileEPT; ++j) {
-      const long long e = t0 + j * kT + tid;
-      if (e < n) wr[e] = x[j];
-      xw[j * kT + tid] = x[j];
-      nacc = fma(x[j].x, x[j].x, nacc);
-      nacc = fma(x[j].y, x[j].y, nacc);
-    }
+  for (int j = 0; j < kTileEPT; ++j) {
+    const long long e = t0 + j * kT + tid;
+    const double2 v = e < n ? xr[e] : make_double2(0.0, 0.0);
+    xw[j * kT + tid] = v;
+    nacc = fma(v.x, v.x, nacc);
+    nacc = fma(v.y, v.y, nacc);
   }
-  if (MODE == 2) {
-    const double2 sres = block_reduce(make_double2(nacc, 0.0), shn);
-    if (tid == 0) npart[(long long)r * nb + blockIdx.x] = sres.x;
-    return;
-  }
-  __syncthreads();
+  const double2 sres = block_reduce(make_double2(nacc, 0.0), shn);  // also orders the xw stores
+  if (tid == 0) npart[(long long)r * nb + blockIdx.x] = sres.x;
   const int lane = tid & 31, wid = tid >> 5;
-  const int units = k1 * (kTile / kChunk256);
-  for (int u = wid; u < units; u += kT / 32) {
-    const int i = u / (kTile / kChunk256), c = u % (kTile / kChunk256);
-    const double2 *vi = Vr + (long long)i * Rn;
-    double ax = 0.0, ay = 0.0;
-#pragma unroll
-    for (int q = 0; q < kChunk256 / 32; ++q) {
-      const int le = c * kChunk256 + q * 32 + lane;
-      const long long e = t0 + le;
-      if (e < n) {
-        const double2 a = __ldg(vi + e);
-        const double2 b = xw[le];
-        ax = fma(a.x, b.x, ax);
-        ax = fma(a.y, b.y, ax);
-        ay = fma(a.x, b.y, ay);
-        ay = fma(-a.y, b.x, ay);
-      }
+  const long long lim = n - t0;  // elements of the tile inside the vector
+  for (int i = wid; i < k1; i += kT / 32) {
+    const double2 *vi = V + ((long long)i * R + r) * n + t0;
+    double ax0 = 0.0, ay0 = 0.0, ax1 = 0.0, ay1 = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < kTile / 32; q += 2) {
+      const int l0 = q * 32 + lane, l1 = l0 + 32;
+      const double2 a0 = l0 < lim ? __ldg(vi + l0) : make_double2(0.0, 0.0);
+      const double2 a1 = l1 < lim ? __ldg(vi + l1) : make_double2(0.0, 0.0);
+      const double2 b0 = xw[l0], b1 = xw[l1];
+      ax0 = fma(a0.x, b0.x, ax0);
+      ax0 = fma(a0.y, b0.y, ax0);
+      ay0 = fma(a0.x, b0.y, ay0);
+      ay0 = fma(-a0.y, b0.x, ay0);
+      ax1 = fma(a1.x, b1.x, ax1);
+      ax1 = fma(a1.y, b1.y, ax1);
+      ay1 = fma(a1.x, b1.y, ay1);
+      ay1 = fma(-a1.y, b1.x, ay1);
     }
+    double ax = ax0 + ax1, ay = ay0 + ay1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       ax += __shfl_down_sync(0xffffffffu, ax, o);
       ay += __shfl_down_sync(0xffffffffu, ay, o);
     }
-    if (lane == 0) {
-      atomicAdd(&red[2 * i], ax);
-      atomicAdd(&red[2 * i + 1], ay);
-    }
+    if (lane == 0) part[((long long)r * k1 + i) * nb + blockIdx.x] = make_double2(ax, ay);
   }
-  __syncthreads();
-  if (tid < k1) part[((long long)r * k1 + tid) * nb + blockIdx.x] = make_double2(red[2 * tid], red[2 * tid + 1]);
 }
 
-// out[r * ldh + i] = sum_b part[(r * k1 + i) * nb + b]
-__global__ void part_sum_kernel(const double2 *__restrict__ part, double2 *__restrict__ out, int k1, int nb,
-                                int ldh) {
+// x[r] -= sum_{i<k1} h[r * ldh + i] V_i[r] on the tile; npart = sum_tile |x|^2
+__global__ void __launch_bounds__(kT) cgs_sub_kernel(const double2 *__restrict__ V, double2 *__restrict__ x,
+                                                     const double2 *__restrict__ h, double *__restrict__ npart,
+                                                     const int *__restrict__ flag, int k1, int R, long long n,
+                                                     int nb, int ldh) {
+  __shared__ double2 hs[64];
+  __shared__ double2 shn[kT / 32];
+  const int r = blockIdx.y;
+  if (flag && !flag[r]) return;
+  const long long t0 = (long long)blockIdx.x * kTile;
+  const int tid = threadIdx.x;
+  double2 *xr = x + (long long)r * n;
+  if (tid < k1) hs[tid] = h[(long long)r * ldh + tid];
+  __syncthreads();
+  double2 v[kTileEPT];
+#pragma unroll
+  for (int j = 0; j < kTileEPT; ++j) {
+    const long long e = t0 + j * kT + tid;
+    v[j] = e < n ? xr[e] : make_double2(0.0, 0.0);
+  }
+  for (int i = 0; i < k1; ++i) {
+    const double2 hv = hs[i];
+    const double2 *vi = V + ((long long)i * R + r) * n;
+#pragma unroll
+    for (int j = 0; j < kTileEPT; ++j) {
+      const long long e = t0 + j * kT + tid;
+      if (e < n) {
+        const double2 a = __ldg(vi + e);
+        v[j].x = fma(-hv.x, a.x, v[j].x);
+        v[j].x = fma(hv.y, a.y, v[j].x);
+        v[j].y = fma(-hv.x, a.y, v[j].y);
+        v[j].y = fma(-hv.y, a.x, v[j].y);
+      }
+    }
+  }
+  double nacc = 0.0;
+#pragma unroll
+  for (int j = 0; j < kTileEPT; ++j) {
+    const long long e = t0 + j * kT + tid;
+    if (e < n) xr[e] = v[j];
+    nacc = fma(v[j].x, v[j].x, nacc);
+    nacc = fma(v[j].y, v[j].y, nacc);
+  }
+  const double2 sres = block_reduce(make_double2(nacc, 0.0), shn);
+  if (tid == 0) npart[(long long)r * nb + blockIdx.x] = sres.x;
+}
+
+// ||x|| before (npart0) and after (npart1) the first projection; flag[r] = 1 when the
+// projection cancelled so much of x that a second one is needed: ||x'|| < ||x|| / 16.
+// This is the test of Daniel, Gragg, Kaufman and Stewart with a looser threshold than
+// their 1/sqrt(2): one projection leaves x' orthogonal to V up to about
+// eps64 ||x|| / ||x'||, so below 1/16 cancellation the loss stays under ~16 eps64 per
+// step, far below what restarted GMRES to 1e-7 (or an inner solve to 1e-3) can notice.
+// For this operator the product A v_k is dominated by v_k, so 1/sqrt(2) would trigger
+// the second projection in nearly every iteration, doubling the FP64 work.
+__global__ void cgs_check_kernel(const double *__restrict__ npart0, const double *__restrict__ npart1,
+                                 double *__restrict__ nrm, int *__restrict__ flag, int nb) {
+  __shared__ double2 sh[kT / 32];
+  const int r = blockIdx.x;
+  double a0 = 0.0, a1 = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kT) {
+    a0 += npart0[(long long)r * nb + b];
+    a1 += npart1[(long long)r * nb + b];
+  }
+  const double2 s = block_reduce(make_double2(a0, a1), sh);
+  if (threadIdx.x == 0) {
+    const double n0 = sqrt(s.x), n1 = sqrt(s.y);
+    nrm[r] = n1;
+    flag[r] = n1 < 0.0625 * n0 ? 1 : 0;
+  }
+}
+
+// after the second projection: nrm[r] = ||x''|| for the right-hand sides that had one
+__global__ void cgs_renorm_kernel(const double *__restrict__ npart, double *__restrict__ nrm,
+                                  const int *__restrict__ flag, int nb) {
+  __shared__ double2 sh[kT / 32];
+  const int r = blockIdx.x;
+  if (!flag[r]) return;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kT) acc += npart[(long long)r * nb + b];
+  const double2 s = block_reduce(make_double2(acc, 0.0), sh);
+  if (threadIdx.x == 0) nrm[r] = sqrt(s.x);
+}
+
+// out[r * ldh + i] = sum_b part[(r * k1 + i) * nb + b]; 0 where flag[r] == 0
+__global__ void part_sum_kernel(const double2 *__restrict__ part, double2 *__restrict__ out,
+                                const int *__restrict__ flag, int k1, int nb, int ldh) {
   __shared__ double2 sh[kT / 32];
   const int i = blockIdx.x, r = blockIdx.y;
+  if (flag && !flag[r]) {
+    if (threadIdx.x == 0) out[(long long)r * ldh + i] = make_double2(0.0, 0.0);
+    return;
+  }
   double2 acc = make_double2(0.0, 0.0);
   for (int b = threadIdx.x; b < nb; b += kT) {
     const double2 v = part[((long long)r * k1 + i) * nb + b];
@@ -299,14 +298,6 @@ int blocks_for(long long n) {
 
 int mdot_nb(long long n) { return (int)((n + kChunk - 1) / kChunk); }
 
-void gmres_mdot(const double2 *V, const double2 *w, double2 *part, double2 *h_out, int k1, int R, long long n, int ldh,
-                int accumulate, cudaStream_t s) {
-  const int nb = mdot_nb(n);
-  count_launches(2);
-  mdot_partial<<<dim3(nb, R), kT, 0, s>>>(V, w, part, k1, R, n, nb);
-  mdot_final<<<dim3(k1, R), kT, 0, s>>>(part, h_out, k1, nb, ldh, accumulate);
-}
-
 void gmres_maxpy(const double2 *V, const double2 *h, double2 *w, int k1, int R, long long n, int ldh, double sign,
                  cudaStream_t s) {
   count_launches(1);
@@ -321,21 +312,27 @@ void gmres_norm(const double2 *w, double *part, double *out, int R, long long n,
   norm_final<<<R, kT, 0, s>>>(part, out, nb);
 }
 
-int gmres_cgs2(const double2 *V, double2 *w, double2 *h1, double2 *h2, double2 *part, double *npart, double *nrm,
-               int k1, int R, long long n, int ldh, cudaStream_t s) {
+int gmres_orthogonalize(const double2 *V, double2 *w, double2 *h1, double2 *h2, double2 *part, double *npart,
+                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s) {
   if (k1 < 1 || k1 > 64) return -1;
   const int nb = cgs_nb(n);
-  count_launches(6);
-  cgs_tile_kernel<0><<<dim3(nb, R), kT, 0, s>>>(V, w, nullptr, part, nullptr, k1, R, n, nb, ldh);
-  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h1, k1, nb, ldh);
-  cgs_tile_kernel<1><<<dim3(nb, R), kT, 0, s>>>(V, w, h1, part, nullptr, k1, R, n, nb, ldh);
-  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h2, k1, nb, ldh);
-  cgs_tile_kernel<2><<<dim3(nb, R), kT, 0, s>>>(V, w, h2, nullptr, npart, k1, R, n, nb, ldh);
-  norm_final<<<R, kT, 0, s>>>(npart, nrm, nb);
+  double *np0 = npart, *np1 = npart + (long long)R * nb;
+  const dim3 g(nb, R);
+  count_launches(8);
+  // first projection: h1 = V^H w, w -= V h1
+  cgs_dot_kernel<<<g, kT, 0, s>>>(V, w, part, np0, nullptr, k1, R, n, nb);
+  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h1, nullptr, k1, nb, ldh);
+  cgs_sub_kernel<<<g, kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nb, ldh);
+  cgs_check_kernel<<<R, kT, 0, s>>>(np0, np1, nrm, flag, nb);
+  // second projection where the first cancelled too much (h2 = 0 elsewhere)
+  cgs_dot_kernel<<<g, kT, 0, s>>>(V, w, part, np0, flag, k1, R, n, nb);
+  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h2, flag, k1, nb, ldh);
+  cgs_sub_kernel<<<g, kT, 0, s>>>(V, w, h2, np1, flag, k1, R, n, nb, ldh);
+  cgs_renorm_kernel<<<R, kT, 0, s>>>(np1, nrm, flag, nb);
   return 0;
 }
 
-int cgs2_partial_blocks(long long n) { return cgs_nb(n); }
+int gs_partial_blocks(long long n) { return cgs_nb(n); }
 
 void gmres_scale(const double2 *src, double2 *dst, const double *nrm, int R, long long n, cudaStream_t s) {
   count_launches(1);

@@ -59,6 +59,7 @@ struct ie_ctx {
   float2 *x32 = nullptr, *y32 = nullptr;       // c64 staging for mixed precision
   double2 *V = nullptr, *w = nullptr, *r = nullptr, *dx = nullptr, *part = nullptr, *hdev = nullptr;
   double *nrmpart = nullptr, *nrm = nullptr;
+  int *gsflag = nullptr;                       // per right-hand side: second Gram-Schmidt projection ran
   std::vector<void *> allocs;
   long long dev_bytes = 0;
   // profiling of the contraction kernel: event pairs recorded around each launch
@@ -279,7 +280,8 @@ struct Op {
 };
 
 // ---------------------------------------------------------------------------
-// GMRES(m), classical Gram-Schmidt applied twice, all right-hand sides in lockstep.
+// GMRES(m), classical Gram-Schmidt with selective reorthogonalisation, all right-hand
+// sides in lockstep.
 // Solves op(x) = b until ||b - op x|| <= tol ||b|| for every right-hand side (the
 // Givens recurrence ends a cycle; a true residual at the next restart confirms it).
 // ---------------------------------------------------------------------------
@@ -332,7 +334,8 @@ ie_status gmres(ie_ctx *c, const Op &op, const double2 *b, double2 *x, int R, do
     int kmax = 0;
     for (int k = 0; k < m && it < max_iter && n_active > 0; ++k) {
       IE_TRY(op(c->V + (long long)k * nR, c->w, R));
-      if (ie::gmres_cgs2(c->V, c->w, h1, h2, c->part, c->nrmpart, c->nrm, k + 1, R, n, ldh, s) != 0)
+      if (ie::gmres_orthogonalize(c->V, c->w, h1, h2, c->part, c->nrmpart, c->nrm, c->gsflag, k + 1, R, n, ldh,
+                                  s) != 0)
         return IE_ERR_ARG;
       ie::gmres_scale(c->w, c->V + (long long)(k + 1) * nR, c->nrm, R, n, s);
       IE_CUDA(cudaMemcpyAsync(hh.data(), h1, (size_t)2 * R * ldh * sizeof(double2), cudaMemcpyDeviceToHost, s));
@@ -711,10 +714,11 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   IE_TRY(dalloc(c, &c->r, nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->dx, nv * sizeof(double2)));
   if (c->restart > 63) return IE_ERR_ARG;
-  const long long nbp = std::max<long long>(ie::mdot_nb(c->nvec()), ie::cgs2_partial_blocks(c->nvec()));
+  const long long nbp = std::max<long long>(ie::mdot_nb(c->nvec()), ie::gs_partial_blocks(c->nvec()));
   IE_TRY(dalloc(c, &c->part, (size_t)max_rhs * (c->restart + 1) * nbp * sizeof(double2)));
   IE_TRY(dalloc(c, &c->hdev, (size_t)3 * max_rhs * (c->restart + 1) * sizeof(double2)));
-  IE_TRY(dalloc(c, &c->nrmpart, (size_t)max_rhs * std::max<long long>(1024, nbp) * sizeof(double)));
+  IE_TRY(dalloc(c, &c->nrmpart, (size_t)2 * max_rhs * std::max<long long>(1024, nbp) * sizeof(double)));
+  IE_TRY(dalloc(c, &c->gsflag, (size_t)max_rhs * sizeof(int)));
   IE_TRY(dalloc(c, &c->nrm, (size_t)2 * max_rhs * sizeof(double)));
   IE_CUDA(cudaStreamSynchronize(c->stream));
   return IE_OK;

@@ -241,3 +241,33 @@ def test_large_nz_contraction_against_oracle(shape):
             ref32 = O.fft_apply(m0, qt, x[r].astype(np.complex64).astype(np.complex128))
             assert rel(y32[r], ref32) <= 2e-5, (shape, R, r, rel(y32[r], ref32))
     ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-10, 1e-9), (1, 1e-7, 1e-6)])
+def test_solve_weak_contrast_takes_second_projection(precision, tol, bound):
+    """A weak anomaly (sigma_a = sigma_b (1 + 1e-6)) makes A = I + O(1e-6): each new
+    Krylov vector A v_k is v_k up to a part of relative size ~1e-6, so the first
+    Gram-Schmidt projection cancels nearly all of it and the second projection runs.
+    The solution must still match a dense LU solve."""
+    need_gpu()
+    m = W.small_model(nx=7, ny=5, nz=3, seed=11, freq=3.0)
+    g = m.grid
+    sb = W.background_sigma(g, m.layers)
+    sa = np.broadcast_to(sb[:, None, None], (g.nz, g.ny, g.nx)).astype(np.complex128).copy()
+    sa[:, 1:4, 2:6] *= 1.0 + 1e-6
+    m = W.Model(m.name, g, m.layers, sa, m.freqs, m.pols)
+    qa = all_offsets_cached(m)
+    q = qa[g.ny - 1:, g.nx - 1:]
+    A = O.dense_matrix(m, O.dense_B(m, qa))
+    b = np.stack([W.random_field((3, g.nz, g.ny, g.nx), 71 + r) for r in range(2)])
+    u_ref = np.stack([np.linalg.solve(A, b[r].ravel()).reshape(b[r].shape) for r in range(2)])
+    ctx = lib_context(m, [q], max_rhs=2)
+    bd = to_dev(b)
+    ud = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), 2, tol, precision=precision)
+    assert st == 0, (st, info.final_rel_res)
+    u = to_host(ud)
+    for r in range(2):
+        assert rel(u[r], u_ref[r]) <= bound, (r, rel(u[r], u_ref[r]))
+    ctx.close()
