@@ -172,6 +172,52 @@ ie_status ie_adjoint_solve(ie_ctx *ctx, int inst, const void *b_dev, void *w_dev
  * scaled by sqrt(Re sigma_b).  u0_dev: device c128 [3][Nz][Ny][Nx]. */
 ie_status ie_rhs_mt(ie_ctx *ctx, int inst, int pol, void *u0_dev);
 
+/* Replace the anomaly conductivities (host, complex interleaved [Nz][Ny][Nx], S/m)
+ * without regenerating the coefficient tensors: S, R2 and the per-cell current and
+ * gradient factors are rebuilt in place.  Waits for the context's stream first.
+ * IE_ERR_GEOMETRY if receivers are set and an anomalous cell would touch their
+ * plane (the context keeps its previous conductivities then). */
+ie_status ie_set_sigma(ie_ctx *ctx, const double *sigma_a_host);
+
+/* Magnetotelluric receivers: n_rec points at the lateral centres of grid cells
+ * (ix_host[r], iy_host[r]), all at depth z_rec with surface <= z_rec <= top of the
+ * grid.  Generates on the device, for every instance's frequency, the kernels that
+ * give E_x, E_y, H_x, H_y at a receiver from the uniform current of a cell (eq.
+ * (APR_lab) with the Green's tensors of eqs. (geh), (green_tensor), (G1G2g), (Ge2):
+ * the vertical functions of U_1, U_sigma at the receiver depth and the point-to-cell
+ * lateral integrals), and the normal field at z_rec.  Only cells strictly below
+ * z_rec radiate; an anomalous cell touching the receiver plane gives
+ * IE_ERR_GEOMETRY.  Synchronous. */
+ie_status ie_set_receivers(ie_ctx *ctx, int n_rec, const int *ix_host, const int *iy_host, double z_rec);
+
+/* Fields at the receivers for nrhs solutions U of instance inst, whose sources are
+ * the plane waves pol_host[p] (0: x, 1: y): f_dev c128 [nrhs][n_rec][4] =
+ * (E_x, E_y, H_x, H_y), the normal field plus sum over cells of the kernels times the
+ * current J = 2 s gamma U (eq. (APR_lab)).  u_dev: c128 [nrhs][3][Nz][Ny][Nx].
+ * Synchronous. */
+ie_status ie_receiver_fields(ie_ctx *ctx, int inst, const void *u_dev, int nrhs, const int *pol_host, void *f_dev);
+
+/* MT impedance and misfit of one frequency from the fields of its x- and
+ * y-polarisation solutions, f_dev c128 [2][n_rec][4] (x first): Z = E H^-1 with
+ * E = [[Ex1, Ex2], [Ey1, Ey2]], H = [[Hx1, Hx2], [Hy1, Hy2]] (z_dev c128
+ * [n_rec][2][2], row-major), phi_host = 1/2 sum |Z - Zobs|^2 (zobs_dev like z_dev),
+ * and the adjoint sources of the misfit, c_dev c128 [2][n_rec][4]: for polarisation
+ * j, c^E_i = (H^-1 D^T)_{ji}, c^H_i = -(H^-1 D^T Z)_{ji}, D = conj(Z - Zobs), so that
+ * dPhi = Re sum c . d(E_x, E_y, H_x, H_y).  Synchronous. */
+ie_status ie_mt_misfit(ie_ctx *ctx, const void *f_dev, const void *zobs_dev, void *z_dev, double *phi_host,
+                       void *c_dev);
+
+/* Right-hand sides of the adjoint solves: rhs_dev c128 [nrhs][3][Nz][Ny][Nx] =
+ * 2 s gamma (G^T c), the transpose of the receiver operator of instance inst applied
+ * to the sources c_dev [nrhs][n_rec][4].  Synchronous. */
+ie_status ie_receiver_adjoint(ie_ctx *ctx, int inst, const void *c_dev, int nrhs, void *rhs_dev);
+
+/* grad_dev (double [Nz][Ny][Nx]) += Re sum_p (dgamma/dln sigma_a)(w_p . u_p)/gamma
+ * for the anomalous cells (gamma != 0; unchanged elsewhere): the misfit gradient in
+ * ln sigma_a from forward solutions u_dev and adjoint solutions w_dev (A^T w = the
+ * adjoint right-hand side), both c128 [nrhs][3][Nz][Ny][Nx].  Synchronous. */
+ie_status ie_gradient_accumulate(ie_ctx *ctx, const void *u_dev, const void *w_dev, int nrhs, void *grad_dev);
+
 /* The context's CUDA stream (a cudaStream_t). */
 void *ie_ctx_stream(ie_ctx *ctx);
 

@@ -336,6 +336,7 @@ struct WParams {
   double t0, dt;
   double near_lh, far_c, far_w, panel_rel, lam_low;
   int max_panels;
+  int point;           // 1: a point seen from the source rectangle (box transform), 0: two cells (tent)
 };
 
 __device__ __forceinline__ double tent_hat(double k, double h) {
@@ -343,6 +344,12 @@ __device__ __forceinline__ double tent_hat(double k, double h) {
   if (fabs(x) < 1e-8) return h * h;
   const double s = sin(x) / x;
   return h * h * s * s;
+}
+// transform of the rectangle's indicator (point-to-cell lateral integrals)
+__device__ __forceinline__ double box_hat(double k, double h) {
+  const double x = 0.5 * k * h;
+  if (fabs(x) < 1e-8) return h;
+  return h * sin(x) / x;
 }
 
 __global__ void weights_kernel(WParams P, const int *offs, int n_off, double *W, double *edges_ws) {
@@ -392,7 +399,7 @@ __global__ void weights_kernel(WParams P, const int *offs, int n_off, double *W,
       double sn, cs;
       sincos(th, &sn, &cs);
       const double kxv = lam * cs, kyv = lam * sn;
-      double base = tent_hat(kxv, P.hx) * tent_hat(kyv, P.hy);
+      double base = P.point ? box_hat(kxv, P.hx) * box_hat(kyv, P.hy) : tent_hat(kxv, P.hx) * tent_hat(kyv, P.hy);
       if (q == 0 || q == nt) base *= 0.5;
       double sx, cx, sy, cy;
       sincos(kxv * Dx, &sx, &cx);
@@ -551,6 +558,88 @@ __global__ void assemble_kernel(const double *Pfar, const double *Pnear, const z
   }
 }
 
+// ---------------------------------------------------------------------------
+// 6. Receiver kernels (eq. (APR_lab)): E and H at a point at depth z_r above the grid
+//    from a cell of uniform current.  Vertical functions of U(z_r, z*) over the source
+//    cell [w1, w2] (zero unless w1 > z_r), sigma_r the conductivity at the receiver:
+//      0 P1 = i w mu0 int U_1        1 X = P1 - (1/sigma_r) d/dz [U_s(z, w2) - U_s(z, w1)]
+//      2 P4 = (1/sigma_r) d/dz int U_s   3 P1z = d/dz int U_1
+//      4 Pg = U_s(z_r, w2) - U_s(z_r, w1) + P1z   5 Ps = int U_s
+//    Fr layout: Fr[kind][t][b].  With the point lateral weights W (box transform):
+//      4 pi E_xx = WJ.P1 + Wxx.X,  4 pi E_yy = WJ.P1 + Wyy.X,  4 pi E_xy = Wxy.X,
+//      4 pi E_xz = Wx.P4,          4 pi E_yz = Wy.P4,
+//      4 pi H_xx = -Wxy.Pg (= -4 pi H_yy),  4 pi H_yx = WJ.P1z + Wxx.Pg,
+//      4 pi H_xy = -WJ.P1z - Wyy.Pg,  4 pi H_xz = Wy.Ps,  4 pi H_yz = -Wx.Ps
+//    (GE = (1/k^2)-weighted derivatives of (Ge2); GH = curl of (green_tensor) / (i w mu0)).
+// ---------------------------------------------------------------------------
+constexpr int kNR = 6;
+constexpr int kNRP = 12;  // products
+constexpr int kRecEntries = 10;
+
+__global__ void receiver_vertical_kernel(int T, double t0, double dt, double omega, LayDev L, GridDev G,
+                                         const zc *spec, double z_r, int r, zc *F) {
+  const int nz = G.nz;
+  const long long tot = (long long)T * nz;
+  const int nl = L.L + 1;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(id / nz), b = (int)(id % nz);
+    const double w1 = G.ze[b], w2 = G.ze[b + 1];
+    const long long st = (long long)T * nz, o = (long long)t * nz + b;
+    if (!(w1 > z_r)) {
+      for (int k = 0; k < kNR; ++k) F[k * st + o] = 0.0;
+      continue;
+    }
+    const int s = G.lay[b];
+    const zc *sp1 = spec + ((size_t)0 * T + t) * nl * 5;
+    const zc *sps = spec + ((size_t)1 * T + t) * nl * 5;
+    const Terms T1 = full_terms(sp1, nl, L, false, r, s, false);
+    const Terms Ts = full_terms(sps, nl, L, true, r, s, false);
+    const zc F1 = F_terms(T1, z_r, w1, w2, false), F1z = F_terms(T1, z_r, w1, w2, true);
+    const zc Fs = F_terms(Ts, z_r, w1, w2, false), Fsz = F_terms(Ts, z_r, w1, w2, true);
+    zc dU = 0.0, Ud = 0.0;
+    for (int i = 0; i < Ts.n; ++i) {
+      const Term &q = Ts.t[i];
+      const zc e2 = q.c * thrust::exp(q.az * z_r + q.azs * w2 + q.k);
+      const zc e1 = q.c * thrust::exp(q.az * z_r + q.azs * w1 + q.k);
+      dU += q.az * (e2 - e1);
+      Ud += e2 - e1;
+    }
+    const zc iwm = zc(0.0, omega * kMu0);
+    const zc inv = 1.0 / sig(L, r);
+    const zc P1 = iwm * F1;
+    F[0 * st + o] = P1;
+    F[1 * st + o] = P1 - inv * dU;
+    F[2 * st + o] = inv * Fsz;
+    F[3 * st + o] = F1z;
+    F[4 * st + o] = Ud + F1z;
+    F[5 * st + o] = Fs;
+  }
+}
+
+// tab[((i * nx + j) * nz + b) * 10 + e], e: E_xx, E_yy, E_xy, E_xz, E_yz, H_xx, H_yx, H_xy, H_xz, H_yz
+__global__ void receiver_assemble_kernel(const double *P, int n_off, int nz, zc *tab) {
+  const long long tot = (long long)n_off * nz;
+  const double inv4pi = 1.0 / (4.0 * kPi);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)(id / nz), b = (int)(id % nz);
+    const double *row = P + (size_t)o * kNRP * 2 * nz;
+    auto g = [&](int k) { return zc(row[2 * (k * nz + b)], row[2 * (k * nz + b) + 1]); };
+    zc *t = tab + ((size_t)o * nz + b) * kRecEntries;
+    t[0] = (g(0) + g(1)) * inv4pi;
+    t[1] = (g(0) + g(2)) * inv4pi;
+    t[2] = g(3) * inv4pi;
+    t[3] = g(4) * inv4pi;
+    t[4] = g(5) * inv4pi;
+    t[5] = -g(6) * inv4pi;
+    t[6] = (g(7) + g(8)) * inv4pi;
+    t[7] = (-g(7) - g(9)) * inv4pi;
+    t[8] = g(10) * inv4pi;
+    t[9] = -g(11) * inv4pi;
+  }
+}
+
 // Gauss-Legendre nodes on [-1, 1] by Newton's iteration on P_n.
 void gauss_legendre(int n, double *x, double *w) {
   for (int i = 0; i < n; ++i) {
@@ -657,7 +746,7 @@ CoefGenStatus generate_coefficients(const CoefGenInput &in, double2 *q_dev, cuda
     count_launches(5);
     spectra_kernel<<<(T + 127) / 128, 128, 0, s>>>(T, t0, dt, omega, L, spec);
     vertical_kernel<<<grid1d((long long)T * np), 256, 0, s>>>(T, t0, dt, omega, L, G, spec, F);
-    WParams P{nx, ny, in.hx, in.hy, hmin, T, t0, dt, near_lh, 80.0, 10.0, 0.25, lam_low, max_panels};
+    WParams P{nx, ny, in.hx, in.hy, hmin, T, t0, dt, near_lh, 80.0, 10.0, 0.25, lam_low, max_panels, 0};
     const size_t smw = sizeof(double) * kNW * T;
     cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
     weights_kernel<<<n_off, 256, smw, s>>>(P, d_offs, n_off, W, edges);
@@ -708,6 +797,89 @@ CoefGenStatus generate_coefficients(const CoefGenInput &in, double2 *q_dev, cuda
   if (hb) cublasDestroy(hb);
   cudaFree(spec); cudaFree(F); cudaFree(W); cudaFree(Wn); cudaFree(edges); cudaFree(Fr);
   cudaFree(Pfar); cudaFree(Pnear); cudaFree(S); cudaFree(d_offs); cudaFree(d_near); cudaFree(d_nidx);
+  return st;
+}
+
+CoefGenStatus generate_receiver_tables(const CoefGenInput &in, double z_r, int r_layer, double2 *tab_dev,
+                                       cudaStream_t s) {
+  const int nx = in.nx, ny = in.ny, nz = in.nz;
+  if (in.n_interfaces < 1 || in.n_interfaces > kMaxLay || nz > 256) return CoefGenStatus::kUnsupported;
+  LayDev L{};
+  L.L = in.n_interfaces;
+  for (int k = 0; k < L.L; ++k) L.d[k + 1] = in.interfaces[k];
+  L.d[0] = L.d[1];
+  L.d[L.L + 1] = L.d[L.L];
+  for (int m = 0; m <= L.L; ++m) {
+    L.l[m] = (m >= 1 && m < L.L) ? L.d[m + 1] - L.d[m] : 0.0;
+    L.sr[m] = in.sigma[2 * m];
+    L.si[m] = in.sigma[2 * m + 1];
+  }
+  GridDev G{};
+  G.nz = nz;
+  for (int k = 0; k <= nz; ++k) G.ze[k] = in.z_edges[k];
+  for (int k = 0; k < nz; ++k) G.lay[k] = in.cell_layer[k];
+  double hz_min = 1e300;
+  for (int k = 0; k < nz; ++k) hz_min = std::min(hz_min, G.ze[k + 1] - G.ze[k]);
+  const double hmin = std::min({in.hx, in.hy, hz_min});
+  const double dt = 0.02, near_lh = 300.0, lam_low = 1e-9;
+  const double t0 = std::log(lam_low) - 5 * dt;
+  const double t1 = std::log(near_lh / hmin) + 5 * dt;
+  const int T = (int)std::ceil((t1 - t0) / dt) + 1;
+  const double omega = 2.0 * kPi * in.freq;
+  CoefGenStatus st = CoefGenStatus::kOk;
+  auto ck = [&](cudaError_t e) { if (e != cudaSuccess && st == CoefGenStatus::kOk) st = CoefGenStatus::kCuda; };
+  std::vector<int> offs;
+  for (int i = 0; i < ny; ++i)
+    for (int j = 0; j < nx; ++j) { offs.push_back(i); offs.push_back(j); }
+  const int n_off = nx * ny;
+  const int max_panels = 4000;
+  const long long ncol = (long long)kNRP * 2 * nz;
+  zc *spec = nullptr, *F = nullptr;
+  double *W = nullptr, *edges = nullptr, *Pm = nullptr;
+  int *d_offs = nullptr;
+  ck(cudaMalloc(&spec, sizeof(zc) * 2 * T * (L.L + 1) * 5));
+  ck(cudaMalloc(&F, sizeof(zc) * kNR * (size_t)T * nz));
+  ck(cudaMalloc(&W, sizeof(double) * kNW * (size_t)n_off * T));
+  ck(cudaMalloc(&edges, sizeof(double) * (size_t)n_off * (max_panels + 1)));
+  ck(cudaMalloc(&Pm, sizeof(double) * (size_t)n_off * ncol));
+  ck(cudaMalloc(&d_offs, sizeof(int) * offs.size()));
+  cublasHandle_t hb = nullptr;
+  if (st == CoefGenStatus::kOk && cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) st = CoefGenStatus::kCuda;
+  if (st == CoefGenStatus::kOk) {
+    ck(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice, s));
+    double gx[kGL], gw[kGL];
+    gauss_legendre(kGL, gx, gw);
+    ck(cudaMemcpyToSymbolAsync(c_glx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, s));
+    ck(cudaMemcpyToSymbolAsync(c_glw, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, s));
+    count_launches(4);
+    spectra_kernel<<<(T + 127) / 128, 128, 0, s>>>(T, t0, dt, omega, L, spec);
+    receiver_vertical_kernel<<<grid1d((long long)T * nz), 256, 0, s>>>(T, t0, dt, omega, L, G, spec, z_r, r_layer, F);
+    WParams P{nx, ny, in.hx, in.hy, hmin, T, t0, dt, near_lh, 80.0, 10.0, 0.25, lam_low, max_panels, 1};
+    const size_t smw = sizeof(double) * kNW * T;
+    cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
+    weights_kernel<<<n_off, 256, smw, s>>>(P, d_offs, n_off, W, edges);
+    ck(cudaGetLastError());
+    cublasSetStream(hb, s);
+    const double one = 1.0, zero = 0.0;
+    const long long fst = (long long)T * nz;
+    auto Fk = [&](int k) { return reinterpret_cast<const double *>(F + (size_t)k * fst); };
+    // (W kind, F kind) of each product, in the order the assembly expects
+    const int prod[kNRP][2] = {{0, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 2}, {5, 2},
+                               {3, 4}, {0, 3}, {1, 4}, {2, 4}, {5, 5}, {4, 5}};
+    for (int g = 0; g < kNRP && st == CoefGenStatus::kOk; ++g) {
+      const double *Am = W + (size_t)prod[g][0] * n_off * T;
+      const cublasStatus_t cs = cublasDgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, (int)(2 * nz), n_off, T, &one,
+                                            Fk(prod[g][1]), (int)(2 * nz), Am, T, &zero,
+                                            Pm + (size_t)g * 2 * nz, (int)ncol);
+      if (cs != CUBLAS_STATUS_SUCCESS) st = CoefGenStatus::kCuda;
+    }
+    receiver_assemble_kernel<<<grid1d((long long)n_off * nz), 256, 0, s>>>(Pm, n_off, nz,
+                                                                           reinterpret_cast<zc *>(tab_dev));
+    ck(cudaGetLastError());
+    ck(cudaStreamSynchronize(s));
+  }
+  if (hb) cublasDestroy(hb);
+  cudaFree(spec); cudaFree(F); cudaFree(W); cudaFree(edges); cudaFree(Pm); cudaFree(d_offs);
   return st;
 }
 

@@ -19,4 +19,12 @@ enum class CoefGenStatus { kOk, kUnsupported, kCuda };
 // Compressed real-space tensor [Ny][Nx][6][Nz][Nz] (c128) written to q_dev.
 CoefGenStatus generate_coefficients(const CoefGenInput &in, double2 *q_dev, cudaStream_t s);
 
+// Receiver kernels for a point at depth z_r (in layer r_layer) above the grid, for
+// every lateral offset i in [0, Ny), j in [0, Nx) (receiver minus cell) and source
+// z-cell b: tab_dev c128 [Ny][Nx][Nz][10], entries E_xx, E_yy, E_xy, E_xz, E_yz,
+// H_xx, H_yx, H_xy, H_xz, H_yz (E_yx = E_xy, H_yy = -H_xx).  Cells not strictly
+// below z_r get zeros.
+CoefGenStatus generate_receiver_tables(const CoefGenInput &in, double z_r, int r_layer, double2 *tab_dev,
+                                       cudaStream_t s);
+
 }  // namespace ie

@@ -13,6 +13,7 @@
 
 #include "blas.cuh"
 #include "coefgen.cuh"
+#include "receivers.cuh"
 #include "contract.cuh"
 #include "fft.cuh"
 #include "setup.cuh"
@@ -38,6 +39,8 @@ struct Instance {
   double freq = 0.0;
   double2 *q64 = nullptr;
   float2 *q32 = nullptr;
+  double2 *rtab = nullptr;         // receiver kernels [Ny][Nx][Nz][10] (after ie_set_receivers)
+  double2 en{0.0, 0.0}, hn{0.0, 0.0};  // normal E^N and E^N'/(i w mu0) at the receiver depth
 };
 
 }  // namespace
@@ -60,6 +63,11 @@ struct ie_ctx {
   double2 *V = nullptr, *w = nullptr, *r = nullptr, *dx = nullptr, *part = nullptr, *hdev = nullptr;
   double *nrmpart = nullptr, *nrm = nullptr;
   int *gsflag = nullptr;                       // per right-hand side: second Gram-Schmidt projection ran
+  void *jfac = nullptr, *gdiv = nullptr;       // per cell: 2 s gamma; (dgamma/dln sigma_a) / gamma (0 off the anomaly)
+  int n_rec = 0;                               // receivers (ie_set_receivers)
+  int *rec_ix = nullptr, *rec_iy = nullptr;
+  double z_rec = 0.0;
+  double *phi_r = nullptr;                     // per-receiver misfit terms
   std::vector<void *> allocs;
   long long dev_bytes = 0;
   // profiling of the contraction kernel: event pairs recorded around each launch
@@ -114,8 +122,8 @@ ie_status upload_cplx(ie_ctx *c, const std::vector<cd> &h, void **dst) {
   using V = ie::C<T>;
   std::vector<V> tmp(h.size());
   for (size_t i = 0; i < h.size(); ++i) tmp[i] = ie::mk<T>((T)h[i].real(), (T)h[i].imag());
-  V *p = nullptr;
-  IE_TRY(dalloc(c, &p, tmp.size() * sizeof(V)));
+  V *p = static_cast<V *>(*dst);
+  if (!p) IE_TRY(dalloc(c, &p, tmp.size() * sizeof(V)));  // an existing buffer is overwritten in place
   IE_CUDA(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(V), cudaMemcpyHostToDevice));
   *dst = p;
   return IE_OK;
@@ -124,7 +132,7 @@ ie_status upload_cplx(ie_ctx *c, const std::vector<cd> &h, void **dst) {
 ie_status build_diagonals(ie_ctx *c) {
   const long long N = c->ncell();
   const double norm = 1.0 / (4.0 * c->nx * c->ny);
-  std::vector<cd> in_f(N), out_f(N), diag(N), in_t(N), out_t(N);
+  std::vector<cd> in_f(N), out_f(N), diag(N), in_t(N), out_t(N), jfac(N), gdiv(N);
   for (int z = 0; z < c->nz; ++z) {
     const cd sb = c->sig[c->lay[z]];
     const double s = std::sqrt(sb.real());
@@ -138,6 +146,10 @@ ie_status build_diagonals(ie_ctx *c) {
       diag[i] = 1.0 - g;
       in_t[i] = -2.0 * s / V;
       out_t[i] = s * g * norm;
+      jfac[i] = 2.0 * s * g;
+      // dgamma/dln(sigma_a) = sigma_a 2 Re(sigma_b) / (sigma_a + conj sigma_b)^2, divided by gamma
+      const cd den = sa + std::conj(sb);
+      gdiv[i] = g == 0.0 ? cd(0.0) : sa * 2.0 * sb.real() / (den * den) / g;
     }
   }
   IE_TRY(upload_cplx<double>(c, in_f, &c->d64.in_f));
@@ -150,6 +162,56 @@ ie_status build_diagonals(ie_ctx *c) {
   IE_TRY(upload_cplx<float>(c, diag, &c->d32.diag));
   IE_TRY(upload_cplx<float>(c, in_t, &c->d32.in_t));
   IE_TRY(upload_cplx<float>(c, out_t, &c->d32.out_t));
+  IE_TRY(upload_cplx<double>(c, jfac, &c->jfac));
+  IE_TRY(upload_cplx<double>(c, gdiv, &c->gdiv));
+  return IE_OK;
+}
+
+// E^N(z) and E^N'(z) / (i w mu0) of the 1-D profile (normalised H(0) = 1) at a depth z
+// in layer m >= 1; same propagation as mt_cell_average.
+void mt_point(const ie_ctx *c, double omega, double z, cd *E_out, cd *H_out) {
+  const int L = (int)c->d.size();
+  std::vector<cd> kap(L + 1), Eb(L + 1), Epb(L + 1);
+  for (int m = 0; m <= L; ++m) kap[m] = std::sqrt(cd(0.0, -omega * kMu0) * c->sig[m]);
+  cd E = 1.0, Ep = -kap[L];
+  for (int m = L - 1; m >= 1; --m) {
+    Eb[m] = E;
+    Epb[m] = Ep;
+    const double l = c->d[m] - c->d[m - 1];
+    const cd ch = std::cosh(kap[m] * l), sh = std::sinh(kap[m] * l);
+    const cd Et = E * ch - Ep * sh / kap[m];
+    const cd Ept = -E * kap[m] * sh + Ep * ch;
+    E = Et;
+    Ep = Ept;
+  }
+  const cd a = cd(0.0, omega * kMu0) / Ep;
+  int m = 1;
+  for (int k = 0; k < L; ++k)
+    if (z >= c->d[k]) m = k + 1;
+  cd e, ep;
+  const cd k = kap[m];
+  if (m == L) {
+    e = a * std::exp(-k * (z - c->d[L - 1]));
+    ep = -k * e;
+  } else {
+    const double zb = c->d[m];
+    e = a * (Eb[m] * std::cosh(k * (z - zb)) + Epb[m] * std::sinh(k * (z - zb)) / k);
+    ep = a * (Eb[m] * k * std::sinh(k * (z - zb)) + Epb[m] * std::cosh(k * (z - zb)));
+  }
+  *E_out = e;
+  *H_out = ep / cd(0.0, omega * kMu0);
+}
+
+// IE_ERR_GEOMETRY if an anomalous cell touches or rises above the receiver plane
+ie_status check_receiver_geometry(const ie_ctx *c) {
+  if (c->n_rec == 0) return IE_OK;
+  const long long plane = (long long)c->nx * c->ny;
+  for (int z = 0; z < c->nz; ++z) {
+    if (c->ze[z] > c->z_rec) continue;
+    const cd sb = c->sig[c->lay[z]];
+    for (long long q = 0; q < plane; ++q)
+      if (c->sigma_a[(long long)z * plane + q] != sb) return IE_ERR_GEOMETRY;
+  }
   return IE_OK;
 }
 
@@ -760,6 +822,115 @@ ie_status ie_solve(ie_ctx *c, int inst, const void *b, void *u, int nrhs, double
 ie_status ie_adjoint_solve(ie_ctx *c, int inst, const void *b, void *w, int nrhs, double tol, int precision,
                            int use_x0, ie_solve_info *info) {
   return solve_impl(c, inst, (const double2 *)b, (double2 *)w, nrhs, tol, precision, use_x0, 1, info);
+}
+
+ie_status ie_set_sigma(ie_ctx *c, const double *sigma_a_host) {
+  if (!c || !sigma_a_host) return IE_ERR_ARG;
+  const long long N = c->ncell();
+  std::vector<cd> sa(N);
+  for (long long i = 0; i < N; ++i) sa[i] = cd(sigma_a_host[2 * i], sigma_a_host[2 * i + 1]);
+  std::swap(sa, c->sigma_a);
+  if (check_receiver_geometry(c) != IE_OK) {
+    std::swap(sa, c->sigma_a);
+    return IE_ERR_GEOMETRY;
+  }
+  IE_CUDA(cudaStreamSynchronize(c->stream));  // no product may be reading the diagonals
+  return build_diagonals(c);
+}
+
+ie_status ie_set_receivers(ie_ctx *c, int n_rec, const int *ix, const int *iy, double z_rec) {
+  if (!c || n_rec < 1 || n_rec > (1 << 16) || !ix || !iy) return IE_ERR_ARG;
+  if (z_rec > c->ze[0] || z_rec < c->d[0]) return IE_ERR_ARG;
+  for (int r = 0; r < n_rec; ++r)
+    if (ix[r] < 0 || ix[r] >= c->nx || iy[r] < 0 || iy[r] >= c->ny) return IE_ERR_ARG;
+  const int old_n = c->n_rec;
+  const double old_z = c->z_rec;
+  c->n_rec = n_rec;
+  c->z_rec = z_rec;
+  if (check_receiver_geometry(c) != IE_OK) {
+    c->n_rec = old_n;
+    c->z_rec = old_z;
+    return IE_ERR_GEOMETRY;
+  }
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  if (old_n < n_rec) {  // grow the per-receiver arrays
+    IE_TRY(dalloc(c, &c->rec_ix, (size_t)n_rec * sizeof(int)));
+    IE_TRY(dalloc(c, &c->rec_iy, (size_t)n_rec * sizeof(int)));
+    IE_TRY(dalloc(c, &c->phi_r, (size_t)n_rec * sizeof(double)));
+  }
+  IE_CUDA(cudaMemcpy(c->rec_ix, ix, (size_t)n_rec * sizeof(int), cudaMemcpyHostToDevice));
+  IE_CUDA(cudaMemcpy(c->rec_iy, iy, (size_t)n_rec * sizeof(int), cudaMemcpyHostToDevice));
+  int r_layer = 0;
+  for (size_t k = 0; k < c->d.size(); ++k)
+    if (z_rec >= c->d[k]) r_layer = (int)k + 1;
+  std::vector<double> sg(2 * c->sig.size());
+  for (size_t k = 0; k < c->sig.size(); ++k) { sg[2 * k] = c->sig[k].real(); sg[2 * k + 1] = c->sig[k].imag(); }
+  const size_t tab_elems = (size_t)c->nx * c->ny * c->nz * 10;
+  for (auto &in : c->inst) {
+    if (!in.rtab) IE_TRY(dalloc(c, &in.rtab, tab_elems * sizeof(double2)));
+    ie::CoefGenInput gi{c->nx, c->ny, c->nz, c->hx, c->hy, c->ze.data(), c->lay.data(), (int)c->d.size(),
+                        c->d.data(), sg.data(), in.freq};
+    const ie::CoefGenStatus gs = ie::generate_receiver_tables(gi, z_rec, r_layer, in.rtab, c->stream);
+    if (gs != ie::CoefGenStatus::kOk) return gs == ie::CoefGenStatus::kUnsupported ? IE_ERR_ARG : IE_ERR_CUDA;
+    cd E, H;
+    mt_point(c, 2.0 * M_PI * in.freq, z_rec, &E, &H);
+    in.en = make_double2(E.real(), E.imag());
+    in.hn = make_double2(H.real(), H.imag());
+  }
+  return IE_OK;
+}
+
+ie_status ie_receiver_fields(ie_ctx *c, int inst, const void *u_dev, int nrhs, const int *pol_host, void *f_dev) {
+  if (!c || !u_dev || !f_dev || !pol_host || inst < 0 || inst >= (int)c->inst.size() || nrhs < 1 || nrhs > 4)
+    return IE_ERR_ARG;
+  if (c->n_rec == 0 || !c->inst[inst].rtab) return IE_ERR_ARG;
+  int pol[4] = {0, 0, 0, 0};
+  for (int p = 0; p < nrhs; ++p) {
+    if (pol_host[p] != 0 && pol_host[p] != 1) return IE_ERR_ARG;
+    pol[p] = pol_host[p];
+  }
+  const Instance &in = c->inst[inst];
+  ie::launch_receiver_fields(in.rtab, c->rec_ix, c->rec_iy, c->n_rec, (const double2 *)u_dev,
+                             (const double2 *)c->jfac, nrhs, c->nx, c->ny, c->nz, pol[0], pol[1], pol[2], pol[3],
+                             in.en, in.hn, (double2 *)f_dev, c->stream);
+  IE_CUDA(cudaGetLastError());
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
+ie_status ie_mt_misfit(ie_ctx *c, const void *f_dev, const void *zobs_dev, void *z_dev, double *phi_host,
+                       void *c_dev) {
+  if (!c || !f_dev || !zobs_dev || !z_dev || !phi_host || !c_dev || c->n_rec == 0) return IE_ERR_ARG;
+  ie::launch_mt_misfit((const double2 *)f_dev, (const double2 *)zobs_dev, c->n_rec, (double2 *)z_dev, c->phi_r,
+                       (double2 *)c_dev, c->stream);
+  IE_CUDA(cudaGetLastError());
+  std::vector<double> ph(c->n_rec);
+  IE_CUDA(cudaMemcpyAsync(ph.data(), c->phi_r, ph.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  double acc = 0.0;
+  for (double v : ph) acc += v;
+  *phi_host = acc;
+  return IE_OK;
+}
+
+ie_status ie_receiver_adjoint(ie_ctx *c, int inst, const void *c_dev, int nrhs, void *rhs_dev) {
+  if (!c || !c_dev || !rhs_dev || inst < 0 || inst >= (int)c->inst.size() || nrhs < 1 || nrhs > 4)
+    return IE_ERR_ARG;
+  if (c->n_rec == 0 || !c->inst[inst].rtab) return IE_ERR_ARG;
+  ie::launch_receiver_adjoint(c->inst[inst].rtab, c->rec_ix, c->rec_iy, c->n_rec, (const double2 *)c_dev,
+                              (const double2 *)c->jfac, nrhs, c->nx, c->ny, c->nz, (double2 *)rhs_dev, c->stream);
+  IE_CUDA(cudaGetLastError());
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
+ie_status ie_gradient_accumulate(ie_ctx *c, const void *u_dev, const void *w_dev, int nrhs, void *grad_dev) {
+  if (!c || !u_dev || !w_dev || !grad_dev || nrhs < 1 || nrhs > 4) return IE_ERR_ARG;
+  ie::launch_gradient_accumulate((const double2 *)u_dev, (const double2 *)w_dev, (const double2 *)c->gdiv, nrhs,
+                                 c->ncell(), (double *)grad_dev, c->stream);
+  IE_CUDA(cudaGetLastError());
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  return IE_OK;
 }
 
 ie_status ie_rhs_mt(ie_ctx *c, int inst, int pol, void *u0) {

@@ -20,7 +20,8 @@ IE_ERR_SCRATCH = -6
 IE_C64, IE_C128 = 0, 1
 IE_FP64, IE_MIXED = 0, 1
 
-EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_rhs_mt", "ie_ctx_stream",
+EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_rhs_mt", "ie_set_sigma", "ie_set_receivers",
+           "ie_receiver_fields", "ie_mt_misfit", "ie_receiver_adjoint", "ie_gradient_accumulate", "ie_ctx_stream",
            "ie_ctx_device_bytes", "ie_profile", "ie_profile_read", "ie_profile_matvec", "ie_kernel_launches",
            "ie_destroy", "ie_status_str")
 
@@ -80,6 +81,18 @@ def load(path: str = LIB_PATH):
     lib.ie_adjoint_solve.restype = I
     lib.ie_rhs_mt.argtypes = [VP, I, I, VP]
     lib.ie_rhs_mt.restype = I
+    lib.ie_set_sigma.argtypes = [VP, VP]
+    lib.ie_set_sigma.restype = I
+    lib.ie_set_receivers.argtypes = [VP, I, VP, VP, D]
+    lib.ie_set_receivers.restype = I
+    lib.ie_receiver_fields.argtypes = [VP, I, VP, I, VP, VP]
+    lib.ie_receiver_fields.restype = I
+    lib.ie_mt_misfit.argtypes = [VP, VP, VP, VP, P(D), VP]
+    lib.ie_mt_misfit.restype = I
+    lib.ie_receiver_adjoint.argtypes = [VP, I, VP, I, VP]
+    lib.ie_receiver_adjoint.restype = I
+    lib.ie_gradient_accumulate.argtypes = [VP, VP, VP, I, VP]
+    lib.ie_gradient_accumulate.restype = I
     lib.ie_ctx_stream.argtypes = [VP]
     lib.ie_ctx_stream.restype = VP
     lib.ie_ctx_device_bytes.argtypes = [VP]
@@ -178,6 +191,7 @@ class Context:
         self.grid = grid
         self.max_rhs = max_rhs
         self.n_unknowns = 3 * grid.nx * grid.ny * grid.nz
+        self.n_instances = len(fr)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -224,3 +238,32 @@ class Context:
 
     def rhs_mt(self, inst, pol, u0_ptr):
         _check(self._lib.ie_rhs_mt(self.ctx, inst, pol, u0_ptr), "ie_rhs_mt")
+
+    def set_sigma(self, sigma_a):
+        """New anomaly conductivities [Nz][Ny][Nx] (complex) without new coefficients."""
+        sa = _cplx_pairs(np.asarray(sigma_a).reshape(-1))
+        _check(self._lib.ie_set_sigma(self.ctx, _dptr(sa)), "ie_set_sigma")
+
+    def set_receivers(self, ix, iy, z_rec=0.0):
+        ix = np.ascontiguousarray(np.asarray(ix, dtype=np.int32))
+        iy = np.ascontiguousarray(np.asarray(iy, dtype=np.int32))
+        if ix.shape != iy.shape:
+            raise ValueError("ix and iy differ in length")
+        _check(self._lib.ie_set_receivers(self.ctx, int(ix.size), ix.ctypes.data, iy.ctypes.data, float(z_rec)),
+               "ie_set_receivers")
+        self.n_rec = int(ix.size)
+
+    def receiver_fields(self, inst, u_ptr, nrhs, pols, f_ptr):
+        pa = np.ascontiguousarray(np.asarray(pols, dtype=np.int32))
+        _check(self._lib.ie_receiver_fields(self.ctx, inst, u_ptr, nrhs, pa.ctypes.data, f_ptr), "ie_receiver_fields")
+
+    def mt_misfit(self, f_ptr, zobs_ptr, z_ptr, c_ptr):
+        phi = ctypes.c_double()
+        _check(self._lib.ie_mt_misfit(self.ctx, f_ptr, zobs_ptr, z_ptr, ctypes.byref(phi), c_ptr), "ie_mt_misfit")
+        return phi.value
+
+    def receiver_adjoint(self, inst, c_ptr, nrhs, rhs_ptr):
+        _check(self._lib.ie_receiver_adjoint(self.ctx, inst, c_ptr, nrhs, rhs_ptr), "ie_receiver_adjoint")
+
+    def gradient_accumulate(self, u_ptr, w_ptr, nrhs, grad_ptr):
+        _check(self._lib.ie_gradient_accumulate(self.ctx, u_ptr, w_ptr, nrhs, grad_ptr), "ie_gradient_accumulate")
