@@ -80,6 +80,8 @@ typedef struct {
   int max_iter;      /* cap on inner iterations per solve; 0 selects 2000 */
   double inner_tol;  /* mixed precision: relative tolerance of each inner c64 solve; 0 selects 1e-3 */
   int max_outer;     /* mixed precision: cap on refinement steps; 0 selects 50 */
+  int autotune;      /* 0 or 1: time the c64 contraction variants at set-up and keep the
+                        fastest per right-hand-side count; -1: built-in choice */
 } ie_options;
 
 typedef struct {
@@ -98,7 +100,9 @@ typedef struct {
  *                  offsets i in [0,Ny), j in [0,Nx); the storage of eq. (matrix_symm)),
  *                  i.e. the 3x3 blocks B_n^m of Appendix A; or NULL, in which case the
  *                  library generates them on the device (ie_generate_coefficients).
- *   max_rhs      : largest number of right-hand sides passed to one call (1..4).
+ *   max_rhs      : largest number of right-hand sides passed to one call (1..16); a
+ *                  product (ie_matvec) or a per-instance block of a batched solve takes
+ *                  at most 4.
  * The tensors are transformed on the device (2N-periodic embedding with the
  * parities of Lemma 2, 2-D DFT) and kept in c128 and c64. */
 ie_status ie_setup(const ie_grid *grid, const ie_layers *layers, const double *sigma_a_host, int n_freq,
@@ -159,6 +163,27 @@ ie_status ie_matvec(ie_ctx *ctx, int inst, const void *x_dev, void *y_dev, int n
  * read from u_dev, otherwise it is zero. */
 ie_status ie_solve(ie_ctx *ctx, int inst, const void *b_dev, void *u_dev, int nrhs, double tol, int precision,
                    int use_x0, ie_solve_info *info);
+
+/* Solve the systems of n_inst instances together (a batch over frequencies of one
+ * grid): instance inst_host[k] with nrhs right-hand sides (1..4) at block k of
+ * b_dev, u_dev (c128 [n_inst][nrhs][3][Nz][Ny][Nx]); n_inst * nrhs <= max_rhs.  One
+ * restarted GMRES advances every right-hand side in lockstep, each in its own Krylov
+ * space; every product runs the FFT passes once for all of them and one contraction
+ * per instance on its slice of the spectrum.  transpose = 1 solves A^T w = b.
+ * Otherwise as ie_solve (info: worst residual over all right-hand sides). */
+ie_status ie_solve_batch(ie_ctx *ctx, int n_inst, const int *inst_host, const void *b_dev, void *u_dev, int nrhs,
+                         double tol, int precision, int use_x0, int transpose, ie_solve_info *info);
+
+/* Contraction variants (no counterpart in the paper): 0 the TMA ring with one slot and
+ * two CTAs per SM, 1 the TMA ring with three slots and one CTA per SM (both c64,
+ * Nz in {16, 24, 32, 48}, 1-2 right-hand sides), 2 the panel-staged kernel (any case).
+ * ie_contract_tuning reports the c64 variant used for 1..4 right-hand sides per
+ * instance (variant_host[4]; -1: built-in choice) and the autotuner's timings
+ * (ms_host[4][3], ms per launch, 0 where not timed; may be NULL).
+ * ie_set_contract_variant overrides the choice for one right-hand-side count
+ * (-1: built-in choice); IE_ERR_ARG if the variant does not apply to this grid. */
+ie_status ie_contract_tuning(ie_ctx *ctx, int *variant_host, double *ms_host);
+ie_status ie_set_contract_variant(ie_ctx *ctx, int nrhs, int variant);
 
 /* Solve the transposed system A^T w = b (same arguments as ie_solve).  The
  * transpose uses the complex symmetry B^T = B of Lorentz reciprocity, so

@@ -42,7 +42,7 @@ __device__ __forceinline__ C<T> block_entry(const C<T> *__restrict__ q, int Nz, 
 // all panels in registers.
 template <typename T, int MAXC>
 __global__ void contract_kernel(C<T> *__restrict__ spec, const C<T> *__restrict__ qf, int Nx, int Ny, int Nz,
-                                int R, int PW) {
+                                int R, int PW, int ldz) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n3 = 3 * Nz;
   C<T> *X = reinterpret_cast<C<T> *>(smem_raw);  // [MAXC][3 Nz]
@@ -50,7 +50,7 @@ __global__ void contract_kernel(C<T> *__restrict__ spec, const C<T> *__restrict_
   const int ldp = PW + 1;
   const int kxb = blockIdx.x, kyb = blockIdx.y;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int CZ = R * n3;
+  const int CZ = ldz;
   const int P = Nz * (Nz + 1) / 2;
   const long long BS = 2LL * Nz * (2 * Nz + 1);
   const C<T> *q = qf + ((long long)kyb * (Nx + 1) + kxb) * BS;
@@ -110,7 +110,7 @@ __global__ void contract_kernel(C<T> *__restrict__ spec, const C<T> *__restrict_
 constexpr size_t kMaxSmem = 227 * 1024;
 
 template <typename T, int MAXC>
-int launch_t(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStream_t s) {
+int launch_t(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, cudaStream_t s) {
   const int n3 = 3 * Nz;
   if (n3 > 1024) return -1;
   const size_t e = sizeof(C<T>);
@@ -129,7 +129,7 @@ int launch_t(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStre
   const int threads = ((n3 + 31) / 32) * 32;
   dim3 grid(Nx + 1, Ny + 1);
   count_launches(1);
-  k<<<grid, threads, sm, s>>>(spec, qf, Nx, Ny, Nz, R, PW);
+  k<<<grid, threads, sm, s>>>(spec, qf, Nx, Ny, Nz, R, PW, ldz);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -147,7 +147,7 @@ int num_sms() {
 }
 
 template <int NZ, int R, int NS>
-bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int per_sm, cudaStream_t s) {
+bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int per_sm, cudaStream_t s) {
   using Cfg = ContractCfg<NZ, R, NS>;
   if (Cfg::SMEM > 227 * 1024) return false;
   auto k = contract_tma_kernel<NZ, R, NS>;
@@ -161,7 +161,7 @@ bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int per_sm, cudaStr
   const int want = per_sm * num_sms();
   const int grid = nf < want ? nf : want;
   count_launches(1);
-  k<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(spec, qf, Nx, Ny, err);
+  k<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(spec, qf, Nx, Ny, ldz, err);
   if (cudaPeekAtLastError() != cudaSuccess) {  // not launched: the caller falls back to the panel kernel
     cudaGetLastError();
     return false;
@@ -169,25 +169,32 @@ bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int per_sm, cudaStr
   return true;
 }
 
-// One ring slot per CTA and two CTAs per SM where they fit (the copy of the next
-// wavenumber overlaps the arithmetic of the current one, and the other CTA on the
-// SM covers the unpacking phase); otherwise one CTA per SM.
+// Ring variants: one slot per CTA and two CTAs per SM where they fit (the copy of the next
+// wavenumber overlaps the arithmetic of the current one, and the other CTA on the SM
+// covers the unpacking phase), or three slots and one CTA per SM.
 template <int NZ, int R>
-bool try_tma_stages(float2 *spec, const float2 *qf, int Nx, int Ny, cudaStream_t s) {
-  if (2 * ContractCfg<NZ, R, 1>::SMEM <= 227 * 1024) return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, 2, s);
-  return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, 1, s);
+bool try_tma_variant(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int variant, cudaStream_t s) {
+  if (variant == kContractTma1) {
+    if (2 * ContractCfg<NZ, R, 1>::SMEM <= 227 * 1024) return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, ldz, 2, s);
+    return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, ldz, 1, s);
+  }
+  if (variant == kContractTma3) return try_tma<NZ, R, 3>(spec, qf, Nx, Ny, ldz, 1, s);
+  return false;
 }
 
 template <int R>
-bool dispatch_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, cudaStream_t s) {
+bool dispatch_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, int variant, cudaStream_t s) {
   switch (Nz) {
-    case 16: return try_tma_stages<16, R>(spec, qf, Nx, Ny, s);
-    case 24: return try_tma_stages<24, R>(spec, qf, Nx, Ny, s);
-    case 32: return try_tma_stages<32, R>(spec, qf, Nx, Ny, s);
-    case 48: return try_tma_stages<48, R>(spec, qf, Nx, Ny, s);
+    case 16: return try_tma_variant<16, R>(spec, qf, Nx, Ny, ldz, variant, s);
+    case 24: return try_tma_variant<24, R>(spec, qf, Nx, Ny, ldz, variant, s);
+    case 32: return try_tma_variant<32, R>(spec, qf, Nx, Ny, ldz, variant, s);
+    case 48: return try_tma_variant<48, R>(spec, qf, Nx, Ny, ldz, variant, s);
     default: return false;
   }
 }
+
+template <int NZ, int R>
+bool tma3_fits() { return ContractCfg<NZ, R, 3>::SMEM <= 227 * 1024; }
 
 }  // namespace
 
@@ -200,21 +207,41 @@ int contract_take_error() {
   return h;
 }
 
-template <typename T>
-int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStream_t s) {
-  if constexpr (sizeof(T) == 4) {
-    if (contract_tma_enabled) {
-      if (R == 1 && dispatch_tma<1>(spec, qf, Nx, Ny, Nz, s)) return 0;
-      if (R == 2 && dispatch_tma<2>(spec, qf, Nx, Ny, Nz, s)) return 0;
+bool contract_variant_available(int variant, int Nz, int R, bool c64) {
+  if (variant == kContractPanel) return R >= 1 && R <= 4 && 3 * Nz <= 1024;
+  if (!c64 || R < 1 || R > 2 || !contract_tma_enabled) return false;
+  if (Nz != 16 && Nz != 24 && Nz != 32 && Nz != 48) return false;
+  if (variant == kContractTma1) return true;
+  if (variant == kContractTma3) {
+    switch (Nz) {
+      case 16: return R == 1 ? tma3_fits<16, 1>() : tma3_fits<16, 2>();
+      case 24: return R == 1 ? tma3_fits<24, 1>() : tma3_fits<24, 2>();
+      case 32: return R == 1 ? tma3_fits<32, 1>() : tma3_fits<32, 2>();
+      default: return R == 1 ? tma3_fits<48, 1>() : tma3_fits<48, 2>();
     }
   }
-  if (R <= 1) return launch_t<T, 4>(spec, qf, Nx, Ny, Nz, R, s);
-  if (R <= 2) return launch_t<T, 8>(spec, qf, Nx, Ny, Nz, R, s);
-  if (R <= 4) return launch_t<T, 16>(spec, qf, Nx, Ny, Nz, R, s);
+  return false;
+}
+
+template <typename T>
+int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant,
+                    cudaStream_t s) {
+  if (ldz < R * 3 * Nz) return -1;
+  if constexpr (sizeof(T) == 4) {
+    if (variant == kContractAuto) variant = contract_variant_available(kContractTma1, Nz, R, true) ? kContractTma1
+                                                                                                    : kContractPanel;
+    if ((variant == kContractTma1 || variant == kContractTma3) && contract_variant_available(variant, Nz, R, true)) {
+      if (R == 1 && dispatch_tma<1>(spec, qf, Nx, Ny, Nz, ldz, variant, s)) return 0;
+      if (R == 2 && dispatch_tma<2>(spec, qf, Nx, Ny, Nz, ldz, variant, s)) return 0;
+    }
+  }
+  if (R <= 1) return launch_t<T, 4>(spec, qf, Nx, Ny, Nz, R, ldz, s);
+  if (R <= 2) return launch_t<T, 8>(spec, qf, Nx, Ny, Nz, R, ldz, s);
+  if (R <= 4) return launch_t<T, 16>(spec, qf, Nx, Ny, Nz, R, ldz, s);
   return -1;
 }
 
-template int launch_contract<float>(float2 *, const float2 *, int, int, int, int, cudaStream_t);
-template int launch_contract<double>(double2 *, const double2 *, int, int, int, int, cudaStream_t);
+template int launch_contract<float>(float2 *, const float2 *, int, int, int, int, int, int, cudaStream_t);
+template int launch_contract<double>(double2 *, const double2 *, int, int, int, int, int, int, cudaStream_t);
 
 }  // namespace ie

@@ -3,10 +3,21 @@
 
 namespace ie {
 
-// Apply the folded spectral blocks in place to spec[2Ny][2Nx][R * 3Nz].
-// Returns -1 if R > 4, 3 Nz > 1024 or a launch fails (nothing is applied then).
+// Kernel variants of the contraction: the TMA ring with one slot and two CTAs per SM,
+// the ring with three slots and one CTA per SM (both c64, Nz in {16, 24, 32, 48},
+// R <= 2), and the panel-staged kernel (any precision and Nz with 3 Nz <= 1024).
+enum ContractVariant { kContractAuto = -1, kContractTma1 = 0, kContractTma3 = 1, kContractPanel = 2 };
+constexpr int kContractVariants = 3;
+bool contract_variant_available(int variant, int Nz, int R, bool c64);
+
+// Apply the folded spectral blocks in place to the R right-hand sides whose spectrum
+// vectors are spec[(ky 2Nx + kx) ldz + 0 .. R 3Nz) (ldz >= R 3Nz).  variant: one of
+// ContractVariant (kContractAuto: the TMA ring where it applies, else the panel kernel;
+// an unavailable variant falls back to the panel kernel).  Returns -1 if R > 4,
+// 3 Nz > 1024, ldz < R 3Nz or a launch fails (nothing is applied then).
 template <typename T>
-int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, cudaStream_t s);
+int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant,
+                    cudaStream_t s);
 
 // Use the TMA-pipelined kernel where it applies (c64, Nz in {16, 24, 32, 48}, R <= 2).
 extern bool contract_tma_enabled;

@@ -2,6 +2,8 @@
 // Sect. 3.3) for compile-time Nz and right-hand-side count.
 //
 // Each CTA walks folded wavenumbers w = blockIdx.x, blockIdx.x + gridDim.x, ...
+// The spectrum vector of a wavenumber is spec[(ky 2Nx + kx) ldz + 0 .. R 3Nz) (ldz >= R 3Nz:
+// several instances may share one spectrum, each with its own slice and coefficients).
 // The packed coefficient block of a wavenumber (2 Nz (2 Nz + 1) complex, contiguous)
 // and its up to four mirror spectrum vectors (R * 3 Nz complex each, contiguous) are
 // fetched by one thread with 1-D bulk TMA copies (cp.async.bulk) into a ring of
@@ -120,7 +122,7 @@ __device__ __forceinline__ Mirrors mirrors_of(int w, int Nx, int Ny) {
 
 template <int NZ, int R, int NSTAGE>
 __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
-    contract_tma_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int *err) {
+    contract_tma_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err) {
   using Cfg = ContractCfg<NZ, R, NSTAGE>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LD = Cfg::LD, MAXC = Cfg::MAXC;
   constexpr int CPT = Cfg::CPT;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
     tma::bulk_g2s(raw + (size_t)s * BS, qf + (size_t)w * BS, (uint32_t)Cfg::RAW_BYTES, &bar[s]);
     for (int m = 0; m < nm; ++m) {
       const int mx = m % mi.nmx, my = m / mi.nmx;
-      tma::bulk_g2s(xraw + (size_t)s * 4 * CZ + (size_t)m * CZ, spec + mi.pos(mx, my, Nx) * CZ, (uint32_t)(CZ * 8),
+      tma::bulk_g2s(xraw + (size_t)s * 4 * CZ + (size_t)m * CZ, spec + mi.pos(mx, my, Nx) * ldz, (uint32_t)(CZ * 8),
                     &bar[s]);
     }
   };
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
           const int mx = m % nmx, my = m / nmx;
           float2 v = upk(acc[c]);
           if ((alpha == 0 && mx == 1) || (alpha == 1 && my == 1)) { v.x = -v.x; v.y = -v.y; }
-          spec[mw.pos(mx, my, Nx) * CZ + r * N3 + row] = v;
+          spec[mw.pos(mx, my, Nx) * ldz + r * N3 + row] = v;
         }
       }
     }

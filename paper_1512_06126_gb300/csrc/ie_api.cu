@@ -53,6 +53,9 @@ struct ie_ctx {
   std::vector<int> lay;
   ie::FftPlan px{}, py{};
   int max_rhs = 1;
+  int cvar[5] = {-1, -1, -1, -1, -1};          // c64 contraction variant per right-hand sides per instance
+  double tune_ms[5][ie::kContractVariants] = {};  // autotuner timings (ms per launch, 0: not timed)
+  bool autotune = true;
   int restart = 30, max_iter = 2000, max_outer = 50;
   double inner_tol = 1e-3;
   std::vector<Instance> inst;
@@ -271,11 +274,42 @@ template <typename T> const ie::C<T> *qf(const Instance &in);
 template <> const double2 *qf<double>(const Instance &in) { return in.q64; }
 template <> const float2 *qf<float>(const Instance &in) { return in.q32; }
 
+// The right-hand sides of one product: n blocks of rpi right-hand sides, block k with
+// the coefficients of instance inst[k] (layout [n][rpi][3][Nz][Ny][Nx]).  The
+// diagonal scalings do not depend on the frequency, so all blocks share the row
+// passes; each block gets its own contraction on its slice of the spectrum.
+struct Group {
+  std::vector<int> inst;
+  int rpi = 1;
+  int R() const { return (int)inst.size() * rpi; }
+};
+
 template <typename T>
-ie_status apply(ie_ctx *c, int inst, const ie::C<T> *x, ie::C<T> *y, int R, int transpose, cudaStream_t s) {
+ie_status contract_group(ie_ctx *c, const Group &g, ie::C<T> *spec, cudaStream_t s) {
+  const int CZ = g.R() * 3 * c->nz;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (c->prof) {
+    cudaEventCreate(&ea);
+    cudaEventCreate(&eb);
+    cudaEventRecord(ea, s);
+  }
+  const int variant = sizeof(T) == 4 ? c->cvar[g.rpi] : ie::kContractPanel;
+  for (size_t k = 0; k < g.inst.size(); ++k)
+    if (ie::launch_contract<T>(spec + k * (size_t)g.rpi * 3 * c->nz, qf<T>(c->inst[g.inst[k]]), c->nx, c->ny, c->nz,
+                               g.rpi, CZ, variant, s) != 0)
+      return IE_ERR_CUDA;
+  if (c->prof) {
+    cudaEventRecord(eb, s);
+    c->prof_rec.push_back({ea, eb, sizeof(T) == 8 ? IE_C128 : IE_C64});
+  }
+  return IE_OK;
+}
+
+template <typename T>
+ie_status apply(ie_ctx *c, const Group &g, const ie::C<T> *x, ie::C<T> *y, int transpose, cudaStream_t s) {
   using V = ie::C<T>;
   const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
-  const int CZ = R * 3 * Nz;
+  const int CZ = g.R() * 3 * Nz;
   const DiagSet &D = diags<T>(c);
   const V *in_s = (const V *)(transpose ? D.in_t : D.in_f);
   const V *out_s = (const V *)(transpose ? D.out_t : D.out_f);
@@ -284,17 +318,7 @@ ie_status apply(ie_ctx *c, int inst, const ie::C<T> *x, ie::C<T> *y, int R, int 
   V *spec = (V *)c->spec;
   ie::launch_fft_rows_fwd<T>(x, in_s, t1, CZ, Nz, Ny, Nx, c->px, s);
   ie::launch_fft_axis<T, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, (T)1, s);
-  cudaEvent_t ea = nullptr, eb = nullptr;
-  if (c->prof) {
-    cudaEventCreate(&ea);
-    cudaEventCreate(&eb);
-    cudaEventRecord(ea, s);
-  }
-  if (ie::launch_contract<T>(spec, qf<T>(c->inst[inst]), Nx, Ny, Nz, R, s) != 0) return IE_ERR_CUDA;
-  if (c->prof) {
-    cudaEventRecord(eb, s);
-    c->prof_rec.push_back({ea, eb, sizeof(T) == 8 ? IE_C128 : IE_C64});
-  }
+  IE_TRY(contract_group<T>(c, g, spec, s));
   ie::launch_fft_axis<T, true>(spec, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, (T)1, s);
   ie::launch_fft_rows_inv<T>(t1, x, dg, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
   return cuda_status(cudaGetLastError());
@@ -303,9 +327,9 @@ ie_status apply(ie_ctx *c, int inst, const ie::C<T> *x, ie::C<T> *y, int R, int 
 // c64 product on FP64 vectors: the row passes read and write FP64 (rounding the scaled
 // input to FP32 on load; the diagonal term and the output in FP64), the FFTs and the
 // contraction run in FP32.
-ie_status apply_mixed(ie_ctx *c, int inst, const double2 *x, double2 *y, int R, int transpose, cudaStream_t s) {
+ie_status apply_mixed(ie_ctx *c, const Group &g, const double2 *x, double2 *y, int transpose, cudaStream_t s) {
   const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
-  const int CZ = R * 3 * Nz;
+  const int CZ = g.R() * 3 * Nz;
   const DiagSet &D = c->d64;
   const double2 *in_s = (const double2 *)(transpose ? D.in_t : D.in_f);
   const double2 *out_s = (const double2 *)(transpose ? D.out_t : D.out_f);
@@ -313,17 +337,7 @@ ie_status apply_mixed(ie_ctx *c, int inst, const double2 *x, double2 *y, int R, 
   float2 *spec = (float2 *)c->spec;
   ie::launch_fft_rows_fwd<float, double>(x, in_s, t1, CZ, Nz, Ny, Nx, c->px, s);
   ie::launch_fft_axis<float, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
-  cudaEvent_t ea = nullptr, eb = nullptr;
-  if (c->prof) {
-    cudaEventCreate(&ea);
-    cudaEventCreate(&eb);
-    cudaEventRecord(ea, s);
-  }
-  if (ie::launch_contract<float>(spec, c->inst[inst].q32, Nx, Ny, Nz, R, s) != 0) return IE_ERR_CUDA;
-  if (c->prof) {
-    cudaEventRecord(eb, s);
-    c->prof_rec.push_back({ea, eb, IE_C64});
-  }
+  IE_TRY(contract_group<float>(c, g, spec, s));
   ie::launch_fft_axis<float, true>(spec, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
   ie::launch_fft_rows_inv<float, double>(t1, x, (const double2 *)D.diag, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
   return cuda_status(cudaGetLastError());
@@ -332,12 +346,13 @@ ie_status apply_mixed(ie_ctx *c, int inst, const double2 *x, double2 *y, int R, 
 // FP64-level operator used by the Krylov solver: c128 product, or the c64 product.
 struct Op {
   ie_ctx *c;
-  int inst;
+  const Group *g;
   int transpose;
   bool single;
   ie_status operator()(const double2 *x, double2 *y, int R) const {
-    if (!single) return apply<double>(c, inst, x, y, R, transpose, c->stream);
-    return apply_mixed(c, inst, x, y, R, transpose, c->stream);
+    if (R != g->R()) return IE_ERR_ARG;
+    if (!single) return apply<double>(c, *g, x, y, transpose, c->stream);
+    return apply_mixed(c, *g, x, y, transpose, c->stream);
   }
 };
 
@@ -462,10 +477,11 @@ ie_status gmres(ie_ctx *c, const Op &op, const double2 *b, double2 *x, int R, do
 }
 
 // max over right-hand sides of ||b - A128 u|| / ||b||; leaves the residual in c->r
-ie_status true_residual(ie_ctx *c, int inst, int transpose, const double2 *b, const double2 *u, int R,
+ie_status true_residual(ie_ctx *c, const Group &g, int transpose, const double2 *b, const double2 *u,
                         std::vector<double> &rel) {
   const long long n = c->nvec();
-  Op op{c, inst, transpose, false};
+  const int R = g.R();
+  Op op{c, &g, transpose, false};
   IE_TRY(op(u, c->r, R));
   ie::vec_sub(b, c->r, c->r, n * R, c->stream);
   std::vector<double> rn(R), bn(R);
@@ -479,10 +495,12 @@ ie_status true_residual(ie_ctx *c, int inst, int transpose, const double2 *b, co
   return IE_OK;
 }
 
-ie_status solve_impl(ie_ctx *c, int inst, const double2 *b, double2 *u, int R, double tol, int precision,
+ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, double tol, int precision,
                      int use_x0, int transpose, ie_solve_info *info) {
-  if (!c || !b || !u || inst < 0 || inst >= (int)c->inst.size() || R < 1 || R > c->max_rhs || !(tol > 0))
-    return IE_ERR_ARG;
+  const int R = g.R();
+  if (!c || !b || !u || g.inst.empty() || g.rpi < 1 || g.rpi > 4 || R > c->max_rhs || !(tol > 0)) return IE_ERR_ARG;
+  for (int k : g.inst)
+    if (k < 0 || k >= (int)c->inst.size()) return IE_ERR_ARG;
   if (precision != IE_FP64 && precision != IE_MIXED) return IE_ERR_ARG;
   const long long n = c->nvec();
   const auto t0 = std::chrono::steady_clock::now();
@@ -492,7 +510,7 @@ ie_status solve_impl(ie_ctx *c, int inst, const double2 *b, double2 *u, int R, d
   std::vector<double> rel;
   if (precision == IE_FP64) {
     GmresResult gr;
-    IE_TRY(gmres(c, Op{c, inst, transpose, false}, b, u, R, tol, c->max_iter, &gr));
+    IE_TRY(gmres(c, Op{c, &g, transpose, false}, b, u, R, tol, c->max_iter, &gr));
     inf.inner_iters = gr.iters;
     inf.outer_iters = gr.cycles;
     conv = gr.converged;
@@ -500,7 +518,7 @@ ie_status solve_impl(ie_ctx *c, int inst, const double2 *b, double2 *u, int R, d
   } else {
     int inner_total = 0;
     for (int outer = 0; outer <= c->max_outer; ++outer) {
-      IE_TRY(true_residual(c, inst, transpose, b, u, R, rel));
+      IE_TRY(true_residual(c, g, transpose, b, u, rel));
       inf.outer_iters = outer + 1;
       double worst = 0;
       for (double v : rel) worst = std::max(worst, v);
@@ -510,7 +528,7 @@ ie_status solve_impl(ie_ctx *c, int inst, const double2 *b, double2 *u, int R, d
       IE_CUDA(cudaMemsetAsync(c->dx, 0, n * R * sizeof(double2), c->stream));
       GmresResult gr;
       const double itol = std::max(c->inner_tol, 0.5 * tol / std::max(worst, 1e-300));
-      IE_TRY(gmres(c, Op{c, inst, transpose, true}, c->r, c->dx, R, std::min(itol, 0.5), c->max_iter - inner_total,
+      IE_TRY(gmres(c, Op{c, &g, transpose, true}, c->r, c->dx, R, std::min(itol, 0.5), c->max_iter - inner_total,
                    &gr));
       inner_total += gr.iters;
       brk = brk || gr.breakdown;
@@ -518,7 +536,7 @@ ie_status solve_impl(ie_ctx *c, int inst, const double2 *b, double2 *u, int R, d
     }
     inf.inner_iters = inner_total;
   }
-  IE_TRY(true_residual(c, inst, transpose, b, u, R, rel));
+  IE_TRY(true_residual(c, g, transpose, b, u, rel));
   double worst = 0;
   for (double v : rel) worst = std::max(worst, v);
   inf.final_rel_res = worst;
@@ -663,7 +681,8 @@ ie_status ie_profile_read(ie_ctx *c, int dtype, double *total_ms, long long *n_l
 }
 
 ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter, double *ms_out) {
-  if (!c || !ms_out || inst < 0 || inst >= (int)c->inst.size() || nrhs < 1 || nrhs > c->max_rhs || n_iter < 1)
+  if (!c || !ms_out || inst < 0 || inst >= (int)c->inst.size() || nrhs < 1 || nrhs > std::min(4, c->max_rhs) ||
+      n_iter < 1)
     return IE_ERR_ARG;
   if (dtype != IE_C64 && dtype != IE_C128) return IE_ERR_ARG;
   const int Nx = c->nx, Ny = c->ny, Nz = c->nz, CZ = nrhs * 3 * Nz;
@@ -681,7 +700,7 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
       cudaEventRecord(ev[1], s);
       ie::launch_fft_axis<double, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0, s);
       cudaEventRecord(ev[2], s);
-      bad |= ie::launch_contract<double>(sp, c->inst[inst].q64, Nx, Ny, Nz, nrhs, s);
+      bad |= ie::launch_contract<double>(sp, c->inst[inst].q64, Nx, Ny, Nz, nrhs, CZ, ie::kContractPanel, s);
       cudaEventRecord(ev[3], s);
       ie::launch_fft_axis<double, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0, s);
       cudaEventRecord(ev[4], s);
@@ -696,7 +715,7 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
       cudaEventRecord(ev[1], s);
       ie::launch_fft_axis<float, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[2], s);
-      bad |= ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, s);
+      bad |= ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, CZ, c->cvar[nrhs], s);
       cudaEventRecord(ev[3], s);
       ie::launch_fft_axis<float, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[4], s);
@@ -717,6 +736,48 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
   return bad ? IE_ERR_CUDA : st;
 }
 long long ie_ctx_device_bytes(ie_ctx *c) { return c ? c->dev_bytes : 0; }
+
+// Autotuner: time every contraction variant that applies to this grid (c64, one and two
+// right-hand sides per instance) on the context's own coefficients and workspaces, and
+// keep the fastest.  The spectrum workspace is zeroed first; the values do not change
+// the work.
+ie_status autotune_contraction(ie_ctx *c) {
+  const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
+  cudaEvent_t e0, e1;
+  IE_CUDA(cudaEventCreate(&e0));
+  IE_CUDA(cudaEventCreate(&e1));
+  ie_status st = IE_OK;
+  for (int rpi = 1; rpi <= std::min(2, c->max_rhs) && st == IE_OK; ++rpi) {
+    const int CZ = rpi * 3 * Nz;
+    float2 *spec = (float2 *)c->spec;
+    cudaMemsetAsync(spec, 0, (size_t)4 * Nx * Ny * CZ * sizeof(float2), c->stream);
+    int best = ie::kContractPanel;
+    double best_ms = 1e300;
+    int n_avail = 0;
+    for (int v = 0; v < ie::kContractVariants; ++v)
+      if (ie::contract_variant_available(v, Nz, rpi, true)) ++n_avail;
+    for (int v = 0; v < ie::kContractVariants && n_avail > 1; ++v) {
+      if (!ie::contract_variant_available(v, Nz, rpi, true)) continue;
+      bool ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->stream) == 0;
+      cudaEventRecord(e0, c->stream);
+      for (int k = 0; k < 3 && ok; ++k)
+        ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->stream) == 0;
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = IE_ERR_CUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (!ok || ie::contract_take_error() != 0) continue;
+      c->tune_ms[rpi][v] = ms / 3.0;
+      if (ms / 3.0 < best_ms) { best_ms = ms / 3.0; best = v; }
+    }
+    if (n_avail == 1) best = ie::kContractPanel;
+    if (n_avail > 1 || ie::contract_variant_available(ie::kContractPanel, Nz, rpi, true)) c->cvar[rpi] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == IE_OK) st = cuda_status(cudaGetLastError());
+  return st;
+}
 
 static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double *sigma_a, int n_freq,
                             const double *freq, const double *q_real, int max_rhs, const ie_options *opt,
@@ -747,6 +808,7 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
     if (opt->max_iter > 0) c->max_iter = opt->max_iter;
     if (opt->inner_tol > 0) c->inner_tol = opt->inner_tol;
     if (opt->max_outer > 0) c->max_outer = opt->max_outer;
+    if (opt->autotune < 0) c->autotune = false;
   }
   if (c->restart < 2) return IE_ERR_ARG;
   try {
@@ -783,6 +845,7 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   IE_TRY(dalloc(c, &c->gsflag, (size_t)max_rhs * sizeof(int)));
   IE_TRY(dalloc(c, &c->nrm, (size_t)2 * max_rhs * sizeof(double)));
   IE_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->autotune) IE_TRY(autotune_contraction(c));
   return IE_OK;
 }
 
@@ -790,7 +853,7 @@ ie_status ie_setup(const ie_grid *g, const ie_layers *lay, const double *sigma_a
                    const double *q_real, int max_rhs, const ie_options *opt, ie_ctx **out) {
   if (!out) return IE_ERR_ARG;
   *out = nullptr;
-  if (!g || !lay || !sigma_a || !freq || n_freq < 1 || max_rhs < 1 || max_rhs > 4) return IE_ERR_ARG;
+  if (!g || !lay || !sigma_a || !freq || n_freq < 1 || max_rhs < 1 || max_rhs > 16) return IE_ERR_ARG;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->hx > 0) || !(g->hy > 0) || !g->z_edges_host) return IE_ERR_ARG;
   if (lay->n_interfaces < 1 || !lay->interfaces_host || !lay->sigma_host) return IE_ERR_ARG;
   ie_ctx *c = new (std::nothrow) ie_ctx();
@@ -805,23 +868,59 @@ ie_status ie_setup(const ie_grid *g, const ie_layers *lay, const double *sigma_a
 }
 
 ie_status ie_matvec(ie_ctx *c, int inst, const void *x, void *y, int nrhs, int dtype, int transpose, void *stream) {
-  if (!c || !x || !y || x == y || inst < 0 || inst >= (int)c->inst.size() || nrhs < 1 || nrhs > c->max_rhs)
+  if (!c || !x || !y || x == y || inst < 0 || inst >= (int)c->inst.size() || nrhs < 1 ||
+      nrhs > std::min(4, c->max_rhs))
     return IE_ERR_ARG;
   cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
   transpose = transpose ? 1 : 0;
-  if (dtype == IE_C128) return apply<double>(c, inst, (const double2 *)x, (double2 *)y, nrhs, transpose, s);
-  if (dtype == IE_C64) return apply<float>(c, inst, (const float2 *)x, (float2 *)y, nrhs, transpose, s);
+  Group g;
+  g.inst = {inst};
+  g.rpi = nrhs;
+  if (dtype == IE_C128) return apply<double>(c, g, (const double2 *)x, (double2 *)y, transpose, s);
+  if (dtype == IE_C64) return apply<float>(c, g, (const float2 *)x, (float2 *)y, transpose, s);
   return IE_ERR_ARG;
 }
 
 ie_status ie_solve(ie_ctx *c, int inst, const void *b, void *u, int nrhs, double tol, int precision, int use_x0,
                    ie_solve_info *info) {
-  return solve_impl(c, inst, (const double2 *)b, (double2 *)u, nrhs, tol, precision, use_x0, 0, info);
+  Group g;
+  g.inst = {inst};
+  g.rpi = nrhs;
+  return solve_impl(c, g, (const double2 *)b, (double2 *)u, tol, precision, use_x0, 0, info);
 }
 
 ie_status ie_adjoint_solve(ie_ctx *c, int inst, const void *b, void *w, int nrhs, double tol, int precision,
                            int use_x0, ie_solve_info *info) {
-  return solve_impl(c, inst, (const double2 *)b, (double2 *)w, nrhs, tol, precision, use_x0, 1, info);
+  Group g;
+  g.inst = {inst};
+  g.rpi = nrhs;
+  return solve_impl(c, g, (const double2 *)b, (double2 *)w, tol, precision, use_x0, 1, info);
+}
+
+ie_status ie_solve_batch(ie_ctx *c, int n_inst, const int *inst_host, const void *b, void *u, int nrhs, double tol,
+                         int precision, int use_x0, int transpose, ie_solve_info *info) {
+  if (!c || n_inst < 1 || !inst_host) return IE_ERR_ARG;
+  Group g;
+  g.inst.assign(inst_host, inst_host + n_inst);
+  g.rpi = nrhs;
+  return solve_impl(c, g, (const double2 *)b, (double2 *)u, tol, precision, use_x0, transpose ? 1 : 0, info);
+}
+
+ie_status ie_contract_tuning(ie_ctx *c, int *variant_host, double *ms_host) {
+  if (!c || !variant_host) return IE_ERR_ARG;
+  for (int r = 1; r <= 4; ++r) {
+    variant_host[r - 1] = c->cvar[r];
+    if (ms_host)
+      for (int v = 0; v < ie::kContractVariants; ++v) ms_host[(r - 1) * ie::kContractVariants + v] = c->tune_ms[r][v];
+  }
+  return IE_OK;
+}
+
+ie_status ie_set_contract_variant(ie_ctx *c, int nrhs, int variant) {
+  if (!c || nrhs < 1 || nrhs > 4 || variant < -1 || variant >= ie::kContractVariants) return IE_ERR_ARG;
+  if (variant >= 0 && !ie::contract_variant_available(variant, c->nz, nrhs, true)) return IE_ERR_ARG;
+  c->cvar[nrhs] = variant;
+  return IE_OK;
 }
 
 ie_status ie_set_sigma(ie_ctx *c, const double *sigma_a_host) {

@@ -82,7 +82,8 @@ extern "C" ie_status ie_matvec_noalloc(int nx, int ny, int nz, int nrhs, const v
   // same call, so nothing left over from a previous call is ever read.
   ie::launch_fft_rows_fwd<float>(x, static_cast<const float2 *>(in_scale_dev), t1, (int)cz, nz, ny, nx, px, s);
   ie::launch_fft_axis<float, false>(t1, spec, 1, ny, 2 * ny, 2LL * nx * cz, py, 1.0f, s);
-  if (ie::launch_contract<float>(spec, static_cast<const float2 *>(qf_dev), nx, ny, nz, nrhs, s) != 0)
+  if (ie::launch_contract<float>(spec, static_cast<const float2 *>(qf_dev), nx, ny, nz, nrhs, (int)cz,
+                                ie::kContractAuto, s) != 0)
     return IE_ERR_CUDA;
   ie::launch_fft_axis<float, true>(spec, t1, 1, 2 * ny, ny, 2LL * nx * cz, py, 1.0f, s);
   ie::launch_fft_rows_inv<float>(t1, x, static_cast<const float2 *>(diag_dev),

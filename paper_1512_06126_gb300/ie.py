@@ -20,7 +20,8 @@ IE_ERR_SCRATCH = -6
 IE_C64, IE_C128 = 0, 1
 IE_FP64, IE_MIXED = 0, 1
 
-EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_rhs_mt", "ie_set_sigma", "ie_set_receivers",
+EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_solve_batch",
+           "ie_contract_tuning", "ie_set_contract_variant", "ie_rhs_mt", "ie_set_sigma", "ie_set_receivers",
            "ie_receiver_fields", "ie_mt_misfit", "ie_receiver_adjoint", "ie_gradient_accumulate", "ie_ctx_stream",
            "ie_ctx_device_bytes", "ie_profile", "ie_profile_read", "ie_profile_matvec", "ie_kernel_launches",
            "ie_destroy", "ie_status_str")
@@ -41,7 +42,7 @@ class ie_layers(ctypes.Structure):
 
 class ie_options(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class ie_solve_info(ctypes.Structure):
@@ -81,6 +82,12 @@ def load(path: str = LIB_PATH):
     lib.ie_adjoint_solve.restype = I
     lib.ie_rhs_mt.argtypes = [VP, I, I, VP]
     lib.ie_rhs_mt.restype = I
+    lib.ie_solve_batch.argtypes = [VP, I, VP, VP, VP, I, D, I, I, I, P(ie_solve_info)]
+    lib.ie_solve_batch.restype = I
+    lib.ie_contract_tuning.argtypes = [VP, VP, VP]
+    lib.ie_contract_tuning.restype = I
+    lib.ie_set_contract_variant.argtypes = [VP, I, I]
+    lib.ie_set_contract_variant.restype = I
     lib.ie_set_sigma.argtypes = [VP, VP]
     lib.ie_set_sigma.restype = I
     lib.ie_set_receivers.argtypes = [VP, I, VP, VP, D]
@@ -166,7 +173,7 @@ class Context:
     generate them on the device."""
 
     def __init__(self, grid, layers, sigma_a, freqs, q_real, max_rhs=2, restart=30, max_iter=2000,
-                 inner_tol=1e-3, max_outer=50):
+                 inner_tol=1e-3, max_outer=50, autotune=True):
         lib = load()
         self._lib = lib
         self._keep = []
@@ -181,7 +188,7 @@ class Context:
             q = None
         else:
             q = _cplx_pairs(np.stack([np.asarray(x, dtype=np.complex128) for x in q_real]).reshape(-1))
-        opt = ie_options(restart, max_iter, inner_tol, max_outer)
+        opt = ie_options(restart, max_iter, inner_tol, max_outer, 1 if autotune else -1)
         ctx = ctypes.c_void_p()
         s = lib.ie_setup(ctypes.byref(g), ctypes.byref(lay), _dptr(sa), len(fr), _dptr(fr),
                          None if q is None else _dptr(q), max_rhs,
@@ -221,6 +228,25 @@ class Context:
         s = fn(self.ctx, inst, b_ptr, u_ptr, nrhs, tol, precision, int(bool(use_x0)), ctypes.byref(info))
         _check(s, "ie_adjoint_solve" if adjoint else "ie_solve", ok=(IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN))
         return s, info
+
+    def solve_batch(self, insts, b_ptr, u_ptr, nrhs, tol, precision=IE_FP64, use_x0=False, adjoint=False):
+        """Solve the instances ``insts`` together (vectors [len(insts)][nrhs][3][Nz][Ny][Nx])."""
+        ia = np.ascontiguousarray(np.asarray(insts, dtype=np.int32))
+        info = ie_solve_info()
+        s = self._lib.ie_solve_batch(self.ctx, int(ia.size), ia.ctypes.data, b_ptr, u_ptr, nrhs, tol, precision,
+                                     int(bool(use_x0)), int(bool(adjoint)), ctypes.byref(info))
+        _check(s, "ie_solve_batch", ok=(IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN))
+        return s, info
+
+    def contract_tuning(self):
+        """(variants for 1..4 right-hand sides per instance, autotuner ms [4][3])."""
+        v = np.zeros(4, dtype=np.int32)
+        ms = np.zeros((4, 3), dtype=np.float64)
+        _check(self._lib.ie_contract_tuning(self.ctx, v.ctypes.data, ms.ctypes.data), "ie_contract_tuning")
+        return v, ms
+
+    def set_contract_variant(self, nrhs, variant):
+        _check(self._lib.ie_set_contract_variant(self.ctx, nrhs, variant), "ie_set_contract_variant")
 
     def profile(self, enable):
         _check(self._lib.ie_profile(self.ctx, int(bool(enable))), "ie_profile")
