@@ -2,6 +2,7 @@
 // transpose between the vector layout [cz][y][x] and the wavenumber-major
 // layout [y][kx][cz] (cz = rhs * 3Nz + component * Nz + z).
 #include "fft.cuh"
+#include "fft_fast.cuh"
 
 #include <stdexcept>
 
@@ -155,11 +156,51 @@ template <typename K> void set_smem(K kern, size_t bytes) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Register-blocked FP32 kernels for L = 16 Q, Q in {8, 16, 32} (0: not applicable).
+int fast_q(int L) { return (L == 128 || L == 256 || L == 512) ? L / 16 : 0; }
+
+template <int Q, bool INV>
+void axis_fast(const float2 *in, float2 *out, int outer, int Lin, int Lout, long long inner, float scale,
+               cudaStream_t s) {
+  auto k = fftfast::axis_kernel<Q, INV>;
+  set_smem(k, fftfast::smem_bytes(Q));
+  dim3 grid((unsigned)((inner + fftfast::kTI - 1) / fftfast::kTI), (unsigned)outer);
+  k<<<grid, fftfast::threads(Q), fftfast::smem_bytes(Q), s>>>(in, out, Lin, Lout, inner, scale);
+}
+
+template <int Q, typename TX>
+void rows_fwd_fast(const C<TX> *x, const C<TX> *in_scale, float2 *t1, int CZ, int Nz, int Ny, int Nx,
+                   cudaStream_t s) {
+  auto k = fftfast::rows_fwd_kernel<Q, TX>;
+  set_smem(k, fftfast::smem_bytes(Q));
+  dim3 grid((unsigned)((CZ + fftfast::kTI - 1) / fftfast::kTI), (unsigned)Ny);
+  k<<<grid, fftfast::threads(Q), fftfast::smem_bytes(Q), s>>>(x, in_scale, t1, CZ, Nz, Ny, Nx);
+}
+
+template <int Q, typename TX>
+void rows_inv_fast(const float2 *t1, const C<TX> *x, const C<TX> *diag, const C<TX> *out_scale, C<TX> *y, int CZ,
+                   int Nz, int Ny, int Nx, cudaStream_t s) {
+  auto k = fftfast::rows_inv_kernel<Q, TX>;
+  set_smem(k, fftfast::smem_bytes(Q));
+  dim3 grid((unsigned)((CZ + fftfast::kTI - 1) / fftfast::kTI), (unsigned)Ny);
+  k<<<grid, fftfast::threads(Q), fftfast::smem_bytes(Q), s>>>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx);
+}
+
 }  // namespace
 
 template <typename T, bool INV>
 void launch_fft_axis(const C<T> *in, C<T> *out, int outer, int Lin, int Lout, long long inner,
                      const FftPlan &plan, T scale, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    const int q = fast_q(plan.L);
+    if (q) {
+      count_launches(1);
+      if (q == 8) axis_fast<8, INV>(in, out, outer, Lin, Lout, inner, scale, s);
+      else if (q == 16) axis_fast<16, INV>(in, out, outer, Lin, Lout, inner, scale, s);
+      else axis_fast<32, INV>(in, out, outer, Lin, Lout, inner, scale, s);
+      return;
+    }
+  }
   constexpr int TI = fft_ti<T>();
   const size_t sm = axis_smem<T>(plan.L);
   auto k = fft_axis_kernel<T, INV>;
@@ -172,6 +213,16 @@ void launch_fft_axis(const C<T> *in, C<T> *out, int outer, int Lin, int Lout, lo
 template <typename T, typename TX>
 void launch_fft_rows_fwd(const C<TX> *x, const C<TX> *in_scale, C<T> *t1, int CZ, int Nz, int Ny, int Nx,
                          const FftPlan &plan, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    const int q = fast_q(plan.L);
+    if (q && plan.L == 2 * Nx) {
+      count_launches(1);
+      if (q == 8) rows_fwd_fast<8, TX>(x, in_scale, t1, CZ, Nz, Ny, Nx, s);
+      else if (q == 16) rows_fwd_fast<16, TX>(x, in_scale, t1, CZ, Nz, Ny, Nx, s);
+      else rows_fwd_fast<32, TX>(x, in_scale, t1, CZ, Nz, Ny, Nx, s);
+      return;
+    }
+  }
   constexpr int TI = fft_ti<T>();
   const size_t sm = rows_smem<T>(plan.L);
   auto k = fft_rows_fwd_kernel<T, TX>;
@@ -184,6 +235,16 @@ void launch_fft_rows_fwd(const C<TX> *x, const C<TX> *in_scale, C<T> *t1, int CZ
 template <typename T, typename TX>
 void launch_fft_rows_inv(const C<T> *t1, const C<TX> *x, const C<TX> *diag, const C<TX> *out_scale, C<TX> *y,
                          int CZ, int Nz, int Ny, int Nx, const FftPlan &plan, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    const int q = fast_q(plan.L);
+    if (q && plan.L == 2 * Nx) {
+      count_launches(1);
+      if (q == 8) rows_inv_fast<8, TX>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx, s);
+      else if (q == 16) rows_inv_fast<16, TX>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx, s);
+      else rows_inv_fast<32, TX>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx, s);
+      return;
+    }
+  }
   constexpr int TI = fft_ti<T>();
   const size_t sm = rows_smem<T>(plan.L);
   auto k = fft_rows_inv_kernel<T, TX>;

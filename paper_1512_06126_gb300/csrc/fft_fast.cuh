@@ -1,0 +1,252 @@
+// Register-blocked FP32 FFTs for transform lengths L = 16 Q, Q in {8, 16, 32}
+// (L = 128, 256, 512: the zero-padded lengths 2N of 64-, 128- and 256-cell grids).
+//
+// A length-L DFT is split as L = 16 x Q: with l = q + Q p and k = k1 + 16 k2,
+//   X[k1 + 16 k2] = sum_q w_Q^(q k2) w_L^(q k1) sum_p x[q + Q p] w_16^(p k1),
+// so one thread per (sequence, q) does a 16-point DFT in registers, multiplies by the
+// twiddles w_L^(q k1), and after one exchange through shared memory one thread per
+// (sequence, k1) does a Q-point DFT in registers.  TI = 16 sequences share a CTA and
+// sit in the lowest thread-index bits, so every global load or store of a half-warp
+// moves 16 consecutive elements of the sequence index (128 bytes).  The in-register
+// DFTs are radix-2 decimation in time, the input permutation resolved at compile time
+// by loading the inputs permuted; their twiddles and the w_L^(q k1) come from one table w_L^m per CTA.
+#pragma once
+#include "ie_common.cuh"
+
+namespace ie {
+namespace fftfast {
+
+constexpr int kTI = 16;
+
+__device__ __forceinline__ float2 fmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <int N>
+__host__ __device__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1; b < N; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// In-register DFT of length N (power of two): the input in bit-reversed order
+// (b[bitrev(i)] = x[i], so callers load it permuted at compile time), the output in
+// natural order, in place.  tw[m] = w_L^m (forward sign), stride = L / N so that
+// w_N^j = tw[j * stride].
+// One butterfly stage of span LEN, then the next (one template instance per stage, so
+// every register index is a compile-time constant).
+template <int N, int LEN, bool INV>
+struct BrStage {
+  static __device__ __forceinline__ void run(float2 (&b)[N], const float2 *tw, int stride) {
+#pragma unroll
+    for (int i = 0; i < N; i += LEN) {
+#pragma unroll
+      for (int j = 0; j < LEN / 2; ++j) {
+        const float2 u = b[i + j];
+        float2 v = b[i + j + LEN / 2];
+        if (j != 0) {
+          float2 w = tw[j * (N / LEN) * stride];
+          if (INV) w.y = -w.y;
+          v = fmul(v, w);
+        }
+        b[i + j] = make_float2(u.x + v.x, u.y + v.y);
+        b[i + j + LEN / 2] = make_float2(u.x - v.x, u.y - v.y);
+      }
+    }
+    BrStage<N, 2 * LEN, INV>::run(b, tw, stride);
+  }
+};
+template <int N, bool INV>
+struct BrStage<N, 2 * N, INV> {
+  static __device__ __forceinline__ void run(float2 (&)[N], const float2 *, int) {}
+};
+
+template <int N, bool INV>
+__device__ __forceinline__ void dft_br(float2 (&b)[N], const float2 *tw, int stride) {
+  BrStage<N, 2, INV>::run(b, tw, stride);
+}
+
+// w_L^m = exp(-2 pi i m / L) for m < L
+__device__ __forceinline__ void fill_table(float2 *tw, int L) {
+  for (int m = threadIdx.x; m < L; m += blockDim.x) {
+    float s, c;
+    sincospif(2.0f * (float)m / (float)L, &s, &c);
+    tw[m] = make_float2(c, -s);
+  }
+}
+
+// Step 1 for one (sequence t, q): v[bitrev(p)] holds x[q + Q p]; writes
+// Y[(q 16 + k1) TI + t].
+template <int Q, bool INV>
+__device__ __forceinline__ void step1(float2 (&v)[16], const float2 *tw, float2 *Y, int q, int t) {
+  constexpr int L = 16 * Q;
+  dft_br<16, INV>(v, tw, L / 16);
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    float2 r = v[k1];
+    if (k1 != 0 && q != 0) {
+      float2 w = tw[q * k1];
+      if (INV) w.y = -w.y;
+      r = fmul(r, w);
+    }
+    Y[(q * 16 + k1) * kTI + t] = r;
+  }
+}
+
+// Step 2 for one (sequence t, k1): returns X[k1 + 16 k2] in w[k2].
+template <int Q, bool INV>
+__device__ __forceinline__ void step2(float2 (&w)[Q], const float2 *tw, const float2 *Y, int k1, int t) {
+  constexpr int L = 16 * Q;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) w[bitrev<Q>(q)] = Y[(q * 16 + k1) * kTI + t];
+  dft_br<Q, INV>(w, tw, L / Q);
+}
+
+template <typename TX>
+__device__ __forceinline__ float2 to_f(typename cplx<TX>::type u) {
+  return make_float2((float)u.x, (float)u.y);
+}
+
+// Transform along the middle axis of in[outer][Lin][inner] (rows >= Lin are zero) ->
+// out[outer][Lout][inner] (rows >= Lout dropped), times scale.
+template <int Q, bool INV>
+__global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) axis_kernel(const float2 *__restrict__ in,
+                                                                     float2 *__restrict__ out, int Lin, int Lout,
+                                                                     long long inner, float scale) {
+  constexpr int L = 16 * Q;
+  extern __shared__ float2 smf[];
+  float2 *tw = smf, *Y = smf + L;
+  const int t = threadIdx.x % kTI, j = threadIdx.x / kTI;
+  const long long i0 = (long long)blockIdx.x * kTI;
+  const long long o = blockIdx.y;
+  const bool live = i0 + t < inner;
+  fill_table(tw, L);
+  __syncthreads();
+  if (j < Q) {
+    float2 v[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+      const int l = j + Q * p;
+      v[bitrev<16>(p)] = (live && l < Lin) ? in[(o * Lin + l) * inner + i0 + t] : make_float2(0.f, 0.f);
+    }
+    step1<Q, INV>(v, tw, Y, j, t);
+  }
+  __syncthreads();
+  if (j < 16) {
+    float2 w[Q];
+    step2<Q, INV>(w, tw, Y, j, t);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      const int l = j + 16 * k2;
+      if (live && l < Lout) out[(o * Lout + l) * inner + i0 + t] = make_float2(w[k2].x * scale, w[k2].y * scale);
+    }
+  }
+}
+
+// Forward row pass: x[CZ][Ny][Nx] times in_scale[Nz][Ny][Nx], zero-padded to L = 2 Nx,
+// transformed along x -> T1[Ny][L][CZ].
+template <int Q, typename TX>
+__global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_fwd_kernel(
+    const typename cplx<TX>::type *__restrict__ x, const typename cplx<TX>::type *__restrict__ in_scale,
+    float2 *__restrict__ t1, int CZ, int Nz, int Ny, int Nx) {
+  constexpr int L = 16 * Q;
+  constexpr int LD = kTI + 1;
+  extern __shared__ float2 smf[];
+  float2 *tw = smf, *Y = smf + L;  // Y: input stage [Nx][LD] first, then the exchange
+  const int t = threadIdx.x % kTI, j = threadIdx.x / kTI;
+  const int cz0 = blockIdx.x * kTI;
+  const int y = blockIdx.y;
+  fill_table(tw, L);
+  for (int e = threadIdx.x; e < Nx * kTI; e += blockDim.x) {
+    const int tt = e / Nx, xx = e % Nx;
+    const int cz = cz0 + tt;
+    float2 v = make_float2(0.f, 0.f);
+    if (cz < CZ) {
+      typename cplx<TX>::type u = x[((long long)cz * Ny + y) * Nx + xx];
+      if (in_scale) u = cmul(u, in_scale[((long long)(cz % Nz) * Ny + y) * Nx + xx]);
+      v = to_f<TX>(u);
+    }
+    Y[xx * LD + tt] = v;
+  }
+  __syncthreads();
+  float2 v[16];
+  if (j < Q) {
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+      const int l = j + Q * p;
+      v[bitrev<16>(p)] = l < Nx ? Y[l * LD + t] : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  if (j < Q) step1<Q, false>(v, tw, Y, j, t);
+  __syncthreads();
+  if (j < 16) {
+    float2 w[Q];
+    step2<Q, false>(w, tw, Y, j, t);
+    if (cz0 + t < CZ) {
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) t1[((long long)y * L + j + 16 * k2) * CZ + cz0 + t] = w[k2];
+    }
+  }
+}
+
+// Inverse row pass: T1[Ny][L][CZ] -> inverse along kx, keep x < Nx, and write
+// y[CZ][Ny][Nx] = diag[cell] x[CZ][cell] + out_scale[cell] value.
+template <int Q, typename TX>
+__global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_inv_kernel(
+    const float2 *__restrict__ t1, const typename cplx<TX>::type *__restrict__ x,
+    const typename cplx<TX>::type *__restrict__ diag, const typename cplx<TX>::type *__restrict__ out_scale,
+    typename cplx<TX>::type *__restrict__ y_out, int CZ, int Nz, int Ny, int Nx) {
+  using V = typename cplx<TX>::type;
+  constexpr int L = 16 * Q;
+  constexpr int LD = kTI + 1;
+  extern __shared__ float2 smf[];
+  float2 *tw = smf, *Y = smf + L;  // Y: the exchange, then the output stage [Nx][LD]
+  const int t = threadIdx.x % kTI, j = threadIdx.x / kTI;
+  const int cz0 = blockIdx.x * kTI;
+  const int y = blockIdx.y;
+  const bool live = cz0 + t < CZ;
+  fill_table(tw, L);
+  __syncthreads();
+  if (j < Q) {
+    float2 v[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p)
+      v[bitrev<16>(p)] = live ? t1[((long long)y * L + j + Q * p) * CZ + cz0 + t] : make_float2(0.f, 0.f);
+    step1<Q, true>(v, tw, Y, j, t);
+  }
+  __syncthreads();
+  float2 w[Q];
+  if (j < 16) step2<Q, true>(w, tw, Y, j, t);
+  __syncthreads();
+  if (j < 16) {
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      const int xx = j + 16 * k2;
+      if (xx < Nx) Y[xx * LD + t] = w[k2];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < Nx * kTI; e += blockDim.x) {
+    const int tt = e / Nx, xx = e % Nx;
+    const int cz = cz0 + tt;
+    if (cz < CZ) {
+      const long long cell = ((long long)(cz % Nz) * Ny + y) * Nx + xx;
+      const long long gi = ((long long)cz * Ny + y) * Nx + xx;
+      const float2 r = Y[xx * LD + tt];
+      V val = cmul(mk<TX>((TX)r.x, (TX)r.y), out_scale[cell]);
+      if (diag) cfma(val, diag[cell], x[gi]);
+      y_out[gi] = val;
+    }
+  }
+}
+
+// dynamic shared memory of every kernel above: the table and the exchange
+constexpr size_t smem_bytes(int Q) { return sizeof(float2) * (size_t)(16 * Q) * (1 + kTI); }
+constexpr int threads(int Q) { return kTI * (Q > 16 ? Q : 16); }
+
+}  // namespace fftfast
+}  // namespace ie

@@ -271,3 +271,39 @@ def test_solve_weak_contrast_takes_second_projection(precision, tol, bound):
     for r in range(2):
         assert rel(u[r], u_ref[r]) <= bound, (r, rel(u[r], u_ref[r]))
     ctx.close()
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 6), (128, 64, 4), (256, 32, 3), (64, 128, 5)])
+def test_fast_fft_lengths_against_c128(shape):
+    """Grids whose padded lengths 2N are 128, 256 or 512 take the register-blocked FP32
+    FFTs; the c64 product (one and two right-hand sides) must match the c128 product,
+    which uses the generic Stockham FFTs in FP64.  The mixed-precision solve (FP64
+    row passes around the FP32 FFTs) must reach the FP64 solve's solution."""
+    need_gpu()
+    nx, ny, nz = shape
+    m0 = W.small_model(nx=nx, ny=ny, nz=nz, seed=7, freq=1.0)
+    g = m0.grid
+    q = W.random_compressed_q(ny, nx, nz, seed=41, decay=0.02)
+    ctx = lib_context(m0, [q], max_rhs=2)
+    s = torch.cuda.current_stream().cuda_stream
+    for R in (1, 2):
+        x = W.random_field((R, 3, nz, ny, nx), 60 + R)
+        x128 = to_dev(x.astype(np.complex64).astype(np.complex128))
+        y128 = torch.empty_like(x128)
+        ctx.matvec(0, x128.data_ptr(), y128.data_ptr(), R, dtype=1, stream=s)
+        x64 = x128.to(torch.complex64)
+        y64 = torch.empty_like(x64)
+        ctx.matvec(0, x64.data_ptr(), y64.data_ptr(), R, dtype=0, stream=s)
+        torch.cuda.synchronize()
+        err = float((y64.to(torch.complex128) - y128).norm() / y128.norm())
+        assert err <= 2e-6, (shape, R, err)
+    b = to_dev(np.stack([normal.rhs_U0(m0, 1.0, "x"), normal.rhs_U0(m0, 1.0, "y")]))
+    u64 = torch.zeros_like(b)
+    umx = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    st, _ = ctx.solve(0, b.data_ptr(), u64.data_ptr(), 2, 1e-9, precision=0)
+    assert st == 0
+    st, _ = ctx.solve(0, b.data_ptr(), umx.data_ptr(), 2, 1e-7, precision=1)
+    assert st == 0
+    assert rel(to_host(umx), to_host(u64)) <= 1e-5
+    ctx.close()
