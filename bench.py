@@ -220,6 +220,7 @@ def run_ours(args, rank, ws):
     ctx = ie.Context(g, model.layers, model.sigma_a, model.freqs[:1], None, max_rhs=R, restart=args.restart,
                      inner_tol=args.inner_tol)
     t_setup = time.perf_counter() - t0
+    tune_v, tune_ms = ctx.contract_tuning()
     b = torch.empty((R, 3, g.nz, g.ny, g.nx), dtype=torch.complex128, device="cuda")
     for r in range(R):
         ctx.rhs_mt(0, r, b[r].data_ptr())
@@ -367,6 +368,9 @@ def run_ours(args, rank, ws):
                         "mixed_iters": iters / args.steps, "mixed_outer": outer / args.steps,
                         "fp64_iters": info64.inner_iters, "final_rel_res": res},
                 "roofline": roof,
+                "contract_tuning": {"variants": ["tma 1 slot", "tma 3 slots", "panel", "tma 1 slot, 1 row/thread"],
+                                    "chosen_for_2_rhs": int(tune_v[1]),
+                                    "ms_per_launch_2_rhs": [float(v) for v in tune_ms[1]]},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 16),
                         "d2h_bytes_per_step": int(b.numel() * 16)},

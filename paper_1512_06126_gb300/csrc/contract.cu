@@ -146,11 +146,11 @@ int num_sms() {
   return n;
 }
 
-template <int NZ, int R, int NS>
+template <int NZ, int R, int NS, int RPT>
 bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int per_sm, cudaStream_t s) {
-  using Cfg = ContractCfg<NZ, R, NS>;
+  using Cfg = ContractCfg<NZ, R, NS, RPT>;
   if (Cfg::SMEM > 227 * 1024) return false;
-  auto k = contract_tma_kernel<NZ, R, NS>;
+  auto k = contract_tma_kernel<NZ, R, NS, RPT>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -174,11 +174,17 @@ bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int per_sm
 // covers the unpacking phase), or three slots and one CTA per SM.
 template <int NZ, int R>
 bool try_tma_variant(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int variant, cudaStream_t s) {
+  constexpr int RPT2 = R == 2 ? 2 : 1;
   if (variant == kContractTma1) {
-    if (2 * ContractCfg<NZ, R, 1>::SMEM <= 227 * 1024) return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, ldz, 2, s);
-    return try_tma<NZ, R, 1>(spec, qf, Nx, Ny, ldz, 1, s);
+    if (2 * ContractCfg<NZ, R, 1, RPT2>::SMEM <= 227 * 1024)
+      return try_tma<NZ, R, 1, RPT2>(spec, qf, Nx, Ny, ldz, 2, s);
+    return try_tma<NZ, R, 1, RPT2>(spec, qf, Nx, Ny, ldz, 1, s);
   }
-  if (variant == kContractTma3) return try_tma<NZ, R, 3>(spec, qf, Nx, Ny, ldz, 1, s);
+  if (variant == kContractTma1Row) {
+    if (2 * ContractCfg<NZ, R, 1, 1>::SMEM <= 227 * 1024) return try_tma<NZ, R, 1, 1>(spec, qf, Nx, Ny, ldz, 2, s);
+    return try_tma<NZ, R, 1, 1>(spec, qf, Nx, Ny, ldz, 1, s);
+  }
+  if (variant == kContractTma3) return try_tma<NZ, R, 3, RPT2>(spec, qf, Nx, Ny, ldz, 1, s);
   return false;
 }
 
@@ -194,7 +200,7 @@ bool dispatch_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ld
 }
 
 template <int NZ, int R>
-bool tma3_fits() { return ContractCfg<NZ, R, 3>::SMEM <= 227 * 1024; }
+bool tma3_fits() { return ContractCfg<NZ, R, 3, (R == 2 ? 2 : 1)>::SMEM <= 227 * 1024; }
 
 }  // namespace
 
@@ -212,6 +218,7 @@ bool contract_variant_available(int variant, int Nz, int R, bool c64) {
   if (!c64 || R < 1 || R > 2 || !contract_tma_enabled) return false;
   if (Nz != 16 && Nz != 24 && Nz != 32 && Nz != 48) return false;
   if (variant == kContractTma1) return true;
+  if (variant == kContractTma1Row) return R == 2;
   if (variant == kContractTma3) {
     switch (Nz) {
       case 16: return R == 1 ? tma3_fits<16, 1>() : tma3_fits<16, 2>();
@@ -230,7 +237,8 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, i
   if constexpr (sizeof(T) == 4) {
     if (variant == kContractAuto) variant = contract_variant_available(kContractTma1, Nz, R, true) ? kContractTma1
                                                                                                     : kContractPanel;
-    if ((variant == kContractTma1 || variant == kContractTma3) && contract_variant_available(variant, Nz, R, true)) {
+    if ((variant == kContractTma1 || variant == kContractTma3 || variant == kContractTma1Row) &&
+        contract_variant_available(variant, Nz, R, true)) {
       if (R == 1 && dispatch_tma<1>(spec, qf, Nx, Ny, Nz, ldz, variant, s)) return 0;
       if (R == 2 && dispatch_tma<2>(spec, qf, Nx, Ny, Nz, ldz, variant, s)) return 0;
     }

@@ -12,8 +12,9 @@
 // unpacked into six padded Nz x (Nz + 1) matrices (stride Nz + 1 makes both row and
 // column reads of 8-byte elements free of bank conflicts) and applied as a small
 // dense product Y = M X, M = [[xx, xy, xz], [xy, yy, yz], [-xz^T, -yz^T, zz]],
-// X = the mirror vectors with the component signs of Lemma 2.  Thread t owns one
-// output row and CPT columns (FP32 FMAs, FP32 accumulation).
+// X = the mirror vectors with the component signs of Lemma 2.  A thread owns RPT output
+// rows (two for two right-hand sides, so that each broadcast load of X feeds twice the
+// FMAs) and CPT = 4 columns; packed two-lane FP32 FMAs, FP32 accumulation.
 //
 // Every wait on an mbarrier is bounded; on timeout the kernel records an error
 // code, waits (bounded) for its outstanding copies and returns.
@@ -75,7 +76,7 @@ __device__ __forceinline__ float2 upk(unsigned long long v) {
 constexpr long long kWaitLimit = 1LL << 28;  // polls before a wait is declared failed
 enum ContractError { kContractOk = 0, kContractTimeout = 1 };
 
-template <int NZ, int R, int NSTAGE>
+template <int NZ, int R, int NSTAGE, int RPT_ = (R == 2 ? 2 : 1)>
 struct ContractCfg {
   static constexpr int N3 = 3 * NZ;
   static constexpr int CZ = R * N3;
@@ -85,7 +86,9 @@ struct ContractCfg {
   static constexpr int MAXC = 4 * R;              // 4 mirrors x R right-hand sides
   static constexpr int CPT = 4;                    // columns per thread
   static constexpr int CG = MAXC / CPT;            // column groups
-  static constexpr int THREADS = N3 * CG;
+  static constexpr int RPT = RPT_;                  // output rows per thread
+  static constexpr int NR = N3 / RPT;              // row slots
+  static constexpr int THREADS = NR * CG;
   // shared memory layout (bytes, 16-byte aligned pieces)
   static constexpr size_t OFF_BAR = 0;
   static constexpr size_t OFF_RAW = 128;
@@ -95,7 +98,7 @@ struct ContractCfg {
   static constexpr size_t OFF_BLK = OFF_XRAW + NSTAGE * XRAW_BYTES;
   static constexpr size_t BLK_BYTES = (size_t)6 * NZ * LD * 8;
   static constexpr size_t OFF_XS = OFF_BLK + BLK_BYTES;
-  static constexpr size_t XS_BYTES = (size_t)2 * N3 * MAXC * 8;  // X and X with re/im swapped
+  static constexpr size_t XS_BYTES = (size_t)N3 * MAXC * 8;
   static constexpr size_t OFF_TRI = OFF_XS + XS_BYTES;
   static constexpr size_t SMEM = OFF_TRI + (size_t)P * 4;
 };
@@ -120,12 +123,12 @@ __device__ __forceinline__ Mirrors mirrors_of(int w, int Nx, int Ny) {
   return m;
 }
 
-template <int NZ, int R, int NSTAGE>
-__global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
+template <int NZ, int R, int NSTAGE, int RPT_>
+__global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE, RPT_>::THREADS)
     contract_tma_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err) {
-  using Cfg = ContractCfg<NZ, R, NSTAGE>;
+  using Cfg = ContractCfg<NZ, R, NSTAGE, RPT_>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LD = Cfg::LD, MAXC = Cfg::MAXC;
-  constexpr int CPT = Cfg::CPT;
+  constexpr int CPT = Cfg::CPT, RPT = Cfg::RPT;
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Cfg::OFF_BAR);
   float2 *raw = reinterpret_cast<float2 *>(sm + Cfg::OFF_RAW);
@@ -169,27 +172,34 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
       if (w < nf) issue(w, k);
     }
   }
-  const int row = tid % N3;
-  const int cg = tid / N3;
-  const int alpha = row / NZ, a = row - alpha * NZ;
-  // per-beta base pointers, strides and signs of M[row][beta*NZ + b]
+  // thread (rr, cg) owns rows rr + k NR (k < RPT) and columns cg CPT .. cg CPT + CPT - 1
+  const int rr = tid % Cfg::NR;
+  const int cg = tid / Cfg::NR;
+  // per (row, beta): base pointer, stride and sign of M[row][beta*NZ + b]
   const float2 *Axx = blk, *Ayy = blk + NZ * LD, *Azz = blk + 2 * NZ * LD, *Axy = blk + 3 * NZ * LD;
   const float2 *Axz = blk + 4 * NZ * LD, *Ayz = blk + 5 * NZ * LD;
-  const float2 *bp[3];
-  int bs[3];
-  float sg[3];
-  if (alpha == 0) {
-    bp[0] = Axx + a; bs[0] = LD; sg[0] = 1.f;
-    bp[1] = Axy + a; bs[1] = LD; sg[1] = 1.f;
-    bp[2] = Axz + a * LD; bs[2] = 1; sg[2] = 1.f;
-  } else if (alpha == 1) {
-    bp[0] = Axy + a; bs[0] = LD; sg[0] = 1.f;
-    bp[1] = Ayy + a; bs[1] = LD; sg[1] = 1.f;
-    bp[2] = Ayz + a * LD; bs[2] = 1; sg[2] = 1.f;
-  } else {
-    bp[0] = Axz + a; bs[0] = LD; sg[0] = -1.f;
-    bp[1] = Ayz + a; bs[1] = LD; sg[1] = -1.f;
-    bp[2] = Azz + a; bs[2] = LD; sg[2] = 1.f;
+  const float2 *bp[RPT][3];
+  int bs[RPT][3];
+  float sg[RPT][3];
+  int alph[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int row = rr + k * Cfg::NR;
+    const int alpha = row / NZ, a = row - alpha * NZ;
+    alph[k] = alpha;
+    if (alpha == 0) {
+      bp[k][0] = Axx + a; bs[k][0] = LD; sg[k][0] = 1.f;
+      bp[k][1] = Axy + a; bs[k][1] = LD; sg[k][1] = 1.f;
+      bp[k][2] = Axz + a * LD; bs[k][2] = 1; sg[k][2] = 1.f;
+    } else if (alpha == 1) {
+      bp[k][0] = Axy + a; bs[k][0] = LD; sg[k][0] = 1.f;
+      bp[k][1] = Ayy + a; bs[k][1] = LD; sg[k][1] = 1.f;
+      bp[k][2] = Ayz + a * LD; bs[k][2] = 1; sg[k][2] = 1.f;
+    } else {
+      bp[k][0] = Axz + a; bs[k][0] = LD; sg[k][0] = -1.f;
+      bp[k][1] = Ayz + a; bs[k][1] = LD; sg[k][1] = -1.f;
+      bp[k][2] = Azz + a; bs[k][2] = LD; sg[k][2] = 1.f;
+    }
   }
 
   int it = 0;
@@ -235,7 +245,6 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
         if ((comp == 0 && mx == 1) || (comp == 1 && my == 1)) { v.x = -v.x; v.y = -v.y; }
       }
       xs[k * MAXC + col] = v;
-      xs[N3 * MAXC + k * MAXC + col] = make_float2(v.y, v.x);
     }
     __syncthreads();
     // slot s is consumed: refill it with wavenumber w + NSTAGE * gridDim.x
@@ -244,49 +253,62 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE>::THREADS)
       if (wn < nf) issue(wn, s);
     }
     if (cg * CPT < ncol) {
-      // complex MAC acc += m x as two packed FMAs: (re, im) += (mr, mr)(xr, xi) and
-      // (re, im) += (-mi, mi)(xi, xr)
-      unsigned long long acc[CPT];
+      // complex MAC as two packed FMAs into two accumulators: a1 += (xr, xi)(mr, mr) and,
+      // in swapped order, a2 += (xr, xi)(mi, -mi); then re = a1.x + a2.y, im = a1.y + a2.x.
+      unsigned long long a1[RPT][CPT], a2[RPT][CPT];
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) acc[c] = 0ull;
+      for (int k = 0; k < RPT; ++k)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) a1[k][c] = a2[k][c] = 0ull;
 #pragma unroll
       for (int beta = 0; beta < 3; ++beta) {
-        unsigned long long tmp[CPT];
+        unsigned long long t1[RPT][CPT], t2[RPT][CPT];
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) tmp[c] = 0ull;
-        const float2 *mp = bp[beta];
-        const int st = bs[beta];
+        for (int k = 0; k < RPT; ++k)
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) t1[k][c] = t2[k][c] = 0ull;
         const ulonglong2 *xp = reinterpret_cast<const ulonglong2 *>(xs + (size_t)beta * NZ * MAXC + cg * CPT);
-        const ulonglong2 *xq = reinterpret_cast<const ulonglong2 *>(xs + (size_t)N3 * MAXC + (size_t)beta * NZ * MAXC +
-                                                                    cg * CPT);
-#pragma unroll 8
+#pragma unroll 4
         for (int b = 0; b < NZ; ++b) {
-          const float2 m = mp[b * st];
-          const unsigned long long mr = pk(m.x, m.x), mi = pk(-m.y, m.y);
           const ulonglong2 x01 = xp[b * (MAXC / 2)], x23 = xp[b * (MAXC / 2) + 1];
-          const ulonglong2 y01 = xq[b * (MAXC / 2)], y23 = xq[b * (MAXC / 2) + 1];
-          tmp[0] = ffma2(mr, x01.x, tmp[0]);
-          tmp[1] = ffma2(mr, x01.y, tmp[1]);
-          tmp[2] = ffma2(mr, x23.x, tmp[2]);
-          tmp[3] = ffma2(mr, x23.y, tmp[3]);
-          tmp[0] = ffma2(mi, y01.x, tmp[0]);
-          tmp[1] = ffma2(mi, y01.y, tmp[1]);
-          tmp[2] = ffma2(mi, y23.x, tmp[2]);
-          tmp[3] = ffma2(mi, y23.y, tmp[3]);
-        }
-        const unsigned long long sgp = pk(sg[beta], sg[beta]);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c] = ffma2(sgp, tmp[c], acc[c]);
+          for (int k = 0; k < RPT; ++k) {
+            const float2 m = bp[k][beta][b * bs[k][beta]];
+            const unsigned long long mr = pk(m.x, m.x), mi = pk(m.y, -m.y);
+            t1[k][0] = ffma2(x01.x, mr, t1[k][0]);
+            t2[k][0] = ffma2(x01.x, mi, t2[k][0]);
+            t1[k][1] = ffma2(x01.y, mr, t1[k][1]);
+            t2[k][1] = ffma2(x01.y, mi, t2[k][1]);
+            t1[k][2] = ffma2(x23.x, mr, t1[k][2]);
+            t2[k][2] = ffma2(x23.x, mi, t2[k][2]);
+            t1[k][3] = ffma2(x23.y, mr, t1[k][3]);
+            t2[k][3] = ffma2(x23.y, mi, t2[k][3]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const unsigned long long sgp = pk(sg[k][beta], sg[k][beta]);
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) {
+            a1[k][c] = ffma2(sgp, t1[k][c], a1[k][c]);
+            a2[k][c] = ffma2(sgp, t2[k][c], a2[k][c]);
+          }
+        }
       }
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        const int col = cg * CPT + c;
-        if (col < ncol) {
-          const int m = col / R, r = col - m * R;
-          const int mx = m % nmx, my = m / nmx;
-          float2 v = upk(acc[c]);
-          if ((alpha == 0 && mx == 1) || (alpha == 1 && my == 1)) { v.x = -v.x; v.y = -v.y; }
-          spec[mw.pos(mx, my, Nx) * ldz + r * N3 + row] = v;
+      for (int k = 0; k < RPT; ++k) {
+        const int row = rr + k * Cfg::NR;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const int col = cg * CPT + c;
+          if (col < ncol) {
+            const int m = col / R, r = col - m * R;
+            const int mx = m % nmx, my = m / nmx;
+            const float2 u1 = upk(a1[k][c]), u2 = upk(a2[k][c]);
+            float2 v = make_float2(u1.x + u2.y, u1.y + u2.x);
+            if ((alph[k] == 0 && mx == 1) || (alph[k] == 1 && my == 1)) { v.x = -v.x; v.y = -v.y; }
+            spec[mw.pos(mx, my, Nx) * ldz + r * N3 + row] = v;
+          }
         }
       }
     }
