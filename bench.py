@@ -408,6 +408,111 @@ def run_matvec_only(args):
     ctx.close()
 
 
+def run_batch(args):
+    """The batched configuration: 16 frequencies x 2 polarisations over four grids
+    (64^2x16, 96^2x24, 128^2x32, 192^2x48; frequency k on grid k mod 4).  Per grid,
+    its four frequencies (8 right-hand sides) are solved in one batched mixed-precision
+    solve (ie_solve_batch), then one instance at a time for comparison.  Device time
+    with CUDA events on the library stream, after one untimed batched solve."""
+    import torch
+    from paper_1512_06126_gb300 import build, ie
+    build.build()
+    out = []
+    t_b = t_s = 0.0
+    for m in W.config3():
+        g = m.grid
+        nf = len(m.freqs)
+        ctx = ie.Context(g, m.layers, m.sigma_a, m.freqs, None, max_rhs=2 * nf, restart=args.restart,
+                         inner_tol=args.inner_tol)
+        b = torch.empty((nf, 2, 3, g.nz, g.ny, g.nx), dtype=torch.complex128, device="cuda")
+        for k in range(nf):
+            for p in range(2):
+                ctx.rhs_mt(k, p, b[k, p].data_ptr())
+        u = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        ext = torch.cuda.ExternalStream(ctx.stream)
+        insts = list(range(nf))
+        ctx.solve_batch(insts, b.data_ptr(), u.data_ptr(), 2, TOL, precision=ie.IE_MIXED)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(ext):
+            e0.record()
+        st, info = ctx.solve_batch(insts, b.data_ptr(), u.data_ptr(), 2, TOL, precision=ie.IE_MIXED)
+        with torch.cuda.stream(ext):
+            e1.record()
+        e1.synchronize()
+        tb = e0.elapsed_time(e1) / 1e3
+        u1 = torch.zeros_like(b[0])
+        with torch.cuda.stream(ext):
+            e0.record()
+        it_single = 0
+        res1 = 0.0
+        for k in range(nf):
+            st1, i1 = ctx.solve(k, b[k].data_ptr(), u1.data_ptr(), 2, TOL, precision=ie.IE_MIXED)
+            it_single += i1.inner_iters
+            res1 = max(res1, i1.final_rel_res)
+        with torch.cuda.stream(ext):
+            e1.record()
+        e1.synchronize()
+        ts = e0.elapsed_time(e1) / 1e3
+        out.append({"grid": f"{g.nx}x{g.ny}x{g.nz}", "instances": 2 * nf, "batched_s": tb,
+                    "batched_iters": info.inner_iters, "batched_res": info.final_rel_res, "one_at_a_time_s": ts,
+                    "one_at_a_time_iters": it_single, "one_at_a_time_res": res1, "status": [st, st1]})
+        t_b += tb
+        t_s += ts
+        ctx.close()
+        del b, u, u1
+        torch.cuda.empty_cache()
+    print(json.dumps({"mode": "batch", "workload": "C3: 32 instances (16 frequencies x 2 polarisations) over 4 grids",
+                      "metric": "solved instances/s (mixed precision, tol 1e-7)",
+                      "batched": 32 / t_b, "one_at_a_time": 32 / t_s, "batched_s": t_b, "one_at_a_time_s": t_s,
+                      "tol": TOL, "per_grid": out}), flush=True)
+
+
+def run_gradient(args):
+    """MT misfit and its gradient on the 64x64x24 workload: 8 frequencies x 2
+    polarisations, 16 x 16 receivers every second cell over the centre, observed
+    impedances from the same model with the anomaly conductivities doubled.  Times one
+    misfit evaluation (16 forward solves, FP64) and one gradient (16 adjoint solves)
+    after one untimed pair."""
+    import torch
+    from paper_1512_06126_gb300 import build, ie, mt
+    build.build()
+    m = W.config4()
+    g = m.grid
+    sb = W.background_sigma(g, m.layers)
+    base = np.broadcast_to(sb[:, None, None], m.sigma_a.shape).astype(np.complex128).copy()
+    ctx = ie.Context(g, m.layers, m.sigma_a, m.freqs, None, max_rhs=2)
+    idx = np.arange(16, 48, 2)
+    ix, iy = np.meshgrid(idx, idx)
+    n_inst = len(m.freqs)
+    P = mt.MTProblem(ctx, ix.ravel(), iy.ravel(), np.zeros((n_inst, ix.size, 2, 2), dtype=np.complex128),
+                     tol=1e-9, precision=ie.IE_FP64)
+    truth = m.sigma_a.copy()
+    an = np.abs(truth - base) > 0
+    truth[an] *= 2.0
+    ctx.set_sigma(truth)
+    P.misfit()
+    P.zobs.copy_(P.z)
+    ctx.set_sigma(m.sigma_a)
+    P.misfit()
+    P.gradient()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phi = P.misfit()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    grad = P.gradient()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    gn = grad.cpu().numpy()
+    print(json.dumps({"mode": "gradient", "workload": "C4: 64x64x24 cells, 8 frequencies x 2 polarisations, "
+                      "16x16 receivers, FP64 solves to 1e-9", "misfit": phi, "misfit_s": t1 - t0,
+                      "gradient_s": t2 - t1, "anomalous_cells": int(an.sum()),
+                      "gradient_norm": float(np.linalg.norm(gn)), "gradient_nonzero": int((gn != 0).sum()),
+                      "forward_iters": P.iters["forward"], "adjoint_iters": P.iters["adjoint"]}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,11 +524,15 @@ def main():
     ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "matvec"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "matvec", "batch", "gradient"], default="solve")
     args = ap.parse_args()
     rank, ws = dist_setup()
     if args.mode == "matvec":
         run_matvec_only(args)
+    elif args.mode == "batch":
+        run_batch(args)
+    elif args.mode == "gradient":
+        run_gradient(args)
     elif args.impl == "reference":
         run_reference(args, rank, ws)
     else:

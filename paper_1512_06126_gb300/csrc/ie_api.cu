@@ -517,22 +517,41 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
     brk = gr.breakdown;
   } else {
     int inner_total = 0;
+    const long long blk = n * g.rpi;  // elements of one instance's block
     for (int outer = 0; outer <= c->max_outer; ++outer) {
       IE_TRY(true_residual(c, g, transpose, b, u, rel));
       inf.outer_iters = outer + 1;
+      // instances with a right-hand side above the tolerance stay in the inner solve;
+      // the others are done and drop out of the group
+      Group act;
+      act.rpi = g.rpi;
+      std::vector<int> pos;
       double worst = 0;
-      for (double v : rel) worst = std::max(worst, v);
-      if (worst <= tol) { conv = true; break; }
+      for (size_t k = 0; k < g.inst.size(); ++k) {
+        double wk = 0;
+        for (int p = 0; p < g.rpi; ++p) wk = std::max(wk, rel[k * g.rpi + p]);
+        worst = std::max(worst, wk);
+        if (wk > tol) { act.inst.push_back(g.inst[k]); pos.push_back((int)k); }
+      }
+      if (act.inst.empty()) { conv = true; break; }
       if (outer == c->max_outer || inner_total >= c->max_iter) break;
+      // pack the residual blocks of the active instances to the front of r (in order:
+      // a block only moves to a lower position, so source and target never overlap)
+      for (size_t a = 0; a < pos.size(); ++a)
+        if ((int)a != pos[a])
+          IE_CUDA(cudaMemcpyAsync(c->r + (long long)a * blk, c->r + (long long)pos[a] * blk, blk * sizeof(double2),
+                                  cudaMemcpyDeviceToDevice, c->stream));
+      const int Ra = act.R();
       // inner: A64 d = r (relative tolerance inner_tol, bounded below so as not to over-solve)
-      IE_CUDA(cudaMemsetAsync(c->dx, 0, n * R * sizeof(double2), c->stream));
+      IE_CUDA(cudaMemsetAsync(c->dx, 0, n * Ra * sizeof(double2), c->stream));
       GmresResult gr;
       const double itol = std::max(c->inner_tol, 0.5 * tol / std::max(worst, 1e-300));
-      IE_TRY(gmres(c, Op{c, &g, transpose, true}, c->r, c->dx, R, std::min(itol, 0.5), c->max_iter - inner_total,
-                   &gr));
+      IE_TRY(gmres(c, Op{c, &act, transpose, true}, c->r, c->dx, Ra, std::min(itol, 0.5),
+                   c->max_iter - inner_total, &gr));
       inner_total += gr.iters;
       brk = brk || gr.breakdown;
-      ie::vec_add(c->dx, u, n * R, c->stream);
+      for (size_t a = 0; a < pos.size(); ++a)
+        ie::vec_add(c->dx + (long long)a * blk, u + (long long)pos[a] * blk, blk, c->stream);
     }
     inf.inner_iters = inner_total;
   }
