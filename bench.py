@@ -53,6 +53,10 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+# (workload, contraction variant, right-hand sides) -> DRAM bytes per contraction launch
+CONTRACT_TRAFFIC = {("C2", 3, 2): 654541312 + 86889728}
+
+
 def workload(name):
     return {"C1": W.config1, "C2": W.config2, "C4": W.config4, "C5": W.config5}[name]()
 
@@ -270,11 +274,21 @@ def run_ours(args, rank, ws):
 
     # ---- time-to-solution: mixed (mean of the timed steps) vs plain FP64 ----
     tts_mixed = t_ms / 1e3 / args.steps
+    # the plain FP64 solve at its own best restart length (longer than the mixed one's),
+    # on a context of its own, after one untimed solve
+    ctx64 = ie.Context(g, model.layers, model.sigma_a, model.freqs[:1], None, max_rhs=R,
+                       restart=args.restart_fp64)
+    u64 = torch.zeros_like(b)
+    st64, info64 = ctx64.solve(0, b.data_ptr(), u64.data_ptr(), R, TOL, precision=ie.IE_FP64)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    info64 = solve(ie.IE_FP64)
+    st64, info64 = ctx64.solve(0, b.data_ptr(), u64.data_ptr(), R, TOL, precision=ie.IE_FP64)
     torch.cuda.synchronize()
     tts_fp64 = time.perf_counter() - t1
+    if st64 != ie.IE_OK:
+        raise RuntimeError(f"FP64 solve did not converge: status {st64}")
+    ctx64.close()
+    del u64
 
     # ---- matvec GB/s (c64, both polarisations) ----
     nf = (g.nx + 1) * (g.ny + 1)
@@ -302,6 +316,10 @@ def run_ours(args, rank, ws):
     # ---- roofline of the contraction kernel (timed during the steps) ----
     hbm_peak, sm_max, peak_src = peaks()
     k3_avg_ms = k3_ms / max(k3_n, 1)
+    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+    # capture of this kernel variant on this workload (profiles/contraction_and_fft_c2.md);
+    # null for any other variant or workload
+    traffic = CONTRACT_TRAFFIC.get((args.workload, int(tune_v[R - 1]), R))
     k3_bytes = q_bytes + 2 * 4 * g.nx * g.ny * 3 * g.nz * R * 8
     k3_flops = 8.0 * 4 * g.nx * g.ny * R * 9 * g.nz * g.nz
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12            # TFLOP/s, FP32 FMA pipes at max clock
@@ -313,13 +331,13 @@ def run_ours(args, rank, ws):
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                 "hbm_GBs": k3_bytes / (k3_avg_ms * 1e-3) / 1e9, "hbm_frac": k3_bytes / (k3_avg_ms * 1e-3) / 1e9 / hbm_peak,
-                "bytes_per_launch": k3_bytes, "flops_per_launch": k3_flops, "traffic": None,
+                "bytes_per_launch": k3_bytes, "flops_per_launch": k3_flops, "traffic": traffic,
                 "launches": k3_n, "avg_ms": k3_avg_ms}
     else:
         achieved = k3_bytes / (k3_avg_ms * 1e-3) / 1e9
         roof = {"kernel": "contract (c64, 2 right-hand sides)", "bound": "hbm", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_src,
-                "bytes_per_launch": k3_bytes, "traffic": None, "launches": k3_n, "avg_ms": k3_avg_ms}
+                "bytes_per_launch": k3_bytes, "traffic": traffic, "launches": k3_n, "avg_ms": k3_avg_ms}
 
     # ---- e2e: through the ABI with host buffers ----
     bh = b.cpu().pin_memory()
@@ -358,6 +376,7 @@ def run_ours(args, rank, ws):
                 "config": {"workload": f"{args.workload}: {g.nx}x{g.ny}x{g.nz} cells, {len(model.layers.sigma) - 1}"
                                        f" layers + air, {model.freqs[0]} Hz, 2 polarisations, tol {TOL}",
                            "unknowns": n_unk, "rhs": R, "restart": args.restart,
+                           "inner_tol": args.inner_tol, "restart_fp64": args.restart_fp64,
                            "l2": "inputs larger than L2 (c64 coefficients %.0f MB)" % (q_bytes / 1e6),
                            "parallelism": f"replicas x{ws}", "coefficients": "generated on the device",
                            "setup_s": t_setup},
@@ -520,8 +539,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="C2", choices=["C1", "C2", "C4", "C5"])
-    ap.add_argument("--restart", type=int, default=30)
-    ap.add_argument("--inner-tol", type=float, default=1e-3)
+    ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--restart-fp64", type=int, default=45)
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", choices=["solve", "matvec", "batch", "gradient"], default="solve")

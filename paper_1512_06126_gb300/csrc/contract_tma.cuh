@@ -98,7 +98,11 @@ struct ContractCfg {
   static constexpr size_t OFF_BLK = OFF_XRAW + NSTAGE * XRAW_BYTES;
   static constexpr size_t BLK_BYTES = (size_t)6 * NZ * LD * 8;
   static constexpr size_t OFF_XS = OFF_BLK + BLK_BYTES;
-  static constexpr size_t XS_BYTES = (size_t)N3 * MAXC * 8;
+  // X rows padded from MAXC to MAXC + 2 complex: the staging stores (consecutive
+  // threads on consecutive rows) then spread over the banks, and rows stay 16-byte
+  // aligned for the 128-bit broadcast loads of the product
+  static constexpr int XLD = MAXC + 2;
+  static constexpr size_t XS_BYTES = (size_t)N3 * XLD * 8;
   static constexpr size_t OFF_TRI = OFF_XS + XS_BYTES;
   static constexpr size_t SMEM = OFF_TRI + (size_t)P * 4;
 };
@@ -128,6 +132,7 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE, RPT_>::THREADS)
     contract_tma_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err) {
   using Cfg = ContractCfg<NZ, R, NSTAGE, RPT_>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LD = Cfg::LD, MAXC = Cfg::MAXC;
+  constexpr int XLD = Cfg::XLD;
   constexpr int CPT = Cfg::CPT, RPT = Cfg::RPT;
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Cfg::OFF_BAR);
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE, RPT_>::THREADS)
         v = xr[(size_t)m * CZ + r * N3 + k];
         if ((comp == 0 && mx == 1) || (comp == 1 && my == 1)) { v.x = -v.x; v.y = -v.y; }
       }
-      xs[k * MAXC + col] = v;
+      xs[k * XLD + col] = v;
     }
     __syncthreads();
     // slot s is consumed: refill it with wavenumber w + NSTAGE * gridDim.x
@@ -267,10 +272,10 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE, RPT_>::THREADS)
         for (int k = 0; k < RPT; ++k)
 #pragma unroll
           for (int c = 0; c < CPT; ++c) t1[k][c] = t2[k][c] = 0ull;
-        const ulonglong2 *xp = reinterpret_cast<const ulonglong2 *>(xs + (size_t)beta * NZ * MAXC + cg * CPT);
+        const ulonglong2 *xp = reinterpret_cast<const ulonglong2 *>(xs + (size_t)beta * NZ * XLD + cg * CPT);
 #pragma unroll 4
         for (int b = 0; b < NZ; ++b) {
-          const ulonglong2 x01 = xp[b * (MAXC / 2)], x23 = xp[b * (MAXC / 2) + 1];
+          const ulonglong2 x01 = xp[b * (XLD / 2)], x23 = xp[b * (XLD / 2) + 1];
 #pragma unroll
           for (int k = 0; k < RPT; ++k) {
             const float2 m = bp[k][beta][b * bs[k][beta]];
