@@ -84,8 +84,9 @@ __global__ void norm_final(const double *__restrict__ part, double *__restrict__
 
 // dst[r] = src[r] / nrm[r]  (dst may alias src)
 __global__ void scale_kernel(const double2 *__restrict__ src, double2 *__restrict__ dst, const double *__restrict__ nrm,
-                             long long n) {
+                             long long n, const int *__restrict__ flag) {
   const int r = blockIdx.y;
+  if (flag && !flag[r]) return;
   const double s = nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -183,15 +184,21 @@ __global__ void __launch_bounds__(kT) cgs_dot_kernel(const double2 *__restrict__
   }
 }
 
-// x[r] -= sum_{i<k1} h[r * ldh + i] V_i[r] on the tile; npart = sum_tile |x|^2
+// x[r] -= sum_{i<k1} h[r * ldh + i] V_i[r] on the tile; npart = sum_tile |x|^2.
+// With vout: a right-hand side whose oflag is 0 instead gets vout[r] = x' / nrm[r]
+// (the next basis vector, normalised by the norm known in advance) and no norm
+// partial; one whose oflag is 1 gets x' in x as above.  A right-hand side whose
+// flag (if given) is 0 is skipped.
 __global__ void __launch_bounds__(kT) cgs_sub_kernel(const double2 *__restrict__ V, double2 *__restrict__ x,
                                                      const double2 *__restrict__ h, double *__restrict__ npart,
                                                      const int *__restrict__ flag, int k1, int R, long long n,
-                                                     int nb, int ldh) {
+                                                     int nb, int ldh, double2 *__restrict__ vout,
+                                                     const double *__restrict__ nrm, const int *__restrict__ oflag) {
   __shared__ double2 hs[64];
   __shared__ double2 shn[kT / 32];
   const int r = blockIdx.y;
   if (flag && !flag[r]) return;
+  const bool scaled = vout && !oflag[r];
   const long long t0 = (long long)blockIdx.x * kTile;
   const int tid = threadIdx.x;
   double2 *xr = x + (long long)r * n;
@@ -218,6 +225,16 @@ __global__ void __launch_bounds__(kT) cgs_sub_kernel(const double2 *__restrict__
       }
     }
   }
+  if (scaled) {
+    const double sc = nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0;
+    double2 *vr = vout + (long long)r * n;
+#pragma unroll
+    for (int j = 0; j < kTileEPT; ++j) {
+      const long long e = t0 + j * kT + tid;
+      if (e < n) vr[e] = make_double2(v[j].x * sc, v[j].y * sc);
+    }
+    return;
+  }
   double nacc = 0.0;
 #pragma unroll
   for (int j = 0; j < kTileEPT; ++j) {
@@ -230,26 +247,31 @@ __global__ void __launch_bounds__(kT) cgs_sub_kernel(const double2 *__restrict__
   if (tid == 0) npart[(long long)r * nb + blockIdx.x] = sres.x;
 }
 
-// ||x|| before (npart0) and after (npart1) the first projection; flag[r] = 1 when the
-// projection cancelled so much of x that a second one is needed: ||x'|| < ||x|| / 16.
-// This is the test of Daniel, Gragg, Kaufman and Stewart with a looser threshold than
-// their 1/sqrt(2): one projection leaves x' orthogonal to V up to about
-// eps64 ||x|| / ||x'||, so below 1/16 cancellation the loss stays under ~16 eps64 per
-// step, far below what restarted GMRES to 1e-7 (or an inner solve to 1e-3) can notice.
-// For this operator the product A v_k is dominated by v_k, so 1/sqrt(2) would trigger
-// the second projection in nearly every iteration, doubling the FP64 work.
-__global__ void cgs_check_kernel(const double *__restrict__ npart0, const double *__restrict__ npart1,
-                                 double *__restrict__ nrm, int *__restrict__ flag, int nb) {
+// Before the subtraction: ||x'||^2 = ||x||^2 - sum_i |h_i|^2 (x' = x - V h is the part
+// of x orthogonal to the basis), flag[r] = 1 where ||x'|| < ||x|| / 16.  The test is
+// that of Daniel, Gragg, Kaufman and Stewart with a looser threshold than their
+// 1/sqrt(2): one projection leaves x' orthogonal to V up to about eps64 ||x|| / ||x'||,
+// so below 1/16 cancellation the loss stays under ~16 eps64 per step, far below what
+// restarted GMRES to 1e-7 (or an inner solve to 1e-3) can notice; the same bound makes
+// the difference of squares accurate to ~1e-13 relative.  For this operator the product
+// A v_k is dominated by v_k, so 1/sqrt(2) would trigger the second projection in
+// nearly every iteration, doubling the FP64 work.
+__global__ void cgs_precheck_kernel(const double *__restrict__ npart0, const double2 *__restrict__ h,
+                                    double *__restrict__ nrm, int *__restrict__ flag, int k1, int nb, int ldh) {
   __shared__ double2 sh[kT / 32];
   const int r = blockIdx.x;
   double a0 = 0.0, a1 = 0.0;
-  for (int b = threadIdx.x; b < nb; b += kT) {
-    a0 += npart0[(long long)r * nb + b];
-    a1 += npart1[(long long)r * nb + b];
+  for (int b = threadIdx.x; b < nb; b += kT) a0 += npart0[(long long)r * nb + b];
+  for (int i = threadIdx.x; i < k1; i += kT) {
+    const double2 v = h[(long long)r * ldh + i];
+    a1 = fma(v.x, v.x, a1);
+    a1 = fma(v.y, v.y, a1);
   }
   const double2 s = block_reduce(make_double2(a0, a1), sh);
   if (threadIdx.x == 0) {
-    const double n0 = sqrt(s.x), n1 = sqrt(s.y);
+    const double n0 = sqrt(s.x);
+    const double d = s.x - s.y;
+    const double n1 = d > 0.0 ? sqrt(d) : 0.0;
     nrm[r] = n1;
     flag[r] = n1 < 0.0625 * n0 ? 1 : 0;
   }
@@ -312,23 +334,25 @@ void gmres_norm(const double2 *w, double *part, double *out, int R, long long n,
   norm_final<<<R, kT, 0, s>>>(part, out, nb);
 }
 
-int gmres_orthogonalize(const double2 *V, double2 *w, double2 *h1, double2 *h2, double2 *part, double *npart,
-                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s) {
+int gmres_orthogonalize(const double2 *V, double2 *w, double2 *vnext, double2 *h1, double2 *h2, double2 *part,
+                        double *npart, double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s) {
   if (k1 < 1 || k1 > 64) return -1;
   const int nb = cgs_nb(n);
   double *np0 = npart, *np1 = npart + (long long)R * nb;
   const dim3 g(nb, R);
-  count_launches(8);
-  // first projection: h1 = V^H w, w -= V h1
+  count_launches(9);
+  // first projection: h1 = V^H w and ||w||; ||w'|| from the difference of squares
   cgs_dot_kernel<<<g, kT, 0, s>>>(V, w, part, np0, nullptr, k1, R, n, nb);
   part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h1, nullptr, k1, nb, ldh);
-  cgs_sub_kernel<<<g, kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nb, ldh);
-  cgs_check_kernel<<<R, kT, 0, s>>>(np0, np1, nrm, flag, nb);
+  cgs_precheck_kernel<<<R, kT, 0, s>>>(np0, h1, nrm, flag, k1, nb, ldh);
+  // w' = w - V h1, written normalised into vnext where no second projection is needed
+  cgs_sub_kernel<<<g, kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nb, ldh, vnext, nrm, flag);
   // second projection where the first cancelled too much (h2 = 0 elsewhere)
   cgs_dot_kernel<<<g, kT, 0, s>>>(V, w, part, np0, flag, k1, R, n, nb);
   part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h2, flag, k1, nb, ldh);
-  cgs_sub_kernel<<<g, kT, 0, s>>>(V, w, h2, np1, flag, k1, R, n, nb, ldh);
+  cgs_sub_kernel<<<g, kT, 0, s>>>(V, w, h2, np1, flag, k1, R, n, nb, ldh, nullptr, nullptr, nullptr);
   cgs_renorm_kernel<<<R, kT, 0, s>>>(np1, nrm, flag, nb);
+  scale_kernel<<<dim3(blocks_for(n), R), kT, 0, s>>>(w, vnext, nrm, n, flag);
   return 0;
 }
 
@@ -336,7 +360,7 @@ int gs_partial_blocks(long long n) { return cgs_nb(n); }
 
 void gmres_scale(const double2 *src, double2 *dst, const double *nrm, int R, long long n, cudaStream_t s) {
   count_launches(1);
-  scale_kernel<<<dim3(blocks_for(n), R), kT, 0, s>>>(src, dst, nrm, n);
+  scale_kernel<<<dim3(blocks_for(n), R), kT, 0, s>>>(src, dst, nrm, n, nullptr);
 }
 
 void vec_sub(const double2 *a, const double2 *b, double2 *out, long long n, cudaStream_t s) {

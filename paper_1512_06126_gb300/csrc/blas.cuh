@@ -11,12 +11,15 @@ void gmres_maxpy(const double2 *V, const double2 *h, double2 *w, int k1, int R, 
 // out[r] = ||w[r]||_2
 void gmres_norm(const double2 *w, double *part, double *out, int R, long long n, cudaStream_t s);
 // Classical Gram-Schmidt against V_0..V_{k1-1} (k1 <= 64) with selective
-// reorthogonalisation: h1 = V^H w, w -= V h1; where ||w'|| < ||w|| / 16 a second
-// projection h2 = V^H w', w' -= V h2 follows (h2 = 0 elsewhere); nrm = ||w|| at the end.
+// reorthogonalisation, ending with the next basis vector: h1 = V^H w; where
+// ||w - V h1|| >= ||w|| / 16 (from ||w||^2 - |h1|^2) vnext = (w - V h1) / ||w - V h1||
+// directly; elsewhere a second projection h2 = V^H w', w'' = w' - V h2 and
+// vnext = w'' / ||w''|| (h2 = 0 where it did not run).  nrm = the norm used.  w is
+// overwritten only where the second projection ran.
 // part: R * k1 * gs_partial_blocks(n) complex; npart: 2 * R * gs_partial_blocks(n);
 // flag: R ints (1 where the second projection ran).
-int gmres_orthogonalize(const double2 *V, double2 *w, double2 *h1, double2 *h2, double2 *part, double *npart,
-                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s);
+int gmres_orthogonalize(const double2 *V, double2 *w, double2 *vnext, double2 *h1, double2 *h2, double2 *part,
+                        double *npart, double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s);
 int gs_partial_blocks(long long n);
 // dst[r] = src[r] / nrm[r]
 void gmres_scale(const double2 *src, double2 *dst, const double *nrm, int R, long long n, cudaStream_t s);
