@@ -356,7 +356,133 @@ int gmres_orthogonalize(const double2 *V, double2 *w, double2 *vnext, double2 *h
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Givens rotations and the least-squares solution of GMRES on the device, one thread
+// per right-hand side (the Hessenberg columns never leave the GPU).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
+
+// new cycle: g = (||r_0||, 0, ...), active where ||r_0|| > thr, no columns yet
+__global__ void givens_init_kernel(GivensState st, const double *nrm, int R, int ldh) {
+  const int r = threadIdx.x;
+  __shared__ int cnt;
+  if (r == 0) cnt = 0;
+  __syncthreads();
+  if (r < R) {
+    for (int i = 0; i < ldh; ++i) st.g[(long long)r * ldh + i] = make_double2(i == 0 ? nrm[r] : 0.0, 0.0);
+    const int act = nrm[r] > st.thr[r] ? 1 : 0;
+    st.active[r] = act;
+    st.kr[r] = 0;
+    st.brk[r] = 0;
+    if (act) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (r == 0) *st.n_active = cnt;
+}
+
+// column k of the Hessenberg matrix (h1 + h2 above the diagonal, nrm below) for every
+// active right-hand side: previous rotations, the new rotation, the residual estimate
+// |g_{k+1}|; a right-hand side leaves the iteration when the estimate reaches thr or
+// the new vector vanished (breakdown).
+__global__ void givens_kernel(GivensState st, const double2 *h1, const double2 *h2, const double *nrm, int k, int R,
+                              int m, int ldh) {
+  const int r = threadIdx.x;
+  __shared__ int cnt;
+  if (r == 0) cnt = 0;
+  __syncthreads();
+  if (r < R && st.active[r]) {
+    double2 *col = st.Rm + ((long long)r * m + k) * ldh;
+    for (int i = 0; i <= k; ++i) {
+      const double2 a = h1[(long long)r * ldh + i], b = h2[(long long)r * ldh + i];
+      col[i] = make_double2(a.x + b.x, a.y + b.y);
+    }
+    const double hk1 = nrm[r];
+    for (int i = 0; i < k; ++i) {
+      const double ci = st.cs[(long long)r * m + i];
+      const double2 si = st.sn[(long long)r * m + i];
+      const double2 ai = col[i], bi = col[i + 1];
+      const double2 t = make_double2(ci * ai.x + zmul(si, bi).x, ci * ai.y + zmul(si, bi).y);
+      const double2 nb = zmul(zconj(si), ai);
+      col[i + 1] = make_double2(-nb.x + ci * bi.x, -nb.y + ci * bi.y);
+      col[i] = t;
+    }
+    const double2 a = col[k];
+    const double aa = zabs(a);
+    const double rho = hypot(aa, hk1);
+    double ck;
+    double2 sk;
+    if (aa == 0.0) {
+      ck = 0.0;
+      sk = make_double2(1.0, 0.0);
+    } else {
+      ck = aa / rho;
+      sk = make_double2(a.x / aa * hk1 / rho, a.y / aa * hk1 / rho);
+    }
+    col[k] = make_double2(ck * a.x + sk.x * hk1, ck * a.y + sk.y * hk1);
+    st.cs[(long long)r * m + k] = ck;
+    st.sn[(long long)r * m + k] = sk;
+    double2 *gr = st.g + (long long)r * ldh;
+    const double2 gk = gr[k];
+    const double2 gn = zmul(zconj(sk), gk);
+    gr[k + 1] = make_double2(-gn.x, -gn.y);
+    gr[k] = make_double2(ck * gk.x, ck * gk.y);
+    st.kr[r] = k + 1;
+    int act = 1;
+    if (hk1 == 0.0) {
+      act = 0;
+      st.brk[r] = 1;
+    }
+    if (zabs(gr[k + 1]) <= st.thr[r]) act = 0;
+    st.active[r] = act;
+  }
+  __syncthreads();
+  if (r < R && st.active[r]) atomicAdd(&cnt, 1);
+  __syncthreads();
+  if (r == 0) *st.n_active = cnt;
+}
+
+// y = R^-1 g over the kr columns of each right-hand side; yd[r * ldh + i] (zero beyond kr)
+__global__ void backsub_kernel(GivensState st, double2 *yd, int R, int m, int ldh) {
+  const int r = threadIdx.x;
+  if (r >= R) return;
+  const int kr = st.kr[r];
+  double2 *y = yd + (long long)r * ldh;
+  for (int i = kr; i < ldh; ++i) y[i] = make_double2(0.0, 0.0);
+  for (int i = kr - 1; i >= 0; --i) {
+    double2 acc = st.g[(long long)r * ldh + i];
+    for (int j = i + 1; j < kr; ++j) {
+      const double2 p = zmul(st.Rm[((long long)r * m + j) * ldh + i], y[j]);
+      acc.x -= p.x;
+      acc.y -= p.y;
+    }
+    const double2 d = st.Rm[((long long)r * m + i) * ldh + i];
+    const double dd = d.x * d.x + d.y * d.y;
+    y[i] = dd == 0.0 ? make_double2(0.0, 0.0)
+                     : make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+  }
+}
+
 int gs_partial_blocks(long long n) { return cgs_nb(n); }
+
+void givens_init(const GivensState &st, const double *nrm, int R, int ldh, cudaStream_t s) {
+  count_launches(1);
+  givens_init_kernel<<<1, 32, 0, s>>>(st, nrm, R, ldh);
+}
+
+void givens_step(const GivensState &st, const double2 *h1, const double2 *h2, const double *nrm, int k, int R, int m,
+                 int ldh, cudaStream_t s) {
+  count_launches(1);
+  givens_kernel<<<1, 32, 0, s>>>(st, h1, h2, nrm, k, R, m, ldh);
+}
+
+void givens_solve(const GivensState &st, double2 *yd, int R, int m, int ldh, cudaStream_t s) {
+  count_launches(1);
+  backsub_kernel<<<1, 32, 0, s>>>(st, yd, R, m, ldh);
+}
 
 void gmres_scale(const double2 *src, double2 *dst, const double *nrm, int R, long long n, cudaStream_t s) {
   count_launches(1);

@@ -21,6 +21,23 @@ void gmres_norm(const double2 *w, double *part, double *out, int R, long long n,
 int gmres_orthogonalize(const double2 *V, double2 *w, double2 *vnext, double2 *h1, double2 *h2, double2 *part,
                         double *npart, double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s);
 int gs_partial_blocks(long long n);
+
+// GMRES least-squares state on the device, per right-hand side r (R <= 32):
+// Rm [R][m][ldh] (rotated Hessenberg columns), cs [R][m], sn [R][m], g [R][ldh],
+// active / kr / brk [R] (still iterating, columns so far, breakdown), thr [R] (stop
+// when |g_{k+1}| <= thr), n_active [1] (right-hand sides still iterating).
+struct GivensState {
+  double2 *Rm, *sn, *g;
+  double *cs, *thr;
+  int *active, *kr, *brk, *n_active;
+};
+// start of a cycle from the residual norms nrm[R]
+void givens_init(const GivensState &st, const double *nrm, int R, int ldh, cudaStream_t s);
+// Hessenberg column k (h1 + h2 above the diagonal, nrm[r] below) for every active r
+void givens_step(const GivensState &st, const double2 *h1, const double2 *h2, const double *nrm, int k, int R, int m,
+                 int ldh, cudaStream_t s);
+// yd[r * ldh + i] = the least-squares solution over the kr[r] columns (zero beyond)
+void givens_solve(const GivensState &st, double2 *yd, int R, int m, int ldh, cudaStream_t s);
 // dst[r] = src[r] / nrm[r]
 void gmres_scale(const double2 *src, double2 *dst, const double *nrm, int R, long long n, cudaStream_t s);
 void vec_sub(const double2 *a, const double2 *b, double2 *out, long long n, cudaStream_t s);

@@ -66,6 +66,9 @@ struct ie_ctx {
   double2 *V = nullptr, *w = nullptr, *r = nullptr, *dx = nullptr, *part = nullptr, *hdev = nullptr;
   double *nrmpart = nullptr, *nrm = nullptr;
   int *gsflag = nullptr;                       // per right-hand side: second Gram-Schmidt projection ran
+  ie::GivensState gst{};                       // device least-squares state of GMRES
+  int *pin_active = nullptr;                   // pinned: active counts (slot 0: cycle start, 1..4: iterations)
+  cudaEvent_t pin_ev[4] = {};
   void *jfac = nullptr, *gdiv = nullptr;       // per cell: 2 s gamma; (dgamma/dln sigma_a) / gamma (0 off the anomaly)
   int n_rec = 0;                               // receivers (ie_set_receivers)
   int *rec_ix = nullptr, *rec_iy = nullptr;
@@ -363,6 +366,9 @@ struct Op {
 // Givens recurrence ends a cycle; a true residual at the next restart confirms it).
 // ---------------------------------------------------------------------------
 
+constexpr int kGivensLag = 2;   // iterations between issuing a Givens step and reading its count
+constexpr int kPinSlots = 4;
+
 struct GmresResult {
   int iters = 0;
   int cycles = 0;
@@ -378,100 +384,68 @@ ie_status gmres(ie_ctx *c, const Op &op, const double2 *b, double2 *x, int R, do
   const int ldh = m + 1;
   cudaStream_t s = c->stream;
   double2 *h1 = c->hdev, *h2 = c->hdev + (size_t)R * ldh, *yd = c->hdev + 2 * (size_t)R * ldh;
-  std::vector<double> bnorm(R), nrm(R);
+  const ie::GivensState &st = c->gst;
+  std::vector<double> bnorm(R), thr(R);
   ie::gmres_norm(b, c->nrmpart, c->nrm, R, n, s);
   IE_CUDA(cudaMemcpyAsync(bnorm.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, s));
   IE_CUDA(cudaStreamSynchronize(s));
-  std::vector<cd> Rm((size_t)R * ldh * m), g((size_t)R * ldh), sn((size_t)R * m);
-  std::vector<double> cs((size_t)R * m);
-  std::vector<double2> hh((size_t)2 * R * ldh), yv((size_t)R * ldh);
-  std::vector<int> kr(R);
-  std::vector<char> active(R);
+  for (int r = 0; r < R; ++r) thr[r] = tol * bnorm[r];
+  IE_CUDA(cudaMemcpyAsync(st.thr, thr.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+  std::vector<int> kr(R), brk(R);
   res->converged = false;
   res->breakdown = false;
-  int it = 0;
+  int it = 0;       // iterations issued (including the few issued after the last right-hand side stopped)
+  bool first = true;
   while (true) {
     IE_TRY(op(x, c->w, R));
     ie::vec_sub(b, c->w, c->w, nR, s);
     ie::gmres_norm(c->w, c->nrmpart, c->nrm, R, n, s);
     ie::gmres_scale(c->w, c->V, c->nrm, R, n, s);
-    IE_CUDA(cudaMemcpyAsync(nrm.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, s));
-    IE_CUDA(cudaStreamSynchronize(s));
-    int n_active = 0;
-    for (int r = 0; r < R; ++r) {
-      active[r] = nrm[r] > tol * bnorm[r];
-      n_active += active[r];
-      kr[r] = 0;
-      for (int i = 0; i < ldh; ++i) g[(size_t)r * ldh + i] = 0.0;
-      g[(size_t)r * ldh] = nrm[r];
+    if (!first) {  // the previous cycle's column counts and breakdowns, before the reset
+      IE_CUDA(cudaMemcpyAsync(kr.data(), st.kr, R * sizeof(int), cudaMemcpyDeviceToHost, s));
+      IE_CUDA(cudaMemcpyAsync(brk.data(), st.brk, R * sizeof(int), cudaMemcpyDeviceToHost, s));
     }
-    if (n_active == 0) { res->converged = true; break; }
+    ie::givens_init(st, c->nrm, R, ldh, s);
+    IE_CUDA(cudaMemcpyAsync(c->pin_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IE_CUDA(cudaStreamSynchronize(s));
+    if (!first) {
+      int kmx = 0;
+      for (int r = 0; r < R; ++r) {
+        kmx = std::max(kmx, kr[r]);
+        if (brk[r]) res->breakdown = true;
+      }
+      res->iters += kmx;
+    }
+    first = false;
+    if (c->pin_active[0] == 0) { res->converged = true; break; }
     if (it >= max_iter) break;
     res->cycles++;
+    // the cycle: products, Gram-Schmidt and Givens steps stay on the device; the host
+    // learns the number of right-hand sides still iterating from a pinned copy made
+    // kLag iterations earlier, so it never waits for the iteration it just issued
     int kmax = 0;
-    for (int k = 0; k < m && it < max_iter && n_active > 0; ++k) {
+    for (int k = 0; k < m && it < max_iter; ++k) {
+      if (k >= kGivensLag) {
+        const int slot = (k - kGivensLag) % kPinSlots;
+        IE_CUDA(cudaEventSynchronize(c->pin_ev[slot]));
+        if (c->pin_active[1 + slot] == 0) break;
+      }
       IE_TRY(op(c->V + (long long)k * nR, c->w, R));
       if (ie::gmres_orthogonalize(c->V, c->w, c->V + (long long)(k + 1) * nR, h1, h2, c->part, c->nrmpart, c->nrm,
                                   c->gsflag, k + 1, R, n, ldh, s) != 0)
         return IE_ERR_ARG;
-      IE_CUDA(cudaMemcpyAsync(hh.data(), h1, (size_t)2 * R * ldh * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      IE_CUDA(cudaMemcpyAsync(nrm.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, s));
-      IE_CUDA(cudaStreamSynchronize(s));
+      ie::givens_step(st, h1, h2, c->nrm, k, R, m, ldh, s);
+      const int slot = k % kPinSlots;
+      IE_CUDA(cudaMemcpyAsync(c->pin_active + 1 + slot, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      IE_CUDA(cudaEventRecord(c->pin_ev[slot], s));
       ++it;
       kmax = k + 1;
-      for (int r = 0; r < R; ++r) {
-        if (!active[r]) continue;
-        cd *col = &Rm[((size_t)r * m + k) * ldh];
-        for (int i = 0; i <= k; ++i) {
-          const double2 a = hh[(size_t)r * ldh + i], bb = hh[(size_t)(R + r) * ldh + i];
-          col[i] = cd(a.x + bb.x, a.y + bb.y);
-        }
-        cd hk1 = nrm[r];
-        for (int i = 0; i < k; ++i) {
-          const double ci = cs[(size_t)r * m + i];
-          const cd si = sn[(size_t)r * m + i];
-          const cd t = ci * col[i] + si * col[i + 1];
-          col[i + 1] = -std::conj(si) * col[i] + ci * col[i + 1];
-          col[i] = t;
-        }
-        const cd a = col[k];
-        const double rho = std::sqrt(std::norm(a) + std::norm(hk1));
-        double ck;
-        cd sk;
-        if (std::abs(a) == 0.0) { ck = 0.0; sk = 1.0; }
-        else { ck = std::abs(a) / rho; sk = (a / std::abs(a)) * std::conj(hk1) / rho; }
-        col[k] = ck * a + sk * hk1;
-        cs[(size_t)r * m + k] = ck;
-        sn[(size_t)r * m + k] = sk;
-        cd *gr = &g[(size_t)r * ldh];
-        gr[k + 1] = -std::conj(sk) * gr[k];
-        gr[k] = ck * gr[k];
-        kr[r] = k + 1;
-        if (nrm[r] == 0.0) { active[r] = 0; res->breakdown = true; }
-        if (std::abs(gr[k + 1]) <= tol * bnorm[r]) active[r] = 0;
-      }
-      n_active = 0;
-      for (int r = 0; r < R; ++r) n_active += active[r];
     }
-    // back substitution and x += V y
-    for (int r = 0; r < R; ++r) {
-      std::vector<cd> y(kr[r]);
-      for (int i = kr[r] - 1; i >= 0; --i) {
-        cd acc = g[(size_t)r * ldh + i];
-        for (int j = i + 1; j < kr[r]; ++j) acc -= Rm[((size_t)r * m + j) * ldh + i] * y[j];
-        const cd d = Rm[((size_t)r * m + i) * ldh + i];
-        y[i] = d == 0.0 ? cd(0.0) : acc / d;
-      }
-      for (int i = 0; i < ldh; ++i) {
-        const cd v = i < kr[r] ? y[i] : cd(0.0);
-        yv[(size_t)r * ldh + i] = make_double2(v.real(), v.imag());
-      }
-    }
-    IE_CUDA(cudaMemcpyAsync(yd, yv.data(), (size_t)R * ldh * sizeof(double2), cudaMemcpyHostToDevice, s));
+    // x += V y with y from the rotated least-squares problem (zero beyond each kr)
+    ie::givens_solve(st, yd, R, m, ldh, s);
     ie::gmres_maxpy(c->V, yd, x, kmax, R, n, ldh, 1.0, s);
     IE_CUDA(cudaGetLastError());
   }
-  res->iters = it;
   return IE_OK;
 }
 
@@ -653,6 +627,9 @@ void ie_destroy(ie_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   prof_clear(c);
   for (void *p : c->allocs) cudaFree(p);
+  if (c->pin_active) cudaFreeHost(c->pin_active);
+  for (auto &e : c->pin_ev)
+    if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -874,6 +851,20 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   IE_TRY(dalloc(c, &c->nrmpart, (size_t)2 * max_rhs * std::max<long long>(1024, nbp) * sizeof(double)));
   IE_TRY(dalloc(c, &c->gsflag, (size_t)max_rhs * sizeof(int)));
   IE_TRY(dalloc(c, &c->nrm, (size_t)2 * max_rhs * sizeof(double)));
+  {
+    const int m = c->restart, ldh = m + 1;
+    IE_TRY(dalloc(c, &c->gst.Rm, (size_t)max_rhs * m * ldh * sizeof(double2)));
+    IE_TRY(dalloc(c, &c->gst.sn, (size_t)max_rhs * m * sizeof(double2)));
+    IE_TRY(dalloc(c, &c->gst.g, (size_t)max_rhs * ldh * sizeof(double2)));
+    IE_TRY(dalloc(c, &c->gst.cs, (size_t)max_rhs * m * sizeof(double)));
+    IE_TRY(dalloc(c, &c->gst.thr, (size_t)max_rhs * sizeof(double)));
+    IE_TRY(dalloc(c, &c->gst.active, (size_t)max_rhs * sizeof(int)));
+    IE_TRY(dalloc(c, &c->gst.kr, (size_t)max_rhs * sizeof(int)));
+    IE_TRY(dalloc(c, &c->gst.brk, (size_t)max_rhs * sizeof(int)));
+    IE_TRY(dalloc(c, &c->gst.n_active, sizeof(int)));
+    IE_CUDA(cudaHostAlloc((void **)&c->pin_active, (1 + kPinSlots) * sizeof(int), cudaHostAllocDefault));
+    for (int k = 0; k < kPinSlots; ++k) IE_CUDA(cudaEventCreateWithFlags(&c->pin_ev[k], cudaEventDisableTiming));
+  }
   IE_CUDA(cudaStreamSynchronize(c->stream));
   if (c->autotune) IE_TRY(autotune_contraction(c));
   return IE_OK;
