@@ -376,49 +376,108 @@ struct GmresResult {
   bool breakdown = false;
 };
 
-ie_status gmres(ie_ctx *c, const Op &op, const double2 *b, double2 *x, int R, double tol, int max_iter,
-                GmresResult *res) {
+// Swap the blocks p and q (elem elements each) of a, through the scratch tmp.
+ie_status swap_blocks(double2 *a, int p, int q, long long elem, double2 *tmp, cudaStream_t s) {
+  const size_t bytes = (size_t)elem * sizeof(double2);
+  IE_CUDA(cudaMemcpyAsync(tmp, a + p * elem, bytes, cudaMemcpyDeviceToDevice, s));
+  IE_CUDA(cudaMemcpyAsync(a + p * elem, a + q * elem, bytes, cudaMemcpyDeviceToDevice, s));
+  IE_CUDA(cudaMemcpyAsync(a + q * elem, tmp, bytes, cudaMemcpyDeviceToDevice, s));
+  return IE_OK;
+}
+
+// Restarted GMRES on the group g0 (its instances' blocks of rpi right-hand sides).
+// With compact (several instances; b then is scratch the solver may reorder), an
+// instance whose right-hand sides have all converged leaves the lockstep at the next
+// restart: its blocks of b and x swap places with an active instance's, and the
+// remaining cycles run on the smaller group.  x is back in the original order on
+// return.
+ie_status gmres(ie_ctx *c, const Group &g0, int transpose, bool single, double2 *b, double2 *x, double tol,
+                int max_iter, GmresResult *res, bool compact) {
   const long long n = c->nvec();
-  const long long nR = n * R;
   const int m = c->restart;
   const int ldh = m + 1;
+  const int rpi = g0.rpi;
+  const long long blk = n * rpi;
   cudaStream_t s = c->stream;
+  Group g = g0;
+  const Op op{c, &g, transpose, single};
+  int R = g.R();
+  long long nR = n * R;
+  const int G = (int)g0.inst.size();
+  std::vector<int> inst_at(G);  // original block index of the block now at each position
+  for (int k = 0; k < G; ++k) inst_at[k] = k;
+  compact = compact && G > 1;
   double2 *h1 = c->hdev, *h2 = c->hdev + (size_t)R * ldh, *yd = c->hdev + 2 * (size_t)R * ldh;
   const ie::GivensState &st = c->gst;
   std::vector<double> bnorm(R), thr(R);
   ie::gmres_norm(b, c->nrmpart, c->nrm, R, n, s);
   IE_CUDA(cudaMemcpyAsync(bnorm.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, s));
   IE_CUDA(cudaStreamSynchronize(s));
-  for (int r = 0; r < R; ++r) thr[r] = tol * bnorm[r];
-  IE_CUDA(cudaMemcpyAsync(st.thr, thr.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
-  std::vector<int> kr(R), brk(R);
+  auto upload_thr = [&]() -> ie_status {
+    for (int r = 0; r < R; ++r) thr[r] = tol * bnorm[r];
+    IE_CUDA(cudaMemcpyAsync(st.thr, thr.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+    return IE_OK;
+  };
+  IE_TRY(upload_thr());
+  std::vector<int> kr(R), brk(R), act(R);
   res->converged = false;
   res->breakdown = false;
-  int it = 0;       // iterations issued (including the few issued after the last right-hand side stopped)
-  bool first = true;
+  int it = 0;  // iterations issued (including the few issued after the last right-hand side stopped)
+  bool pending = false;  // a finished cycle's column counts are being copied
+  int R_prev = R;
   while (true) {
+    h1 = c->hdev;
+    h2 = c->hdev + (size_t)R * ldh;
+    yd = c->hdev + 2 * (size_t)R * ldh;
     IE_TRY(op(x, c->w, R));
     ie::vec_sub(b, c->w, c->w, nR, s);
     ie::gmres_norm(c->w, c->nrmpart, c->nrm, R, n, s);
     ie::gmres_scale(c->w, c->V, c->nrm, R, n, s);
-    if (!first) {  // the previous cycle's column counts and breakdowns, before the reset
-      IE_CUDA(cudaMemcpyAsync(kr.data(), st.kr, R * sizeof(int), cudaMemcpyDeviceToHost, s));
-      IE_CUDA(cudaMemcpyAsync(brk.data(), st.brk, R * sizeof(int), cudaMemcpyDeviceToHost, s));
-    }
     ie::givens_init(st, c->nrm, R, ldh, s);
     IE_CUDA(cudaMemcpyAsync(c->pin_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (compact) IE_CUDA(cudaMemcpyAsync(act.data(), st.active, R * sizeof(int), cudaMemcpyDeviceToHost, s));
     IE_CUDA(cudaStreamSynchronize(s));
-    if (!first) {
+    if (pending) {
       int kmx = 0;
-      for (int r = 0; r < R; ++r) {
+      for (int r = 0; r < R_prev; ++r) {
         kmx = std::max(kmx, kr[r]);
         if (brk[r]) res->breakdown = true;
       }
       res->iters += kmx;
+      pending = false;
     }
-    first = false;
     if (c->pin_active[0] == 0) { res->converged = true; break; }
     if (it >= max_iter) break;
+    if (compact) {
+      // instances with no right-hand side left above its threshold leave the group
+      const int Gc = (int)g.inst.size();
+      std::vector<char> ia(Gc, 0);
+      int n_act = 0;
+      for (int p = 0; p < Gc; ++p) {
+        for (int j = 0; j < rpi; ++j) ia[p] |= act[p * rpi + j] ? 1 : 0;
+        n_act += ia[p];
+      }
+      if (n_act < Gc) {
+        int p = 0, q = Gc - 1;
+        while (p < q) {
+          if (ia[p]) { ++p; continue; }
+          if (!ia[q]) { --q; continue; }
+          IE_TRY(swap_blocks(b, p, q, blk, c->w, s));
+          IE_TRY(swap_blocks(x, p, q, blk, c->w, s));
+          std::swap(inst_at[p], inst_at[q]);
+          std::swap(g.inst[p], g.inst[q]);
+          for (int j = 0; j < rpi; ++j) std::swap(bnorm[p * rpi + j], bnorm[q * rpi + j]);
+          std::swap(ia[p], ia[q]);
+          ++p;
+          --q;
+        }
+        g.inst.resize(n_act);
+        R = n_act * rpi;
+        nR = n * R;
+        IE_TRY(upload_thr());
+        continue;  // residual of the smaller group
+      }
+    }
     res->cycles++;
     // the cycle: products, Gram-Schmidt and Givens steps stay on the device; the host
     // learns the number of right-hand sides still iterating from a pinned copy made
@@ -444,8 +503,29 @@ ie_status gmres(ie_ctx *c, const Op &op, const double2 *b, double2 *x, int R, do
     // x += V y with y from the rotated least-squares problem (zero beyond each kr)
     ie::givens_solve(st, yd, R, m, ldh, s);
     ie::gmres_maxpy(c->V, yd, x, kmax, R, n, ldh, 1.0, s);
+    IE_CUDA(cudaMemcpyAsync(kr.data(), st.kr, R * sizeof(int), cudaMemcpyDeviceToHost, s));
+    IE_CUDA(cudaMemcpyAsync(brk.data(), st.brk, R * sizeof(int), cudaMemcpyDeviceToHost, s));
+    pending = true;
+    R_prev = R;
     IE_CUDA(cudaGetLastError());
   }
+  if (pending) {  // only reached when the loop left before the next synchronisation
+    IE_CUDA(cudaStreamSynchronize(s));
+    int kmx = 0;
+    for (int r = 0; r < R_prev; ++r) {
+      kmx = std::max(kmx, kr[r]);
+      if (brk[r]) res->breakdown = true;
+    }
+    res->iters += kmx;
+  }
+  // blocks back to their original positions
+  for (int p = 0; p < G; ++p)
+    while (inst_at[p] != p) {
+      const int q = inst_at[p];
+      IE_TRY(swap_blocks(x, p, q, blk, c->w, s));
+      IE_TRY(swap_blocks(b, p, q, blk, c->w, s));
+      std::swap(inst_at[p], inst_at[q]);
+    }
   return IE_OK;
 }
 
@@ -483,7 +563,14 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
   std::vector<double> rel;
   if (precision == IE_FP64) {
     GmresResult gr;
-    IE_TRY(gmres(c, Op{c, &g, transpose, false}, b, u, R, tol, c->max_iter, &gr));
+    // several instances: GMRES reorders the right-hand sides, so it works on a copy of b
+    const bool comp = g.inst.size() > 1;
+    double2 *bw = const_cast<double2 *>(b);
+    if (comp) {
+      IE_CUDA(cudaMemcpyAsync(c->r, b, n * R * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+      bw = c->r;
+    }
+    IE_TRY(gmres(c, g, transpose, false, bw, u, tol, c->max_iter, &gr, comp));
     inf.inner_iters = gr.iters;
     inf.outer_iters = gr.cycles;
     conv = gr.converged;
@@ -530,8 +617,8 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
       IE_CUDA(cudaMemsetAsync(c->dx, 0, n * Ra * sizeof(double2), c->stream));
       GmresResult gr;
       const double itol = std::max(c->inner_tol, 0.5 * tol / std::max(worst, 1e-300));
-      IE_TRY(gmres(c, Op{c, &act, transpose, true}, c->r, c->dx, Ra, std::min(itol, 0.5),
-                   c->max_iter - inner_total, &gr));
+      IE_TRY(gmres(c, act, transpose, true, c->r, c->dx, std::min(itol, 0.5), c->max_iter - inner_total, &gr,
+                   act.inst.size() > 1));
       inner_total += gr.iters;
       brk = brk || gr.breakdown;
       for (size_t a = 0; a < pos.size(); ++a)
