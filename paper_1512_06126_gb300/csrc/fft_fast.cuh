@@ -160,16 +160,23 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_fwd_kernel(
   const int cz0 = blockIdx.x * kTI;
   const int y = blockIdx.y;
   fill_table(tw, L);
-  for (int e = threadIdx.x; e < Nx * kTI; e += blockDim.x) {
-    const int tt = e / Nx, xx = e % Nx;
-    const int cz = cz0 + tt;
-    float2 v = make_float2(0.f, 0.f);
-    if (cz < CZ) {
-      typename cplx<TX>::type u = x[((long long)cz * Ny + y) * Nx + xx];
-      if (in_scale) u = cmul(u, in_scale[((long long)(cz % Nz) * Ny + y) * Nx + xx]);
-      v = to_f<TX>(u);
+  // Nx = L / 2 = 8 Q here, so the staging loop has a compile-time trip count and its
+  // loads are issued together
+  constexpr int NXC = 8 * Q, NT = kTI * (Q > 16 ? Q : 16);
+#pragma unroll
+  for (int it = 0; it < (NXC * kTI + NT - 1) / NT; ++it) {
+    const int e = threadIdx.x + it * NT;
+    if (e < NXC * kTI) {
+      const int tt = e / NXC, xx = e % NXC;
+      const int cz = cz0 + tt;
+      float2 v = make_float2(0.f, 0.f);
+      if (cz < CZ) {
+        typename cplx<TX>::type u = x[((long long)cz * Ny + y) * NXC + xx];
+        if (in_scale) u = cmul(u, in_scale[((long long)(cz % Nz) * Ny + y) * NXC + xx]);
+        v = to_f<TX>(u);
+      }
+      Y[xx * LD + tt] = v;
     }
-    Y[xx * LD + tt] = v;
   }
   __syncthreads();
   float2 v[16];
@@ -230,12 +237,15 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_inv_kernel(
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < Nx * kTI; e += blockDim.x) {
-    const int tt = e / Nx, xx = e % Nx;
+  constexpr int NXC = 8 * Q, NT = kTI * (Q > 16 ? Q : 16);
+#pragma unroll
+  for (int it = 0; it < (NXC * kTI + NT - 1) / NT; ++it) {
+    const int e = threadIdx.x + it * NT;
+    const int tt = e / NXC, xx = e % NXC;
     const int cz = cz0 + tt;
-    if (cz < CZ) {
-      const long long cell = ((long long)(cz % Nz) * Ny + y) * Nx + xx;
-      const long long gi = ((long long)cz * Ny + y) * Nx + xx;
+    if (e < NXC * kTI && cz < CZ) {
+      const long long cell = ((long long)(cz % Nz) * Ny + y) * NXC + xx;
+      const long long gi = ((long long)cz * Ny + y) * NXC + xx;
       const float2 r = Y[xx * LD + tt];
       V val = cmul(mk<TX>((TX)r.x, (TX)r.y), out_scale[cell]);
       if (diag) cfma(val, diag[cell], x[gi]);
