@@ -154,10 +154,11 @@ ie_status ie_matvec(ie_ctx *ctx, int inst, const void *x_dev, void *y_dev, int n
                     void *stream);
 
 /* Solve A u = b for instance inst (Sect. 3.3 (ii): restarted GMRES; classical
- * Gram-Schmidt in FP64 with a second projection wherever the first one cancels more
- * than 15/16 of the new vector's norm).  precision IE_FP64: every product with the c128 operator.
- * IE_MIXED: iterative refinement whose residual uses the c128 operator and whose
- * corrections come from GMRES on the c64 operator with FP64 Arnoldi vectors.
+ * Gram-Schmidt with a second projection wherever the first one cancels more than
+ * 15/16 of the new vector's norm).  precision IE_FP64: c128 vectors and every product
+ * with the c128 operator.  IE_MIXED: iterative refinement whose residual uses the c128
+ * operator and whose corrections come from GMRES in c64 (c64 operator, c64 Krylov
+ * vectors; Hessenberg entries, norms and rotations in FP64).
  * Stops when ||b - A u|| <= tol ||b|| for every right-hand side.
  * b_dev, u_dev: device c128 [nrhs][3][Nz][Ny][Nx]; if use_x0 the initial guess is
  * read from u_dev, otherwise it is zero. */

@@ -1,7 +1,10 @@
-// FP64 Krylov kernels for restarted GMRES (the iterative method of Sect. 3.3 (ii)):
+// Krylov kernels for restarted GMRES (the iterative method of Sect. 3.3 (ii)):
 // classical Gram-Schmidt with selective reorthogonalisation, norms, scaling and the
 // basis update.  All right-hand sides advance in lockstep; each has its own Krylov
-// space.
+// space.  Vectors are c128 (the FP64 solver) or c64 (the inner solver of the mixed
+// precision refinement); the Hessenberg entries, norms and every cross-thread sum are
+// FP64.  c64 kernels form short per-thread sums (at most 64 terms) in FP32 and
+// combine them in FP64.
 //
 // Layout: a basis vector block is V[i][r][n] (basis index i, right-hand side r,
 // element n), so basis vector i of right-hand side r starts at V + (i*R + r)*n.
@@ -36,38 +39,49 @@ __device__ __forceinline__ double2 block_reduce(double2 v, double2 *sh) {
   return r;
 }
 
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+template <typename T> __device__ __forceinline__ C<T> to_c(double2 v) { return mk<T>((T)v.x, (T)v.y); }
+
 // w[r] -= sum_{i<k1} h[r * ldh + i] * V_i[r]   (sign = -1), or x[r] += ... (sign = +1)
-__global__ void maxpy_kernel(const double2 *__restrict__ V, const double2 *__restrict__ h, double2 *__restrict__ w,
-                             int k1, int R, long long n, int ldh, double sign) {
+template <typename T>
+__global__ void maxpy_kernel(const C<T> *__restrict__ V, const double2 *__restrict__ h, C<T> *__restrict__ w, int k1,
+                             int R, long long n, int ldh, double sign) {
+  __shared__ C<T> hs[64];
   const int r = blockIdx.y;
-  const double2 *hr = h + (long long)r * ldh;
+  if (threadIdx.x < k1) hs[threadIdx.x] = to_c<T>(h[(long long)r * ldh + threadIdx.x]);
+  __syncthreads();
+  const T sg = (T)sign;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
+    C<T> acc = mk<T>(0, 0);
     for (int i = 0; i < k1; ++i) {
-      const double2 a = V[((long long)i * R + r) * n + idx];
-      const double2 c = hr[i];
-      acc.x = fma(c.x, a.x, acc.x);
-      acc.x = fma(-c.y, a.y, acc.x);
-      acc.y = fma(c.x, a.y, acc.y);
-      acc.y = fma(c.y, a.x, acc.y);
+      const C<T> a = V[((long long)i * R + r) * n + idx];
+      const C<T> c = hs[i];
+      acc.x = mad(c.x, a.x, acc.x);
+      acc.x = mad(-c.y, a.y, acc.x);
+      acc.y = mad(c.x, a.y, acc.y);
+      acc.y = mad(c.y, a.x, acc.y);
     }
-    double2 v = w[(long long)r * n + idx];
-    v.x += sign * acc.x;
-    v.y += sign * acc.y;
+    C<T> v = w[(long long)r * n + idx];
+    v.x += sg * acc.x;
+    v.y += sg * acc.y;
     w[(long long)r * n + idx] = v;
   }
 }
 
-__global__ void __launch_bounds__(kT) norm_partial(const double2 *__restrict__ w, double *__restrict__ part,
-                                                   long long n, int nb) {
+// (FP64 sums also for c64 vectors: the norms set the thresholds and the first basis
+// vector of every cycle)
+template <typename T>
+__global__ void __launch_bounds__(kT) norm_partial(const C<T> *__restrict__ w, double *__restrict__ part, long long n,
+                                                   int nb) {
   __shared__ double2 sh[kT / 32];
   const int r = blockIdx.y;
   double acc = 0.0;
   for (long long idx = blockIdx.x * (long long)kT + threadIdx.x; idx < n; idx += (long long)nb * kT) {
-    const double2 v = w[(long long)r * n + idx];
-    acc = fma(v.x, v.x, acc);
-    acc = fma(v.y, v.y, acc);
+    const C<T> v = w[(long long)r * n + idx];
+    acc = fma((double)v.x, (double)v.x, acc);
+    acc = fma((double)v.y, (double)v.y, acc);
   }
   const double2 s = block_reduce(make_double2(acc, 0.0), sh);
   if (threadIdx.x == 0) part[(long long)r * nb + blockIdx.x] = s.x;
@@ -83,98 +97,113 @@ __global__ void norm_final(const double *__restrict__ part, double *__restrict__
 }
 
 // dst[r] = src[r] / nrm[r]  (dst may alias src)
-__global__ void scale_kernel(const double2 *__restrict__ src, double2 *__restrict__ dst, const double *__restrict__ nrm,
+template <typename T>
+__global__ void scale_kernel(const C<T> *__restrict__ src, C<T> *__restrict__ dst, const double *__restrict__ nrm,
                              long long n, const int *__restrict__ flag) {
   const int r = blockIdx.y;
   if (flag && !flag[r]) return;
-  const double s = nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0;
+  const T s = (T)(nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
-    double2 v = src[(long long)r * n + idx];
-    dst[(long long)r * n + idx] = make_double2(v.x * s, v.y * s);
+    C<T> v = src[(long long)r * n + idx];
+    dst[(long long)r * n + idx] = mk<T>(v.x * s, v.y * s);
   }
 }
 
 // out = a - b
-__global__ void sub_kernel(const double2 *__restrict__ a, const double2 *__restrict__ b, double2 *__restrict__ out,
+template <typename T>
+__global__ void sub_kernel(const C<T> *__restrict__ a, const C<T> *__restrict__ b, C<T> *__restrict__ out,
                            long long n) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
-    const double2 u = a[idx], v = b[idx];
-    out[idx] = make_double2(u.x - v.x, u.y - v.y);
+    const C<T> u = a[idx], v = b[idx];
+    out[idx] = mk<T>(u.x - v.x, u.y - v.y);
   }
 }
 
-// y += x
-__global__ void add_kernel(const double2 *__restrict__ x, double2 *__restrict__ y, long long n) {
+// y += x  (x c128 or c64, y c128)
+template <typename T>
+__global__ void add_kernel(const C<T> *__restrict__ x, double2 *__restrict__ y, long long n) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
-    const double2 u = x[idx];
+    const C<T> u = x[idx];
     double2 v = y[idx];
-    v.x += u.x;
-    v.y += u.y;
+    v.x += (double)u.x;
+    v.y += (double)u.y;
     y[idx] = v;
   }
 }
 
+// y = x rounded to c64
+__global__ void round_kernel(const double2 *__restrict__ x, float2 *__restrict__ y, long long n) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double2 u = x[idx];
+    y[idx] = make_float2((float)u.x, (float)u.y);
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Classical Gram-Schmidt with selective reorthogonalisation.  FP64 arithmetic sets
-// the pace here (the vector length times the basis size in complex FMAs per pass), so
-// the passes are organised to spend the FP64 pipe on multiply-adds and little else.
+// Classical Gram-Schmidt with selective reorthogonalisation.  In FP64 the arithmetic
+// sets the pace (the vector length times the basis size in complex FMAs per pass), so
+// the passes are organised to spend the FP64 pipe on multiply-adds and little else; in
+// FP32 the same passes are bound by the basis reads from HBM.
 // A block owns a tile of kTile consecutive elements of one right-hand side.
 //   dot pass: part_i = sum_tile conj(V_i) x  and  npart = sum_tile |x|^2
 //   sub pass: x -= sum_i h_i V_i on the tile  and  npart = sum_tile |x|^2
 // In the dot pass the tile of x sits in shared memory and warp j owns basis vectors
 // j, j + 8, ...: each lane accumulates over 64 elements of the tile before a single
-// warp reduction per (vector, tile).  With a per-right-hand-side flag the block of a
-// right-hand side whose flag is 0 returns at once.
+// warp reduction (in FP64) per (vector, tile).  With a per-right-hand-side flag the
+// block of a right-hand side whose flag is 0 returns at once.
 // ---------------------------------------------------------------------------
 constexpr int kTileEPT = 8;
 constexpr int kTile = kT * kTileEPT;  // 2048 elements
 
-__global__ void __launch_bounds__(kT) cgs_dot_kernel(const double2 *__restrict__ V, const double2 *__restrict__ x,
+template <typename T>
+__global__ void __launch_bounds__(kT) cgs_dot_kernel(const C<T> *__restrict__ V, const C<T> *__restrict__ x,
                                                      double2 *__restrict__ part, double *__restrict__ npart,
                                                      const int *__restrict__ flag, int k1, int R, long long n,
                                                      int nb) {
-  __shared__ double2 xw[kTile];
+  __shared__ C<T> xw[kTile];
   __shared__ double2 shn[kT / 32];
   const int r = blockIdx.y;
   if (flag && !flag[r]) return;
   const long long t0 = (long long)blockIdx.x * kTile;
   const int tid = threadIdx.x;
-  const double2 *xr = x + (long long)r * n;
-  double nacc = 0.0;
+  const C<T> *xr = x + (long long)r * n;
+  const C<T> zero = mk<T>(0, 0);
+  T nacc = 0;
 #pragma unroll
   for (int j = 0; j < kTileEPT; ++j) {
     const long long e = t0 + j * kT + tid;
-    const double2 v = e < n ? xr[e] : make_double2(0.0, 0.0);
+    const C<T> v = e < n ? xr[e] : zero;
     xw[j * kT + tid] = v;
-    nacc = fma(v.x, v.x, nacc);
-    nacc = fma(v.y, v.y, nacc);
+    nacc = mad(v.x, v.x, nacc);
+    nacc = mad(v.y, v.y, nacc);
   }
-  const double2 sres = block_reduce(make_double2(nacc, 0.0), shn);  // also orders the xw stores
+  const double2 sres = block_reduce(make_double2((double)nacc, 0.0), shn);  // also orders the xw stores
   if (tid == 0) npart[(long long)r * nb + blockIdx.x] = sres.x;
   const int lane = tid & 31, wid = tid >> 5;
   const long long lim = n - t0;  // elements of the tile inside the vector
   for (int i = wid; i < k1; i += kT / 32) {
-    const double2 *vi = V + ((long long)i * R + r) * n + t0;
-    double ax0 = 0.0, ay0 = 0.0, ax1 = 0.0, ay1 = 0.0;
+    const C<T> *vi = V + ((long long)i * R + r) * n + t0;
+    T ax0 = 0, ay0 = 0, ax1 = 0, ay1 = 0;
 #pragma unroll 8
     for (int q = 0; q < kTile / 32; q += 2) {
       const int l0 = q * 32 + lane, l1 = l0 + 32;
-      const double2 a0 = l0 < lim ? __ldg(vi + l0) : make_double2(0.0, 0.0);
-      const double2 a1 = l1 < lim ? __ldg(vi + l1) : make_double2(0.0, 0.0);
-      const double2 b0 = xw[l0], b1 = xw[l1];
-      ax0 = fma(a0.x, b0.x, ax0);
-      ax0 = fma(a0.y, b0.y, ax0);
-      ay0 = fma(a0.x, b0.y, ay0);
-      ay0 = fma(-a0.y, b0.x, ay0);
-      ax1 = fma(a1.x, b1.x, ax1);
-      ax1 = fma(a1.y, b1.y, ax1);
-      ay1 = fma(a1.x, b1.y, ay1);
-      ay1 = fma(-a1.y, b1.x, ay1);
+      const C<T> a0 = l0 < lim ? __ldg(vi + l0) : zero;
+      const C<T> a1 = l1 < lim ? __ldg(vi + l1) : zero;
+      const C<T> b0 = xw[l0], b1 = xw[l1];
+      ax0 = mad(a0.x, b0.x, ax0);
+      ax0 = mad(a0.y, b0.y, ax0);
+      ay0 = mad(a0.x, b0.y, ay0);
+      ay0 = mad(-a0.y, b0.x, ay0);
+      ax1 = mad(a1.x, b1.x, ax1);
+      ax1 = mad(a1.y, b1.y, ax1);
+      ay1 = mad(a1.x, b1.y, ay1);
+      ay1 = mad(-a1.y, b1.x, ay1);
     }
-    double ax = ax0 + ax1, ay = ay0 + ay1;
+    double ax = (double)ax0 + (double)ax1, ay = (double)ay0 + (double)ay1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       ax += __shfl_down_sync(0xffffffffu, ax, o);
@@ -189,73 +218,76 @@ __global__ void __launch_bounds__(kT) cgs_dot_kernel(const double2 *__restrict__
 // (the next basis vector, normalised by the norm known in advance) and no norm
 // partial; one whose oflag is 1 gets x' in x as above.  A right-hand side whose
 // flag (if given) is 0 is skipped.
-__global__ void __launch_bounds__(kT) cgs_sub_kernel(const double2 *__restrict__ V, double2 *__restrict__ x,
+template <typename T>
+__global__ void __launch_bounds__(kT) cgs_sub_kernel(const C<T> *__restrict__ V, C<T> *__restrict__ x,
                                                      const double2 *__restrict__ h, double *__restrict__ npart,
                                                      const int *__restrict__ flag, int k1, int R, long long n,
-                                                     int nb, int ldh, double2 *__restrict__ vout,
+                                                     int nb, int ldh, C<T> *__restrict__ vout,
                                                      const double *__restrict__ nrm, const int *__restrict__ oflag) {
-  __shared__ double2 hs[64];
+  __shared__ C<T> hs[64];
   __shared__ double2 shn[kT / 32];
   const int r = blockIdx.y;
   if (flag && !flag[r]) return;
   const bool scaled = vout && !oflag[r];
   const long long t0 = (long long)blockIdx.x * kTile;
   const int tid = threadIdx.x;
-  double2 *xr = x + (long long)r * n;
-  if (tid < k1) hs[tid] = h[(long long)r * ldh + tid];
+  C<T> *xr = x + (long long)r * n;
+  if (tid < k1) hs[tid] = to_c<T>(h[(long long)r * ldh + tid]);
   __syncthreads();
-  double2 v[kTileEPT];
+  C<T> v[kTileEPT];
 #pragma unroll
   for (int j = 0; j < kTileEPT; ++j) {
     const long long e = t0 + j * kT + tid;
-    v[j] = e < n ? xr[e] : make_double2(0.0, 0.0);
+    v[j] = e < n ? xr[e] : mk<T>(0, 0);
   }
   for (int i = 0; i < k1; ++i) {
-    const double2 hv = hs[i];
-    const double2 *vi = V + ((long long)i * R + r) * n;
+    const C<T> hv = hs[i];
+    const C<T> *vi = V + ((long long)i * R + r) * n;
 #pragma unroll
     for (int j = 0; j < kTileEPT; ++j) {
       const long long e = t0 + j * kT + tid;
       if (e < n) {
-        const double2 a = __ldg(vi + e);
-        v[j].x = fma(-hv.x, a.x, v[j].x);
-        v[j].x = fma(hv.y, a.y, v[j].x);
-        v[j].y = fma(-hv.x, a.y, v[j].y);
-        v[j].y = fma(-hv.y, a.x, v[j].y);
+        const C<T> a = __ldg(vi + e);
+        v[j].x = mad(-hv.x, a.x, v[j].x);
+        v[j].x = mad(hv.y, a.y, v[j].x);
+        v[j].y = mad(-hv.x, a.y, v[j].y);
+        v[j].y = mad(-hv.y, a.x, v[j].y);
       }
     }
   }
   if (scaled) {
-    const double sc = nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0;
-    double2 *vr = vout + (long long)r * n;
+    const T sc = (T)(nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0);
+    C<T> *vr = vout + (long long)r * n;
 #pragma unroll
     for (int j = 0; j < kTileEPT; ++j) {
       const long long e = t0 + j * kT + tid;
-      if (e < n) vr[e] = make_double2(v[j].x * sc, v[j].y * sc);
+      if (e < n) vr[e] = mk<T>(v[j].x * sc, v[j].y * sc);
     }
     return;
   }
-  double nacc = 0.0;
+  T nacc = 0;
 #pragma unroll
   for (int j = 0; j < kTileEPT; ++j) {
     const long long e = t0 + j * kT + tid;
     if (e < n) xr[e] = v[j];
-    nacc = fma(v[j].x, v[j].x, nacc);
-    nacc = fma(v[j].y, v[j].y, nacc);
+    nacc = mad(v[j].x, v[j].x, nacc);
+    nacc = mad(v[j].y, v[j].y, nacc);
   }
-  const double2 sres = block_reduce(make_double2(nacc, 0.0), shn);
+  const double2 sres = block_reduce(make_double2((double)nacc, 0.0), shn);
   if (tid == 0) npart[(long long)r * nb + blockIdx.x] = sres.x;
 }
 
 // Before the subtraction: ||x'||^2 = ||x||^2 - sum_i |h_i|^2 (x' = x - V h is the part
 // of x orthogonal to the basis), flag[r] = 1 where ||x'|| < ||x|| / 16.  The test is
 // that of Daniel, Gragg, Kaufman and Stewart with a looser threshold than their
-// 1/sqrt(2): one projection leaves x' orthogonal to V up to about eps64 ||x|| / ||x'||,
-// so below 1/16 cancellation the loss stays under ~16 eps64 per step, far below what
-// restarted GMRES to 1e-7 (or an inner solve to 1e-3) can notice; the same bound makes
-// the difference of squares accurate to ~1e-13 relative.  For this operator the product
-// A v_k is dominated by v_k, so 1/sqrt(2) would trigger the second projection in
-// nearly every iteration, doubling the FP64 work.
+// 1/sqrt(2): one projection leaves x' orthogonal to V up to about eps ||x|| / ||x'||,
+// so below 1/16 cancellation the loss stays under ~16 eps per step: ~4e-15 in FP64,
+// far below what restarted GMRES to 1e-7 can notice, and ~2e-6 in FP32, below the
+// relative tolerance (>= 1e-4) of the inner solves that run in FP32.  The difference of
+// squares is as accurate as the sums (FP64 ~1e-13, FP32 ~1e-6 of ||x||^2), i.e. at
+// worst 256 times less relative to ||x'||^2.  For this operator the product A v_k is
+// dominated by v_k, so 1/sqrt(2) would trigger the second projection in nearly every
+// iteration, doubling the work.
 __global__ void cgs_precheck_kernel(const double *__restrict__ npart0, const double2 *__restrict__ h,
                                     double *__restrict__ nrm, int *__restrict__ flag, int k1, int nb, int ldh) {
   __shared__ double2 sh[kT / 32];
@@ -320,39 +352,42 @@ int blocks_for(long long n) {
 
 int mdot_nb(long long n) { return (int)((n + kChunk - 1) / kChunk); }
 
-void gmres_maxpy(const double2 *V, const double2 *h, double2 *w, int k1, int R, long long n, int ldh, double sign,
+template <typename T>
+void gmres_maxpy(const C<T> *V, const double2 *h, C<T> *w, int k1, int R, long long n, int ldh, double sign,
                  cudaStream_t s) {
   count_launches(1);
-  maxpy_kernel<<<dim3(blocks_for(n), R), kT, 0, s>>>(V, h, w, k1, R, n, ldh, sign);
+  maxpy_kernel<T><<<dim3(blocks_for(n), R), kT, 0, s>>>(V, h, w, k1, R, n, ldh, sign);
 }
 
-void gmres_norm(const double2 *w, double *part, double *out, int R, long long n, cudaStream_t s) {
+template <typename T>
+void gmres_norm(const C<T> *w, double *part, double *out, int R, long long n, cudaStream_t s) {
   int nb = mdot_nb(n);
   if (nb > 1024) nb = 1024;
   count_launches(2);
-  norm_partial<<<dim3(nb, R), kT, 0, s>>>(w, part, n, nb);
+  norm_partial<T><<<dim3(nb, R), kT, 0, s>>>(w, part, n, nb);
   norm_final<<<R, kT, 0, s>>>(part, out, nb);
 }
 
-int gmres_orthogonalize(const double2 *V, double2 *w, double2 *vnext, double2 *h1, double2 *h2, double2 *part,
-                        double *npart, double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s) {
+template <typename T>
+int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double2 *h2, double2 *part, double *npart,
+                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s) {
   if (k1 < 1 || k1 > 64) return -1;
   const int nb = cgs_nb(n);
   double *np0 = npart, *np1 = npart + (long long)R * nb;
   const dim3 g(nb, R);
   count_launches(9);
   // first projection: h1 = V^H w and ||w||; ||w'|| from the difference of squares
-  cgs_dot_kernel<<<g, kT, 0, s>>>(V, w, part, np0, nullptr, k1, R, n, nb);
+  cgs_dot_kernel<T><<<g, kT, 0, s>>>(V, w, part, np0, nullptr, k1, R, n, nb);
   part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h1, nullptr, k1, nb, ldh);
   cgs_precheck_kernel<<<R, kT, 0, s>>>(np0, h1, nrm, flag, k1, nb, ldh);
   // w' = w - V h1, written normalised into vnext where no second projection is needed
-  cgs_sub_kernel<<<g, kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nb, ldh, vnext, nrm, flag);
+  cgs_sub_kernel<T><<<g, kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nb, ldh, vnext, nrm, flag);
   // second projection where the first cancelled too much (h2 = 0 elsewhere)
-  cgs_dot_kernel<<<g, kT, 0, s>>>(V, w, part, np0, flag, k1, R, n, nb);
+  cgs_dot_kernel<T><<<g, kT, 0, s>>>(V, w, part, np0, flag, k1, R, n, nb);
   part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h2, flag, k1, nb, ldh);
-  cgs_sub_kernel<<<g, kT, 0, s>>>(V, w, h2, np1, flag, k1, R, n, nb, ldh, nullptr, nullptr, nullptr);
+  cgs_sub_kernel<T><<<g, kT, 0, s>>>(V, w, h2, np1, flag, k1, R, n, nb, ldh, nullptr, nullptr, nullptr);
   cgs_renorm_kernel<<<R, kT, 0, s>>>(np1, nrm, flag, nb);
-  scale_kernel<<<dim3(blocks_for(n), R), kT, 0, s>>>(w, vnext, nrm, n, flag);
+  scale_kernel<T><<<dim3(blocks_for(n), R), kT, 0, s>>>(w, vnext, nrm, n, flag);
   return 0;
 }
 
@@ -484,19 +519,40 @@ void givens_solve(const GivensState &st, double2 *yd, int R, int m, int ldh, cud
   backsub_kernel<<<1, 32, 0, s>>>(st, yd, R, m, ldh);
 }
 
-void gmres_scale(const double2 *src, double2 *dst, const double *nrm, int R, long long n, cudaStream_t s) {
+template <typename T>
+void gmres_scale(const C<T> *src, C<T> *dst, const double *nrm, int R, long long n, cudaStream_t s) {
   count_launches(1);
-  scale_kernel<<<dim3(blocks_for(n), R), kT, 0, s>>>(src, dst, nrm, n, nullptr);
+  scale_kernel<T><<<dim3(blocks_for(n), R), kT, 0, s>>>(src, dst, nrm, n, nullptr);
 }
 
-void vec_sub(const double2 *a, const double2 *b, double2 *out, long long n, cudaStream_t s) {
+template <typename T>
+void vec_sub(const C<T> *a, const C<T> *b, C<T> *out, long long n, cudaStream_t s) {
   count_launches(1);
-  sub_kernel<<<blocks_for(n), kT, 0, s>>>(a, b, out, n);
+  sub_kernel<T><<<blocks_for(n), kT, 0, s>>>(a, b, out, n);
 }
 
-void vec_add(const double2 *x, double2 *y, long long n, cudaStream_t s) {
+template <typename T>
+void vec_add(const C<T> *x, double2 *y, long long n, cudaStream_t s) {
   count_launches(1);
-  add_kernel<<<blocks_for(n), kT, 0, s>>>(x, y, n);
+  add_kernel<T><<<blocks_for(n), kT, 0, s>>>(x, y, n);
 }
+
+void vec_round(const double2 *x, float2 *y, long long n, cudaStream_t s) {
+  count_launches(1);
+  round_kernel<<<blocks_for(n), kT, 0, s>>>(x, y, n);
+}
+
+#define IE_BLAS_INSTANTIATE(T)                                                                                      \
+  template void gmres_maxpy<T>(const C<T> *, const double2 *, C<T> *, int, int, long long, int, double,            \
+                               cudaStream_t);                                                                       \
+  template void gmres_norm<T>(const C<T> *, double *, double *, int, long long, cudaStream_t);                      \
+  template int gmres_orthogonalize<T>(const C<T> *, C<T> *, C<T> *, double2 *, double2 *, double2 *, double *,      \
+                                      double *, int *, int, int, long long, int, cudaStream_t);                     \
+  template void gmres_scale<T>(const C<T> *, C<T> *, const double *, int, long long, cudaStream_t);                 \
+  template void vec_sub<T>(const C<T> *, const C<T> *, C<T> *, long long, cudaStream_t);                           \
+  template void vec_add<T>(const C<T> *, double2 *, long long, cudaStream_t);
+IE_BLAS_INSTANTIATE(float)
+IE_BLAS_INSTANTIATE(double)
+#undef IE_BLAS_INSTANTIATE
 
 }  // namespace ie

@@ -5,11 +5,15 @@ namespace ie {
 
 // number of partial blocks used by gmres_norm for length n
 int mdot_nb(long long n);
+// Vectors are C<T>: c128 (T = double) or c64 (T = float); h, norms and partial sums
+// are FP64 in both.
 // w[r] += sign * sum_i h[r * ldh + i] V_i[r]
-void gmres_maxpy(const double2 *V, const double2 *h, double2 *w, int k1, int R, long long n, int ldh, double sign,
+template <typename T>
+void gmres_maxpy(const C<T> *V, const double2 *h, C<T> *w, int k1, int R, long long n, int ldh, double sign,
                  cudaStream_t s);
 // out[r] = ||w[r]||_2
-void gmres_norm(const double2 *w, double *part, double *out, int R, long long n, cudaStream_t s);
+template <typename T>
+void gmres_norm(const C<T> *w, double *part, double *out, int R, long long n, cudaStream_t s);
 // Classical Gram-Schmidt against V_0..V_{k1-1} (k1 <= 64) with selective
 // reorthogonalisation, ending with the next basis vector: h1 = V^H w; where
 // ||w - V h1|| >= ||w|| / 16 (from ||w||^2 - |h1|^2) vnext = (w - V h1) / ||w - V h1||
@@ -18,8 +22,9 @@ void gmres_norm(const double2 *w, double *part, double *out, int R, long long n,
 // overwritten only where the second projection ran.
 // part: R * k1 * gs_partial_blocks(n) complex; npart: 2 * R * gs_partial_blocks(n);
 // flag: R ints (1 where the second projection ran).
-int gmres_orthogonalize(const double2 *V, double2 *w, double2 *vnext, double2 *h1, double2 *h2, double2 *part,
-                        double *npart, double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s);
+template <typename T>
+int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double2 *h2, double2 *part, double *npart,
+                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s);
 int gs_partial_blocks(long long n);
 
 // GMRES least-squares state on the device, per right-hand side r (R <= 32):
@@ -39,8 +44,15 @@ void givens_step(const GivensState &st, const double2 *h1, const double2 *h2, co
 // yd[r * ldh + i] = the least-squares solution over the kr[r] columns (zero beyond)
 void givens_solve(const GivensState &st, double2 *yd, int R, int m, int ldh, cudaStream_t s);
 // dst[r] = src[r] / nrm[r]
-void gmres_scale(const double2 *src, double2 *dst, const double *nrm, int R, long long n, cudaStream_t s);
-void vec_sub(const double2 *a, const double2 *b, double2 *out, long long n, cudaStream_t s);
-void vec_add(const double2 *x, double2 *y, long long n, cudaStream_t s);
+template <typename T>
+void gmres_scale(const C<T> *src, C<T> *dst, const double *nrm, int R, long long n, cudaStream_t s);
+// out = a - b
+template <typename T>
+void vec_sub(const C<T> *a, const C<T> *b, C<T> *out, long long n, cudaStream_t s);
+// y += x (y c128)
+template <typename T>
+void vec_add(const C<T> *x, double2 *y, long long n, cudaStream_t s);
+// y = x rounded to c64
+void vec_round(const double2 *x, float2 *y, long long n, cudaStream_t s);
 
 }  // namespace ie

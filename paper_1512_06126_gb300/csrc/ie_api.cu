@@ -62,8 +62,8 @@ struct ie_ctx {
   DiagSet d64, d32;
   cudaStream_t stream = nullptr;
   void *t1 = nullptr, *spec = nullptr;        // FFT workspaces (sized for c128, max_rhs)
-  float2 *x32 = nullptr, *y32 = nullptr;       // c64 staging for mixed precision
-  double2 *V = nullptr, *w = nullptr, *r = nullptr, *dx = nullptr, *part = nullptr, *hdev = nullptr;
+  float2 *x32 = nullptr, *y32 = nullptr;       // c64 right-hand side and correction of the inner solves
+  double2 *V = nullptr, *w = nullptr, *r = nullptr, *part = nullptr, *hdev = nullptr;
   double *nrmpart = nullptr, *nrm = nullptr;
   int *gsflag = nullptr;                       // per right-hand side: second Gram-Schmidt projection ran
   ie::GivensState gst{};                       // device least-squares state of GMRES
@@ -327,35 +327,16 @@ ie_status apply(ie_ctx *c, const Group &g, const ie::C<T> *x, ie::C<T> *y, int t
   return cuda_status(cudaGetLastError());
 }
 
-// c64 product on FP64 vectors: the row passes read and write FP64 (rounding the scaled
-// input to FP32 on load; the diagonal term and the output in FP64), the FFTs and the
-// contraction run in FP32.
-ie_status apply_mixed(ie_ctx *c, const Group &g, const double2 *x, double2 *y, int transpose, cudaStream_t s) {
-  const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
-  const int CZ = g.R() * 3 * Nz;
-  const DiagSet &D = c->d64;
-  const double2 *in_s = (const double2 *)(transpose ? D.in_t : D.in_f);
-  const double2 *out_s = (const double2 *)(transpose ? D.out_t : D.out_f);
-  float2 *t1 = (float2 *)c->t1;
-  float2 *spec = (float2 *)c->spec;
-  ie::launch_fft_rows_fwd<float, double>(x, in_s, t1, CZ, Nz, Ny, Nx, c->px, s);
-  ie::launch_fft_axis<float, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
-  IE_TRY(contract_group<float>(c, g, spec, s));
-  ie::launch_fft_axis<float, true>(spec, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
-  ie::launch_fft_rows_inv<float, double>(t1, x, (const double2 *)D.diag, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
-  return cuda_status(cudaGetLastError());
-}
-
-// FP64-level operator used by the Krylov solver: c128 product, or the c64 product.
+// The operator the Krylov solver applies: the c128 product on c128 vectors (T =
+// double) or the c64 product on c64 vectors (T = float).
+template <typename T>
 struct Op {
   ie_ctx *c;
   const Group *g;
   int transpose;
-  bool single;
-  ie_status operator()(const double2 *x, double2 *y, int R) const {
+  ie_status operator()(const ie::C<T> *x, ie::C<T> *y, int R) const {
     if (R != g->R()) return IE_ERR_ARG;
-    if (!single) return apply<double>(c, *g, x, y, transpose, c->stream);
-    return apply_mixed(c, *g, x, y, transpose, c->stream);
+    return apply<T>(c, *g, x, y, transpose, c->stream);
   }
 };
 
@@ -377,8 +358,9 @@ struct GmresResult {
 };
 
 // Swap the blocks p and q (elem elements each) of a, through the scratch tmp.
-ie_status swap_blocks(double2 *a, int p, int q, long long elem, double2 *tmp, cudaStream_t s) {
-  const size_t bytes = (size_t)elem * sizeof(double2);
+template <typename V>
+ie_status swap_blocks(V *a, int p, int q, long long elem, V *tmp, cudaStream_t s) {
+  const size_t bytes = (size_t)elem * sizeof(V);
   IE_CUDA(cudaMemcpyAsync(tmp, a + p * elem, bytes, cudaMemcpyDeviceToDevice, s));
   IE_CUDA(cudaMemcpyAsync(a + p * elem, a + q * elem, bytes, cudaMemcpyDeviceToDevice, s));
   IE_CUDA(cudaMemcpyAsync(a + q * elem, tmp, bytes, cudaMemcpyDeviceToDevice, s));
@@ -390,9 +372,14 @@ ie_status swap_blocks(double2 *a, int p, int q, long long elem, double2 *tmp, cu
 // instance whose right-hand sides have all converged leaves the lockstep at the next
 // restart: its blocks of b and x swap places with an active instance's, and the
 // remaining cycles run on the smaller group.  x is back in the original order on
-// return.
-ie_status gmres(ie_ctx *c, const Group &g0, int transpose, bool single, double2 *b, double2 *x, double tol,
-                int max_iter, GmresResult *res, bool compact) {
+// return.  T = double: c128 vectors and operator; T = float: c64 vectors and
+// operator, the basis in the same storage (half of it used).
+template <typename T>
+ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T> *x, double tol, int max_iter,
+                GmresResult *res, bool compact) {
+  using Vt = ie::C<T>;
+  Vt *const Vb = (Vt *)c->V;
+  Vt *const w = (Vt *)c->w;
   const long long n = c->nvec();
   const int m = c->restart;
   const int ldh = m + 1;
@@ -400,7 +387,7 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, bool single, double2 
   const long long blk = n * rpi;
   cudaStream_t s = c->stream;
   Group g = g0;
-  const Op op{c, &g, transpose, single};
+  const Op<T> op{c, &g, transpose};
   int R = g.R();
   long long nR = n * R;
   const int G = (int)g0.inst.size();
@@ -410,7 +397,7 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, bool single, double2 
   double2 *h1 = c->hdev, *h2 = c->hdev + (size_t)R * ldh, *yd = c->hdev + 2 * (size_t)R * ldh;
   const ie::GivensState &st = c->gst;
   std::vector<double> bnorm(R), thr(R);
-  ie::gmres_norm(b, c->nrmpart, c->nrm, R, n, s);
+  ie::gmres_norm<T>(b, c->nrmpart, c->nrm, R, n, s);
   IE_CUDA(cudaMemcpyAsync(bnorm.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, s));
   IE_CUDA(cudaStreamSynchronize(s));
   auto upload_thr = [&]() -> ie_status {
@@ -429,10 +416,10 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, bool single, double2 
     h1 = c->hdev;
     h2 = c->hdev + (size_t)R * ldh;
     yd = c->hdev + 2 * (size_t)R * ldh;
-    IE_TRY(op(x, c->w, R));
-    ie::vec_sub(b, c->w, c->w, nR, s);
-    ie::gmres_norm(c->w, c->nrmpart, c->nrm, R, n, s);
-    ie::gmres_scale(c->w, c->V, c->nrm, R, n, s);
+    IE_TRY(op(x, w, R));
+    ie::vec_sub<T>(b, w, w, nR, s);
+    ie::gmres_norm<T>(w, c->nrmpart, c->nrm, R, n, s);
+    ie::gmres_scale<T>(w, Vb, c->nrm, R, n, s);
     ie::givens_init(st, c->nrm, R, ldh, s);
     IE_CUDA(cudaMemcpyAsync(c->pin_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (compact) IE_CUDA(cudaMemcpyAsync(act.data(), st.active, R * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -462,8 +449,8 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, bool single, double2 
         while (p < q) {
           if (ia[p]) { ++p; continue; }
           if (!ia[q]) { --q; continue; }
-          IE_TRY(swap_blocks(b, p, q, blk, c->w, s));
-          IE_TRY(swap_blocks(x, p, q, blk, c->w, s));
+          IE_TRY(swap_blocks(b, p, q, blk, w, s));
+          IE_TRY(swap_blocks(x, p, q, blk, w, s));
           std::swap(inst_at[p], inst_at[q]);
           std::swap(g.inst[p], g.inst[q]);
           for (int j = 0; j < rpi; ++j) std::swap(bnorm[p * rpi + j], bnorm[q * rpi + j]);
@@ -489,8 +476,8 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, bool single, double2 
         IE_CUDA(cudaEventSynchronize(c->pin_ev[slot]));
         if (c->pin_active[1 + slot] == 0) break;
       }
-      IE_TRY(op(c->V + (long long)k * nR, c->w, R));
-      if (ie::gmres_orthogonalize(c->V, c->w, c->V + (long long)(k + 1) * nR, h1, h2, c->part, c->nrmpart, c->nrm,
+      IE_TRY(op(Vb + (long long)k * nR, w, R));
+      if (ie::gmres_orthogonalize<T>(Vb, w, Vb + (long long)(k + 1) * nR, h1, h2, c->part, c->nrmpart, c->nrm,
                                   c->gsflag, k + 1, R, n, ldh, s) != 0)
         return IE_ERR_ARG;
       ie::givens_step(st, h1, h2, c->nrm, k, R, m, ldh, s);
@@ -502,7 +489,7 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, bool single, double2 
     }
     // x += V y with y from the rotated least-squares problem (zero beyond each kr)
     ie::givens_solve(st, yd, R, m, ldh, s);
-    ie::gmres_maxpy(c->V, yd, x, kmax, R, n, ldh, 1.0, s);
+    ie::gmres_maxpy<T>(Vb, yd, x, kmax, R, n, ldh, 1.0, s);
     IE_CUDA(cudaMemcpyAsync(kr.data(), st.kr, R * sizeof(int), cudaMemcpyDeviceToHost, s));
     IE_CUDA(cudaMemcpyAsync(brk.data(), st.brk, R * sizeof(int), cudaMemcpyDeviceToHost, s));
     pending = true;
@@ -522,8 +509,8 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, bool single, double2 
   for (int p = 0; p < G; ++p)
     while (inst_at[p] != p) {
       const int q = inst_at[p];
-      IE_TRY(swap_blocks(x, p, q, blk, c->w, s));
-      IE_TRY(swap_blocks(b, p, q, blk, c->w, s));
+      IE_TRY(swap_blocks(x, p, q, blk, w, s));
+      IE_TRY(swap_blocks(b, p, q, blk, w, s));
       std::swap(inst_at[p], inst_at[q]);
     }
   return IE_OK;
@@ -534,13 +521,13 @@ ie_status true_residual(ie_ctx *c, const Group &g, int transpose, const double2 
                         std::vector<double> &rel) {
   const long long n = c->nvec();
   const int R = g.R();
-  Op op{c, &g, transpose, false};
+  Op<double> op{c, &g, transpose};
   IE_TRY(op(u, c->r, R));
-  ie::vec_sub(b, c->r, c->r, n * R, c->stream);
+  ie::vec_sub<double>(b, c->r, c->r, n * R, c->stream);
   std::vector<double> rn(R), bn(R);
-  ie::gmres_norm(c->r, c->nrmpart, c->nrm, R, n, c->stream);
+  ie::gmres_norm<double>(c->r, c->nrmpart, c->nrm, R, n, c->stream);
   IE_CUDA(cudaMemcpyAsync(rn.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  ie::gmres_norm(b, c->nrmpart, c->nrm + R, R, n, c->stream);
+  ie::gmres_norm<double>(b, c->nrmpart, c->nrm + R, R, n, c->stream);
   IE_CUDA(cudaMemcpyAsync(bn.data(), c->nrm + R, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   IE_CUDA(cudaStreamSynchronize(c->stream));
   rel.resize(R);
@@ -570,7 +557,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
       IE_CUDA(cudaMemcpyAsync(c->r, b, n * R * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
       bw = c->r;
     }
-    IE_TRY(gmres(c, g, transpose, false, bw, u, tol, c->max_iter, &gr, comp));
+    IE_TRY(gmres<double>(c, g, transpose, bw, u, tol, c->max_iter, &gr, comp));
     inf.inner_iters = gr.iters;
     inf.outer_iters = gr.cycles;
     conv = gr.converged;
@@ -581,9 +568,8 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
     for (int outer = 0; outer <= c->max_outer; ++outer) {
       if (outer == 0 && !use_x0) {
         // u = 0: the residual is b itself (no c128 product needed)
-        IE_CUDA(cudaMemcpyAsync(c->r, b, n * R * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
         std::vector<double> bn(R);
-        ie::gmres_norm(b, c->nrmpart, c->nrm, R, n, c->stream);
+        ie::gmres_norm<double>(b, c->nrmpart, c->nrm, R, n, c->stream);
         IE_CUDA(cudaMemcpyAsync(bn.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         IE_CUDA(cudaStreamSynchronize(c->stream));
         rel.assign(R, 0.0);
@@ -606,23 +592,22 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
       }
       if (act.inst.empty()) { conv = true; break; }
       if (outer == c->max_outer || inner_total >= c->max_iter) break;
-      // pack the residual blocks of the active instances to the front of r (in order:
-      // a block only moves to a lower position, so source and target never overlap)
+      // the residual blocks of the active instances, rounded to c64, packed in order
+      const double2 *rsrc = (outer == 0 && !use_x0) ? b : c->r;
       for (size_t a = 0; a < pos.size(); ++a)
-        if ((int)a != pos[a])
-          IE_CUDA(cudaMemcpyAsync(c->r + (long long)a * blk, c->r + (long long)pos[a] * blk, blk * sizeof(double2),
-                                  cudaMemcpyDeviceToDevice, c->stream));
+        ie::vec_round(rsrc + (long long)pos[a] * blk, c->x32 + (long long)a * blk, blk, c->stream);
       const int Ra = act.R();
-      // inner: A64 d = r (relative tolerance inner_tol, bounded below so as not to over-solve)
-      IE_CUDA(cudaMemsetAsync(c->dx, 0, n * Ra * sizeof(double2), c->stream));
+      // inner: A64 d = r in c64 (relative tolerance inner_tol, bounded below so as not
+      // to over-solve)
+      IE_CUDA(cudaMemsetAsync(c->y32, 0, n * Ra * sizeof(float2), c->stream));
       GmresResult gr;
       const double itol = std::max(c->inner_tol, 0.5 * tol / std::max(worst, 1e-300));
-      IE_TRY(gmres(c, act, transpose, true, c->r, c->dx, std::min(itol, 0.5), c->max_iter - inner_total, &gr,
-                   act.inst.size() > 1));
+      IE_TRY(gmres<float>(c, act, transpose, c->x32, c->y32, std::min(itol, 0.5), c->max_iter - inner_total, &gr,
+                          act.inst.size() > 1));
       inner_total += gr.iters;
       brk = brk || gr.breakdown;
       for (size_t a = 0; a < pos.size(); ++a)
-        ie::vec_add(c->dx + (long long)a * blk, u + (long long)pos[a] * blk, blk, c->stream);
+        ie::vec_add<float>(c->y32 + (long long)a * blk, u + (long long)pos[a] * blk, blk, c->stream);
     }
     inf.inner_iters = inner_total;
   }
@@ -930,7 +915,6 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   IE_TRY(dalloc(c, &c->V, (size_t)(c->restart + 1) * nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->w, nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->r, nv * sizeof(double2)));
-  IE_TRY(dalloc(c, &c->dx, nv * sizeof(double2)));
   if (c->restart > 63) return IE_ERR_ARG;
   const long long nbp = std::max<long long>(ie::mdot_nb(c->nvec()), ie::gs_partial_blocks(c->nvec()));
   IE_TRY(dalloc(c, &c->part, (size_t)max_rhs * (c->restart + 1) * nbp * sizeof(double2)));
