@@ -13,6 +13,7 @@
 // (Lemma 2), so one CTA loads a block once and applies it to all its mirrors and
 // all right-hand sides.
 #include "contract.cuh"
+#include "contract_mma.cuh"
 #include "contract_tma.cuh"
 
 namespace ie {
@@ -188,6 +189,59 @@ bool try_tma_variant(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, in
   return false;
 }
 
+// The tensor-core kernels (persistent: as many resident CTAs per SM as registers and
+// shared memory allow).
+template <typename K>
+bool launch_persistent(K k, int threads, size_t smem, int *per_sm, float2 *spec, const float2 *qf, int Nx, int Ny,
+                       int ldz, cudaStream_t s) {
+  if (smem > 227 * 1024) return false;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (*per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem) != cudaSuccess || *per_sm < 1) {
+      cudaGetLastError();
+      *per_sm = 1;
+    }
+  }
+  int *err = nullptr;
+  cudaGetSymbolAddress((void **)&err, g_contract_err);
+  const int nf = (Nx + 1) * (Ny + 1);
+  const int want = *per_sm * num_sms();
+  const int grid = nf < want ? nf : want;
+  count_launches(1);
+  k<<<grid, threads, smem, s>>>(spec, qf, Nx, Ny, ldz, err);
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+template <int NZ, int R>
+bool try_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, bool unpack, cudaStream_t s) {
+  if (unpack) {
+    static int per_sm = 0;
+    using Cfg = MmaUnpackCfg<NZ, R>;
+    return launch_persistent(contract_mma_unpack_kernel<NZ, R>, Cfg::THREADS, Cfg::SMEM, &per_sm, spec, qf, Nx, Ny,
+                             ldz, s);
+  }
+  static int per_sm = 0;
+  using Cfg = MmaCfg<NZ, R, 2>;
+  return launch_persistent(contract_mma_kernel<NZ, R, 2>, Cfg::THREADS, Cfg::SMEM, &per_sm, spec, qf, Nx, Ny, ldz, s);
+}
+
+template <int R>
+bool dispatch_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, bool unpack, cudaStream_t s) {
+  switch (Nz) {
+    case 16: return try_mma<16, R>(spec, qf, Nx, Ny, ldz, unpack, s);
+    case 32: return try_mma<32, R>(spec, qf, Nx, Ny, ldz, unpack, s);
+    case 48: return try_mma<48, R>(spec, qf, Nx, Ny, ldz, unpack, s);
+    default: return false;
+  }
+}
+
 template <int R>
 bool dispatch_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, int variant, cudaStream_t s) {
   switch (Nz) {
@@ -217,6 +271,7 @@ bool contract_variant_available(int variant, int Nz, int R, bool c64) {
   if (variant == kContractPanel) return R >= 1 && R <= 4 && 3 * Nz <= 1024;
   if (!c64 || R < 1 || R > 2 || !contract_tma_enabled) return false;
   if (Nz != 16 && Nz != 24 && Nz != 32 && Nz != 48) return false;
+  if (variant == kContractMma || variant == kContractMmaUnpack) return Nz % 16 == 0;
   if (variant == kContractTma1) return true;
   if (variant == kContractTma1Row) return R == 2;
   if (variant == kContractTma3) {
@@ -237,6 +292,12 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, i
   if constexpr (sizeof(T) == 4) {
     if (variant == kContractAuto) variant = contract_variant_available(kContractTma1, Nz, R, true) ? kContractTma1
                                                                                                     : kContractPanel;
+    if ((variant == kContractMma || variant == kContractMmaUnpack) &&
+        contract_variant_available(variant, Nz, R, true)) {
+      const bool unpack = variant == kContractMmaUnpack;
+      if (R == 1 && dispatch_mma<1>(spec, qf, Nx, Ny, Nz, ldz, unpack, s)) return 0;
+      if (R == 2 && dispatch_mma<2>(spec, qf, Nx, Ny, Nz, ldz, unpack, s)) return 0;
+    }
     if ((variant == kContractTma1 || variant == kContractTma3 || variant == kContractTma1Row) &&
         contract_variant_available(variant, Nz, R, true)) {
       if (R == 1 && dispatch_tma<1>(spec, qf, Nx, Ny, Nz, ldz, variant, s)) return 0;

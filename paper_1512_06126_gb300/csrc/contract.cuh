@@ -6,12 +6,15 @@ namespace ie {
 // Kernel variants of the contraction: the TMA ring with one slot and two CTAs per SM
 // (two output rows per thread for two right-hand sides), the ring with three slots and
 // one CTA per SM (both c64, Nz in {16, 24, 32, 48}, R <= 2), the panel-staged kernel
-// (any precision and Nz with 3 Nz <= 1024), and the one-slot ring with one output row
-// per thread (two right-hand sides only).
+// (any precision and Nz with 3 Nz <= 1024), the one-slot ring with one output row
+// per thread (two right-hand sides only), and two kernels feeding 3xTF32 tensor-core
+// MMAs (c64, Nz in {16, 32, 48}, R <= 2): a producer warp with a two-slot ring and
+// fragments read in place, or the one-slot ring with an unpacking pass.
 enum ContractVariant {
-  kContractAuto = -1, kContractTma1 = 0, kContractTma3 = 1, kContractPanel = 2, kContractTma1Row = 3
+  kContractAuto = -1, kContractTma1 = 0, kContractTma3 = 1, kContractPanel = 2, kContractTma1Row = 3,
+  kContractMma = 4, kContractMmaUnpack = 5
 };
-constexpr int kContractVariants = 4;
+constexpr int kContractVariants = 6;
 bool contract_variant_available(int variant, int Nz, int R, bool c64);
 
 // Apply the folded spectral blocks in place to the R right-hand sides whose spectrum

@@ -239,9 +239,9 @@ class Context:
         return s, info
 
     def contract_tuning(self):
-        """(variants for 1..4 right-hand sides per instance, autotuner ms [4][4])."""
+        """(variants for 1..4 right-hand sides per instance, autotuner ms [4][6])."""
         v = np.zeros(4, dtype=np.int32)
-        ms = np.zeros((4, 4), dtype=np.float64)
+        ms = np.zeros((4, 6), dtype=np.float64)
         _check(self._lib.ie_contract_tuning(self.ctx, v.ctypes.data, ms.ctypes.data), "ie_contract_tuning")
         return v, ms
 
