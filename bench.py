@@ -4,9 +4,10 @@
 Workload (default): the single-solve configuration, Nx = Ny = 128, Nz = 32 cells of
 50 m (1,572,864 unknowns), 5-layer seeded background, 20 seeded anomalies of
 0.01-0.1 ohm-m, 1 Hz, both MT polarisations; coefficients generated on the
-device by the library.  One step = one mixed-precision solve (c64 FFT products
-with FP32 accumulation, FP64 Arnoldi and FP64 c128 refinement residual) of both
-polarisations to ||b - A u|| <= 1e-7 ||b||, i.e. every step of the hot path.
+device by the library.  One step = one mixed-precision solve (inner GMRES in c64:
+c64 FFT products and Krylov vectors, FP64 Hessenberg and sums; FP64 c128 refinement
+residual) of both polarisations to ||b - A u|| <= 1e-7 ||b||, i.e. every step of the
+hot path.
 
 Printed (one JSON line, rank 0):
   value         unknowns * Krylov iterations / s over the timed steps (device-resident
@@ -54,7 +55,17 @@ def peaks():
 
 
 # (workload, contraction variant, right-hand sides) -> DRAM bytes per contraction launch
-CONTRACT_TRAFFIC = {("C2", 3, 2): 654541312 + 86889728}
+CONTRACT_TRAFFIC = {("C2", 3, 2): 654541312 + 86889728}  # variant 3; variant 5 after its next capture
+
+
+def bf16_peak():
+    """(dense bf16 TFLOP/s burst, source) from the measured peaks, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
 
 
 def workload(name):
@@ -270,6 +281,18 @@ def run_ours(args, rank, ws):
     l1 = ie.kernel_launches()
     k3_ms, k3_n = ctx.profile_read(ie.IE_C64)
     ctx.profile(False)
+    # ---- where an inner iteration goes: one more (untimed) solve with every step timed ----
+    ctx.profile(2)
+    info_b = solve(ie.IE_MIXED)
+    spans = {}
+    for key, kind in (("product_c64", ie.IE_PROF_PRODUCT_C64), ("gram_schmidt_c64", ie.IE_PROF_GS_C64),
+                      ("givens", ie.IE_PROF_GIVENS), ("contraction_c64", ie.IE_C64),
+                      ("contraction_c128", ie.IE_C128)):
+        ms_k, n_k = ctx.profile_read(kind)
+        spans[key] = {"ms_total": ms_k, "records": n_k, "ms_each": ms_k / max(n_k, 1)}
+    ctx.profile(False)
+    breakdown = {"inner_iters": info_b.inner_iters, "outer": info_b.outer_iters, "solve_s": info_b.t_solve,
+                 "spans": spans}
     clk = clocks.stop()
     t_ms = ev0.elapsed_time(ev1)
     t_max = allreduce_max(t_ms / 1e3, ws)
@@ -321,27 +344,42 @@ def run_ours(args, rank, ws):
     hbm_peak, sm_max, peak_src = peaks()
     k3_avg_ms = k3_ms / max(k3_n, 1)
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-    # capture of this kernel variant on this workload (profiles/contraction_and_fft_c2.md);
-    # null for any other variant or workload
+    # capture of this kernel variant, as it is now, on this workload (profiles/); null for
+    # any other variant or workload
     traffic = CONTRACT_TRAFFIC.get((args.workload, int(tune_v[R - 1]), R))
     k3_bytes = q_bytes + 2 * 4 * g.nx * g.ny * 3 * g.nz * R * 8
     k3_flops = 8.0 * 4 * g.nx * g.ny * R * 9 * g.nz * g.nz
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12            # TFLOP/s, FP32 FMA pipes at max clock
+    variant = int(tune_v[R - 1])
     t_hbm = k3_bytes / (hbm_peak * 1e9)
-    t_alu = k3_flops / (fp32_peak * 1e12)
-    if t_alu > t_hbm:
+    if variant in (4, 5):
+        # tensor-core variants: 3 TF32 products per FP32 product (3xTF32); TF32 peak =
+        # the measured bf16 peak x the nominal TF32 / bf16 ratio (1.1 / 2.25)
+        bf16 = bf16_peak()
+        tf32_peak = bf16[0] * 1.1 / 2.25
+        t_cmp = 3 * k3_flops / (tf32_peak * 1e12)
+        cmp = {"compute": "tensor, 3xTF32", "flops_per_launch": 3 * k3_flops, "compute_peak_TFLOPs": tf32_peak,
+               "compute_peak_source": f"{bf16[1]} bf16 {bf16[0]:.0f} TFLOP/s x 1.1/2.25",
+               "compute_TFLOPs": 3 * k3_flops / (k3_avg_ms * 1e-3) / 1e12}
+    else:
+        t_cmp = k3_flops / (fp32_peak * 1e12)
+        cmp = {"compute": "FP32 FMA", "flops_per_launch": k3_flops, "compute_peak_TFLOPs": fp32_peak,
+               "compute_peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+               "compute_TFLOPs": k3_flops / (k3_avg_ms * 1e-3) / 1e12}
+    kname = f"contract (c64, 2 right-hand sides, variant {variant})"
+    if variant not in (4, 5) and t_cmp > t_hbm:
         achieved = k3_flops / (k3_avg_ms * 1e-3) / 1e12
-        roof = {"kernel": "contract (c64, 2 right-hand sides)", "bound": "alu", "achieved": achieved,
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                "peak_source": cmp["compute_peak_source"],
                 "hbm_GBs": k3_bytes / (k3_avg_ms * 1e-3) / 1e9, "hbm_frac": k3_bytes / (k3_avg_ms * 1e-3) / 1e9 / hbm_peak,
                 "bytes_per_launch": k3_bytes, "flops_per_launch": k3_flops, "traffic": traffic,
                 "launches": k3_n, "avg_ms": k3_avg_ms}
     else:
         achieved = k3_bytes / (k3_avg_ms * 1e-3) / 1e9
-        roof = {"kernel": "contract (c64, 2 right-hand sides)", "bound": "hbm", "achieved": achieved,
+        roof = {"kernel": kname, "bound": "hbm" if t_hbm >= t_cmp else "tensor", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_src,
-                "bytes_per_launch": k3_bytes, "traffic": traffic, "launches": k3_n, "avg_ms": k3_avg_ms}
+                "bytes_per_launch": k3_bytes, "traffic": traffic, "launches": k3_n, "avg_ms": k3_avg_ms, **cmp}
 
     # ---- e2e: through the ABI with host buffers ----
     bh = b.cpu().pin_memory()
@@ -391,6 +429,7 @@ def run_ours(args, rank, ws):
                         "mixed_iters": iters / args.steps, "mixed_outer": outer / args.steps,
                         "fp64_iters": info64.inner_iters, "final_rel_res": res},
                 "roofline": roof,
+                "solve_breakdown": breakdown,
                 "contract_tuning": {"variants": ["tma 1 slot", "tma 3 slots", "panel", "tma 1 slot, 1 row/thread", "3xTF32 mma.sync, producer warp, 2 slots", "3xTF32 mma.sync, 1 slot, unpacked"],
                                     "chosen_for_2_rhs": int(tune_v[1]),
                                     "ms_per_launch_2_rhs": [float(v) for v in tune_ms[1]]},

@@ -89,6 +89,7 @@ typedef struct {
   int inner_iters;       /* total Krylov iterations */
   double final_rel_res;  /* max over right-hand sides of ||b - A u|| / ||b|| with the c128 operator */
   double t_solve;        /* wall time of the solve, s */
+  int reorth;            /* Gram-Schmidt steps that took a second projection (all right-hand sides) */
 } ie_solve_info;
 
 /* Build a context for one grid, one layered background, one anomaly and n_freq
@@ -254,11 +255,17 @@ void *ie_ctx_stream(ie_ctx *ctx);
 /* Bytes of device memory held by the context. */
 long long ie_ctx_device_bytes(ie_ctx *ctx);
 
-/* Profiling.  ie_profile(ctx, 1) clears earlier records and starts recording a pair
- * of CUDA events around every launch of the wavenumber-contraction kernel (step 2
- * of Sect. 3.3) on the stream it runs on; ie_profile(ctx, 0) stops.  ie_profile_read
- * waits for the recorded events and returns the summed duration (ms) and the number
- * of launches for one element type (IE_C64 or IE_C128). */
+/* Profiling (no counterpart in the paper).  ie_profile(ctx, 1) clears earlier records
+ * and starts recording a pair of CUDA events around every launch of the
+ * wavenumber-contraction kernel (step 2 of Sect. 3.3) on the stream it runs on;
+ * ie_profile(ctx, 2) also records, in every iteration of the Krylov solver, the
+ * operator product, the Gram-Schmidt step and the Givens step; ie_profile(ctx, 0)
+ * stops.  ie_profile_read waits for the recorded events and returns the summed
+ * duration (ms) and the number of records of one kind: IE_C64 or IE_C128 (the
+ * contraction) or one of IE_PROF_*. */
+enum {
+  IE_PROF_PRODUCT_C64 = 2, IE_PROF_PRODUCT_C128 = 3, IE_PROF_GS_C64 = 4, IE_PROF_GS_C128 = 5, IE_PROF_GIVENS = 6
+};
 ie_status ie_profile(ie_ctx *ctx, int enable);
 ie_status ie_profile_read(ie_ctx *ctx, int dtype, double *total_ms, long long *n_launch);
 

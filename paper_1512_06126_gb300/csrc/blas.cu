@@ -10,6 +10,10 @@
 // element n), so basis vector i of right-hand side r starts at V + (i*R + r)*n.
 #include "blas.cuh"
 
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
 namespace ie {
 namespace {
 
@@ -17,6 +21,7 @@ constexpr int kT = 256;
 constexpr int kEPT = 4;            // elements per thread in the reductions
 constexpr int kChunk = kT * kEPT;  // elements per block
 
+// Sum over the block; the total is valid in thread 0 only.
 __device__ __forceinline__ double2 block_reduce(double2 v, double2 *sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -145,140 +150,179 @@ __global__ void round_kernel(const double2 *__restrict__ x, float2 *__restrict__
 
 // ---------------------------------------------------------------------------
 // Classical Gram-Schmidt with selective reorthogonalisation.  In FP64 the arithmetic
-// sets the pace (the vector length times the basis size in complex FMAs per pass), so
-// the passes are organised to spend the FP64 pipe on multiply-adds and little else; in
-// FP32 the same passes are bound by the basis reads from HBM.
-// A block owns a tile of kTile consecutive elements of one right-hand side.
-//   dot pass: part_i = sum_tile conj(V_i) x  and  npart = sum_tile |x|^2
-//   sub pass: x -= sum_i h_i V_i on the tile  and  npart = sum_tile |x|^2
-// In the dot pass the tile of x sits in shared memory and warp j owns basis vectors
-// j, j + 8, ...: each lane accumulates over 64 elements of the tile before a single
-// warp reduction (in FP64) per (vector, tile).  With a per-right-hand-side flag the
-// block of a right-hand side whose flag is 0 returns at once.
+// sets the pace (the vector length times the basis size in complex FMAs per pass); in
+// FP32 the passes are bound by the basis reads from HBM, so both are organised to keep
+// every SM busy with loads in flight and no wave tail:
+//   dot pass: one warp per unit (right-hand side r, chunk c of kCh<T> elements, basis
+//     vector i), units of one chunk consecutive so that the chunk of x comes from HBM
+//     once and from L2 for the other vectors; part(r, i, c) = sum_chunk conj(V_i) x and,
+//     with the i = 0 unit, npart(r, c) = sum_chunk |x|^2.  The grid is sized so that
+//     every warp gets the same number of units.
+//   sub pass: persistent blocks per right-hand side stream x -= sum_i h_i V_i over
+//     chunks of kT * kSubEPT elements (the same number of chunks per block) and leave
+//     one partial of |x|^2 per block.
+// A right-hand side whose flag (if given) is 0 is skipped.
 // ---------------------------------------------------------------------------
-constexpr int kTileEPT = 8;
-constexpr int kTile = kT * kTileEPT;  // 2048 elements
+template <typename T> struct GsShape;
+template <> struct GsShape<float> { static constexpr int kCh = 512; static constexpr int kSubEPT = 8; };
+template <> struct GsShape<double> { static constexpr int kCh = 2048; static constexpr int kSubEPT = 8; };
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+// lane 0 gets the warp's sum: FP32 vectors reduce in FP32 (32 lane sums of at most 32
+// products each, ~1e-6 of the sum of magnitudes) and convert once; FP64 in FP64
+__device__ __forceinline__ double warp_total(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return (double)v;
+}
+__device__ __forceinline__ double warp_total(double v) { return warp_sum(v); }
+
+// one unit of the dot pass (a warp): (ax, ay) = sum conj(v) x over the chunk, nn = sum |x|^2
+template <typename T, bool NORM>
+__device__ __forceinline__ void dot_unit(const C<T> *__restrict__ vi, const C<T> *__restrict__ xr, long long lim,
+                                         int lane, double &ax, double &ay, double &nn) {
+  constexpr int PER = GsShape<T>::kCh / 32;
+  const C<T> zero = mk<T>(0, 0);
+  T ax0 = 0, ay0 = 0, ax1 = 0, ay1 = 0, n0 = 0, n1 = 0;
+#pragma unroll 8
+  for (int j = 0; j < PER; j += 2) {
+    const int l0 = j * 32 + lane, l1 = l0 + 32;
+    const C<T> a0 = l0 < lim ? __ldg(vi + l0) : zero, a1 = l1 < lim ? __ldg(vi + l1) : zero;
+    const C<T> b0 = l0 < lim ? __ldg(xr + l0) : zero, b1 = l1 < lim ? __ldg(xr + l1) : zero;
+    ax0 = mad(a0.x, b0.x, ax0);
+    ax0 = mad(a0.y, b0.y, ax0);
+    ay0 = mad(a0.x, b0.y, ay0);
+    ay0 = mad(-a0.y, b0.x, ay0);
+    ax1 = mad(a1.x, b1.x, ax1);
+    ax1 = mad(a1.y, b1.y, ax1);
+    ay1 = mad(a1.x, b1.y, ay1);
+    ay1 = mad(-a1.y, b1.x, ay1);
+    if (NORM) {
+      n0 = mad(b0.x, b0.x, n0);
+      n0 = mad(b0.y, b0.y, n0);
+      n1 = mad(b1.x, b1.x, n1);
+      n1 = mad(b1.y, b1.y, n1);
+    }
+  }
+  ax = warp_total(ax0 + ax1);
+  ay = warp_total(ay0 + ay1);
+  if (NORM) nn = warp_total(n0 + n1);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kT) cgs_dot_kernel(const C<T> *__restrict__ V, const C<T> *__restrict__ x,
                                                      double2 *__restrict__ part, double *__restrict__ npart,
                                                      const int *__restrict__ flag, int k1, int R, long long n,
-                                                     int nb) {
-  __shared__ C<T> xw[kTile];
-  __shared__ double2 shn[kT / 32];
-  const int r = blockIdx.y;
-  if (flag && !flag[r]) return;
-  const long long t0 = (long long)blockIdx.x * kTile;
-  const int tid = threadIdx.x;
-  const C<T> *xr = x + (long long)r * n;
-  const C<T> zero = mk<T>(0, 0);
-  T nacc = 0;
-#pragma unroll
-  for (int j = 0; j < kTileEPT; ++j) {
-    const long long e = t0 + j * kT + tid;
-    const C<T> v = e < n ? xr[e] : zero;
-    xw[j * kT + tid] = v;
-    nacc = mad(v.x, v.x, nacc);
-    nacc = mad(v.y, v.y, nacc);
+                                                     int nch) {
+  constexpr int CH = GsShape<T>::kCh;
+  if (flag) {  // nothing to do unless some right-hand side is flagged
+    int any = 0;
+    for (int r = 0; r < R; ++r) any |= flag[r];
+    if (!any) return;
   }
-  const double2 sres = block_reduce(make_double2((double)nacc, 0.0), shn);  // also orders the xw stores
-  if (tid == 0) npart[(long long)r * nb + blockIdx.x] = sres.x;
-  const int lane = tid & 31, wid = tid >> 5;
-  const long long lim = n - t0;  // elements of the tile inside the vector
-  for (int i = wid; i < k1; i += kT / 32) {
-    const C<T> *vi = V + ((long long)i * R + r) * n + t0;
-    T ax0 = 0, ay0 = 0, ax1 = 0, ay1 = 0;
-#pragma unroll 8
-    for (int q = 0; q < kTile / 32; q += 2) {
-      const int l0 = q * 32 + lane, l1 = l0 + 32;
-      const C<T> a0 = l0 < lim ? __ldg(vi + l0) : zero;
-      const C<T> a1 = l1 < lim ? __ldg(vi + l1) : zero;
-      const C<T> b0 = xw[l0], b1 = xw[l1];
-      ax0 = mad(a0.x, b0.x, ax0);
-      ax0 = mad(a0.y, b0.y, ax0);
-      ay0 = mad(a0.x, b0.y, ay0);
-      ay0 = mad(-a0.y, b0.x, ay0);
-      ax1 = mad(a1.x, b1.x, ax1);
-      ax1 = mad(a1.y, b1.y, ax1);
-      ay1 = mad(a1.x, b1.y, ay1);
-      ay1 = mad(-a1.y, b1.x, ay1);
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (kT / 32);
+  const int units = R * nch * k1;  // < 2^31 for every grid the library accepts
+  for (int u = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); u < units; u += nw) {
+    const int i = u % k1, rc = u / k1;
+    const int c = rc % nch, r = rc / nch;
+    if (flag && !flag[r]) continue;
+    const long long e0 = (long long)c * CH;
+    const C<T> *vi = V + ((long long)i * R + r) * n + e0;
+    const C<T> *xr = x + (long long)r * n + e0;
+    double ax, ay, nn = 0.0;
+    if (i == 0)
+      dot_unit<T, true>(vi, xr, n - e0, lane, ax, ay, nn);
+    else
+      dot_unit<T, false>(vi, xr, n - e0, lane, ax, ay, nn);
+    if (lane == 0) {
+      part[((long long)r * k1 + i) * nch + c] = make_double2(ax, ay);
+      if (i == 0) npart[(long long)r * nch + c] = nn;
     }
-    double ax = (double)ax0 + (double)ax1, ay = (double)ay0 + (double)ay1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ax += __shfl_down_sync(0xffffffffu, ax, o);
-      ay += __shfl_down_sync(0xffffffffu, ay, o);
-    }
-    if (lane == 0) part[((long long)r * k1 + i) * nb + blockIdx.x] = make_double2(ax, ay);
   }
 }
 
-// x[r] -= sum_{i<k1} h[r * ldh + i] V_i[r] on the tile; npart = sum_tile |x|^2.
-// With vout: a right-hand side whose oflag is 0 instead gets vout[r] = x' / nrm[r]
-// (the next basis vector, normalised by the norm known in advance) and no norm
-// partial; one whose oflag is 1 gets x' in x as above.  A right-hand side whose
-// flag (if given) is 0 is skipped.
+// x[r] -= sum_{i<k1} h[r * ldh + i] V_i[r]; npart[r * nbs + block] = the block's part of
+// |x'|^2.  With vout: a right-hand side whose oflag is 0 instead gets vout[r] = x' /
+// nrm[r] (the next basis vector, normalised by the norm known in advance) and no norm
+// partial; one whose oflag is 1 gets x' in x as above.
 template <typename T>
 __global__ void __launch_bounds__(kT) cgs_sub_kernel(const C<T> *__restrict__ V, C<T> *__restrict__ x,
                                                      const double2 *__restrict__ h, double *__restrict__ npart,
                                                      const int *__restrict__ flag, int k1, int R, long long n,
-                                                     int nb, int ldh, C<T> *__restrict__ vout,
+                                                     int nbs, int ldh, C<T> *__restrict__ vout,
                                                      const double *__restrict__ nrm, const int *__restrict__ oflag) {
+  constexpr int EPT = GsShape<T>::kSubEPT;
   __shared__ C<T> hs[64];
   __shared__ double2 shn[kT / 32];
   const int r = blockIdx.y;
   if (flag && !flag[r]) return;
   const bool scaled = vout && !oflag[r];
-  const long long t0 = (long long)blockIdx.x * kTile;
   const int tid = threadIdx.x;
-  C<T> *xr = x + (long long)r * n;
   if (tid < k1) hs[tid] = to_c<T>(h[(long long)r * ldh + tid]);
   __syncthreads();
-  C<T> v[kTileEPT];
+  const T sc = (T)(scaled && nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0);
+  C<T> *xr = x + (long long)r * n;
+  C<T> *vr = vout ? vout + (long long)r * n : nullptr;
+  T nacc = 0;
+  for (long long c0 = (long long)blockIdx.x * kT * EPT; c0 < n; c0 += (long long)nbs * kT * EPT) {
+    C<T> v[EPT];
 #pragma unroll
-  for (int j = 0; j < kTileEPT; ++j) {
-    const long long e = t0 + j * kT + tid;
-    v[j] = e < n ? xr[e] : mk<T>(0, 0);
-  }
-  for (int i = 0; i < k1; ++i) {
-    const C<T> hv = hs[i];
-    const C<T> *vi = V + ((long long)i * R + r) * n;
+    for (int j = 0; j < EPT; ++j) {
+      const long long e = c0 + j * kT + tid;
+      v[j] = e < n ? xr[e] : mk<T>(0, 0);
+    }
+#pragma unroll 2
+    for (int i = 0; i < k1; ++i) {
+      const C<T> hv = hs[i];
+      const C<T> *vi = V + ((long long)i * R + r) * n + c0 + tid;
 #pragma unroll
-    for (int j = 0; j < kTileEPT; ++j) {
-      const long long e = t0 + j * kT + tid;
+      for (int j = 0; j < EPT; ++j) {
+        if (c0 + j * kT + tid < n) {
+          const C<T> a = __ldg(vi + j * kT);
+          v[j].x = mad(-hv.x, a.x, v[j].x);
+          v[j].x = mad(hv.y, a.y, v[j].x);
+          v[j].y = mad(-hv.x, a.y, v[j].y);
+          v[j].y = mad(-hv.y, a.x, v[j].y);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+      const long long e = c0 + j * kT + tid;
       if (e < n) {
-        const C<T> a = __ldg(vi + e);
-        v[j].x = mad(-hv.x, a.x, v[j].x);
-        v[j].x = mad(hv.y, a.y, v[j].x);
-        v[j].y = mad(-hv.x, a.y, v[j].y);
-        v[j].y = mad(-hv.y, a.x, v[j].y);
+        if (scaled) {
+          vr[e] = mk<T>(v[j].x * sc, v[j].y * sc);
+        } else {
+          xr[e] = v[j];
+          nacc = mad(v[j].x, v[j].x, nacc);
+          nacc = mad(v[j].y, v[j].y, nacc);
+        }
       }
     }
   }
-  if (scaled) {
-    const T sc = (T)(nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0);
-    C<T> *vr = vout + (long long)r * n;
-#pragma unroll
-    for (int j = 0; j < kTileEPT; ++j) {
-      const long long e = t0 + j * kT + tid;
-      if (e < n) vr[e] = mk<T>(v[j].x * sc, v[j].y * sc);
-    }
-    return;
-  }
-  T nacc = 0;
-#pragma unroll
-  for (int j = 0; j < kTileEPT; ++j) {
-    const long long e = t0 + j * kT + tid;
-    if (e < n) xr[e] = v[j];
-    nacc = mad(v[j].x, v[j].x, nacc);
-    nacc = mad(v[j].y, v[j].y, nacc);
-  }
+  if (scaled) return;
   const double2 sres = block_reduce(make_double2((double)nacc, 0.0), shn);
-  if (tid == 0) npart[(long long)r * nb + blockIdx.x] = sres.x;
+  if (tid == 0) npart[(long long)r * nbs + blockIdx.x] = sres.x;
 }
 
-// Before the subtraction: ||x'||^2 = ||x||^2 - sum_i |h_i|^2 (x' = x - V h is the part
-// of x orthogonal to the basis), flag[r] = 1 where ||x'|| < ||x|| / 16.  The test is
+// The test: ||x'||^2 = ||x||^2 - sum_i |h_i|^2 before the subtraction (x' = x - V h is the
+// part of x orthogonal to the basis), flag[r] = 1 where ||x'|| < ||x|| / 16.  The test is
 // that of Daniel, Gragg, Kaufman and Stewart with a looser threshold than their
 // 1/sqrt(2): one projection leaves x' orthogonal to V up to about eps ||x|| / ||x'||,
 // so below 1/16 cancellation the loss stays under ~16 eps per step: ~4e-15 in FP64,
@@ -288,63 +332,198 @@ __global__ void __launch_bounds__(kT) cgs_sub_kernel(const C<T> *__restrict__ V,
 // worst 256 times less relative to ||x'||^2.  For this operator the product A v_k is
 // dominated by v_k, so 1/sqrt(2) would trigger the second projection in nearly every
 // iteration, doubling the work.
-__global__ void cgs_precheck_kernel(const double *__restrict__ npart0, const double2 *__restrict__ h,
-                                    double *__restrict__ nrm, int *__restrict__ flag, int k1, int nb, int ldh) {
+//
+// First projection, after the dot pass: block (i < k1, r) sums the chunk partials of
+// h1[r][i] (and zeroes h2[r][i]), block (k1, r) those of ||w||^2 (kept in nrm[R + r]);
+// the last of the k1 + 1 blocks of r to finish (a ticket counter, reset by it) runs the
+// test below on r.
+__global__ void __launch_bounds__(kT) cgs_hsum_kernel(const double2 *__restrict__ part,
+                                                      const double *__restrict__ npart, double2 *__restrict__ h,
+                                                      double2 *__restrict__ h2, double *__restrict__ nrm,
+                                                      int *__restrict__ flag, unsigned *__restrict__ tick, int k1,
+                                                      int R, int nch, int ldh) {
   __shared__ double2 sh[kT / 32];
-  const int r = blockIdx.x;
-  double a0 = 0.0, a1 = 0.0;
-  for (int b = threadIdx.x; b < nb; b += kT) a0 += npart0[(long long)r * nb + b];
-  for (int i = threadIdx.x; i < k1; i += kT) {
-    const double2 v = h[(long long)r * ldh + i];
+  __shared__ int last;
+  const int i = blockIdx.x, r = blockIdx.y, tid = threadIdx.x;
+  double2 acc = make_double2(0.0, 0.0);
+  if (i < k1) {
+    for (int c = tid; c < nch; c += kT) {
+      const double2 v = part[((long long)r * k1 + i) * nch + c];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+  } else {
+    for (int c = tid; c < nch; c += kT) acc.x += npart[(long long)r * nch + c];
+  }
+  acc = block_reduce(acc, sh);
+  if (tid == 0) {
+    if (i < k1) {
+      h[(long long)r * ldh + i] = acc;
+      h2[(long long)r * ldh + i] = make_double2(0.0, 0.0);
+    } else {
+      nrm[R + r] = acc.x;
+    }
+    __threadfence();
+    last = atomicAdd(&tick[r], 1u) == (unsigned)k1;
+  }
+  __syncthreads();
+  if (!last) return;
+  double a1 = 0.0;
+  for (int j = tid; j < k1; j += kT) {
+    const double2 v = __ldcg(&h[(long long)r * ldh + j]);
     a1 = fma(v.x, v.x, a1);
     a1 = fma(v.y, v.y, a1);
   }
-  const double2 s = block_reduce(make_double2(a0, a1), sh);
-  if (threadIdx.x == 0) {
-    const double n0 = sqrt(s.x);
-    const double d = s.x - s.y;
+  const double2 sa = block_reduce(make_double2(a1, 0.0), sh);
+  if (tid == 0) {
+    const double s0 = __ldcg(&nrm[R + r]);
+    const double n0 = sqrt(s0);
+    const double d = s0 - sa.x;
     const double n1 = d > 0.0 ? sqrt(d) : 0.0;
     nrm[r] = n1;
     flag[r] = n1 < 0.0625 * n0 ? 1 : 0;
+    if (flag[r]) atomicAdd(&flag[32], 1);  // second projections so far
+    tick[r] = 0u;
   }
 }
 
-// after the second projection: nrm[r] = ||x''|| for the right-hand sides that had one
-__global__ void cgs_renorm_kernel(const double *__restrict__ npart, double *__restrict__ nrm,
-                                  const int *__restrict__ flag, int nb) {
-  __shared__ double2 sh[kT / 32];
-  const int r = blockIdx.x;
-  if (!flag[r]) return;
-  double acc = 0.0;
-  for (int b = threadIdx.x; b < nb; b += kT) acc += npart[(long long)r * nb + b];
-  const double2 s = block_reduce(make_double2(acc, 0.0), sh);
-  if (threadIdx.x == 0) nrm[r] = sqrt(s.x);
+// The second projection of every flagged right-hand side r in one cooperative launch
+// (the grid is co-resident), which returns at once when no flag is set:
+//   h2 = V^H w' (dot units), w'' = w' - V h2, nrm = ||w''||, vnext = w'' / nrm.
+// The per-block norm partials go to npart[r * gridDim.x + block] (gridDim.x <= 1024).
+template <typename T>
+__global__ void __launch_bounds__(kT) cgs_second_kernel(const C<T> *__restrict__ V, C<T> *__restrict__ w,
+                                                        C<T> *__restrict__ vnext, double2 *__restrict__ h2,
+                                                        double2 *__restrict__ part, double *__restrict__ npart,
+                                                        double *__restrict__ nrm, const int *__restrict__ flag,
+                                                        int k1, int R, long long n, int ldh, int nch) {
+  int any = 0;
+  for (int r = 0; r < R; ++r) any |= flag[r];
+  if (!any) return;  // the same decision in every block: no block reaches a grid barrier
+  cg::grid_group grid = cg::this_grid();
+  __shared__ C<T> hs[64];
+  __shared__ double2 shn[kT / 32];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nw = gridDim.x * (kT / 32), gw = blockIdx.x * (kT / 32) + (tid >> 5);
+  constexpr int CH = GsShape<T>::kCh;
+  // h2 partials
+  const int units = R * nch * k1;
+  for (int u = gw; u < units; u += nw) {
+    const int i = u % k1, rc = u / k1;
+    const int c = rc % nch, r = rc / nch;
+    if (!flag[r]) continue;
+    const long long e0 = (long long)c * CH;
+    double ax, ay, nn = 0.0;
+    dot_unit<T, false>(V + ((long long)i * R + r) * n + e0, w + (long long)r * n + e0, n - e0, lane, ax, ay, nn);
+    if (lane == 0) part[((long long)r * k1 + i) * nch + c] = make_double2(ax, ay);
+  }
+  grid.sync();
+  // h2[r][i]: one warp per (r, i)
+  for (int p = gw; p < R * k1; p += nw) {
+    const int r = p / k1, i = p % k1;
+    if (!flag[r]) continue;
+    double ax = 0.0, ay = 0.0;
+    for (int c = lane; c < nch; c += 32) {
+      const double2 v = __ldcg(&part[((long long)r * k1 + i) * nch + c]);
+      ax += v.x;
+      ay += v.y;
+    }
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if (lane == 0) h2[(long long)r * ldh + i] = make_double2(ax, ay);
+  }
+  grid.sync();
+  // w'' = w' - V h2 and the block's part of ||w''||^2
+  for (int r = 0; r < R; ++r) {
+    if (!flag[r]) continue;
+    __syncthreads();
+    if (tid < k1) hs[tid] = to_c<T>(__ldcg(&h2[(long long)r * ldh + tid]));
+    __syncthreads();
+    T nacc = 0;
+    for (long long e = (long long)blockIdx.x * kT + tid; e < n; e += (long long)gridDim.x * kT) {
+      C<T> v = w[(long long)r * n + e];
+      for (int i = 0; i < k1; ++i) {
+        const C<T> a = V[((long long)i * R + r) * n + e], hv = hs[i];
+        v.x = mad(-hv.x, a.x, v.x);
+        v.x = mad(hv.y, a.y, v.x);
+        v.y = mad(-hv.x, a.y, v.y);
+        v.y = mad(-hv.y, a.x, v.y);
+      }
+      w[(long long)r * n + e] = v;
+      nacc = mad(v.x, v.x, nacc);
+      nacc = mad(v.y, v.y, nacc);
+    }
+    const double2 sres = block_reduce(make_double2((double)nacc, 0.0), shn);
+    if (tid == 0) npart[(long long)r * gridDim.x + blockIdx.x] = sres.x;
+  }
+  grid.sync();
+  // nrm = ||w''|| (every block sums the partials itself) and vnext = w'' / nrm
+  for (int r = 0; r < R; ++r) {
+    if (!flag[r]) continue;
+    double a = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += kT) a += __ldcg(&npart[(long long)r * gridDim.x + b]);
+    const double2 sr = block_reduce(make_double2(a, 0.0), shn);  // the total in thread 0
+    if (tid == 0) shn[0].x = sqrt(sr.x);
+    __syncthreads();
+    const double nr = shn[0].x;
+    __syncthreads();
+    if (blockIdx.x == 0 && tid == 0) nrm[r] = nr;
+    const T sc = (T)(nr > 0.0 ? 1.0 / nr : 0.0);
+    for (long long e = (long long)blockIdx.x * kT + tid; e < n; e += (long long)gridDim.x * kT) {
+      const C<T> v = w[(long long)r * n + e];
+      vnext[(long long)r * n + e] = mk<T>(v.x * sc, v.y * sc);
+    }
+  }
 }
 
-// out[r * ldh + i] = sum_b part[(r * k1 + i) * nb + b]; 0 where flag[r] == 0
-__global__ void part_sum_kernel(const double2 *__restrict__ part, double2 *__restrict__ out,
-                                const int *__restrict__ flag, int k1, int nb, int ldh) {
-  __shared__ double2 sh[kT / 32];
-  const int i = blockIdx.x, r = blockIdx.y;
-  if (flag && !flag[r]) {
-    if (threadIdx.x == 0) out[(long long)r * ldh + i] = make_double2(0.0, 0.0);
-    return;
-  }
-  double2 acc = make_double2(0.0, 0.0);
-  for (int b = threadIdx.x; b < nb; b += kT) {
-    const double2 v = part[((long long)r * k1 + i) * nb + b];
-    acc.x += v.x;
-    acc.y += v.y;
-  }
-  const double2 t = block_reduce(acc, sh);
-  if (threadIdx.x == 0) out[(long long)r * ldh + i] = t;
+// chunks of the dot pass per right-hand side
+template <typename T> int cgs_nch(long long n) {
+  return (int)((n + GsShape<T>::kCh - 1) / GsShape<T>::kCh);
 }
 
-int cgs_nb(long long n) { return (int)((n + kTile - 1) / kTile); }
+// resident blocks per SM of the two passes (occupancy of the compiled kernels)
+template <typename T> int sub_per_sm() {
+  static int v = 0;
+  if (v == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, cgs_sub_kernel<T>, kT, 0) != cudaSuccess || v < 1)) {
+    cudaGetLastError();
+    v = 1;
+  }
+  return v;
+}
+template <typename T> int dot_per_sm() {
+  static int v = 0;
+  if (v == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, cgs_dot_kernel<T>, kT, 0) != cudaSuccess || v < 1)) {
+    cudaGetLastError();
+    v = 1;
+  }
+  return v;
+}
 
+// blocks per right-hand side of the sub pass: at most one wave of the GPU over all R,
+// every block the same number of chunks
+template <typename T> int cgs_nbs(long long n, int R) {
+  const long long chunks = (n + (long long)kT * GsShape<T>::kSubEPT - 1) / ((long long)kT * GsShape<T>::kSubEPT);
+  long long maxb = ((long long)sub_per_sm<T>() * sm_count()) / R;
+  if (maxb < 1) maxb = 1;
+  const long long per = (chunks + maxb - 1) / maxb;
+  return (int)((chunks + per - 1) / per);
+}
+
+// blocks of the dot pass: at most one wave, every warp the same number of units
+template <typename T> int cgs_dot_blocks(long long units) {
+  const long long maxw = (long long)dot_per_sm<T>() * sm_count() * (kT / 32);
+  const long long per = (units + maxw - 1) / maxw;
+  const long long warps = (units + per - 1) / per;
+  const long long b = (warps + kT / 32 - 1) / (kT / 32);
+  return (int)(b < 1 ? 1 : b);
+}
+
+// grid of the element-wise kernels (grid-stride loops): up to eight 256-thread blocks
+// per SM
 int blocks_for(long long n) {
   long long g = (n + kT - 1) / kT;
-  if (g > 152LL * 32) g = 152LL * 32;
+  const long long cap = 8LL * sm_count();
+  if (g > cap) g = cap;
   return (int)(g < 1 ? 1 : g);
 }
 
@@ -368,26 +547,46 @@ void gmres_norm(const C<T> *w, double *part, double *out, int R, long long n, cu
   norm_final<<<R, kT, 0, s>>>(part, out, nb);
 }
 
+template <typename T> int second_blocks() {
+  static int v = 0;
+  if (v == 0) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cgs_second_kernel<T>, kT, 0) != cudaSuccess || per < 1) {
+      cudaGetLastError();
+      per = 1;
+    }
+    v = per * sm_count();
+    if (v > 1024) v = 1024;
+  }
+  return v;
+}
+
 template <typename T>
 int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double2 *h2, double2 *part, double *npart,
                         double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s) {
-  if (k1 < 1 || k1 > 64) return -1;
-  const int nb = cgs_nb(n);
-  double *np0 = npart, *np1 = npart + (long long)R * nb;
-  const dim3 g(nb, R);
-  count_launches(9);
+  if (k1 < 1 || k1 > 64 || R < 1 || R > 16) return -1;
+  const int nch = cgs_nch<T>(n), nbs = cgs_nbs<T>(n, R);
+  double *np0 = npart, *np1 = npart + (long long)R * nch;
+  unsigned *tick = reinterpret_cast<unsigned *>(flag + 16);
+  const int gd = cgs_dot_blocks<T>((long long)R * nch * k1);
+  count_launches(4);
   // first projection: h1 = V^H w and ||w||; ||w'|| from the difference of squares
-  cgs_dot_kernel<T><<<g, kT, 0, s>>>(V, w, part, np0, nullptr, k1, R, n, nb);
-  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h1, nullptr, k1, nb, ldh);
-  cgs_precheck_kernel<<<R, kT, 0, s>>>(np0, h1, nrm, flag, k1, nb, ldh);
+  cgs_dot_kernel<T><<<gd, kT, 0, s>>>(V, w, part, np0, nullptr, k1, R, n, nch);
+  cgs_hsum_kernel<<<dim3(k1 + 1, R), kT, 0, s>>>(part, np0, h1, h2, nrm, flag, tick, k1, R, nch, ldh);
   // w' = w - V h1, written normalised into vnext where no second projection is needed
-  cgs_sub_kernel<T><<<g, kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nb, ldh, vnext, nrm, flag);
+  cgs_sub_kernel<T><<<dim3(nbs, R), kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nbs, ldh, vnext, nrm, flag);
   // second projection where the first cancelled too much (h2 = 0 elsewhere)
-  cgs_dot_kernel<T><<<g, kT, 0, s>>>(V, w, part, np0, flag, k1, R, n, nb);
-  part_sum_kernel<<<dim3(k1, R), kT, 0, s>>>(part, h2, flag, k1, nb, ldh);
-  cgs_sub_kernel<T><<<g, kT, 0, s>>>(V, w, h2, np1, flag, k1, R, n, nb, ldh, nullptr, nullptr, nullptr);
-  cgs_renorm_kernel<<<R, kT, 0, s>>>(np1, nrm, flag, nb);
-  scale_kernel<T><<<dim3(blocks_for(n), R), kT, 0, s>>>(w, vnext, nrm, n, flag);
+  const C<T> *Va = V;
+  C<T> *wa = w, *va = vnext;
+  double2 *h2a = h2, *pa = part;
+  double *npa = np1, *nrma = nrm;
+  const int *fa = flag;
+  int k1a = k1, Ra = R, ldha = ldh, ncha = nch;
+  long long na = n;
+  void *args[] = {&Va, &wa, &va, &h2a, &pa, &npa, &nrma, &fa, &k1a, &Ra, &na, &ldha, &ncha};
+  if (cudaLaunchCooperativeKernel((const void *)cgs_second_kernel<T>, dim3(second_blocks<T>()), dim3(kT), args, 0, s) !=
+      cudaSuccess)
+    return -1;
   return 0;
 }
 
@@ -422,62 +621,80 @@ __global__ void givens_init_kernel(GivensState st, const double *nrm, int R, int
 // column k of the Hessenberg matrix (h1 + h2 above the diagonal, nrm below) for every
 // active right-hand side: previous rotations, the new rotation, the residual estimate
 // |g_{k+1}|; a right-hand side leaves the iteration when the estimate reaches thr or
-// the new vector vanished (breakdown).
-__global__ void givens_kernel(GivensState st, const double2 *h1, const double2 *h2, const double *nrm, int k, int R,
-                              int m, int ldh) {
-  const int r = threadIdx.x;
+// the new vector vanished (breakdown).  One warp per right-hand side: the lanes stage
+// the column and the rotations in shared memory, lane 0 runs the recurrence from there.
+constexpr int kGivWarps = 16;
+__global__ void __launch_bounds__(kGivWarps * 32) givens_kernel(GivensState st, const double2 *h1, const double2 *h2,
+                                                               const double *nrm, int k, int R, int m, int ldh) {
+  __shared__ double2 col_s[kGivWarps][64];
+  __shared__ double2 sn_s[kGivWarps][64];
+  __shared__ double cs_s[kGivWarps][64];
   __shared__ int cnt;
-  if (r == 0) cnt = 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
-  if (r < R && st.active[r]) {
-    double2 *col = st.Rm + ((long long)r * m + k) * ldh;
-    for (int i = 0; i <= k; ++i) {
+  for (int r = wid; r < R; r += nwarp) {
+    if (!st.active[r]) continue;
+    double2 *cs_col = col_s[wid];
+    for (int i = lane; i <= k; i += 32) {
       const double2 a = h1[(long long)r * ldh + i], b = h2[(long long)r * ldh + i];
-      col[i] = make_double2(a.x + b.x, a.y + b.y);
+      cs_col[i] = make_double2(a.x + b.x, a.y + b.y);
     }
-    const double hk1 = nrm[r];
-    for (int i = 0; i < k; ++i) {
-      const double ci = st.cs[(long long)r * m + i];
-      const double2 si = st.sn[(long long)r * m + i];
-      const double2 ai = col[i], bi = col[i + 1];
-      const double2 t = make_double2(ci * ai.x + zmul(si, bi).x, ci * ai.y + zmul(si, bi).y);
-      const double2 nb = zmul(zconj(si), ai);
-      col[i + 1] = make_double2(-nb.x + ci * bi.x, -nb.y + ci * bi.y);
-      col[i] = t;
+    for (int i = lane; i < k; i += 32) {
+      cs_s[wid][i] = st.cs[(long long)r * m + i];
+      sn_s[wid][i] = st.sn[(long long)r * m + i];
     }
-    const double2 a = col[k];
-    const double aa = zabs(a);
-    const double rho = hypot(aa, hk1);
-    double ck;
-    double2 sk;
-    if (aa == 0.0) {
-      ck = 0.0;
-      sk = make_double2(1.0, 0.0);
-    } else {
-      ck = aa / rho;
-      sk = make_double2(a.x / aa * hk1 / rho, a.y / aa * hk1 / rho);
+    __syncwarp();
+    if (lane == 0) {
+      const double hk1 = nrm[r];
+      double2 bi_next = cs_col[0];
+      for (int i = 0; i < k; ++i) {
+        const double ci = cs_s[wid][i];
+        const double2 si = sn_s[wid][i];
+        const double2 ai = bi_next, bi = cs_col[i + 1];
+        const double2 t = make_double2(ci * ai.x + zmul(si, bi).x, ci * ai.y + zmul(si, bi).y);
+        const double2 nb = zmul(zconj(si), ai);
+        bi_next = make_double2(-nb.x + ci * bi.x, -nb.y + ci * bi.y);
+        cs_col[i] = t;
+      }
+      const double2 a = bi_next;
+      const double aa = zabs(a);
+      const double rho = hypot(aa, hk1);
+      double ck;
+      double2 sk;
+      if (aa == 0.0) {
+        ck = 0.0;
+        sk = make_double2(1.0, 0.0);
+      } else {
+        ck = aa / rho;
+        sk = make_double2(a.x / aa * hk1 / rho, a.y / aa * hk1 / rho);
+      }
+      cs_col[k] = make_double2(ck * a.x + sk.x * hk1, ck * a.y + sk.y * hk1);
+      st.cs[(long long)r * m + k] = ck;
+      st.sn[(long long)r * m + k] = sk;
+      double2 *gr = st.g + (long long)r * ldh;
+      const double2 gk = gr[k];
+      const double2 gn = zmul(zconj(sk), gk);
+      gr[k + 1] = make_double2(-gn.x, -gn.y);
+      gr[k] = make_double2(ck * gk.x, ck * gk.y);
+      st.kr[r] = k + 1;
+      int act = 1;
+      if (hk1 == 0.0) {
+        act = 0;
+        st.brk[r] = 1;
+      }
+      if (zabs(gr[k + 1]) <= st.thr[r]) act = 0;
+      st.active[r] = act;
     }
-    col[k] = make_double2(ck * a.x + sk.x * hk1, ck * a.y + sk.y * hk1);
-    st.cs[(long long)r * m + k] = ck;
-    st.sn[(long long)r * m + k] = sk;
-    double2 *gr = st.g + (long long)r * ldh;
-    const double2 gk = gr[k];
-    const double2 gn = zmul(zconj(sk), gk);
-    gr[k + 1] = make_double2(-gn.x, -gn.y);
-    gr[k] = make_double2(ck * gk.x, ck * gk.y);
-    st.kr[r] = k + 1;
-    int act = 1;
-    if (hk1 == 0.0) {
-      act = 0;
-      st.brk[r] = 1;
-    }
-    if (zabs(gr[k + 1]) <= st.thr[r]) act = 0;
-    st.active[r] = act;
+    __syncwarp();
+    double2 *col = st.Rm + ((long long)r * m + k) * ldh;
+    for (int i = lane; i <= k; i += 32) col[i] = cs_col[i];
+    __syncwarp();
   }
   __syncthreads();
-  if (r < R && st.active[r]) atomicAdd(&cnt, 1);
+  if ((int)threadIdx.x < R && st.active[threadIdx.x]) atomicAdd(&cnt, 1);
   __syncthreads();
-  if (r == 0) *st.n_active = cnt;
+  if (threadIdx.x == 0) *st.n_active = cnt;
 }
 
 // y = R^-1 g over the kr columns of each right-hand side; yd[r * ldh + i] (zero beyond kr)
@@ -501,7 +718,7 @@ __global__ void backsub_kernel(GivensState st, double2 *yd, int R, int m, int ld
   }
 }
 
-int gs_partial_blocks(long long n) { return cgs_nb(n); }
+int gs_partial_blocks(long long n) { return cgs_nch<float>(n) > cgs_nch<double>(n) ? cgs_nch<float>(n) : cgs_nch<double>(n); }
 
 void givens_init(const GivensState &st, const double *nrm, int R, int ldh, cudaStream_t s) {
   count_launches(1);
@@ -511,7 +728,8 @@ void givens_init(const GivensState &st, const double *nrm, int R, int ldh, cudaS
 void givens_step(const GivensState &st, const double2 *h1, const double2 *h2, const double *nrm, int k, int R, int m,
                  int ldh, cudaStream_t s) {
   count_launches(1);
-  givens_kernel<<<1, 32, 0, s>>>(st, h1, h2, nrm, k, R, m, ldh);
+  const int warps = R < kGivWarps ? R : kGivWarps;
+  givens_kernel<<<1, 32 * (warps > 0 ? warps : 1), 0, s>>>(st, h1, h2, nrm, k, R, m, ldh);
 }
 
 void givens_solve(const GivensState &st, double2 *yd, int R, int m, int ldh, cudaStream_t s) {

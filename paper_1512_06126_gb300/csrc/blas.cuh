@@ -20,14 +20,17 @@ void gmres_norm(const C<T> *w, double *part, double *out, int R, long long n, cu
 // directly; elsewhere a second projection h2 = V^H w', w'' = w' - V h2 and
 // vnext = w'' / ||w''|| (h2 = 0 where it did not run).  nrm = the norm used.  w is
 // overwritten only where the second projection ran.
-// part: R * k1 * gs_partial_blocks(n) complex; npart: 2 * R * gs_partial_blocks(n);
-// flag: R ints (1 where the second projection ran).
+// R <= 16.  part: R * k1 * gs_partial_blocks(n) complex; npart: R * gs_partial_blocks(n)
+// + R * 1024 doubles; nrm: 2 R doubles; flag: 48 ints, zero before the first call (flags
+// [0, R): 1 where the second projection ran; [16, 16 + R): reduction tickets, left zero;
+// [32]: incremented by every second projection).
+// Returns -1 (nothing launched) for arguments out of range or a failed launch.
 template <typename T>
 int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double2 *h2, double2 *part, double *npart,
                         double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s);
 int gs_partial_blocks(long long n);
 
-// GMRES least-squares state on the device, per right-hand side r (R <= 32):
+// GMRES least-squares state on the device, per right-hand side r (m < 64):
 // Rm [R][m][ldh] (rotated Hessenberg columns), cs [R][m], sn [R][m], g [R][ldh],
 // active / kr / brk [R] (still iterating, columns so far, breakdown), thr [R] (stop
 // when |g_{k+1}| <= thr), n_active [1] (right-hand sides still iterating).

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <limits>
 #include <complex>
 #include <cstring>
 #include <new>
@@ -77,7 +78,7 @@ struct ie_ctx {
   std::vector<void *> allocs;
   long long dev_bytes = 0;
   // profiling of the contraction kernel: event pairs recorded around each launch
-  bool prof = false;
+  int prof = 0;  // 0 off, 1 contraction launches, 2 also the steps of every Krylov iteration
   struct ProfRec { cudaEvent_t a, b; int dtype; };
   std::vector<ProfRec> prof_rec;
 
@@ -340,6 +341,24 @@ struct Op {
   }
 };
 
+// A pair of events around one step of a Krylov iteration (profiling level 2).
+struct ProfSpan {
+  ie_ctx *c;
+  int kind;
+  cudaEvent_t a = nullptr;
+  ProfSpan(ie_ctx *c_, int kind_) : c(c_), kind(kind_) {
+    if (c->prof >= 2 && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, c->stream);
+  }
+  void end() {
+    cudaEvent_t b = nullptr;
+    if (a && cudaEventCreate(&b) == cudaSuccess) {
+      cudaEventRecord(b, c->stream);
+      c->prof_rec.push_back({a, b, kind});
+      a = nullptr;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // GMRES(m), classical Gram-Schmidt with selective reorthogonalisation, all right-hand
 // sides in lockstep.
@@ -476,11 +495,17 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
         IE_CUDA(cudaEventSynchronize(c->pin_ev[slot]));
         if (c->pin_active[1 + slot] == 0) break;
       }
+      ProfSpan sp_op(c, sizeof(T) == 4 ? IE_PROF_PRODUCT_C64 : IE_PROF_PRODUCT_C128);
       IE_TRY(op(Vb + (long long)k * nR, w, R));
+      sp_op.end();
+      ProfSpan sp_gs(c, sizeof(T) == 4 ? IE_PROF_GS_C64 : IE_PROF_GS_C128);
       if (ie::gmres_orthogonalize<T>(Vb, w, Vb + (long long)(k + 1) * nR, h1, h2, c->part, c->nrmpart, c->nrm,
                                   c->gsflag, k + 1, R, n, ldh, s) != 0)
         return IE_ERR_ARG;
+      sp_gs.end();
+      ProfSpan sp_gv(c, IE_PROF_GIVENS);
       ie::givens_step(st, h1, h2, c->nrm, k, R, m, ldh, s);
+      sp_gv.end();
       const int slot = k % kPinSlots;
       IE_CUDA(cudaMemcpyAsync(c->pin_active + 1 + slot, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
       IE_CUDA(cudaEventRecord(c->pin_ev[slot], s));
@@ -545,6 +570,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
   const long long n = c->nvec();
   const auto t0 = std::chrono::steady_clock::now();
   if (!use_x0) IE_CUDA(cudaMemsetAsync(u, 0, n * R * sizeof(double2), c->stream));
+  IE_CUDA(cudaMemsetAsync(c->gsflag + 32, 0, sizeof(int), c->stream));
   ie_solve_info inf{};
   bool conv = false, brk = false;
   std::vector<double> rel;
@@ -573,7 +599,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
         IE_CUDA(cudaMemcpyAsync(bn.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         IE_CUDA(cudaStreamSynchronize(c->stream));
         rel.assign(R, 0.0);
-        for (int r = 0; r < R; ++r) rel[r] = bn[r] > 0 ? 1.0 : 0.0;
+        for (int r = 0; r < R; ++r) rel[r] = !std::isfinite(bn[r]) ? bn[r] : (bn[r] > 0 ? 1.0 : 0.0);
       } else {
         IE_TRY(true_residual(c, g, transpose, b, u, rel));
       }
@@ -584,12 +610,17 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
       act.rpi = g.rpi;
       std::vector<int> pos;
       double worst = 0;
+      bool finite = true;
       for (size_t k = 0; k < g.inst.size(); ++k) {
         double wk = 0;
-        for (int p = 0; p < g.rpi; ++p) wk = std::max(wk, rel[k * g.rpi + p]);
+        for (int p = 0; p < g.rpi; ++p) {
+          wk = std::max(wk, rel[k * g.rpi + p]);
+          finite = finite && std::isfinite(rel[k * g.rpi + p]);
+        }
         worst = std::max(worst, wk);
         if (wk > tol) { act.inst.push_back(g.inst[k]); pos.push_back((int)k); }
       }
+      if (!finite) { brk = true; break; }  // a non-finite residual ends the refinement, unconverged
       if (act.inst.empty()) { conv = true; break; }
       if (outer == c->max_outer || inner_total >= c->max_iter) break;
       // the residual blocks of the active instances, rounded to c64, packed in order
@@ -615,8 +646,9 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
   // otherwise (and after a plain FP64 solve) measure it here
   if (!(precision == IE_MIXED && conv)) IE_TRY(true_residual(c, g, transpose, b, u, rel));
   double worst = 0;
-  for (double v : rel) worst = std::max(worst, v);
+  for (double v : rel) worst = std::isfinite(v) ? std::max(worst, v) : std::numeric_limits<double>::infinity();
   inf.final_rel_res = worst;
+  IE_CUDA(cudaMemcpy(&inf.reorth, c->gsflag + 32, sizeof(int), cudaMemcpyDeviceToHost));
   inf.t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;
   if (worst <= tol) return IE_OK;
@@ -738,7 +770,7 @@ ie_status ie_profile(ie_ctx *c, int enable) {
   if (!c) return IE_ERR_ARG;
   IE_CUDA(cudaStreamSynchronize(c->stream));
   prof_clear(c);
-  c->prof = enable != 0;
+  c->prof = enable < 0 ? 0 : (enable > 2 ? 2 : enable);
   return IE_OK;
 }
 
@@ -920,7 +952,8 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   IE_TRY(dalloc(c, &c->part, (size_t)max_rhs * (c->restart + 1) * nbp * sizeof(double2)));
   IE_TRY(dalloc(c, &c->hdev, (size_t)3 * max_rhs * (c->restart + 1) * sizeof(double2)));
   IE_TRY(dalloc(c, &c->nrmpart, (size_t)2 * max_rhs * std::max<long long>(1024, nbp) * sizeof(double)));
-  IE_TRY(dalloc(c, &c->gsflag, (size_t)max_rhs * sizeof(int)));
+  IE_TRY(dalloc(c, &c->gsflag, (size_t)48 * sizeof(int)));  // flags, reduction tickets, a counter
+  IE_CUDA(cudaMemset(c->gsflag, 0, (size_t)48 * sizeof(int)));
   IE_TRY(dalloc(c, &c->nrm, (size_t)2 * max_rhs * sizeof(double)));
   {
     const int m = c->restart, ldh = m + 1;

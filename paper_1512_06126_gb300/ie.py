@@ -19,6 +19,7 @@ IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN = 0, 1, 2
 IE_ERR_SCRATCH = -6
 IE_C64, IE_C128 = 0, 1
 IE_FP64, IE_MIXED = 0, 1
+IE_PROF_PRODUCT_C64, IE_PROF_PRODUCT_C128, IE_PROF_GS_C64, IE_PROF_GS_C128, IE_PROF_GIVENS = 2, 3, 4, 5, 6
 
 EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_solve_batch",
            "ie_contract_tuning", "ie_set_contract_variant", "ie_rhs_mt", "ie_set_sigma", "ie_set_receivers",
@@ -47,7 +48,8 @@ class ie_options(ctypes.Structure):
 
 class ie_solve_info(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
-                ("final_rel_res", ctypes.c_double), ("t_solve", ctypes.c_double)]
+                ("final_rel_res", ctypes.c_double), ("t_solve", ctypes.c_double),
+                ("reorth", ctypes.c_int)]
 
 
 class IEError(RuntimeError):
@@ -249,7 +251,9 @@ class Context:
         _check(self._lib.ie_set_contract_variant(self.ctx, nrhs, variant), "ie_set_contract_variant")
 
     def profile(self, enable):
-        _check(self._lib.ie_profile(self.ctx, int(bool(enable))), "ie_profile")
+        """0/False off, 1/True the contraction launches, 2 also the steps of every Krylov
+        iteration."""
+        _check(self._lib.ie_profile(self.ctx, int(enable)), "ie_profile")
 
     def profile_read(self, dtype):
         ms = ctypes.c_double()

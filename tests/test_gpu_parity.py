@@ -267,9 +267,31 @@ def test_solve_weak_contrast_takes_second_projection(precision, tol, bound):
     torch.cuda.synchronize()
     st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), 2, tol, precision=precision)
     assert st == 0, (st, info.final_rel_res)
+    assert info.reorth > 0, info.reorth
     u = to_host(ud)
     for r in range(2):
         assert rel(u[r], u_ref[r]) <= bound, (r, rel(u[r], u_ref[r]))
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_nan_rhs_is_not_converged(precision):
+    """A right-hand side holding a NaN must not come back as a converged solve (a NaN
+    residual compares false against every tolerance)."""
+    need_gpu()
+    m = W.small_model(nx=7, ny=5, nz=3, seed=11, freq=3.0)
+    g = m.grid
+    qa = all_offsets_cached(m)
+    q = qa[g.ny - 1:, g.nx - 1:]
+    ctx = lib_context(m, [q], max_rhs=2)
+    b = np.stack([W.random_field((3, g.nz, g.ny, g.nx), 81 + r) for r in range(2)])
+    b[1, 2, 1, 2, 3] = np.nan
+    bd = to_dev(b)
+    ud = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), 2, 1e-7, precision=precision)
+    assert st != 0, (st, info.final_rel_res)
+    assert not info.final_rel_res <= 1e-7
     ctx.close()
 
 
@@ -277,8 +299,8 @@ def test_solve_weak_contrast_takes_second_projection(precision, tol, bound):
 def test_fast_fft_lengths_against_c128(shape):
     """Grids whose padded lengths 2N are 128, 256 or 512 take the register-blocked FP32
     FFTs; the c64 product (one and two right-hand sides) must match the c128 product,
-    which uses the generic Stockham FFTs in FP64.  The mixed-precision solve (FP64
-    row passes around the FP32 FFTs) must reach the FP64 solve's solution."""
+    which uses the generic Stockham FFTs in FP64.  The mixed-precision solve (inner
+    GMRES in c64 through the same FFTs) must reach the FP64 solve's solution."""
     need_gpu()
     nx, ny, nz = shape
     m0 = W.small_model(nx=nx, ny=ny, nz=nz, seed=7, freq=1.0)
