@@ -54,7 +54,7 @@ typedef enum {
   IE_ERR_SCRATCH = -6    /* the problem needs more work space than ie_matvec_noalloc's fixed array */
 } ie_status;
 
-enum { IE_C64 = 0, IE_C128 = 1 };                 /* element type of matvec vectors */
+enum { IE_C64 = 0, IE_C128 = 1, IE_C128_DF = 7 };  /* element type of matvec vectors (see ie_matvec) */
 enum { IE_FP64 = 0, IE_MIXED = 1 };              /* solve precision */
 
 /* Grid of Nx*Ny*Nz cells (eq. (bcyl)): equal lateral sizes hx, hy; z_edges_host holds
@@ -148,7 +148,10 @@ ie_status ie_generate_coefficients(const ie_grid *grid, const ie_layers *layers,
                                    void *stream);
 
 /* y = A x (transpose = 0) or y = A^T x (transpose = 1) for instance inst, with nrhs
- * right-hand sides.  dtype selects c64 (IE_C64, the c64 coefficient copy) or c128.
+ * right-hand sides.  dtype selects c64 (IE_C64, the c64 coefficient copy) or c128
+ * (IE_C128; IE_C128_DF: c128 vectors and FFTs with the contraction in compensated
+ * double-float arithmetic on the FP32 pipe, as in the residuals of the mixed-precision
+ * solver: about twice-FP32 accuracy, no counterpart in the paper).
  * x_dev, y_dev: device arrays [nrhs][3][Nz][Ny][Nx] of that type; they must not
  * alias.  stream: a cudaStream_t, or NULL for the context stream.  Asynchronous. */
 ie_status ie_matvec(ie_ctx *ctx, int inst, const void *x_dev, void *y_dev, int nrhs, int dtype, int transpose,

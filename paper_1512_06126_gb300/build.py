@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libie_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["fft.cu", "contract.cu", "setup.cu", "blas.cu", "coefgen.cu", "ie_api.cu", "noalloc.cu", "receivers.cu"]
+SOURCES = ["fft.cu", "contract.cu", "contract_df.cu", "setup.cu", "blas.cu", "coefgen.cu", "ie_api.cu", "noalloc.cu",
+           "receivers.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + CSRC, "-I" + INCLUDE]
 

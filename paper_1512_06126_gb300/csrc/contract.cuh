@@ -26,6 +26,14 @@ template <typename T>
 int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant,
                     cudaStream_t s);
 
+// Double-float copy of packed blocks: qdf[i] = (hi, lo of re, hi, lo of im) of q64[i],
+// hi = fl32(x), lo = fl32(x - hi).
+void launch_split_df(const double2 *q64, float4 *qdf, long long count, cudaStream_t s);
+// The contraction of c128 spectra in compensated double-float arithmetic (the FP32
+// pipe; about twice-FP32 accuracy) from the double-float copy of the blocks.  R <= 4;
+// returns -1 (nothing applied) if the grid or R does not fit or the launch fails.
+int launch_contract_df(double2 *spec, const float4 *qdf, int Nx, int Ny, int Nz, int R, int ldz, cudaStream_t s);
+
 // Use the TMA-pipelined kernel where it applies (c64, Nz in {16, 24, 32, 48}, R <= 2).
 extern bool contract_tma_enabled;
 // Error code recorded by a contraction kernel since the last call (0: none); resets it.

@@ -40,6 +40,7 @@ struct Instance {
   double freq = 0.0;
   double2 *q64 = nullptr;
   float2 *q32 = nullptr;
+  float4 *qdf = nullptr;           // double-float copy of q64 (residuals of the mixed solver)
   double2 *rtab = nullptr;         // receiver kernels [Ny][Nx][Nz][10] (after ie_set_receivers)
   double2 en{0.0, 0.0}, hn{0.0, 0.0};  // normal E^N and E^N'/(i w mu0) at the receiver depth
 };
@@ -264,7 +265,10 @@ ie_status build_spectral(ie_ctx *c, Instance &in, const double *q_host) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(dq);
   cudaFree(buf);
-  return cuda_status(e);
+  IE_TRY(cuda_status(e));
+  IE_TRY(dalloc(c, &in.qdf, nf * BS * sizeof(float4)));
+  ie::launch_split_df(in.q64, in.qdf, nf * BS, c->stream);
+  return cuda_status(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------
@@ -289,7 +293,7 @@ struct Group {
 };
 
 template <typename T>
-ie_status contract_group(ie_ctx *c, const Group &g, ie::C<T> *spec, cudaStream_t s) {
+ie_status contract_group(ie_ctx *c, const Group &g, ie::C<T> *spec, cudaStream_t s, bool df = false) {
   const int CZ = g.R() * 3 * c->nz;
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (c->prof) {
@@ -298,10 +302,14 @@ ie_status contract_group(ie_ctx *c, const Group &g, ie::C<T> *spec, cudaStream_t
     cudaEventRecord(ea, s);
   }
   const int variant = sizeof(T) == 4 ? c->cvar[g.rpi] : ie::kContractPanel;
-  for (size_t k = 0; k < g.inst.size(); ++k)
-    if (ie::launch_contract<T>(spec + k * (size_t)g.rpi * 3 * c->nz, qf<T>(c->inst[g.inst[k]]), c->nx, c->ny, c->nz,
-                               g.rpi, CZ, variant, s) != 0)
+  for (size_t k = 0; k < g.inst.size(); ++k) {
+    ie::C<T> *sk = spec + k * (size_t)g.rpi * 3 * c->nz;
+    if constexpr (sizeof(T) == 8) {
+      if (df && ie::launch_contract_df(sk, c->inst[g.inst[k]].qdf, c->nx, c->ny, c->nz, g.rpi, CZ, s) == 0) continue;
+    }
+    if (ie::launch_contract<T>(sk, qf<T>(c->inst[g.inst[k]]), c->nx, c->ny, c->nz, g.rpi, CZ, variant, s) != 0)
       return IE_ERR_CUDA;
+  }
   if (c->prof) {
     cudaEventRecord(eb, s);
     c->prof_rec.push_back({ea, eb, sizeof(T) == 8 ? IE_C128 : IE_C64});
@@ -309,8 +317,10 @@ ie_status contract_group(ie_ctx *c, const Group &g, ie::C<T> *spec, cudaStream_t
   return IE_OK;
 }
 
+// df (c128 only): the contraction in double-float arithmetic (launch_contract_df)
 template <typename T>
-ie_status apply(ie_ctx *c, const Group &g, const ie::C<T> *x, ie::C<T> *y, int transpose, cudaStream_t s) {
+ie_status apply(ie_ctx *c, const Group &g, const ie::C<T> *x, ie::C<T> *y, int transpose, cudaStream_t s,
+                bool df = false) {
   using V = ie::C<T>;
   const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
   const int CZ = g.R() * 3 * Nz;
@@ -322,7 +332,7 @@ ie_status apply(ie_ctx *c, const Group &g, const ie::C<T> *x, ie::C<T> *y, int t
   V *spec = (V *)c->spec;
   ie::launch_fft_rows_fwd<T>(x, in_s, t1, CZ, Nz, Ny, Nx, c->px, s);
   ie::launch_fft_axis<T, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, (T)1, s);
-  IE_TRY(contract_group<T>(c, g, spec, s));
+  IE_TRY(contract_group<T>(c, g, spec, s, df));
   ie::launch_fft_axis<T, true>(spec, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, (T)1, s);
   ie::launch_fft_rows_inv<T>(t1, x, dg, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
   return cuda_status(cudaGetLastError());
@@ -335,9 +345,10 @@ struct Op {
   ie_ctx *c;
   const Group *g;
   int transpose;
+  bool df = false;  // c128: double-float contraction
   ie_status operator()(const ie::C<T> *x, ie::C<T> *y, int R) const {
     if (R != g->R()) return IE_ERR_ARG;
-    return apply<T>(c, *g, x, y, transpose, c->stream);
+    return apply<T>(c, *g, x, y, transpose, c->stream, df);
   }
 };
 
@@ -541,12 +552,14 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
   return IE_OK;
 }
 
-// max over right-hand sides of ||b - A128 u|| / ||b||; leaves the residual in c->r
+// max over right-hand sides of ||b - A128 u|| / ||b||; leaves the residual in c->r.  df:
+// the product's contraction in double-float arithmetic (the residuals of the mixed
+// solver), else FP64.
 ie_status true_residual(ie_ctx *c, const Group &g, int transpose, const double2 *b, const double2 *u,
-                        std::vector<double> &rel) {
+                        std::vector<double> &rel, bool df = false) {
   const long long n = c->nvec();
   const int R = g.R();
-  Op<double> op{c, &g, transpose};
+  Op<double> op{c, &g, transpose, df};
   IE_TRY(op(u, c->r, R));
   ie::vec_sub<double>(b, c->r, c->r, n * R, c->stream);
   std::vector<double> rn(R), bn(R);
@@ -601,7 +614,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
         rel.assign(R, 0.0);
         for (int r = 0; r < R; ++r) rel[r] = !std::isfinite(bn[r]) ? bn[r] : (bn[r] > 0 ? 1.0 : 0.0);
       } else {
-        IE_TRY(true_residual(c, g, transpose, b, u, rel));
+        IE_TRY(true_residual(c, g, transpose, b, u, rel, true));
       }
       inf.outer_iters = outer + 1;
       // instances with a right-hand side above the tolerance stay in the inner solve;
@@ -644,7 +657,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
   }
   // the refinement loop ends on a true residual of the final iterate when it converged;
   // otherwise (and after a plain FP64 solve) measure it here
-  if (!(precision == IE_MIXED && conv)) IE_TRY(true_residual(c, g, transpose, b, u, rel));
+  if (!(precision == IE_MIXED && conv)) IE_TRY(true_residual(c, g, transpose, b, u, rel, precision == IE_MIXED));
   double worst = 0;
   for (double v : rel) worst = std::isfinite(v) ? std::max(worst, v) : std::numeric_limits<double>::infinity();
   inf.final_rel_res = worst;
@@ -1002,6 +1015,7 @@ ie_status ie_matvec(ie_ctx *c, int inst, const void *x, void *y, int nrhs, int d
   g.inst = {inst};
   g.rpi = nrhs;
   if (dtype == IE_C128) return apply<double>(c, g, (const double2 *)x, (double2 *)y, transpose, s);
+  if (dtype == IE_C128_DF) return apply<double>(c, g, (const double2 *)x, (double2 *)y, transpose, s, true);
   if (dtype == IE_C64) return apply<float>(c, g, (const float2 *)x, (float2 *)y, transpose, s);
   return IE_ERR_ARG;
 }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libie_gb300.so")
 IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN = 0, 1, 2
 IE_ERR_SCRATCH = -6
 IE_C64, IE_C128 = 0, 1
+IE_C128_DF = 7
 IE_FP64, IE_MIXED = 0, 1
 IE_PROF_PRODUCT_C64, IE_PROF_PRODUCT_C128, IE_PROF_GS_C64, IE_PROF_GS_C128, IE_PROF_GIVENS = 2, 3, 4, 5, 6
 

@@ -181,6 +181,35 @@ def test_c64_pipelined_contraction_against_c128(shape):
     ctx.close()
 
 
+@pytest.mark.parametrize("shape", [(24, 20, 32), (20, 16, 24), (12, 10, 48)])
+def test_c128_double_float_contraction_matches_fp64(shape):
+    """The c128 product with its contraction in compensated double-float arithmetic
+    (the mixed solver's residuals) against the FP64 product on generated coefficients,
+    for 1, 2 and 4 right-hand sides and both transposes.  Bound: the compensated dot
+    product is as accurate as one in twice FP32 precision, an error of about
+    (3 Nz eps32)^2 ~ 3e-11 of the sum of magnitudes at Nz = 32; 1e-10 relative to the
+    whole product leaves a margin for the FFTs' own FP64 error (~1e-15)."""
+    need_gpu()
+    nx, ny, nz = shape
+    m0 = W.small_model(nx=nx, ny=ny, nz=nz, seed=5, freq=1.0)
+    g = m0.grid
+    from paper_1512_06126_gb300 import build, ie
+    build.build()
+    ctx = ie.Context(g, m0.layers, m0.sigma_a, m0.freqs[:1], None, max_rhs=4)
+    s = torch.cuda.current_stream().cuda_stream
+    for R in (1, 2, 4):
+        x = to_dev(W.random_field((R, 3, nz, ny, nx), 90 + R), torch.complex128)
+        for tr in (0, 1):
+            y64 = torch.empty_like(x)
+            ydf = torch.empty_like(x)
+            ctx.matvec(0, x.data_ptr(), y64.data_ptr(), R, dtype=ie.IE_C128, transpose=tr, stream=s)
+            ctx.matvec(0, x.data_ptr(), ydf.data_ptr(), R, dtype=ie.IE_C128_DF, transpose=tr, stream=s)
+            torch.cuda.synchronize()
+            err = float((ydf - y64).norm() / y64.norm())
+            assert err <= 1e-10, (shape, R, tr, err)
+    ctx.close()
+
+
 @pytest.mark.parametrize("shape", [(24, 20, 32), (24, 20, 16), (20, 16, 24), (12, 10, 48)])
 def test_c64_pipelined_contraction_generated_coefficients(shape):
     """The pipelined c64 contraction on coefficients from the device generator (the
