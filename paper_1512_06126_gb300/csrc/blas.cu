@@ -159,8 +159,8 @@ __global__ void round_kernel(const double2 *__restrict__ x, float2 *__restrict__
 //     with the i = 0 unit, npart(r, c) = sum_chunk |x|^2.  The grid is sized so that
 //     every warp gets the same number of units.
 //   sub pass: persistent blocks per right-hand side stream x -= sum_i h_i V_i over
-//     chunks of kT * kSubEPT elements (the same number of chunks per block) and leave
-//     one partial of |x|^2 per block.
+//     chunks of kT * kSubEPT elements (the same number of chunks per block), one basis
+//     vector at a time, and leave one partial of |x|^2 per block.
 // A right-hand side whose flag (if given) is 0 is skipped.
 // ---------------------------------------------------------------------------
 template <typename T> struct GsShape;
@@ -287,7 +287,9 @@ __global__ void __launch_bounds__(kT) cgs_sub_kernel(const C<T> *__restrict__ V,
       const long long e = c0 + j * kT + tid;
       v[j] = e < n ? xr[e] : mk<T>(0, 0);
     }
-#pragma unroll 2
+    // one basis vector at a time (8 loads in flight per thread): unrolling over vectors
+    // costs registers and occupancy and measured slower (5.1 against 6.0 TB/s at k1 = 10)
+#pragma unroll 1
     for (int i = 0; i < k1; ++i) {
       const C<T> hv = hs[i];
       const C<T> *vi = V + ((long long)i * R + r) * n + c0 + tid;
@@ -347,12 +349,14 @@ __global__ void __launch_bounds__(kT) cgs_hsum_kernel(const double2 *__restrict_
   const int i = blockIdx.x, r = blockIdx.y, tid = threadIdx.x;
   double2 acc = make_double2(0.0, 0.0);
   if (i < k1) {
+#pragma unroll 4
     for (int c = tid; c < nch; c += kT) {
       const double2 v = part[((long long)r * k1 + i) * nch + c];
       acc.x += v.x;
       acc.y += v.y;
     }
   } else {
+#pragma unroll 4
     for (int c = tid; c < nch; c += kT) acc.x += npart[(long long)r * nch + c];
   }
   acc = block_reduce(acc, sh);
@@ -555,7 +559,9 @@ template <typename T> int second_blocks() {
       cudaGetLastError();
       per = 1;
     }
-    v = per * sm_count();
+    // two blocks per SM at most: the launch is cheap when nothing is flagged (the usual
+    // case) and still streams at full width when something is
+    v = (per < 2 ? per : 2) * sm_count();
     if (v > 1024) v = 1024;
   }
   return v;
@@ -718,6 +724,26 @@ __global__ void backsub_kernel(GivensState st, double2 *yd, int R, int m, int ld
   }
 }
 
+// z[r] = Q^H (g_kr e_kr): the residual of the cycle's least-squares solution in the
+// basis V_0..V_kr (the rotations applied in reverse, G_i^H (a, b) = (c a - s b,
+// conj(s) a + c b)); zero beyond kr
+__global__ void residual_coeffs_kernel(GivensState st, double2 *z, int R, int m, int ldh) {
+  const int r = threadIdx.x;
+  if (r >= R) return;
+  const int kr = st.kr[r];
+  double2 *zr = z + (long long)r * ldh;
+  for (int i = 0; i < ldh; ++i) zr[i] = make_double2(0.0, 0.0);
+  zr[kr] = st.g[(long long)r * ldh + kr];
+  for (int i = kr - 1; i >= 0; --i) {
+    const double c = st.cs[(long long)r * m + i];
+    const double2 sn = st.sn[(long long)r * m + i];
+    const double2 a = zr[i], b = zr[i + 1];
+    const double2 sb = zmul(sn, b), sa = zmul(zconj(sn), a);
+    zr[i] = make_double2(c * a.x - sb.x, c * a.y - sb.y);
+    zr[i + 1] = make_double2(sa.x + c * b.x, sa.y + c * b.y);
+  }
+}
+
 int gs_partial_blocks(long long n) { return cgs_nch<float>(n) > cgs_nch<double>(n) ? cgs_nch<float>(n) : cgs_nch<double>(n); }
 
 void givens_init(const GivensState &st, const double *nrm, int R, int ldh, cudaStream_t s) {
@@ -730,6 +756,11 @@ void givens_step(const GivensState &st, const double2 *h1, const double2 *h2, co
   count_launches(1);
   const int warps = R < kGivWarps ? R : kGivWarps;
   givens_kernel<<<1, 32 * (warps > 0 ? warps : 1), 0, s>>>(st, h1, h2, nrm, k, R, m, ldh);
+}
+
+void givens_residual(const GivensState &st, double2 *z, int R, int m, int ldh, cudaStream_t s) {
+  count_launches(1);
+  residual_coeffs_kernel<<<1, 32, 0, s>>>(st, z, R, m, ldh);
 }
 
 void givens_solve(const GivensState &st, double2 *yd, int R, int m, int ldh, cudaStream_t s) {

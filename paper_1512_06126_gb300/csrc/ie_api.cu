@@ -404,9 +404,12 @@ ie_status swap_blocks(V *a, int p, int q, long long elem, V *tmp, cudaStream_t s
 // remaining cycles run on the smaller group.  x is back in the original order on
 // return.  T = double: c128 vectors and operator; T = float: c64 vectors and
 // operator, the basis in the same storage (half of it used).
+// x_zero: x is zero on entry (the first residual is b).  For c64 vectors the residual
+// at a restart comes from the Krylov relation (b - A x = V_{k+1} Q^H g_{k+1} e_{k+1},
+// one combination of the basis instead of a product); c128 solves recompute it.
 template <typename T>
 ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T> *x, double tol, int max_iter,
-                GmresResult *res, bool compact) {
+                GmresResult *res, bool compact, bool x_zero) {
   using Vt = ie::C<T>;
   Vt *const Vb = (Vt *)c->V;
   Vt *const w = (Vt *)c->w;
@@ -442,12 +445,19 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
   int it = 0;  // iterations issued (including the few issued after the last right-hand side stopped)
   bool pending = false;  // a finished cycle's column counts are being copied
   int R_prev = R;
+  bool have_res = false;  // w holds b - A x from the Krylov relation
   while (true) {
     h1 = c->hdev;
     h2 = c->hdev + (size_t)R * ldh;
     yd = c->hdev + 2 * (size_t)R * ldh;
-    IE_TRY(op(x, w, R));
-    ie::vec_sub<T>(b, w, w, nR, s);
+    if (x_zero) {
+      IE_CUDA(cudaMemcpyAsync(w, b, nR * sizeof(Vt), cudaMemcpyDeviceToDevice, s));
+      x_zero = false;
+    } else if (!have_res) {
+      IE_TRY(op(x, w, R));
+      ie::vec_sub<T>(b, w, w, nR, s);
+    }
+    have_res = false;
     ie::gmres_norm<T>(w, c->nrmpart, c->nrm, R, n, s);
     ie::gmres_scale<T>(w, Vb, c->nrm, R, n, s);
     ie::givens_init(st, c->nrm, R, ldh, s);
@@ -492,6 +502,7 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
         R = n_act * rpi;
         nR = n * R;
         IE_TRY(upload_thr());
+        have_res = false;
         continue;  // residual of the smaller group
       }
     }
@@ -526,6 +537,13 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
     // x += V y with y from the rotated least-squares problem (zero beyond each kr)
     ie::givens_solve(st, yd, R, m, ldh, s);
     ie::gmres_maxpy<T>(Vb, yd, x, kmax, R, n, ldh, 1.0, s);
+    if (sizeof(T) == 4) {
+      // the next cycle's residual from the basis: w = V_0..V_kmax z
+      ie::givens_residual(st, h1, R, m, ldh, s);
+      IE_CUDA(cudaMemsetAsync(w, 0, nR * sizeof(Vt), s));
+      ie::gmres_maxpy<T>(Vb, h1, w, kmax + 1, R, n, ldh, 1.0, s);
+      have_res = true;
+    }
     IE_CUDA(cudaMemcpyAsync(kr.data(), st.kr, R * sizeof(int), cudaMemcpyDeviceToHost, s));
     IE_CUDA(cudaMemcpyAsync(brk.data(), st.brk, R * sizeof(int), cudaMemcpyDeviceToHost, s));
     pending = true;
@@ -596,7 +614,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
       IE_CUDA(cudaMemcpyAsync(c->r, b, n * R * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
       bw = c->r;
     }
-    IE_TRY(gmres<double>(c, g, transpose, bw, u, tol, c->max_iter, &gr, comp));
+    IE_TRY(gmres<double>(c, g, transpose, bw, u, tol, c->max_iter, &gr, comp, !use_x0));
     inf.inner_iters = gr.iters;
     inf.outer_iters = gr.cycles;
     conv = gr.converged;
@@ -647,7 +665,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
       GmresResult gr;
       const double itol = std::max(c->inner_tol, 0.5 * tol / std::max(worst, 1e-300));
       IE_TRY(gmres<float>(c, act, transpose, c->x32, c->y32, std::min(itol, 0.5), c->max_iter - inner_total, &gr,
-                          act.inst.size() > 1));
+                          act.inst.size() > 1, true));
       inner_total += gr.iters;
       brk = brk || gr.breakdown;
       for (size_t a = 0; a < pos.size(); ++a)
