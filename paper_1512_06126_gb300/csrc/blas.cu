@@ -630,71 +630,75 @@ __global__ void givens_init_kernel(GivensState st, const double *nrm, int R, int
 // the new vector vanished (breakdown).  One warp per right-hand side: the lanes stage
 // the column and the rotations in shared memory, lane 0 runs the recurrence from there.
 constexpr int kGivWarps = 16;
+// A: the arithmetic of the recurrence (FP32 for the c64 inner solves, whose tolerance is
+// at least 1e-4; FP64 otherwise); the state stays FP64 in memory.
+template <typename A>
 __global__ void __launch_bounds__(kGivWarps * 32) givens_kernel(GivensState st, const double2 *h1, const double2 *h2,
                                                                const double *nrm, int k, int R, int m, int ldh) {
-  __shared__ double2 col_s[kGivWarps][64];
-  __shared__ double2 sn_s[kGivWarps][64];
-  __shared__ double cs_s[kGivWarps][64];
+  using Z = C<A>;
+  __shared__ Z col_s[kGivWarps][64];
+  __shared__ Z sn_s[kGivWarps][64];
+  __shared__ A cs_s[kGivWarps][64];
   __shared__ int cnt;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   for (int r = wid; r < R; r += nwarp) {
     if (!st.active[r]) continue;
-    double2 *cs_col = col_s[wid];
+    Z *cs_col = col_s[wid];
     for (int i = lane; i <= k; i += 32) {
       const double2 a = h1[(long long)r * ldh + i], b = h2[(long long)r * ldh + i];
-      cs_col[i] = make_double2(a.x + b.x, a.y + b.y);
+      cs_col[i] = mk<A>((A)(a.x + b.x), (A)(a.y + b.y));
     }
     for (int i = lane; i < k; i += 32) {
-      cs_s[wid][i] = st.cs[(long long)r * m + i];
-      sn_s[wid][i] = st.sn[(long long)r * m + i];
+      cs_s[wid][i] = (A)st.cs[(long long)r * m + i];
+      const double2 v = st.sn[(long long)r * m + i];
+      sn_s[wid][i] = mk<A>((A)v.x, (A)v.y);
     }
     __syncwarp();
     if (lane == 0) {
-      const double hk1 = nrm[r];
-      double2 bi_next = cs_col[0];
+      const A hk1 = (A)nrm[r];
+      Z bi_next = cs_col[0];
       for (int i = 0; i < k; ++i) {
-        const double ci = cs_s[wid][i];
-        const double2 si = sn_s[wid][i];
-        const double2 ai = bi_next, bi = cs_col[i + 1];
-        const double2 t = make_double2(ci * ai.x + zmul(si, bi).x, ci * ai.y + zmul(si, bi).y);
-        const double2 nb = zmul(zconj(si), ai);
-        bi_next = make_double2(-nb.x + ci * bi.x, -nb.y + ci * bi.y);
-        cs_col[i] = t;
+        const A ci = cs_s[wid][i];
+        const Z si = sn_s[wid][i];
+        const Z ai = bi_next, bi = cs_col[i + 1];
+        const Z sb = cmul(si, bi), na = cmul(cconj(si), ai);
+        cs_col[i] = mk<A>(ci * ai.x + sb.x, ci * ai.y + sb.y);
+        bi_next = mk<A>(-na.x + ci * bi.x, -na.y + ci * bi.y);
       }
-      const double2 a = bi_next;
-      const double aa = zabs(a);
-      const double rho = hypot(aa, hk1);
-      double ck;
-      double2 sk;
-      if (aa == 0.0) {
-        ck = 0.0;
-        sk = make_double2(1.0, 0.0);
+      const Z a = bi_next;
+      const A aa = hypot(a.x, a.y);
+      const A rho = hypot(aa, hk1);
+      A ck;
+      Z sk;
+      if (aa == (A)0) {
+        ck = (A)0;
+        sk = mk<A>((A)1, (A)0);
       } else {
         ck = aa / rho;
-        sk = make_double2(a.x / aa * hk1 / rho, a.y / aa * hk1 / rho);
+        sk = mk<A>(a.x / aa * hk1 / rho, a.y / aa * hk1 / rho);
       }
-      cs_col[k] = make_double2(ck * a.x + sk.x * hk1, ck * a.y + sk.y * hk1);
-      st.cs[(long long)r * m + k] = ck;
-      st.sn[(long long)r * m + k] = sk;
+      cs_col[k] = mk<A>(ck * a.x + sk.x * hk1, ck * a.y + sk.y * hk1);
+      st.cs[(long long)r * m + k] = (double)ck;
+      st.sn[(long long)r * m + k] = make_double2((double)sk.x, (double)sk.y);
       double2 *gr = st.g + (long long)r * ldh;
-      const double2 gk = gr[k];
-      const double2 gn = zmul(zconj(sk), gk);
-      gr[k + 1] = make_double2(-gn.x, -gn.y);
-      gr[k] = make_double2(ck * gk.x, ck * gk.y);
+      const Z gk = mk<A>((A)gr[k].x, (A)gr[k].y);
+      const Z gn = cmul(cconj(sk), gk);
+      gr[k + 1] = make_double2(-(double)gn.x, -(double)gn.y);
+      gr[k] = make_double2((double)(ck * gk.x), (double)(ck * gk.y));
       st.kr[r] = k + 1;
       int act = 1;
-      if (hk1 == 0.0) {
+      if (hk1 == (A)0) {
         act = 0;
         st.brk[r] = 1;
       }
-      if (zabs(gr[k + 1]) <= st.thr[r]) act = 0;
+      if (hypot(gn.x, gn.y) <= (A)st.thr[r]) act = 0;
       st.active[r] = act;
     }
     __syncwarp();
     double2 *col = st.Rm + ((long long)r * m + k) * ldh;
-    for (int i = lane; i <= k; i += 32) col[i] = cs_col[i];
+    for (int i = lane; i <= k; i += 32) col[i] = make_double2((double)cs_col[i].x, (double)cs_col[i].y);
     __syncwarp();
   }
   __syncthreads();
@@ -752,10 +756,14 @@ void givens_init(const GivensState &st, const double *nrm, int R, int ldh, cudaS
 }
 
 void givens_step(const GivensState &st, const double2 *h1, const double2 *h2, const double *nrm, int k, int R, int m,
-                 int ldh, cudaStream_t s) {
+                 int ldh, bool fp32, cudaStream_t s) {
   count_launches(1);
   const int warps = R < kGivWarps ? R : kGivWarps;
-  givens_kernel<<<1, 32 * (warps > 0 ? warps : 1), 0, s>>>(st, h1, h2, nrm, k, R, m, ldh);
+  const dim3 blk(32 * (warps > 0 ? warps : 1));
+  if (fp32)
+    givens_kernel<float><<<1, blk, 0, s>>>(st, h1, h2, nrm, k, R, m, ldh);
+  else
+    givens_kernel<double><<<1, blk, 0, s>>>(st, h1, h2, nrm, k, R, m, ldh);
 }
 
 void givens_residual(const GivensState &st, double2 *z, int R, int m, int ldh, cudaStream_t s) {

@@ -41,9 +41,10 @@ struct GivensState {
 };
 // start of a cycle from the residual norms nrm[R]
 void givens_init(const GivensState &st, const double *nrm, int R, int ldh, cudaStream_t s);
-// Hessenberg column k (h1 + h2 above the diagonal, nrm[r] below) for every active r
+// Hessenberg column k (h1 + h2 above the diagonal, nrm[r] below) for every active r;
+// fp32: the recurrence in FP32 arithmetic (the state stays FP64)
 void givens_step(const GivensState &st, const double2 *h1, const double2 *h2, const double *nrm, int k, int R, int m,
-                 int ldh, cudaStream_t s);
+                 int ldh, bool fp32, cudaStream_t s);
 // z[r * ldh + i], i <= kr[r]: coefficients of the residual of the cycle's least-squares
 // solution in the basis V_0..V_kr (zero beyond kr): b - A x = sum_i z_i V_i
 void givens_residual(const GivensState &st, double2 *z, int R, int m, int ldh, cudaStream_t s);

@@ -526,7 +526,7 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
         return IE_ERR_ARG;
       sp_gs.end();
       ProfSpan sp_gv(c, IE_PROF_GIVENS);
-      ie::givens_step(st, h1, h2, c->nrm, k, R, m, ldh, s);
+      ie::givens_step(st, h1, h2, c->nrm, k, R, m, ldh, sizeof(T) == 4, s);
       sp_gv.end();
       const int slot = k % kPinSlots;
       IE_CUDA(cudaMemcpyAsync(c->pin_active + 1 + slot, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
