@@ -55,7 +55,7 @@ def peaks():
 
 
 # (workload, contraction variant, right-hand sides) -> DRAM bytes per contraction launch
-CONTRACT_TRAFFIC = {("C2", 3, 2): 654541312 + 86889728}  # variant 3; variant 5 after its next capture
+CONTRACT_TRAFFIC = {("C2", 3, 2): 654541312 + 86889728, ("C2", 5, 2): 654550784 + 88402176}
 
 
 def bf16_peak():

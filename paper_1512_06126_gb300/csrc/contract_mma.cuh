@@ -316,12 +316,16 @@ struct MmaUnpackCfg {
   static constexpr size_t OFF_BAR = 0;
   static constexpr size_t OFF_RAW = 128;
   static constexpr size_t RAW_BYTES = (size_t)BS * 8;
-  static constexpr size_t XRAW_BYTES = (size_t)4 * CZ * 8;
+  // the mirror vectors at a stride of CZ + 4 complex (= 4 mod 16 for the staging reads)
+  static constexpr int LDXR = CZ + 4;
+  static constexpr size_t XRAW_BYTES = (size_t)4 * LDXR * 8;
   static constexpr size_t OFF_XRAW = OFF_RAW + RAW_BYTES;
   static constexpr size_t OFF_BLK = OFF_XRAW + XRAW_BYTES;
   static constexpr size_t BLK_BYTES = (size_t)6 * NZ * LD * 8;
   static constexpr size_t OFF_XS = OFF_BLK + BLK_BYTES;
-  static constexpr size_t XS_BYTES = (size_t)KS * 32 * 32;  // per (k-step, lane): hi, lo of 2 complex
+  // X split, in two planes (hi, lo), each [k-step][lane] of 16 bytes
+  static constexpr size_t XS_PLANE = (size_t)KS * 32 * 16;
+  static constexpr size_t XS_BYTES = 2 * XS_PLANE;
   static constexpr size_t OFF_TRI = OFF_XS + XS_BYTES;
   static constexpr size_t SMEM = OFF_TRI + (size_t)P * 4;
 };
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(MmaUnpackCfg<NZ, R>::THREADS)
   float2 *raw = reinterpret_cast<float2 *>(sm + Cfg::OFF_RAW);
   float2 *xraw = reinterpret_cast<float2 *>(sm + Cfg::OFF_XRAW);
   float2 *blk = reinterpret_cast<float2 *>(sm + Cfg::OFF_BLK);
-  uint32_t *xs = reinterpret_cast<uint32_t *>(sm + Cfg::OFF_XS);
+  uint4 *xs = reinterpret_cast<uint4 *>(sm + Cfg::OFF_XS);
   uint32_t *tri = reinterpret_cast<uint32_t *>(sm + Cfg::OFF_TRI);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nf = (Nx + 1) * (Ny + 1);
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(MmaUnpackCfg<NZ, R>::THREADS)
     tma::bulk_g2s(raw, qf + (size_t)w * BS, (uint32_t)Cfg::RAW_BYTES, &bar[0]);
     for (int m = 0; m < nm; ++m) {
       const int mx = m % mi.nmx, my = m / mi.nmx;
-      tma::bulk_g2s(xraw + (size_t)m * CZ, spec + mi.pos(mx, my, Nx) * ldz, (uint32_t)(CZ * 8), &bar[0]);
+      tma::bulk_g2s(xraw + (size_t)m * Cfg::LDXR, spec + mi.pos(mx, my, Nx) * ldz, (uint32_t)(CZ * 8), &bar[0]);
     }
   };
 
@@ -413,28 +417,33 @@ __global__ void __launch_bounds__(MmaUnpackCfg<NZ, R>::THREADS)
       const int a = r2 / NZ, b = r2 - a * NZ;
       blk[(4 + kind) * NZ * LD + a * LD + b] = raw[4 * P + e];
     }
-    // X split and in fragment order: entry (k-step ks, lane 4 col + t) holds the hi
-    // parts (re, im of row 8 ks + t, re, im of row 8 ks + t + 4) of column col, then
-    // the lo parts; with the mirror component signs; zero beyond ncol
-    for (int e = tid; e < 8 * N3; e += THREADS) {
-      const int col = e / N3, k = e - col * N3;
-      float2 v = make_float2(0.f, 0.f);
+    // X split and in fragment order: entry (k-step ks, lane 4 col + t) of the hi plane
+    // holds re, im of row 8 ks + t and re, im of row 8 ks + t + 4 of column col (the lo
+    // plane the same for the lo parts), with the mirror component signs; zero beyond
+    // ncol.  One thread per entry, 16-byte stores.
+    for (int e = tid; e < Cfg::KS * 32; e += THREADS) {
+      const int ks = e >> 5, col = (e >> 2) & 7, t = e & 3;
+      const int k0 = ks * 8 + t;  // rows k0 and k0 + 4 lie in the same component (NZ % 8 == 0)
+      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
       if (col < ncol) {
         const int m = col / R, r = col - m * R;
         const int mx = m % nmx, my = m / nmx;
-        const int comp = k / NZ;
-        v = xraw[(size_t)m * CZ + r * N3 + k];
-        if ((comp == 0 && mx == 1) || (comp == 1 && my == 1)) { v.x = -v.x; v.y = -v.y; }
+        const int comp = k0 / NZ;
+        const float2 *xp = xraw + (size_t)m * Cfg::LDXR + r * N3 + k0;
+        v0 = xp[0];
+        v1 = xp[4];
+        if ((comp == 0 && mx == 1) || (comp == 1 && my == 1)) {
+          v0 = make_float2(-v0.x, -v0.y);
+          v1 = make_float2(-v1.x, -v1.y);
+        }
       }
-      const int ks = k >> 3, kk = k & 7;
-      uint32_t *d = xs + (ks * 32 + col * 4 + (kk & 3)) * 8 + (kk >> 2) * 2;
-      uint32_t hr, lr, hi, li;
-      mma::split(v.x, hr, lr);
-      mma::split(v.y, hi, li);
-      d[0] = hr;
-      d[1] = hi;
-      d[4] = lr;
-      d[5] = li;
+      uint4 h, l;
+      mma::split(v0.x, h.x, l.x);
+      mma::split(v0.y, h.y, l.y);
+      mma::split(v1.x, h.z, l.z);
+      mma::split(v1.y, h.w, l.w);
+      xs[e] = h;
+      xs[Cfg::KS * 32 + e] = l;
     }
     __syncthreads();
     // the raw slot is consumed: refill it with wavenumber w + gridDim.x
@@ -448,7 +457,7 @@ __global__ void __launch_bounds__(MmaUnpackCfg<NZ, R>::THREADS)
         for (int h = 0; h < 2; ++h)
 #pragma unroll
           for (int c = 0; c < 4; ++c) acc[i][j][h][c] = 0.f;
-    const uint4 *xf = reinterpret_cast<const uint4 *>(xs);
+    const uint4 *xfh = xs, *xfl = xs + Cfg::KS * 32;
 #pragma unroll
     for (int beta = 0; beta < 3; ++beta) {
       const bool trb = tr && beta < 2;
@@ -465,7 +474,7 @@ __global__ void __launch_bounds__(MmaUnpackCfg<NZ, R>::THREADS)
         m[2] = p[4 * cs];
         m[3] = p[8 * rs + 4 * cs];
         const int ks = beta * (NZ / 8) + bb / 8;
-        const uint4 xh = xf[(ks * 32 + lane) * 2], xl = xf[(ks * 32 + lane) * 2 + 1];
+        const uint4 xh = xfh[ks * 32 + lane], xl = xfl[ks * 32 + lane];
         const uint32_t brh[2] = {xh.x ^ neg, xh.z ^ neg}, bih[2] = {xh.y ^ neg, xh.w ^ neg};
         const uint32_t brl[2] = {xl.x ^ neg, xl.z ^ neg}, bil[2] = {xl.y ^ neg, xl.w ^ neg};
         uint32_t arh[4], arl[4], aih[4], ail[4];
