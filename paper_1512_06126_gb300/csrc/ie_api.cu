@@ -65,9 +65,12 @@ struct ie_ctx {
   cudaStream_t stream = nullptr;
   void *t1 = nullptr, *spec = nullptr;        // FFT workspaces (sized for c128, max_rhs)
   float2 *x32 = nullptr, *y32 = nullptr;       // c64 right-hand side and correction of the inner solves
+  // Krylov basis V [restart + 1][R][3N] and work vector w: sized for c128, used as c64
+  // by the inner solves of the mixed solver; r: c128 residual; part / nrmpart: partial
+  // sums of the Gram-Schmidt passes and norms; hdev: Hessenberg columns and solutions
   double2 *V = nullptr, *w = nullptr, *r = nullptr, *part = nullptr, *hdev = nullptr;
   double *nrmpart = nullptr, *nrm = nullptr;
-  int *gsflag = nullptr;                       // per right-hand side: second Gram-Schmidt projection ran
+  int *gsflag = nullptr;                       // 48 ints: second-projection flags, reduction tickets, a counter
   ie::GivensState gst{};                       // device least-squares state of GMRES
   int *pin_active = nullptr;                   // pinned: active counts (slot 0: cycle start, 1..4: iterations)
   cudaEvent_t pin_ev[4] = {};
@@ -78,8 +81,9 @@ struct ie_ctx {
   double *phi_r = nullptr;                     // per-receiver misfit terms
   std::vector<void *> allocs;
   long long dev_bytes = 0;
-  // profiling of the contraction kernel: event pairs recorded around each launch
-  int prof = 0;  // 0 off, 1 contraction launches, 2 also the steps of every Krylov iteration
+  // profiling: event pairs recorded around each contraction launch (level 1) and also
+  // around the steps of every Krylov iteration (level 2)
+  int prof = 0;
   struct ProfRec { cudaEvent_t a, b; int dtype; };
   std::vector<ProfRec> prof_rec;
 
@@ -698,7 +702,6 @@ std::vector<cd> mt_cell_average(const ie_ctx *c, double omega) {
   std::vector<cd> kap(L + 1), Eb(L + 1), Epb(L + 1);
   for (int m = 0; m <= L; ++m) kap[m] = std::sqrt(cd(0.0, -omega * kMu0) * c->sig[m]);
   cd E = 1.0, Ep = -kap[L];
-  double scale_log = 0.0;  // not needed for realistic layers; states are renormalised below
   for (int m = L - 1; m >= 1; --m) {
     Eb[m] = E;
     Epb[m] = Ep;
@@ -709,7 +712,6 @@ std::vector<cd> mt_cell_average(const ie_ctx *c, double omega) {
     E = Et;
     Ep = Ept;
   }
-  (void)scale_log;
   const cd a = cd(0.0, omega * kMu0) / Ep;  // E'(0) = i w mu0
   const cd EL = a;                          // E at the top of the basement before scaling was 1
   std::vector<cd> out(c->nz);
