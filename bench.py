@@ -414,7 +414,7 @@ def run_ours(args, rank, ws):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "c64 products, c128 refinement", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64 inner GMRES (products, Krylov vectors), c128 refinement residual", "data": "synthetic",
                 "config": {"workload": f"{args.workload}: {g.nx}x{g.ny}x{g.nz} cells, {len(model.layers.sigma) - 1}"
                                        f" layers + air, {model.freqs[0]} Hz, 2 polarisations, tol {TOL}",
                            "unknowns": n_unk, "rhs": R, "restart": args.restart,
