@@ -316,6 +316,20 @@ def run_ours(args, rank, ws):
         raise RuntimeError(f"FP64 solve did not converge: status {st64}")
     ctx64.close()
     del u64
+    # the mixed solve with FP64 Krylov vectors, Gram-Schmidt and rotations in its inner
+    # solves and the FP64 contraction in its residuals, on the same context (after one
+    # untimed solve)
+    ufk = torch.zeros_like(b)
+    ctx.solve(0, b.data_ptr(), ufk.data_ptr(), R, TOL, precision=ie.IE_MIXED_FP64K)
+    ufk.zero_()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    stfk, infofk = ctx.solve(0, b.data_ptr(), ufk.data_ptr(), R, TOL, precision=ie.IE_MIXED_FP64K)
+    torch.cuda.synchronize()
+    tts_fp64k = time.perf_counter() - t2
+    if stfk != ie.IE_OK:
+        raise RuntimeError(f"mixed FP64-Krylov solve did not converge: status {stfk}")
+    del ufk
 
     # ---- matvec GB/s (c64, both polarisations) ----
     nf = (g.nx + 1) * (g.ny + 1)
@@ -427,7 +441,9 @@ def run_ours(args, rank, ws):
                                          "cols_inv": kern_ms[3], "rows_inv": kern_ms[4]}},
                 "tts": {"mixed_s": tts_mixed, "fp64_s": tts_fp64, "speedup": tts_fp64 / tts_mixed,
                         "mixed_iters": iters / args.steps, "mixed_outer": outer / args.steps,
-                        "fp64_iters": info64.inner_iters, "final_rel_res": res},
+                        "fp64_iters": info64.inner_iters, "final_rel_res": res,
+                        "mixed_fp64_krylov_s": tts_fp64k, "mixed_fp64_krylov_iters": infofk.inner_iters,
+                        "mixed_fp64_krylov_final_rel_res": infofk.final_rel_res},
                 "roofline": roof,
                 "solve_breakdown": breakdown,
                 "contract_tuning": {"variants": ["tma 1 slot", "tma 3 slots", "panel", "tma 1 slot, 1 row/thread", "3xTF32 mma.sync, producer warp, 2 slots", "3xTF32 mma.sync, 1 slot, unpacked"],

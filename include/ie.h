@@ -55,7 +55,7 @@ typedef enum {
 } ie_status;
 
 enum { IE_C64 = 0, IE_C128 = 1, IE_C128_DF = 7 };  /* element type of matvec vectors (see ie_matvec) */
-enum { IE_FP64 = 0, IE_MIXED = 1 };              /* solve precision */
+enum { IE_FP64 = 0, IE_MIXED = 1, IE_MIXED_FP64K = 2 };  /* solve precision (see ie_solve) */
 
 /* Grid of Nx*Ny*Nz cells (eq. (bcyl)): equal lateral sizes hx, hy; z_edges_host holds
  * the nz+1 increasing cell boundaries (m).  x0, y0 are the lateral origin (m). */
@@ -161,8 +161,11 @@ ie_status ie_matvec(ie_ctx *ctx, int inst, const void *x_dev, void *y_dev, int n
  * Gram-Schmidt with a second projection wherever the first one cancels more than
  * 15/16 of the new vector's norm).  precision IE_FP64: c128 vectors and every product
  * with the c128 operator.  IE_MIXED: iterative refinement whose residual uses the c128
- * operator and whose corrections come from GMRES in c64 (c64 operator, c64 Krylov
- * vectors; Hessenberg entries, norms and rotations in FP64).
+ * operator (FP64 vectors and FFTs, double-float contraction) and whose corrections come
+ * from GMRES in c64 (c64 operator, c64 Krylov vectors, FP32 rotations; Hessenberg
+ * entries and cross-thread sums in FP64).  IE_MIXED_FP64K: the same refinement with the
+ * FP64 contraction in the residual and inner GMRES on the c64 operator with FP64 Krylov
+ * vectors, Gram-Schmidt and rotations.
  * Stops when ||b - A u|| <= tol ||b|| for every right-hand side.
  * b_dev, u_dev: device c128 [nrhs][3][Nz][Ny][Nx]; if use_x0 the initial guess is
  * read from u_dev, otherwise it is zero. */

@@ -266,10 +266,14 @@ template void launch_fft_rows_fwd<float, float>(const float2 *, const float2 *, 
                                                 const FftPlan &, cudaStream_t);
 template void launch_fft_rows_fwd<double, double>(const double2 *, const double2 *, double2 *, int, int, int, int,
                                                   const FftPlan &, cudaStream_t);
+template void launch_fft_rows_fwd<float, double>(const double2 *, const double2 *, float2 *, int, int, int, int,
+                                                 const FftPlan &, cudaStream_t);
 template void launch_fft_rows_inv<float, float>(const float2 *, const float2 *, const float2 *, const float2 *,
                                                 float2 *, int, int, int, int, const FftPlan &, cudaStream_t);
 template void launch_fft_rows_inv<double, double>(const double2 *, const double2 *, const double2 *,
                                                   const double2 *, double2 *, int, int, int, int, const FftPlan &,
                                                   cudaStream_t);
+template void launch_fft_rows_inv<float, double>(const float2 *, const double2 *, const double2 *, const double2 *,
+                                                 double2 *, int, int, int, int, const FftPlan &, cudaStream_t);
 
 }  // namespace ie

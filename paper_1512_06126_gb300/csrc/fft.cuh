@@ -135,14 +135,15 @@ void launch_fft_axis(const C<T> *in, C<T> *out, int outer, int Lin, int Lout, lo
 
 // Forward row pass: x[CZ][Ny][Nx] times in_scale[Nz][Ny][Nx] (cz -> z = cz % Nz), zero-padded
 // to 2Nx and transformed along x -> T1[Ny][2Nx][CZ].
-// T: arithmetic of the transform; TX: element type of x and in_scale (instantiated
-// with TX = T).
+// T: arithmetic of the transform; TX: element type of x and in_scale (TX = double with
+// T = float reads FP64 vectors and rounds the scaled values to FP32 on load).
 template <typename T, typename TX = T>
 void launch_fft_rows_fwd(const C<TX> *x, const C<TX> *in_scale, C<T> *t1, int CZ, int Nz, int Ny, int Nx,
                          const FftPlan &plan, cudaStream_t s);
 
 // Inverse row pass: T1[Ny][2Nx][CZ] -> inverse along kx, keep x < Nx, and write
 // y[CZ][Ny][Nx] = diag[cell] * x[CZ][cell] + out_scale[cell] * value.
+// (TX = double with T = float: the diagonal term and the output are FP64.)
 template <typename T, typename TX = T>
 void launch_fft_rows_inv(const C<T> *t1, const C<TX> *x, const C<TX> *diag, const C<TX> *out_scale, C<TX> *y,
                          int CZ, int Nz, int Ny, int Nx, const FftPlan &plan, cudaStream_t s);

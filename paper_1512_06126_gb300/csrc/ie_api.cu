@@ -67,8 +67,9 @@ struct ie_ctx {
   float2 *x32 = nullptr, *y32 = nullptr;       // c64 right-hand side and correction of the inner solves
   // Krylov basis V [restart + 1][R][3N] and work vector w: sized for c128, used as c64
   // by the inner solves of the mixed solver; r: c128 residual; part / nrmpart: partial
-  // sums of the Gram-Schmidt passes and norms; hdev: Hessenberg columns and solutions
-  double2 *V = nullptr, *w = nullptr, *r = nullptr, *part = nullptr, *hdev = nullptr;
+  // sums of the Gram-Schmidt passes and norms; hdev: Hessenberg columns and solutions;
+  // dx: c128 correction of the IE_MIXED_FP64K inner solves
+  double2 *V = nullptr, *w = nullptr, *r = nullptr, *dx = nullptr, *part = nullptr, *hdev = nullptr;
   double *nrmpart = nullptr, *nrm = nullptr;
   int *gsflag = nullptr;                       // 48 ints: second-projection flags, reduction tickets, a counter
   ie::GivensState gst{};                       // device least-squares state of GMRES
@@ -342,16 +343,40 @@ ie_status apply(ie_ctx *c, const Group &g, const ie::C<T> *x, ie::C<T> *y, int t
   return cuda_status(cudaGetLastError());
 }
 
+// c64 product on FP64 vectors (the inner solves of IE_MIXED_FP64K): the row passes
+// read and write FP64 (rounding the scaled input to FP32 on load; the diagonal term and
+// the output in FP64), the FFTs and the contraction run in FP32.
+ie_status apply_mixed(ie_ctx *c, const Group &g, const double2 *x, double2 *y, int transpose, cudaStream_t s) {
+  const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
+  const int CZ = g.R() * 3 * Nz;
+  const DiagSet &D = c->d64;
+  const double2 *in_s = (const double2 *)(transpose ? D.in_t : D.in_f);
+  const double2 *out_s = (const double2 *)(transpose ? D.out_t : D.out_f);
+  float2 *t1 = (float2 *)c->t1;
+  float2 *spec = (float2 *)c->spec;
+  ie::launch_fft_rows_fwd<float, double>(x, in_s, t1, CZ, Nz, Ny, Nx, c->px, s);
+  ie::launch_fft_axis<float, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
+  IE_TRY(contract_group<float>(c, g, spec, s));
+  ie::launch_fft_axis<float, true>(spec, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
+  ie::launch_fft_rows_inv<float, double>(t1, x, (const double2 *)D.diag, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
+  return cuda_status(cudaGetLastError());
+}
+
 // The operator the Krylov solver applies: the c128 product on c128 vectors (T =
-// double) or the c64 product on c64 vectors (T = float).
+// double), the c64 product on c64 vectors (T = float), or the c64 product on c128
+// vectors (T = double with single).
 template <typename T>
 struct Op {
   ie_ctx *c;
   const Group *g;
   int transpose;
-  bool df = false;  // c128: double-float contraction
+  bool df = false;      // c128: double-float contraction
+  bool single = false;  // T = double: the c64 product (apply_mixed)
   ie_status operator()(const ie::C<T> *x, ie::C<T> *y, int R) const {
     if (R != g->R()) return IE_ERR_ARG;
+    if constexpr (sizeof(T) == 8) {
+      if (single) return apply_mixed(c, *g, x, y, transpose, c->stream);
+    }
     return apply<T>(c, *g, x, y, transpose, c->stream, df);
   }
 };
@@ -413,7 +438,7 @@ ie_status swap_blocks(V *a, int p, int q, long long elem, V *tmp, cudaStream_t s
 // one combination of the basis instead of a product); c128 solves recompute it.
 template <typename T>
 ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T> *x, double tol, int max_iter,
-                GmresResult *res, bool compact, bool x_zero) {
+                GmresResult *res, bool compact, bool x_zero, bool single = false) {
   using Vt = ie::C<T>;
   Vt *const Vb = (Vt *)c->V;
   Vt *const w = (Vt *)c->w;
@@ -424,7 +449,7 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
   const long long blk = n * rpi;
   cudaStream_t s = c->stream;
   Group g = g0;
-  const Op<T> op{c, &g, transpose};
+  const Op<T> op{c, &g, transpose, false, single};
   int R = g.R();
   long long nR = n * R;
   const int G = (int)g0.inst.size();
@@ -601,7 +626,8 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
   if (!c || !b || !u || g.inst.empty() || g.rpi < 1 || g.rpi > 4 || R > c->max_rhs || !(tol > 0)) return IE_ERR_ARG;
   for (int k : g.inst)
     if (k < 0 || k >= (int)c->inst.size()) return IE_ERR_ARG;
-  if (precision != IE_FP64 && precision != IE_MIXED) return IE_ERR_ARG;
+  if (precision != IE_FP64 && precision != IE_MIXED && precision != IE_MIXED_FP64K) return IE_ERR_ARG;
+  const bool k64 = precision == IE_MIXED_FP64K;  // inner solves with FP64 Krylov vectors
   const long long n = c->nvec();
   const auto t0 = std::chrono::steady_clock::now();
   if (!use_x0) IE_CUDA(cudaMemsetAsync(u, 0, n * R * sizeof(double2), c->stream));
@@ -623,7 +649,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
     inf.outer_iters = gr.cycles;
     conv = gr.converged;
     brk = gr.breakdown;
-  } else {
+  } else {  // IE_MIXED, IE_MIXED_FP64K: iterative refinement
     int inner_total = 0;
     const long long blk = n * g.rpi;  // elements of one instance's block
     for (int outer = 0; outer <= c->max_outer; ++outer) {
@@ -636,7 +662,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
         rel.assign(R, 0.0);
         for (int r = 0; r < R; ++r) rel[r] = !std::isfinite(bn[r]) ? bn[r] : (bn[r] > 0 ? 1.0 : 0.0);
       } else {
-        IE_TRY(true_residual(c, g, transpose, b, u, rel, true));
+        IE_TRY(true_residual(c, g, transpose, b, u, rel, !k64));
       }
       inf.outer_iters = outer + 1;
       // instances with a right-hand side above the tolerance stay in the inner solve;
@@ -658,16 +684,34 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
       if (!finite) { brk = true; break; }  // a non-finite residual ends the refinement, unconverged
       if (act.inst.empty()) { conv = true; break; }
       if (outer == c->max_outer || inner_total >= c->max_iter) break;
-      // the residual blocks of the active instances, rounded to c64, packed in order
       const double2 *rsrc = (outer == 0 && !use_x0) ? b : c->r;
+      const int Ra = act.R();
+      const double itol = std::max(c->inner_tol, 0.5 * tol / std::max(worst, 1e-300));
+      if (k64) {
+        // the residual blocks of the active instances packed in order into r (a block
+        // only moves to a lower position, so source and target never overlap); inner
+        // GMRES with FP64 Krylov vectors on the c64 operator
+        for (size_t a = 0; a < pos.size(); ++a)
+          if (rsrc != c->r || (int)a != pos[a])
+            IE_CUDA(cudaMemcpyAsync(c->r + (long long)a * blk, rsrc + (long long)pos[a] * blk,
+                                    blk * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+        IE_CUDA(cudaMemsetAsync(c->dx, 0, n * Ra * sizeof(double2), c->stream));
+        GmresResult gr;
+        IE_TRY(gmres<double>(c, act, transpose, c->r, c->dx, std::min(itol, 0.5), c->max_iter - inner_total, &gr,
+                             act.inst.size() > 1, true, true));
+        inner_total += gr.iters;
+        brk = brk || gr.breakdown;
+        for (size_t a = 0; a < pos.size(); ++a)
+          ie::vec_add<double>(c->dx + (long long)a * blk, u + (long long)pos[a] * blk, blk, c->stream);
+        continue;
+      }
+      // the residual blocks of the active instances, rounded to c64, packed in order
       for (size_t a = 0; a < pos.size(); ++a)
         ie::vec_round(rsrc + (long long)pos[a] * blk, c->x32 + (long long)a * blk, blk, c->stream);
-      const int Ra = act.R();
       // inner: A64 d = r in c64 (relative tolerance inner_tol, bounded below so as not
       // to over-solve)
       IE_CUDA(cudaMemsetAsync(c->y32, 0, n * Ra * sizeof(float2), c->stream));
       GmresResult gr;
-      const double itol = std::max(c->inner_tol, 0.5 * tol / std::max(worst, 1e-300));
       IE_TRY(gmres<float>(c, act, transpose, c->x32, c->y32, std::min(itol, 0.5), c->max_iter - inner_total, &gr,
                           act.inst.size() > 1, true));
       inner_total += gr.iters;
@@ -679,7 +723,7 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
   }
   // the refinement loop ends on a true residual of the final iterate when it converged;
   // otherwise (and after a plain FP64 solve) measure it here
-  if (!(precision == IE_MIXED && conv)) IE_TRY(true_residual(c, g, transpose, b, u, rel, precision == IE_MIXED));
+  if (!(precision != IE_FP64 && conv)) IE_TRY(true_residual(c, g, transpose, b, u, rel, precision == IE_MIXED));
   double worst = 0;
   for (double v : rel) worst = std::isfinite(v) ? std::max(worst, v) : std::numeric_limits<double>::infinity();
   inf.final_rel_res = worst;
@@ -980,6 +1024,7 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   IE_TRY(dalloc(c, &c->V, (size_t)(c->restart + 1) * nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->w, nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->r, nv * sizeof(double2)));
+  IE_TRY(dalloc(c, &c->dx, nv * sizeof(double2)));  // correction of IE_MIXED_FP64K inner solves
   if (c->restart > 63) return IE_ERR_ARG;
   const long long nbp = std::max<long long>(ie::mdot_nb(c->nvec()), ie::gs_partial_blocks(c->nvec()));
   IE_TRY(dalloc(c, &c->part, (size_t)max_rhs * (c->restart + 1) * nbp * sizeof(double2)));

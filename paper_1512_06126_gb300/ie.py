@@ -19,7 +19,7 @@ IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN = 0, 1, 2
 IE_ERR_SCRATCH = -6
 IE_C64, IE_C128 = 0, 1
 IE_C128_DF = 7
-IE_FP64, IE_MIXED = 0, 1
+IE_FP64, IE_MIXED, IE_MIXED_FP64K = 0, 1, 2
 IE_PROF_PRODUCT_C64, IE_PROF_PRODUCT_C128, IE_PROF_GS_C64, IE_PROF_GS_C128, IE_PROF_GIVENS = 2, 3, 4, 5, 6
 
 EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_solve_batch",

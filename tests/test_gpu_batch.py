@@ -17,7 +17,7 @@ def _lib():
     return ie
 
 
-@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-10, 1e-9), (1, 1e-7, 1e-5)])
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-10, 1e-9), (1, 1e-7, 1e-5), (2, 1e-7, 1e-5)])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_batch_solve_against_lu(precision, tol, bound, adjoint):
     """Three frequencies x two polarisations in one lockstep solve; every block

@@ -76,7 +76,7 @@ def test_rhs_mt_matches_oracle(case):
         assert rel(to_host(u0), ref) <= 1e-12
 
 
-@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-10, 1e-9), (1, 1e-7, 1e-5)])
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-10, 1e-9), (1, 1e-7, 1e-5), (2, 1e-7, 1e-5)])
 def test_solve_against_lu(case, precision, tol, bound):
     m, q, A, ctx = case
     g = m.grid
@@ -272,7 +272,7 @@ def test_large_nz_contraction_against_oracle(shape):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-10, 1e-9), (1, 1e-7, 1e-6)])
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-10, 1e-9), (1, 1e-7, 1e-6), (2, 1e-7, 1e-6)])
 def test_solve_weak_contrast_takes_second_projection(precision, tol, bound):
     """A weak anomaly (sigma_a = sigma_b (1 + 1e-6)) makes A = I + O(1e-6): each new
     Krylov vector A v_k is v_k up to a part of relative size ~1e-6, so the first
@@ -303,7 +303,7 @@ def test_solve_weak_contrast_takes_second_projection(precision, tol, bound):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_nan_rhs_is_not_converged(precision):
     """A right-hand side holding a NaN must not come back as a converged solve (a NaN
     residual compares false against every tolerance)."""
