@@ -18,7 +18,8 @@ electromagnetics based on Galerkin method"):
                       of lambda (Appendix C, eq. (transf)).
 * ``static``       -- closed-form box-to-box integrals of 1/r used to take the
                       quasi-static singular part of touching cells out of the
-                      lambda integral (a reading of Appendix C).
+                      lambda integral (a reading of Appendix C, whose filter
+                      output functions are not printed).
 * ``coefficients`` -- the 3x3 blocks B_n^m of Appendix A assembled into the
                       compressed tensor Q(i, j) of eq. (matrix_symm).
 * ``normal``       -- the MT plane-wave normal field E^N and U^0 of (slae_matricies).

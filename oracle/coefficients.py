@@ -19,7 +19,7 @@ For field cell n and source cell m with lateral offset D = (j hx, i hy)
 with the lateral kernels K of ``lateral`` and the vertical integrals V of
 ``layered``.
 
-Readings of the paper used here (listed in the design doc):
+Readings of the paper used here:
 * V3 in Ixx, Iyy, Ixy is the classical derivative: the delta of
   d/dz d/dz* U_sigma at z = z* is excluded, i.e. V3 = V3w + (2/sigma_a) |a cap b|
   with V3w the cell-face (nested-integral) value.  Only then does

@@ -11,7 +11,7 @@ It is built with the recursions (pq_req) for p_m, q_m, the amplitudes (A_rs),
 and evaluated in the overflow-free form (UU2): every exponential is grouped so
 that its exponent has a non-positive real part at the point of evaluation.
 
-Readings (listed in DESIGN.md):
+Readings of the paper used here:
 * (UU2), second branch: the third exponent is read as e^{-(eta_r z_r - eta_s z_s)},
   the mirror of the first branch.
 * (U_explicit), second branch (field point below the source point): the
