@@ -68,6 +68,13 @@ def bf16_peak():
     return 1900.0, "fallback"
 
 
+def workload_desc(name, model):
+    """The workload as the bench line names it (the same string on both arms)."""
+    g = model.grid
+    return (f"{name}: {g.nx}x{g.ny}x{g.nz} cells, {len(model.layers.sigma) - 1} layers + air, "
+            f"{model.freqs[0]} Hz, 2 polarisations, tol {TOL}")
+
+
 def workload(name):
     return {"C1": W.config1, "C2": W.config2, "C4": W.config4, "C5": W.config5}[name]()
 
@@ -209,7 +216,8 @@ def run_reference(args, rank, ws):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": args.workload, "grid": [g.nx, g.ny, g.nz]},
+            "data": "synthetic", "config": {"workload": workload_desc(args.workload, model), "unknowns": n_unk,
+                                            "grid": [g.nx, g.ny, g.nz]},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
                              "sample": "one FP64 GMRES iteration (FFT product + CGS2) of the oracle per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -429,8 +437,7 @@ def run_ours(args, rank, ws):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64 inner GMRES (products, Krylov vectors), c128 refinement residual", "data": "synthetic",
-                "config": {"workload": f"{args.workload}: {g.nx}x{g.ny}x{g.nz} cells, {len(model.layers.sigma) - 1}"
-                                       f" layers + air, {model.freqs[0]} Hz, 2 polarisations, tol {TOL}",
+                "config": {"workload": workload_desc(args.workload, model),
                            "unknowns": n_unk, "rhs": R, "restart": args.restart,
                            "inner_tol": args.inner_tol, "restart_fp64": args.restart_fp64,
                            "l2": "inputs larger than L2 (c64 coefficients %.0f MB)" % (q_bytes / 1e6),
