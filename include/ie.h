@@ -28,6 +28,10 @@
  * Errors.  Every call returns an ie_status; nothing is thrown across the ABI.
  * On IE_ERR_* the outputs are unspecified.  A solve that reaches its iteration
  * cap returns IE_NOT_CONVERGED with info filled and the best iterate in u.
+ * The contraction kernels wait on asynchronous copies with a bounded number of
+ * polls; a wait that runs out is recorded in the context's error word and reported
+ * as IE_ERR_TIMEOUT by the next solve synchronisation (restart or end of a solve) or,
+ * for asynchronous products, by ie_sync (ie_noalloc_sync without a context).
  *
  * Streams.  Calls are ordered on the context's stream (ie_ctx_stream); matvec
  * accepts an explicit stream.  ie_setup and the solves synchronise before they
@@ -51,7 +55,8 @@ typedef enum {
   IE_ERR_COEFF = -3,     /* coefficient tensor missing or inconsistent */
   IE_ERR_OOM = -4,       /* device allocation failed */
   IE_ERR_CUDA = -5,      /* a CUDA call failed */
-  IE_ERR_SCRATCH = -6    /* the problem needs more work space than ie_matvec_noalloc's fixed array */
+  IE_ERR_SCRATCH = -6,   /* the problem needs more work space than ie_matvec_noalloc's fixed array */
+  IE_ERR_TIMEOUT = -7    /* a bounded wait inside a contraction kernel ran out: that product is incomplete */
 } ie_status;
 
 enum { IE_C64 = 0, IE_C128 = 1, IE_C128_DF = 7 };  /* element type of matvec vectors (see ie_matvec) */
@@ -125,7 +130,10 @@ ie_status ie_setup(const ie_grid *grid, const ie_layers *layers, const double *s
  *   diag_dev      : c64 per cell, S = 1 - gamma (may be NULL for y = R1 B R2 x).
  *   x_dev, y_dev  : c64 [nrhs][3][Nz][Ny][Nx], must not alias; nrhs 1..4.
  * The work space needs (6 Nx Ny) * nrhs * 3 Nz * 8 bytes; larger problems return
- * IE_ERR_SCRATCH.  The first call on a device looks up the array's device address
+ * IE_ERR_SCRATCH.  Shapes the contraction cannot stage in shared memory return
+ * IE_ERR_ARG before anything is launched: 3 Nz <= 1024 and 24 Nz (MAXC + 17) <= 227 KiB
+ * with MAXC = 4, 8, 16 for 1, 2, 3..4 right-hand sides (Nz <= 341 for one or two,
+ * Nz <= 293 for three or four).  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call outside any stream capture.  All calls
  * share the array: calls whose kernels overlap on the GPU (two streams, two threads)
  * race on it and must be serialised by the caller.  Nothing in the array needs to
@@ -134,6 +142,11 @@ ie_status ie_setup(const ie_grid *grid, const ie_layers *layers, const double *s
 ie_status ie_matvec_noalloc(int nx, int ny, int nz, int nrhs, const void *qf_dev, const void *in_scale_dev,
                             const void *out_scale_dev, const void *diag_dev, const void *x_dev, void *y_dev,
                             void *stream);
+
+/* Wait for stream (a cudaStream_t, NULL for the legacy default stream) and report
+ * whether a contraction launched by ie_matvec_noalloc since the last call ran out of a
+ * bounded wait (IE_ERR_TIMEOUT; the word is cleared) or not (IE_OK).  No allocation. */
+ie_status ie_noalloc_sync(void *stream);
 
 /* Generate the compressed real-space coefficient tensor of one frequency on the device
  * (Appendices A-C): the vertical integrals (Ver_Int) of the layered-medium fundamental
@@ -153,9 +166,22 @@ ie_status ie_generate_coefficients(const ie_grid *grid, const ie_layers *layers,
  * double-float arithmetic on the FP32 pipe, as in the residuals of the mixed-precision
  * solver: about twice-FP32 accuracy, no counterpart in the paper).
  * x_dev, y_dev: device arrays [nrhs][3][Nz][Ny][Nx] of that type; they must not
- * alias.  stream: a cudaStream_t, or NULL for the context stream.  Asynchronous. */
+ * alias.  stream: a cudaStream_t, or NULL for the context stream.  Asynchronous: a
+ * contraction wait that ran out is reported by ie_sync. */
 ie_status ie_matvec(ie_ctx *ctx, int inst, const void *x_dev, void *y_dev, int nrhs, int dtype, int transpose,
                     void *stream);
+
+/* Wait for stream (NULL: the context stream) and return IE_ERR_TIMEOUT if a
+ * contraction of this context ran out of a bounded wait since the last check (the
+ * error word is then cleared), IE_OK otherwise. */
+ie_status ie_sync(ie_ctx *ctx, void *stream);
+
+/* In-cell electric field E_n = U_n / a_n, a_n = (sigma_a^n + conj sigma_b^n) / (2 s_n),
+ * s_n = sqrt(Re sigma_b^n): the change of variables of eq. (iEH320op) undone for nrhs
+ * solutions U (u_dev) into e_dev, both device c128 [nrhs][3][Nz][Ny][Nx] (they may be
+ * the same array).  nrhs <= max_rhs.  stream: a cudaStream_t or NULL for the context
+ * stream.  Asynchronous. */
+ie_status ie_fields(ie_ctx *ctx, const void *u_dev, void *e_dev, int nrhs, void *stream);
 
 /* Solve A u = b for instance inst (Sect. 3.3 (ii): restarted GMRES; classical
  * Gram-Schmidt with a second projection wherever the first one cancels more than
@@ -283,6 +309,13 @@ ie_status ie_profile_matvec(ie_ctx *ctx, int inst, int nrhs, int dtype, int n_it
 
 /* Number of kernels the library has launched in this process (all contexts). */
 long long ie_kernel_launches(void);
+
+/* Testing aid (no counterpart in the paper): the number of polls after which the main
+ * waits of every contraction launched afterwards give up (a negative value restores the
+ * default, 2^28).  0 makes every such wait give up at once, so that the IE_ERR_TIMEOUT
+ * path can be exercised without a GPU fault; each kernel still drains its own copies in
+ * flight with the default limit before it returns. */
+void ie_debug_set_wait_limit(long long polls);
 
 void ie_destroy(ie_ctx *ctx);
 const char *ie_status_str(ie_status s);

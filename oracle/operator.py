@@ -39,6 +39,19 @@ def diagonals(model):
     return gamma, s, V
 
 
+def in_cell_field(model, U):
+    """E_n = U_n / a_n with a_n = (sigma_a^n + conj sigma_b^n) / (2 s_n): the change of
+    variables under eq. (iEH320op) undone.  U: [R][3][Nz][Ny][Nx] or [3][Nz][Ny][Nx].
+    Pinned by sigma_a = sigma_b (E = the cell average of the normal field) and by the
+    scattering current (sigma_a - sigma_b) E = 2 s gamma U of eq. (APR_lab) (tests)."""
+    g = model.grid
+    sb = background_sigma(g, model.layers)
+    sa = np.asarray(model.sigma_a, dtype=np.complex128)
+    s = np.sqrt(sb.real)
+    a = (sa + np.conj(sb)[:, None, None]) / (2.0 * s[:, None, None])
+    return np.asarray(U) / a
+
+
 def dense_B(model, q_all):
     """Brute-force 3N x 3N matrix of the blocks B_n^m from their values at every signed
     offset (q_all as returned by coefficients.all_offsets; no symmetry is used)."""

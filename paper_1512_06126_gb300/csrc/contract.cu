@@ -134,7 +134,18 @@ int launch_t(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz,
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Error word of the launches that are given none (ie_matvec_noalloc, the autotuner).
 __device__ int g_contract_err = 0;
+long long g_wait_limit = kWaitLimit;
+
+int *default_err() {
+  int *err = nullptr;
+  if (cudaGetSymbolAddress((void **)&err, g_contract_err) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return err;
+}
 
 int num_sms() {
   static int n = 0;
@@ -148,7 +159,7 @@ int num_sms() {
 }
 
 template <int NZ, int R, int NS, int RPT>
-bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int per_sm, cudaStream_t s) {
+bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int per_sm, int *err, cudaStream_t s) {
   using Cfg = ContractCfg<NZ, R, NS, RPT>;
   if (Cfg::SMEM > 227 * 1024) return false;
   auto k = contract_tma_kernel<NZ, R, NS, RPT>;
@@ -156,13 +167,11 @@ bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int per_sm
     cudaGetLastError();
     return false;
   }
-  int *err = nullptr;
-  cudaGetSymbolAddress((void **)&err, g_contract_err);
   const int nf = (Nx + 1) * (Ny + 1);
   const int want = per_sm * num_sms();
   const int grid = nf < want ? nf : want;
   count_launches(1);
-  k<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(spec, qf, Nx, Ny, ldz, err);
+  k<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(spec, qf, Nx, Ny, ldz, err, g_wait_limit);
   if (cudaPeekAtLastError() != cudaSuccess) {  // not launched: the caller falls back to the panel kernel
     cudaGetLastError();
     return false;
@@ -174,18 +183,20 @@ bool try_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int per_sm
 // wavenumber overlaps the arithmetic of the current one, and the other CTA on the SM
 // covers the unpacking phase), or three slots and one CTA per SM.
 template <int NZ, int R>
-bool try_tma_variant(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int variant, cudaStream_t s) {
+bool try_tma_variant(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int variant, int *err,
+                     cudaStream_t s) {
   constexpr int RPT2 = R == 2 ? 2 : 1;
   if (variant == kContractTma1) {
     if (2 * ContractCfg<NZ, R, 1, RPT2>::SMEM <= 227 * 1024)
-      return try_tma<NZ, R, 1, RPT2>(spec, qf, Nx, Ny, ldz, 2, s);
-    return try_tma<NZ, R, 1, RPT2>(spec, qf, Nx, Ny, ldz, 1, s);
+      return try_tma<NZ, R, 1, RPT2>(spec, qf, Nx, Ny, ldz, 2, err, s);
+    return try_tma<NZ, R, 1, RPT2>(spec, qf, Nx, Ny, ldz, 1, err, s);
   }
   if (variant == kContractTma1Row) {
-    if (2 * ContractCfg<NZ, R, 1, 1>::SMEM <= 227 * 1024) return try_tma<NZ, R, 1, 1>(spec, qf, Nx, Ny, ldz, 2, s);
-    return try_tma<NZ, R, 1, 1>(spec, qf, Nx, Ny, ldz, 1, s);
+    if (2 * ContractCfg<NZ, R, 1, 1>::SMEM <= 227 * 1024)
+      return try_tma<NZ, R, 1, 1>(spec, qf, Nx, Ny, ldz, 2, err, s);
+    return try_tma<NZ, R, 1, 1>(spec, qf, Nx, Ny, ldz, 1, err, s);
   }
-  if (variant == kContractTma3) return try_tma<NZ, R, 3, RPT2>(spec, qf, Nx, Ny, ldz, 1, s);
+  if (variant == kContractTma3) return try_tma<NZ, R, 3, RPT2>(spec, qf, Nx, Ny, ldz, 1, err, s);
   return false;
 }
 
@@ -193,7 +204,7 @@ bool try_tma_variant(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, in
 // shared memory allow).
 template <typename K>
 bool launch_persistent(K k, int threads, size_t smem, int *per_sm, float2 *spec, const float2 *qf, int Nx, int Ny,
-                       int ldz, cudaStream_t s) {
+                       int ldz, int *err, cudaStream_t s) {
   if (smem > 227 * 1024) return false;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
@@ -205,13 +216,11 @@ bool launch_persistent(K k, int threads, size_t smem, int *per_sm, float2 *spec,
       *per_sm = 1;
     }
   }
-  int *err = nullptr;
-  cudaGetSymbolAddress((void **)&err, g_contract_err);
   const int nf = (Nx + 1) * (Ny + 1);
   const int want = *per_sm * num_sms();
   const int grid = nf < want ? nf : want;
   count_launches(1);
-  k<<<grid, threads, smem, s>>>(spec, qf, Nx, Ny, ldz, err);
+  k<<<grid, threads, smem, s>>>(spec, qf, Nx, Ny, ldz, err, g_wait_limit);
   if (cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -220,35 +229,38 @@ bool launch_persistent(K k, int threads, size_t smem, int *per_sm, float2 *spec,
 }
 
 template <int NZ, int R>
-bool try_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, bool unpack, cudaStream_t s) {
+bool try_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, bool unpack, int *err, cudaStream_t s) {
   if (unpack) {
     static int per_sm = 0;
     using Cfg = MmaUnpackCfg<NZ, R>;
     return launch_persistent(contract_mma_unpack_kernel<NZ, R>, Cfg::THREADS, Cfg::SMEM, &per_sm, spec, qf, Nx, Ny,
-                             ldz, s);
+                             ldz, err, s);
   }
   static int per_sm = 0;
   using Cfg = MmaCfg<NZ, R, 2>;
-  return launch_persistent(contract_mma_kernel<NZ, R, 2>, Cfg::THREADS, Cfg::SMEM, &per_sm, spec, qf, Nx, Ny, ldz, s);
+  return launch_persistent(contract_mma_kernel<NZ, R, 2>, Cfg::THREADS, Cfg::SMEM, &per_sm, spec, qf, Nx, Ny, ldz,
+                           err, s);
 }
 
 template <int R>
-bool dispatch_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, bool unpack, cudaStream_t s) {
+bool dispatch_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, bool unpack, int *err,
+                  cudaStream_t s) {
   switch (Nz) {
-    case 16: return try_mma<16, R>(spec, qf, Nx, Ny, ldz, unpack, s);
-    case 32: return try_mma<32, R>(spec, qf, Nx, Ny, ldz, unpack, s);
-    case 48: return try_mma<48, R>(spec, qf, Nx, Ny, ldz, unpack, s);
+    case 16: return try_mma<16, R>(spec, qf, Nx, Ny, ldz, unpack, err, s);
+    case 32: return try_mma<32, R>(spec, qf, Nx, Ny, ldz, unpack, err, s);
+    case 48: return try_mma<48, R>(spec, qf, Nx, Ny, ldz, unpack, err, s);
     default: return false;
   }
 }
 
 template <int R>
-bool dispatch_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, int variant, cudaStream_t s) {
+bool dispatch_tma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, int variant, int *err,
+                  cudaStream_t s) {
   switch (Nz) {
-    case 16: return try_tma_variant<16, R>(spec, qf, Nx, Ny, ldz, variant, s);
-    case 24: return try_tma_variant<24, R>(spec, qf, Nx, Ny, ldz, variant, s);
-    case 32: return try_tma_variant<32, R>(spec, qf, Nx, Ny, ldz, variant, s);
-    case 48: return try_tma_variant<48, R>(spec, qf, Nx, Ny, ldz, variant, s);
+    case 16: return try_tma_variant<16, R>(spec, qf, Nx, Ny, ldz, variant, err, s);
+    case 24: return try_tma_variant<24, R>(spec, qf, Nx, Ny, ldz, variant, err, s);
+    case 32: return try_tma_variant<32, R>(spec, qf, Nx, Ny, ldz, variant, err, s);
+    case 48: return try_tma_variant<48, R>(spec, qf, Nx, Ny, ldz, variant, err, s);
     default: return false;
   }
 }
@@ -260,11 +272,26 @@ bool tma3_fits() { return ContractCfg<NZ, R, 3, (R == 2 ? 2 : 1)>::SMEM <= 227 *
 
 bool contract_tma_enabled = true;
 
-int contract_take_error() {
-  int h = 0, z = 0;
-  cudaMemcpyFromSymbol(&h, g_contract_err, sizeof(int));
-  if (h) cudaMemcpyToSymbol(g_contract_err, &z, sizeof(int));
+int contract_take_error(int *err, cudaStream_t s) {
+  if (!err) err = default_err();
+  if (!err) return -1;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -1;
+  if (h && (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess))
+    return -1;
   return h;
+}
+
+void set_wait_limit(long long polls) { g_wait_limit = polls >= 0 ? polls : kWaitLimit; }
+
+bool contract_fits(int Nz, int R, bool c64) {
+  if (Nz < 1 || R < 1 || R > 4 || 3 * Nz > 1024) return false;
+  const size_t e = c64 ? sizeof(float2) : sizeof(double2);
+  const size_t maxc = R <= 1 ? 4 : (R <= 2 ? 8 : 16);
+  // launch_t with its narrowest panel (16 columns)
+  return e * (size_t)3 * Nz * (maxc + 17) <= kMaxSmem;
 }
 
 bool contract_variant_available(int variant, int Nz, int R, bool c64) {
@@ -286,22 +313,24 @@ bool contract_variant_available(int variant, int Nz, int R, bool c64) {
 }
 
 template <typename T>
-int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant,
+int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant, int *err,
                     cudaStream_t s) {
   if (ldz < R * 3 * Nz) return -1;
   if constexpr (sizeof(T) == 4) {
+    if (!err) err = default_err();
+    if (!err) return -1;
     if (variant == kContractAuto) variant = contract_variant_available(kContractTma1, Nz, R, true) ? kContractTma1
                                                                                                     : kContractPanel;
     if ((variant == kContractMma || variant == kContractMmaUnpack) &&
         contract_variant_available(variant, Nz, R, true)) {
       const bool unpack = variant == kContractMmaUnpack;
-      if (R == 1 && dispatch_mma<1>(spec, qf, Nx, Ny, Nz, ldz, unpack, s)) return 0;
-      if (R == 2 && dispatch_mma<2>(spec, qf, Nx, Ny, Nz, ldz, unpack, s)) return 0;
+      if (R == 1 && dispatch_mma<1>(spec, qf, Nx, Ny, Nz, ldz, unpack, err, s)) return 0;
+      if (R == 2 && dispatch_mma<2>(spec, qf, Nx, Ny, Nz, ldz, unpack, err, s)) return 0;
     }
     if ((variant == kContractTma1 || variant == kContractTma3 || variant == kContractTma1Row) &&
         contract_variant_available(variant, Nz, R, true)) {
-      if (R == 1 && dispatch_tma<1>(spec, qf, Nx, Ny, Nz, ldz, variant, s)) return 0;
-      if (R == 2 && dispatch_tma<2>(spec, qf, Nx, Ny, Nz, ldz, variant, s)) return 0;
+      if (R == 1 && dispatch_tma<1>(spec, qf, Nx, Ny, Nz, ldz, variant, err, s)) return 0;
+      if (R == 2 && dispatch_tma<2>(spec, qf, Nx, Ny, Nz, ldz, variant, err, s)) return 0;
     }
   }
   if (R <= 1) return launch_t<T, 4>(spec, qf, Nx, Ny, Nz, R, ldz, s);
@@ -310,7 +339,7 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, i
   return -1;
 }
 
-template int launch_contract<float>(float2 *, const float2 *, int, int, int, int, int, int, cudaStream_t);
-template int launch_contract<double>(double2 *, const double2 *, int, int, int, int, int, int, cudaStream_t);
+template int launch_contract<float>(float2 *, const float2 *, int, int, int, int, int, int, int *, cudaStream_t);
+template int launch_contract<double>(double2 *, const double2 *, int, int, int, int, int, int, int *, cudaStream_t);
 
 }  // namespace ie

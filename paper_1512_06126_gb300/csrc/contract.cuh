@@ -16,14 +16,19 @@ enum ContractVariant {
 };
 constexpr int kContractVariants = 6;
 bool contract_variant_available(int variant, int Nz, int R, bool c64);
+// Whether the panel kernel, the fallback of every variant, can stage a contraction of
+// Nz layers and R right-hand sides (c64 or c128) in shared memory.
+bool contract_fits(int Nz, int R, bool c64);
 
 // Apply the folded spectral blocks in place to the R right-hand sides whose spectrum
 // vectors are spec[(ky 2Nx + kx) ldz + 0 .. R 3Nz) (ldz >= R 3Nz).  variant: one of
 // ContractVariant (kContractAuto: the TMA ring where it applies, else the panel kernel;
 // an unavailable variant falls back to the panel kernel).  Returns -1 if R > 4,
 // 3 Nz > 1024, ldz < R 3Nz or a launch fails (nothing is applied then).
+// err: device word in which a kernel records a wait that ran out (kContractTimeout; the
+// wavenumbers it had not reached stay uncontracted); NULL: the library's own word.
 template <typename T>
-int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant,
+int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant, int *err,
                     cudaStream_t s);
 
 // Double-float copy of packed blocks: qdf[i] = (hi, lo of re, hi, lo of im) of q64[i],
@@ -36,7 +41,11 @@ int launch_contract_df(double2 *spec, const float4 *qdf, int Nx, int Ny, int Nz,
 
 // Use the TMA-pipelined kernel where it applies (c64, Nz in {16, 24, 32, 48}, R <= 2).
 extern bool contract_tma_enabled;
-// Error code recorded by a contraction kernel since the last call (0: none); resets it.
-int contract_take_error();
+// Error code recorded in err (NULL: the library's own word) by a contraction kernel
+// since the last call (0: none; -1 if it cannot be read); waits for stream s, resets it.
+int contract_take_error(int *err, cudaStream_t s);
+// Polls of the main waits of every contraction launched afterwards (< 0: the default;
+// 0: every main wait gives up without polling, which tests the error path).
+void set_wait_limit(long long polls);
 
 }  // namespace ie

@@ -131,7 +131,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 template <int NZ, int R, int NSTAGE>
 __global__ void __launch_bounds__(MmaCfg<NZ, R, NSTAGE>::THREADS, MmaCfg<NZ, R, NSTAGE>::MINB)
-    contract_mma_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err) {
+    contract_mma_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err,
+                        long long lim) {
   using Cfg = MmaCfg<NZ, R, NSTAGE>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LDF = Cfg::LDF, LDX = Cfg::LDX;
   constexpr int SLOT = Cfg::SLOT, OFF_F = Cfg::OFF_F, OFF_X = Cfg::OFF_X;
@@ -185,12 +186,17 @@ __global__ void __launch_bounds__(MmaCfg<NZ, R, NSTAGE>::THREADS, MmaCfg<NZ, R, 
     int it = 0;
     for (int w = w0; w < nf; w += gridDim.x, ++it) {
       const int s = it % NSTAGE;
-      if (it >= NSTAGE && !tma::mbar_wait_bounded(&empty[s], (uint32_t)((it / NSTAGE - 1) & 1), kWaitLimit)) {
+      if (it >= NSTAGE && !tma::mbar_wait_bounded(&empty[s], (uint32_t)((it / NSTAGE - 1) & 1), lim)) {
         if (lane == 0) atomicExch(err, kContractTimeout);
         break;
       }
       issue(w, s);
     }
+    // drain: the copies of the last NSTAGE issues must land before the CTA exits, even
+    // where the compute warps gave up on them
+    const int n_issued = it;
+    for (int k = n_issued - NSTAGE > 0 ? n_issued - NSTAGE : 0; k < n_issued; ++k)
+      tma::mbar_wait_bounded(&full[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1), kWaitLimit);
     return;
   }
 
@@ -206,9 +212,9 @@ __global__ void __launch_bounds__(MmaCfg<NZ, R, NSTAGE>::THREADS, MmaCfg<NZ, R, 
   for (int w = w0; w < nf; w += gridDim.x, ++it) {
     const int s = it % NSTAGE;
     const uint32_t phase = (uint32_t)((it / NSTAGE) & 1);
-    if (!tma::mbar_wait_bounded(&full[s], phase, kWaitLimit)) {
+    if (!tma::mbar_wait_bounded(&full[s], phase, lim)) {
+      // the producer warp drains the copies it issued before the CTA exits
       if (lane == 0) atomicExch(err, kContractTimeout);
-      for (int k = 0; k < NSTAGE; ++k) tma::mbar_wait_bounded(&full[(s + k) % NSTAGE], phase, kWaitLimit);
       return;
     }
     const Mirrors mw = mirrors_of(w, Nx, Ny);
@@ -333,7 +339,7 @@ struct MmaUnpackCfg {
 template <int NZ, int R>
 __global__ void __launch_bounds__(MmaUnpackCfg<NZ, R>::THREADS)
     contract_mma_unpack_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz,
-                               int *err) {
+                               int *err, long long lim) {
   using Cfg = MmaUnpackCfg<NZ, R>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LD = Cfg::LD;
   constexpr int THREADS = Cfg::THREADS;
@@ -392,8 +398,9 @@ __global__ void __launch_bounds__(MmaUnpackCfg<NZ, R>::THREADS)
 
   int it = 0;
   for (int w = w0; w < nf; w += gridDim.x, ++it) {
-    if (!tma::mbar_wait_bounded(&bar[0], (uint32_t)(it & 1), kWaitLimit)) {
+    if (!tma::mbar_wait_bounded(&bar[0], (uint32_t)(it & 1), lim)) {
       if (tid == 0) atomicExch(err, kContractTimeout);
+      // drain the one copy in flight
       tma::mbar_wait_bounded(&bar[0], (uint32_t)(it & 1), kWaitLimit);
       return;
     }

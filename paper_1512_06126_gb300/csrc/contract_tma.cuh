@@ -73,7 +73,11 @@ __device__ __forceinline__ float2 upk(unsigned long long v) {
   return make_float2(__uint_as_float((unsigned)(v & 0xffffffffu)), __uint_as_float((unsigned)(v >> 32)));
 }
 
-constexpr long long kWaitLimit = 1LL << 28;  // polls before a wait is declared failed
+// Polls before a wait is declared failed.  The main waits of a kernel take their limit
+// as an argument (normally kWaitLimit; a test may lower it to make a wait run out);
+// the drain after a timeout, which only waits for the CTA's own copies in flight,
+// always uses kWaitLimit.
+constexpr long long kWaitLimit = 1LL << 28;
 enum ContractError { kContractOk = 0, kContractTimeout = 1 };
 
 template <int NZ, int R, int NSTAGE, int RPT_ = (R == 2 ? 2 : 1)>
@@ -129,7 +133,8 @@ __device__ __forceinline__ Mirrors mirrors_of(int w, int Nx, int Ny) {
 
 template <int NZ, int R, int NSTAGE, int RPT_>
 __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE, RPT_>::THREADS)
-    contract_tma_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err) {
+    contract_tma_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err,
+                        long long lim) {
   using Cfg = ContractCfg<NZ, R, NSTAGE, RPT_>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LD = Cfg::LD, MAXC = Cfg::MAXC;
   constexpr int XLD = Cfg::XLD;
@@ -211,10 +216,13 @@ __global__ void __launch_bounds__(ContractCfg<NZ, R, NSTAGE, RPT_>::THREADS)
   for (int w = w0; w < nf; w += gridDim.x, ++it) {
     const int s = it % NSTAGE;
     const uint32_t phase = (uint32_t)((it / NSTAGE) & 1);
-    if (!tma::mbar_wait_bounded(&bar[s], phase, kWaitLimit)) {
+    if (!tma::mbar_wait_bounded(&bar[s], phase, lim)) {
       if (tid == 0) atomicExch(err, kContractTimeout);
-      // drain: wait (bounded) for every slot that may still have copies in flight
-      for (int k = 0; k < NSTAGE; ++k) tma::mbar_wait_bounded(&bar[(s + k) % NSTAGE], phase, kWaitLimit);
+      // drain: the slots hold the copies of iterations it .. it + NSTAGE - 1 (those that
+      // were issued), each completing the phase of its own iteration
+      for (int k = 0; k < NSTAGE; ++k)
+        if (w + k * (int)gridDim.x < nf)
+          tma::mbar_wait_bounded(&bar[(s + k) % NSTAGE], (uint32_t)(((it + k) / NSTAGE) & 1), kWaitLimit);
       return;
     }
     const Mirrors mw = mirrors_of(w, Nx, Ny);

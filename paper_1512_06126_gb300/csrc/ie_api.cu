@@ -73,9 +73,12 @@ struct ie_ctx {
   double *nrmpart = nullptr, *nrm = nullptr;
   int *gsflag = nullptr;                       // 48 ints: second-projection flags, reduction tickets, a counter
   ie::GivensState gst{};                       // device least-squares state of GMRES
-  int *pin_active = nullptr;                   // pinned: active counts (slot 0: cycle start, 1..4: iterations)
+  int *pin_active = nullptr;                   // pinned: active counts (slot 0: cycle start, 1..4: iterations),
+                                               // slot 5: the contraction error word
+  int *err = nullptr;                          // device: contraction error word of this context's launches
   cudaEvent_t pin_ev[4] = {};
   void *jfac = nullptr, *gdiv = nullptr;       // per cell: 2 s gamma; (dgamma/dln sigma_a) / gamma (0 off the anomaly)
+  void *efac = nullptr;                        // per cell: 1 / a = 2 s / (sigma_a + conj sigma_b) (E = U / a)
   int n_rec = 0;                               // receivers (ie_set_receivers)
   int *rec_ix = nullptr, *rec_iy = nullptr;
   double z_rec = 0.0;
@@ -145,7 +148,7 @@ ie_status upload_cplx(ie_ctx *c, const std::vector<cd> &h, void **dst) {
 ie_status build_diagonals(ie_ctx *c) {
   const long long N = c->ncell();
   const double norm = 1.0 / (4.0 * c->nx * c->ny);
-  std::vector<cd> in_f(N), out_f(N), diag(N), in_t(N), out_t(N), jfac(N), gdiv(N);
+  std::vector<cd> in_f(N), out_f(N), diag(N), in_t(N), out_t(N), jfac(N), gdiv(N), efac(N);
   for (int z = 0; z < c->nz; ++z) {
     const cd sb = c->sig[c->lay[z]];
     const double s = std::sqrt(sb.real());
@@ -160,6 +163,7 @@ ie_status build_diagonals(ie_ctx *c) {
       in_t[i] = -2.0 * s / V;
       out_t[i] = s * g * norm;
       jfac[i] = 2.0 * s * g;
+      efac[i] = 2.0 * s / (sa + std::conj(sb));
       // dgamma/dln(sigma_a) = sigma_a 2 Re(sigma_b) / (sigma_a + conj sigma_b)^2, divided by gamma
       const cd den = sa + std::conj(sb);
       gdiv[i] = g == 0.0 ? cd(0.0) : sa * 2.0 * sb.real() / (den * den) / g;
@@ -177,6 +181,7 @@ ie_status build_diagonals(ie_ctx *c) {
   IE_TRY(upload_cplx<float>(c, out_t, &c->d32.out_t));
   IE_TRY(upload_cplx<double>(c, jfac, &c->jfac));
   IE_TRY(upload_cplx<double>(c, gdiv, &c->gdiv));
+  IE_TRY(upload_cplx<double>(c, efac, &c->efac));
   return IE_OK;
 }
 
@@ -312,7 +317,8 @@ ie_status contract_group(ie_ctx *c, const Group &g, ie::C<T> *spec, cudaStream_t
     if constexpr (sizeof(T) == 8) {
       if (df && ie::launch_contract_df(sk, c->inst[g.inst[k]].qdf, c->nx, c->ny, c->nz, g.rpi, CZ, s) == 0) continue;
     }
-    if (ie::launch_contract<T>(sk, qf<T>(c->inst[g.inst[k]]), c->nx, c->ny, c->nz, g.rpi, CZ, variant, s) != 0)
+    if (ie::launch_contract<T>(sk, qf<T>(c->inst[g.inst[k]]), c->nx, c->ny, c->nz, g.rpi, CZ, variant, c->err, s) !=
+        0)
       return IE_ERR_CUDA;
   }
   if (c->prof) {
@@ -408,6 +414,23 @@ struct ProfSpan {
 
 constexpr int kGivensLag = 2;   // iterations between issuing a Givens step and reading its count
 constexpr int kPinSlots = 4;
+constexpr int kPinErr = 1 + kPinSlots;  // pinned slot of the contraction error word
+
+// Queue a copy of the contraction error word into its pinned slot (read after the
+// caller's next synchronisation).
+ie_status queue_err_read(ie_ctx *c, cudaStream_t s) {
+  IE_CUDA(cudaMemcpyAsync(c->pin_active + kPinErr, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return IE_OK;
+}
+// After that synchronisation: IE_ERR_TIMEOUT (and the word cleared) if a contraction
+// kernel recorded a wait that ran out, whose product is then incomplete.
+ie_status take_err(ie_ctx *c, cudaStream_t s) {
+  if (c->pin_active[kPinErr] == 0) return IE_OK;
+  c->pin_active[kPinErr] = 0;
+  IE_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), s));
+  IE_CUDA(cudaStreamSynchronize(s));
+  return IE_ERR_TIMEOUT;
+}
 
 struct GmresResult {
   int iters = 0;
@@ -492,7 +515,9 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
     ie::givens_init(st, c->nrm, R, ldh, s);
     IE_CUDA(cudaMemcpyAsync(c->pin_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (compact) IE_CUDA(cudaMemcpyAsync(act.data(), st.active, R * sizeof(int), cudaMemcpyDeviceToHost, s));
+    IE_TRY(queue_err_read(c, s));
     IE_CUDA(cudaStreamSynchronize(s));
+    IE_TRY(take_err(c, s));
     if (pending) {
       int kmx = 0;
       for (int r = 0; r < R_prev; ++r) {
@@ -580,7 +605,9 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
     IE_CUDA(cudaGetLastError());
   }
   if (pending) {  // only reached when the loop left before the next synchronisation
+    IE_TRY(queue_err_read(c, s));
     IE_CUDA(cudaStreamSynchronize(s));
+    IE_TRY(take_err(c, s));
     int kmx = 0;
     for (int r = 0; r < R_prev; ++r) {
       kmx = std::max(kmx, kr[r]);
@@ -614,7 +641,9 @@ ie_status true_residual(ie_ctx *c, const Group &g, int transpose, const double2 
   IE_CUDA(cudaMemcpyAsync(rn.data(), c->nrm, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   ie::gmres_norm<double>(b, c->nrmpart, c->nrm + R, R, n, c->stream);
   IE_CUDA(cudaMemcpyAsync(bn.data(), c->nrm + R, R * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  IE_TRY(queue_err_read(c, c->stream));
   IE_CUDA(cudaStreamSynchronize(c->stream));
+  IE_TRY(take_err(c, c->stream));
   rel.resize(R);
   for (int r = 0; r < R; ++r) rel[r] = bn[r] > 0 ? rn[r] / bn[r] : rn[r];
   return IE_OK;
@@ -727,7 +756,10 @@ ie_status solve_impl(ie_ctx *c, const Group &g, const double2 *b, double2 *u, do
   double worst = 0;
   for (double v : rel) worst = std::isfinite(v) ? std::max(worst, v) : std::numeric_limits<double>::infinity();
   inf.final_rel_res = worst;
-  IE_CUDA(cudaMemcpy(&inf.reorth, c->gsflag + 32, sizeof(int), cudaMemcpyDeviceToHost));
+  IE_CUDA(cudaMemcpyAsync(&inf.reorth, c->gsflag + 32, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  IE_TRY(queue_err_read(c, c->stream));
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  IE_TRY(take_err(c, c->stream));
   inf.t_solve = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;
   if (worst <= tol) return IE_OK;
@@ -798,6 +830,7 @@ const char *ie_status_str(ie_status s) {
     case IE_ERR_OOM: return "out of device memory";
     case IE_ERR_CUDA: return "CUDA error";
     case IE_ERR_SCRATCH: return "problem larger than the fixed work space of ie_matvec_noalloc";
+    case IE_ERR_TIMEOUT: return "a wait inside a contraction kernel ran out; the product is incomplete";
   }
   return "unknown status";
 }
@@ -888,7 +921,7 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
       cudaEventRecord(ev[1], s);
       ie::launch_fft_axis<double, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0, s);
       cudaEventRecord(ev[2], s);
-      bad |= ie::launch_contract<double>(sp, c->inst[inst].q64, Nx, Ny, Nz, nrhs, CZ, ie::kContractPanel, s);
+      bad |= ie::launch_contract<double>(sp, c->inst[inst].q64, Nx, Ny, Nz, nrhs, CZ, ie::kContractPanel, c->err, s);
       cudaEventRecord(ev[3], s);
       ie::launch_fft_axis<double, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0, s);
       cudaEventRecord(ev[4], s);
@@ -903,7 +936,7 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
       cudaEventRecord(ev[1], s);
       ie::launch_fft_axis<float, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[2], s);
-      bad |= ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, CZ, c->cvar[nrhs], s);
+      bad |= ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, CZ, c->cvar[nrhs], c->err, s);
       cudaEventRecord(ev[3], s);
       ie::launch_fft_axis<float, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[4], s);
@@ -921,7 +954,9 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
   for (auto &e : ev) cudaEventDestroy(e);
   for (int k = 0; k < 5; ++k) ms_out[k] = acc[k] / n_iter;
   const ie_status st = cuda_status(cudaGetLastError());
-  return bad ? IE_ERR_CUDA : st;
+  if (bad) return IE_ERR_CUDA;
+  if (st == IE_OK && ie::contract_take_error(c->err, s) != 0) return IE_ERR_TIMEOUT;
+  return st;
 }
 long long ie_ctx_device_bytes(ie_ctx *c) { return c ? c->dev_bytes : 0; }
 
@@ -946,15 +981,15 @@ ie_status autotune_contraction(ie_ctx *c) {
       if (ie::contract_variant_available(v, Nz, rpi, true)) ++n_avail;
     for (int v = 0; v < ie::kContractVariants && n_avail > 1; ++v) {
       if (!ie::contract_variant_available(v, Nz, rpi, true)) continue;
-      bool ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->stream) == 0;
+      bool ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream) == 0;
       cudaEventRecord(e0, c->stream);
       for (int k = 0; k < 3 && ok; ++k)
-        ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->stream) == 0;
+        ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream) == 0;
       cudaEventRecord(e1, c->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) { st = IE_ERR_CUDA; break; }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (!ok || ie::contract_take_error() != 0) continue;
+      if (!ok || ie::contract_take_error(c->err, c->stream) != 0) continue;
       c->tune_ms[rpi][v] = ms / 3.0;
       if (ms / 3.0 < best_ms) { best_ms = ms / 3.0; best = v; }
     }
@@ -999,6 +1034,8 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
     if (opt->autotune < 0) c->autotune = false;
   }
   if (c->restart < 2) return IE_ERR_ARG;
+  // every product of up to four right-hand sides must fit the panel contraction (c128)
+  if (!ie::contract_fits(c->nz, std::min(4, max_rhs), false)) return IE_ERR_ARG;
   try {
     c->px = ie::make_plan(2 * c->nx);
     c->py = ie::make_plan(2 * c->ny);
@@ -1044,7 +1081,10 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
     IE_TRY(dalloc(c, &c->gst.kr, (size_t)max_rhs * sizeof(int)));
     IE_TRY(dalloc(c, &c->gst.brk, (size_t)max_rhs * sizeof(int)));
     IE_TRY(dalloc(c, &c->gst.n_active, sizeof(int)));
-    IE_CUDA(cudaHostAlloc((void **)&c->pin_active, (1 + kPinSlots) * sizeof(int), cudaHostAllocDefault));
+    IE_CUDA(cudaHostAlloc((void **)&c->pin_active, (2 + kPinSlots) * sizeof(int), cudaHostAllocDefault));
+    for (int k = 0; k < 2 + kPinSlots; ++k) c->pin_active[k] = 0;
+    IE_TRY(dalloc(c, &c->err, sizeof(int)));
+    IE_CUDA(cudaMemset(c->err, 0, sizeof(int)));
     for (int k = 0; k < kPinSlots; ++k) IE_CUDA(cudaEventCreateWithFlags(&c->pin_ev[k], cudaEventDisableTiming));
   }
   IE_CUDA(cudaStreamSynchronize(c->stream));
@@ -1084,6 +1124,17 @@ ie_status ie_matvec(ie_ctx *c, int inst, const void *x, void *y, int nrhs, int d
   if (dtype == IE_C64) return apply<float>(c, g, (const float2 *)x, (float2 *)y, transpose, s);
   return IE_ERR_ARG;
 }
+
+ie_status ie_sync(ie_ctx *c, void *stream) {
+  if (!c) return IE_ERR_ARG;
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+  IE_CUDA(cudaStreamSynchronize(s));
+  const int e = ie::contract_take_error(c->err, s);
+  if (e < 0) return IE_ERR_CUDA;
+  return e ? IE_ERR_TIMEOUT : IE_OK;
+}
+
+void ie_debug_set_wait_limit(long long polls) { ie::set_wait_limit(polls); }
 
 ie_status ie_solve(ie_ctx *c, int inst, const void *b, void *u, int nrhs, double tol, int precision, int use_x0,
                    ie_solve_info *info) {
@@ -1234,6 +1285,13 @@ ie_status ie_gradient_accumulate(ie_ctx *c, const void *u_dev, const void *w_dev
   IE_CUDA(cudaGetLastError());
   IE_CUDA(cudaStreamSynchronize(c->stream));
   return IE_OK;
+}
+
+ie_status ie_fields(ie_ctx *c, const void *u_dev, void *e_dev, int nrhs, void *stream) {
+  if (!c || !u_dev || !e_dev || nrhs < 1 || nrhs > c->max_rhs) return IE_ERR_ARG;
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+  ie::launch_cell_scale((const double2 *)u_dev, (const double2 *)c->efac, 3 * nrhs, c->ncell(), (double2 *)e_dev, s);
+  return cuda_status(cudaGetLastError());
 }
 
 ie_status ie_rhs_mt(ie_ctx *c, int inst, int pol, void *u0) {

@@ -58,6 +58,8 @@ extern "C" ie_status ie_matvec_noalloc(int nx, int ny, int nz, int nrhs, const v
   if (nx < 1 || ny < 1 || nz < 1 || nrhs < 1 || nrhs > 4 || !qf_dev || !in_scale_dev || !out_scale_dev ||
       !x_dev || !y_dev || x_dev == y_dev)
     return IE_ERR_ARG;
+  // shapes the contraction cannot stage are argument errors, found before any launch
+  if (!ie::contract_fits(nz, nrhs, true)) return IE_ERR_ARG;
   const long long cz = (long long)nrhs * 3 * nz;
   const long long t1_elems = (long long)ny * 2 * nx * cz;
   const long long spec_elems = 4LL * nx * ny * cz;
@@ -82,11 +84,21 @@ extern "C" ie_status ie_matvec_noalloc(int nx, int ny, int nz, int nrhs, const v
   // same call, so nothing left over from a previous call is ever read.
   ie::launch_fft_rows_fwd<float>(x, static_cast<const float2 *>(in_scale_dev), t1, (int)cz, nz, ny, nx, px, s);
   ie::launch_fft_axis<float, false>(t1, spec, 1, ny, 2 * ny, 2LL * nx * cz, py, 1.0f, s);
+  // a wait that runs out inside the contraction is recorded in the library's own error
+  // word, which ie_noalloc_sync reports
   if (ie::launch_contract<float>(spec, static_cast<const float2 *>(qf_dev), nx, ny, nz, nrhs, (int)cz,
-                                ie::kContractAuto, s) != 0)
+                                ie::kContractAuto, nullptr, s) != 0)
     return IE_ERR_CUDA;
   ie::launch_fft_axis<float, true>(spec, t1, 1, 2 * ny, ny, 2LL * nx * cz, py, 1.0f, s);
   ie::launch_fft_rows_inv<float>(t1, x, static_cast<const float2 *>(diag_dev),
                                  static_cast<const float2 *>(out_scale_dev), y, (int)cz, nz, ny, nx, px, s);
   return cudaGetLastError() == cudaSuccess ? IE_OK : IE_ERR_CUDA;
+}
+
+extern "C" ie_status ie_noalloc_sync(void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return IE_ERR_CUDA;
+  const int e = ie::contract_take_error(nullptr, s);
+  if (e < 0) return IE_ERR_CUDA;
+  return e ? IE_ERR_TIMEOUT : IE_OK;
 }

@@ -228,6 +228,14 @@ __global__ void gradient_kernel(const double2 *__restrict__ u, const double2 *__
   }
 }
 
+// e[p][c][m] = u[p][c][m] * fac[m]: the in-cell field E = U / a of every component
+__global__ void cell_scale_kernel(const double2 *__restrict__ u, const double2 *__restrict__ fac, long long N,
+                                  long long total, double2 *__restrict__ e) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    e[i] = cm(u[i], __ldg(fac + i % N));
+}
+
 int grid_for(long long n) {
   long long g = (n + kRT - 1) / kRT;
   return (int)(g < 1 ? 1 : (g > 152LL * 16 ? 152LL * 16 : g));
@@ -260,6 +268,12 @@ void launch_gradient_accumulate(const double2 *u, const double2 *w, const double
                                 double *grad, cudaStream_t s) {
   count_launches(1);
   gradient_kernel<<<grid_for(ncell), kRT, 0, s>>>(u, w, gdiv, nrhs, ncell, grad);
+}
+
+void launch_cell_scale(const double2 *u, const double2 *fac, int nvec, long long ncell, double2 *e, cudaStream_t s) {
+  count_launches(1);
+  const long long total = (long long)nvec * ncell;
+  cell_scale_kernel<<<grid_for(total), kRT, 0, s>>>(u, fac, ncell, total, e);
 }
 
 }  // namespace ie

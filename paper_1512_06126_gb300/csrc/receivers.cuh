@@ -29,4 +29,7 @@ void launch_mt_misfit(const double2 *f, const double2 *zobs, int n_rec, double2 
 void launch_gradient_accumulate(const double2 *u, const double2 *w, const double2 *gdiv, int nrhs, long long ncell,
                                 double *grad, cudaStream_t s);
 
+// e = u times the per-cell factor fac, for nvec vectors of ncell cells each
+void launch_cell_scale(const double2 *u, const double2 *fac, int nvec, long long ncell, double2 *e, cudaStream_t s);
+
 }  // namespace ie

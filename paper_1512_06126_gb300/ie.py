@@ -16,13 +16,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libie_gb300.so")
 
 IE_OK, IE_NOT_CONVERGED, IE_BREAKDOWN = 0, 1, 2
+IE_ERR_ARG = -1
 IE_ERR_SCRATCH = -6
+IE_ERR_TIMEOUT = -7
 IE_C64, IE_C128 = 0, 1
 IE_C128_DF = 7
 IE_FP64, IE_MIXED, IE_MIXED_FP64K = 0, 1, 2
 IE_PROF_PRODUCT_C64, IE_PROF_PRODUCT_C128, IE_PROF_GS_C64, IE_PROF_GS_C128, IE_PROF_GIVENS = 2, 3, 4, 5, 6
 
-EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_matvec", "ie_solve", "ie_adjoint_solve", "ie_solve_batch",
+EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_noalloc_sync", "ie_matvec", "ie_sync",
+           "ie_fields", "ie_debug_set_wait_limit", "ie_solve", "ie_adjoint_solve", "ie_solve_batch",
            "ie_contract_tuning", "ie_set_contract_variant", "ie_rhs_mt", "ie_set_sigma", "ie_set_receivers",
            "ie_receiver_fields", "ie_mt_misfit", "ie_receiver_adjoint", "ie_gradient_accumulate", "ie_ctx_stream",
            "ie_ctx_device_bytes", "ie_profile", "ie_profile_read", "ie_profile_matvec", "ie_kernel_launches",
@@ -77,8 +80,16 @@ def load(path: str = LIB_PATH):
     lib.ie_generate_coefficients.restype = I
     lib.ie_matvec_noalloc.argtypes = [I, I, I, I, VP, VP, VP, VP, VP, VP, VP]
     lib.ie_matvec_noalloc.restype = I
+    lib.ie_noalloc_sync.argtypes = [VP]
+    lib.ie_noalloc_sync.restype = I
     lib.ie_matvec.argtypes = [VP, I, VP, VP, I, I, I, VP]
     lib.ie_matvec.restype = I
+    lib.ie_sync.argtypes = [VP, VP]
+    lib.ie_sync.restype = I
+    lib.ie_fields.argtypes = [VP, VP, VP, I, VP]
+    lib.ie_fields.restype = I
+    lib.ie_debug_set_wait_limit.argtypes = [ctypes.c_longlong]
+    lib.ie_debug_set_wait_limit.restype = None
     lib.ie_solve.argtypes = [VP, I, VP, VP, I, D, I, I, P(ie_solve_info)]
     lib.ie_solve.restype = I
     lib.ie_adjoint_solve.argtypes = [VP, I, VP, VP, I, D, I, I, P(ie_solve_info)]
@@ -132,6 +143,18 @@ def matvec_noalloc(nx, ny, nz, nrhs, qf_ptr, in_scale_ptr, out_scale_ptr, diag_p
     status code (IE_OK, or IE_ERR_SCRATCH for a problem above the fixed work space)."""
     return load().ie_matvec_noalloc(nx, ny, nz, nrhs, qf_ptr, in_scale_ptr, out_scale_ptr, diag_ptr, x_ptr, y_ptr,
                                     stream)
+
+
+def noalloc_sync(stream=None):
+    """Wait for the stream; IE_ERR_TIMEOUT if a contraction of ie_matvec_noalloc ran out of
+    a bounded wait since the last call, else IE_OK."""
+    return load().ie_noalloc_sync(stream)
+
+
+def debug_set_wait_limit(polls: int):
+    """Testing aid: polls before the main waits of later contraction launches give up
+    (0: at once; negative: the default)."""
+    load().ie_debug_set_wait_limit(int(polls))
 
 
 def status_str(s: int) -> str:
@@ -224,6 +247,14 @@ class Context:
     def matvec(self, inst, x_ptr, y_ptr, nrhs, dtype=IE_C128, transpose=False, stream=None):
         s = self._lib.ie_matvec(self.ctx, inst, x_ptr, y_ptr, nrhs, dtype, int(bool(transpose)), stream)
         _check(s, "ie_matvec")
+
+    def sync(self, stream=None):
+        """Wait for the stream (None: the context stream); returns IE_OK or IE_ERR_TIMEOUT."""
+        return self._lib.ie_sync(self.ctx, stream)
+
+    def fields(self, u_ptr, e_ptr, nrhs, stream=None):
+        """E = U / a for nrhs c128 solutions (asynchronous)."""
+        _check(self._lib.ie_fields(self.ctx, u_ptr, e_ptr, nrhs, stream), "ie_fields")
 
     def solve(self, inst, b_ptr, u_ptr, nrhs, tol, precision=IE_FP64, use_x0=False, adjoint=False):
         info = ie_solve_info()

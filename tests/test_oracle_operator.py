@@ -129,3 +129,34 @@ def test_lu_equals_gmres_and_contraction_rate(c1):
     assert np.linalg.norm(u - u_lu) <= 1e-10 * np.linalg.norm(u_lu)
     res = np.linalg.norm(b - O.fft_apply(m, qt, u)) / np.linalg.norm(b)
     assert res <= 1e-11
+
+
+def test_in_cell_field_without_anomaly_is_the_normal_field():
+    """sigma_a = sigma_b: U = U^0 = s <E^N>, so E = U / a must be the cell average of the
+    1-D normal field itself (a = Re sigma_b / s = s)."""
+    m0 = W.small_model(nx=4, ny=3, nz=4, seed=7, freq=2.0)
+    sb = W.background_sigma(m0.grid, m0.layers)
+    m = W.Model(m0.name, m0.grid, m0.layers, np.broadcast_to(sb[:, None, None], m0.sigma_a.shape).copy(),
+                m0.freqs, m0.pols)
+    ze = m.grid.z_edges_array()
+    om = 2 * np.pi * m.freqs[0]
+    avg = np.array([normal.cell_average(m.layers, om, ze[k], ze[k + 1]) for k in range(m.grid.nz)])
+    for pol, c in (("x", 0), ("y", 1)):
+        E = O.in_cell_field(m, normal.rhs_U0(m, m.freqs[0], pol))
+        ref = np.zeros_like(E)
+        ref[c] = avg[:, None, None]
+        assert np.abs(E - ref).max() <= 1e-13 * np.abs(avg).max()
+
+
+def test_in_cell_field_gives_the_scattering_current():
+    """(sigma_a - sigma_b) E = 2 s gamma U: the current of (APR_lab) written with the
+    in-cell field equals the one written with gamma of (slae_matricies)."""
+    m = W.small_model(nx=5, ny=4, nz=3, seed=11, freq=3.0)
+    U = W.random_field((2, 3, m.grid.nz, m.grid.ny, m.grid.nx), 5)
+    gamma, s, V = O.diagonals(m)
+    sb = W.background_sigma(m.grid, m.layers)
+    J1 = (m.sigma_a - sb[:, None, None]) * O.in_cell_field(m, U)
+    J2 = 2.0 * s[:, None, None] * gamma * U
+    assert np.abs(gamma).max() > 0.1
+    assert np.abs(J1 - J2).max() <= 1e-13 * np.abs(J2).max()
+

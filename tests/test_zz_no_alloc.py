@@ -73,6 +73,12 @@ def test_noalloc_matches_matvec_on_two_calls(case):
         a, b = to_host(y_new).astype(np.complex128), to_host(y_ref).astype(np.complex128)
         assert np.all(np.isfinite(a))
         assert rel(a, b) <= 2e-5, (case, call, rel(a, b))
+        # and against the oracle's FFT product of the same (c64-rounded) input
+        qt = O.full_spectrum_blocks(O.embed_spectrum(q))
+        for r in range(R):
+            ref = O.fft_apply(m, qt, x[r].astype(np.complex64).astype(np.complex128))
+            assert rel(a[r], ref) <= 2e-5, (case, call, r, rel(a[r], ref))
+    assert ie.noalloc_sync(stream) == ie.IE_OK
     ctx.close()
 
 
@@ -85,3 +91,50 @@ def test_noalloc_rejects_problems_above_the_work_space():
     p = d.data_ptr()
     st = ie.matvec_noalloc(256, 256, 64, 2, p, p, p, p, p, p + 8, None)
     assert st == ie.IE_ERR_SCRATCH
+
+
+def test_noalloc_rejects_shapes_the_contraction_cannot_stage():
+    """Four right-hand sides over 300 layers fit the work space (a 1 x 1 grid) but not
+    the contraction's shared-memory staging: an argument error before any launch."""
+    need_gpu()
+    from paper_1512_06126_gb300 import build, ie
+    build.build()
+    d = torch.zeros(16, dtype=torch.complex64, device="cuda")
+    p = d.data_ptr()
+    assert ie.matvec_noalloc(1, 1, 300, 4, p, p, p, p, p, p + 8, None) == ie.IE_ERR_ARG
+    assert ie.noalloc_sync(None) == ie.IE_OK
+
+
+def test_noalloc_reports_a_timed_out_contraction():
+    """With every main wait of the contraction giving up at once (testing aid), the
+    call still returns IE_OK (it is asynchronous) and ie_noalloc_sync reports
+    IE_ERR_TIMEOUT once; a later call with the default limit is exact again."""
+    need_gpu()
+    from paper_1512_06126_gb300 import ie
+    m = W.small_model(nx=24, ny=20, nz=16, seed=3, freq=1.0)
+    q = W.random_compressed_q(20, 24, 16, seed=31)
+    g = m.grid
+    R = 2
+    qf = to_dev(folded_spectral_c64(q), torch.complex64)
+    in_s, out_s, diag = (to_dev(a, torch.complex64) for a in scales(m))
+    x = W.random_field((R, 3, g.nz, g.ny, g.nx), 7)
+    xd = to_dev(x, torch.complex64)
+    yd = torch.empty_like(xd)
+    stream = torch.cuda.current_stream().cuda_stream
+    args = (g.nx, g.ny, g.nz, R, qf.data_ptr(), in_s.data_ptr(), out_s.data_ptr(), diag.data_ptr(),
+            xd.data_ptr(), yd.data_ptr(), stream)
+    try:
+        ie.debug_set_wait_limit(0)
+        assert ie.matvec_noalloc(*args) == ie.IE_OK
+        assert ie.noalloc_sync(stream) == ie.IE_ERR_TIMEOUT
+    finally:
+        ie.debug_set_wait_limit(-1)
+    assert ie.noalloc_sync(stream) == ie.IE_OK
+    assert ie.matvec_noalloc(*args) == ie.IE_OK
+    assert ie.noalloc_sync(stream) == ie.IE_OK
+    qt = O.full_spectrum_blocks(O.embed_spectrum(q))
+    y = to_host(yd).astype(np.complex128)
+    for r in range(R):
+        ref = O.fft_apply(m, qt, x[r].astype(np.complex64).astype(np.complex128))
+        assert rel(y[r], ref) <= 2e-5
+
