@@ -1,0 +1,104 @@
+"""The kernels the large workloads run, checked against the oracle.
+
+* every c64 contraction variant, forced, against the oracle's FFT product for
+  Nz in {16, 32, 48} and one and two right-hand sides (2e-5 relative, the c64 bound of
+  the other product tests: FP32 FFTs and FP32 accumulation over 3 Nz terms);
+* solves on a 64 x 64 x 32 grid (register-blocked FFTs of length 128, tensor-core
+  contraction) and on the 128 x 128 x 32 single-solve grid, in all three precision
+  modes, each solution checked by its residual under the oracle's FFT product:
+  at tol 1e-7 the GPU's own residual is below 1e-7 with its c128 operator, which
+  agrees with the oracle's to ~1e-15 (FP64) or ~1e-10 (the double-float residual of
+  IE_MIXED), so the oracle residual must be below 2e-7.
+The operators are proxies (tests/proxy.py): the workload's grid and layers with a
+seeded random coefficient tensor scaled to make GMRES converge."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import normal, operator as O
+from tests.gpu_support import lib_context, need_gpu, rel, to_dev, to_host, torch
+from tests.proxy import contracting_q, moderate_contrast, oracle_residual
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 16), (20, 18, 32), (12, 10, 48)])
+def test_forced_contraction_variants_against_oracle(shape):
+    need_gpu()
+    from paper_1512_06126_gb300 import ie
+    nx, ny, nz = shape
+    m = W.small_model(nx=nx, ny=ny, nz=nz, seed=3, freq=1.0)
+    q = W.random_compressed_q(ny, nx, nz, seed=31)
+    qt = O.full_spectrum_blocks(O.embed_spectrum(q))
+    ctx = lib_context(m, [q], max_rhs=2)
+    s = torch.cuda.current_stream().cuda_stream
+    tried = []
+    for R in (1, 2):
+        x = W.random_field((R, 3, nz, ny, nx), 50 + R)
+        refs = [O.fft_apply(m, qt, x[r].astype(np.complex64).astype(np.complex128)) for r in range(R)]
+        xd = to_dev(x, torch.complex64)
+        for v in range(ie.N_CONTRACT_VARIANTS):
+            try:
+                ctx.set_contract_variant(R, v)
+            except ie.IEError:
+                continue  # not available for this Nz / R
+            yd = torch.full_like(xd, complex(float("nan"), 0.0))
+            ctx.matvec(0, xd.data_ptr(), yd.data_ptr(), R, dtype=ie.IE_C64, stream=s)
+            assert ctx.sync(s) == ie.IE_OK
+            y = to_host(yd).astype(np.complex128)
+            for r in range(R):
+                err = rel(y[r], refs[r])
+                assert err <= 2e-5, (shape, R, v, r, err)
+            tried.append((R, v))
+        ctx.set_contract_variant(R, -1)
+    # the tensor-core variants run wherever Nz is a multiple of 16
+    assert (2, 5) in tried and (1, 2) in tried, tried
+    ctx.close()
+
+
+def _solve_all_modes(m, q, qt, variant=None, restart=16):
+    from paper_1512_06126_gb300 import ie
+    g = m.grid
+    ctx = lib_context(m, [q], max_rhs=2, restart=restart, inner_tol=1e-4)
+    if variant is not None:
+        ctx.set_contract_variant(2, variant)
+    b = np.stack([normal.rhs_U0(m, m.freqs[0], "x"), normal.rhs_U0(m, m.freqs[0], "y")])
+    bd = to_dev(b)
+    out = {}
+    for prec in (ie.IE_FP64, ie.IE_MIXED, ie.IE_MIXED_FP64K):
+        ud = torch.zeros_like(bd)
+        torch.cuda.synchronize()
+        st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), 2, 1e-7, precision=prec)
+        assert st == 0, (prec, st, info.final_rel_res)
+        assert info.final_rel_res <= 1e-7
+        out[prec] = (oracle_residual(m, qt, b, to_host(ud)), info.inner_iters)
+    tuned = ctx.contract_tuning()[0]
+    ctx.close()
+    return out, tuned
+
+
+@pytest.mark.parametrize("variant", [None, 5])
+def test_fast_path_solves_against_oracle(variant):
+    """64 x 64 x 32 cells (the C2 background and anomaly layout cut to 64 x 64):
+    register-blocked FFTs of length 128 and the tensor-core contraction (the
+    autotuner's choice, then the unpacking 3xTF32 kernel forced)."""
+    need_gpu()
+    c2 = W.config2()
+    g = W.Grid(64, 64, 32, c2.grid.hx, c2.grid.hy, c2.grid.z_edges)
+    m0 = W.Model("C2-64", g, c2.layers, c2.sigma_a[:, 32:96, 32:96].copy(), c2.freqs, c2.pols)
+    m = moderate_contrast(m0)
+    q, qt = contracting_q(m, seed=61, target=8.0)
+    res, tuned = _solve_all_modes(m, q, qt, variant)
+    for prec, (r, it) in res.items():
+        assert r <= 2e-7, (variant, tuned, prec, r, it)
+
+
+def test_single_solve_grid_against_oracle():
+    """128 x 128 x 32 cells (the single-solve workload's grid, layers and anomaly
+    layout at a moderate contrast), two polarisations, all three modes."""
+    need_gpu()
+    m = moderate_contrast(W.config2())
+    q, qt = contracting_q(m, seed=62, target=8.0)
+    res, tuned = _solve_all_modes(m, q, qt)
+    for prec, (r, it) in res.items():
+        assert r <= 2e-7, (tuned, prec, r, it)
