@@ -4,19 +4,24 @@
 Workload (default): the single-solve configuration, Nx = Ny = 128, Nz = 32 cells of
 50 m (1,572,864 unknowns), 5-layer seeded background, 20 seeded anomalies of
 0.01-0.1 ohm-m, 1 Hz, both MT polarisations; coefficients generated on the
-device by the library.  One step = one mixed-precision solve (inner GMRES in c64:
-c64 FFT products and Krylov vectors, FP64 Hessenberg and sums; FP64 c128 refinement
-residual) of both polarisations to ||b - A u|| <= 1e-7 ||b||, i.e. every step of the
-hot path.
+device by the library.  One step = one mixed-precision solve of both polarisations
+to ||b - A u|| <= 1e-7 ||b|| in the IE_MIXED_FP64K mode: iterative refinement whose
+residual is the c128 product with the FP64 contraction, and whose corrections come
+from GMRES on the c64 product (FP32 FFTs and contraction) with FP64 Krylov vectors,
+Gram-Schmidt and Givens rotations -- every step of the hot path.
 
 Printed (one JSON line, rank 0):
   value         unknowns * Krylov iterations / s over the timed steps (device-resident
                 inputs), summed over ranks (replicas) / max time
   matvec        the IE matrix-vector product: algorithmic GB/s (coefficients once +
                 input and output vectors) of the c64 product for both polarisations
-  tts           time-to-solution at 1e-7: mixed vs plain FP64 (c128 products only)
+  tts           time-to-solution at 1e-7 (median and spread of repeated solves): the
+                timed mode, the c64-Krylov mode IE_MIXED and the plain FP64 solve
   roofline      the contraction kernel, timed with CUDA events during the timed steps
-  cpu_baseline  the FP64 oracle (numpy) on the host: GMRES iterations of the same grid
+  err_vs_oracle residual of GPU solutions under the oracle's FFT product on a proxy
+                operator of the same size (cpu_baseline leg)
+  cpu_baseline  the FP64 oracle (numpy) on the host: GMRES iterations of the same grid,
+                one thread and all threads
   e2e           the same metric through the C ABI with host buffers (H2D of the
                 right-hand sides and D2H of the solution inside the timed region)
 
@@ -32,6 +37,23 @@ import subprocess
 import sys
 import tempfile
 import time
+
+
+def _pin_threads_early():
+    """Thread caps of numpy's BLAS / OpenMP, set before numpy is imported: --threads T
+    for a CPU sample, all host cores for the reference arm."""
+    n = None
+    if "--cpu-sample" in sys.argv and "--threads" in sys.argv:
+        n = sys.argv[sys.argv.index("--threads") + 1]
+    elif "--impl" in sys.argv and sys.argv[sys.argv.index("--impl") + 1] == "reference":
+        n = str(os.cpu_count() or 1)
+    if n is not None:
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                  "NUMEXPR_NUM_THREADS"):
+            os.environ[v] = n
+
+
+_pin_threads_early()
 
 import numpy as np
 
@@ -56,6 +78,9 @@ def peaks():
 
 # (workload, contraction variant, right-hand sides) -> DRAM bytes per contraction launch
 CONTRACT_TRAFFIC = {("C2", 3, 2): 654541312 + 86889728, ("C2", 5, 2): 654550784 + 88402176}
+VARIANT_NAMES = ["tma 1 slot", "tma 3 slots", "panel", "tma 1 slot, 1 row/thread",
+                 "3xTF32 mma.sync, producer warp, 2 slots", "3xTF32 mma.sync, 1 slot, unpacked"]
+TENSOR_VARIANTS = (4, 5)
 
 
 def bf16_peak():
@@ -179,7 +204,10 @@ class OracleSample:
 
     The coefficient values do not change the oracle's cost, so a seeded random tensor
     of the workload's shape stands in for the generated one.  The spectral blocks are
-    built once (setup, untimed); run(n) times n GMRES iterations."""
+    built once (setup, untimed).  run(n) times one restart cycle of n iterations (the
+    oracle's GMRES with restart n, so that its Krylov array holds n + 1 vectors) and
+    subtracts the one product that computes the cycle's initial residual, timed on its
+    own: the result is the cost of n iterations, each one product and one CGS2 step."""
 
     def __init__(self, model, seed=41):
         from oracle import operator as O
@@ -191,11 +219,36 @@ class OracleSample:
         del q
         self.b = W.random_field((3, g.nz, g.ny, g.nx), seed + 1)
 
+    def apply(self, v):
+        return self.O.fft_apply(self.model, self.qt, v)
+
     def run(self, n_iters):
         O = self.O
         t0 = time.perf_counter()
-        O.gmres(lambda v: O.fft_apply(self.model, self.qt, v), self.b, tol=1e-30, m=30, max_iter=n_iters)
-        return time.perf_counter() - t0, n_iters
+        self.apply(self.b)
+        t_apply = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.gmres(self.apply, self.b, tol=1e-30, m=n_iters, max_iter=n_iters)
+        return max(time.perf_counter() - t0 - t_apply, 1e-9), n_iters
+
+
+def run_cpu_sample(args):
+    """Child process of the CPU baseline: thread caps already set from --threads before
+    numpy was imported; prints one JSON line."""
+    model = workload(args.workload)
+    sample = OracleSample(model)
+    t, n = sample.run(args.iters)
+    print(json.dumps({"threads": int(args.threads), "seconds": t, "iters": n}), flush=True)
+
+
+def cpu_leg(workload_name, threads, iters):
+    """Run OracleSample in a child process with `threads` BLAS/OpenMP threads."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--threads", str(threads), "--iters",
+           str(iters), "--workload", workload_name]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(f"CPU sample failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args, rank, ws):
@@ -204,6 +257,7 @@ def run_reference(args, rank, ws):
     model = workload(args.workload)
     g = model.grid
     n_unk = 3 * g.nx * g.ny * g.nz
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
     sample = OracleSample(model)
     for _ in range(args.warmup):
         sample.run(1)
@@ -218,15 +272,56 @@ def run_reference(args, rank, ws):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": {"workload": workload_desc(args.workload, model), "unknowns": n_unk,
                                             "grid": [g.nx, g.ny, g.nz]},
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
-                             "sample": "one FP64 GMRES iteration (FFT product + CGS2) of the oracle per step"},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": threads,
+                             "sample": "one FP64 GMRES iteration (FFT product + CGS2) of the oracle per step, one "
+                                       "right-hand side; the cycle's initial-residual product timed apart and "
+                                       f"subtracted; BLAS/OpenMP threads capped at {threads} (numpy's FFT and "
+                                       "einsum run on one thread)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def oracle_check(model, args):
+    """The cpu_baseline leg's accuracy check: GPU solutions of a proxy operator of the
+    workload's size (its grid, layers and anomaly layout at a moderate contrast, a
+    seeded random coefficient tensor scaled to make GMRES converge), in the timed
+    mode and in IE_MIXED, and their residuals under the oracle's FFT product."""
+    import torch
+    from oracle import normal
+    from oracle.proxy import contracting_q, moderate_contrast, oracle_residual
+    from paper_1512_06126_gb300 import ie
+    t0 = time.perf_counter()
+    mp = moderate_contrast(model)
+    q, qt = contracting_q(mp, seed=62, target=8.0)
+    g = mp.grid
+    b = np.stack([normal.rhs_U0(mp, mp.freqs[0], "x"), normal.rhs_U0(mp, mp.freqs[0], "y")])
+    ctx = ie.Context(g, mp.layers, mp.sigma_a, mp.freqs[:1], [q], max_rhs=2, restart=args.restart,
+                     inner_tol=args.inner_tol)
+    del q
+    bd = torch.from_numpy(b).to("cuda")
+    out = {"operator": "proxy: the workload's grid, layers and anomaly layout at 3x contrast, seeded random "
+                       "coefficient tensor scaled (oracle/proxy.py); residual ||b - A u|| / ||b|| of the GPU "
+                       "solution (tol 1e-7) under the oracle's FFT product, max over both polarisations"}
+    for name, prec in (("mixed_fp64_krylov", ie.IE_MIXED_FP64K), ("mixed_c64_krylov", ie.IE_MIXED),
+                       ("fp64", ie.IE_FP64)):
+        ud = torch.zeros_like(bd)
+        st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), 2, TOL, precision=prec)
+        torch.cuda.synchronize()
+        out[name] = {"status": int(st), "iters": info.inner_iters, "gpu_res": info.final_rel_res,
+                     "oracle_res": oracle_residual(mp, qt, b, ud.cpu().numpy())}
+    ctx.close()
+    out["seconds"] = time.perf_counter() - t0
+    return out
 
 
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+
+def _stats(xs):
+    xs = sorted(xs)
+    return {"median": float(np.median(xs)), "min": float(xs[0]), "max": float(xs[-1]), "n": len(xs)}
+
 
 def run_ours(args, rank, ws):
     import torch
@@ -250,16 +345,17 @@ def run_ours(args, rank, ws):
     u = torch.zeros_like(b)
     torch.cuda.synchronize()
     ext = torch.cuda.ExternalStream(ctx.stream)
+    PREC = ie.IE_MIXED_FP64K
 
-    def solve(precision):
-        st, info = ctx.solve(0, b.data_ptr(), u.data_ptr(), R, TOL, precision=precision)
+    def solve(c, precision, uu=u):
+        st, info = c.solve(0, b.data_ptr(), uu.data_ptr(), R, TOL, precision=precision)
         if st != ie.IE_OK:
             raise RuntimeError(f"solve did not converge: status {st}, residual {info.final_rel_res:.2e}")
         return info
 
     for _ in range(args.warmup):
-        solve(ie.IE_MIXED)
-    # ---- timed region: K mixed solves, device-resident inputs ----
+        solve(ctx, PREC)
+    # ---- timed region: K solves in the timed mode, device-resident inputs ----
     clocks = Clocks(dev)
     barrier(ws)
     torch.cuda.synchronize()
@@ -269,75 +365,85 @@ def run_ours(args, rank, ws):
     # effect otherwise)
     torch.cuda.profiler.start()
     l0 = ie.kernel_launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with torch.cuda.stream(ext):
-        ev0.record()
+        evs[0].record()
     iters = 0
     outer = 0
     res = 0.0
-    for _ in range(args.steps):
-        info = solve(ie.IE_MIXED)
+    for k in range(args.steps):
+        info = solve(ctx, PREC)
         iters += info.inner_iters
         outer += info.outer_iters
         res = max(res, info.final_rel_res)
-    with torch.cuda.stream(ext):
-        ev1.record()
-    ev1.synchronize()
+        with torch.cuda.stream(ext):
+            evs[k + 1].record()
+    evs[-1].synchronize()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     barrier(ws)
     l1 = ie.kernel_launches()
     k3_ms, k3_n = ctx.profile_read(ie.IE_C64)
     ctx.profile(False)
-    # ---- where an inner iteration goes: one more (untimed) solve with every step timed ----
-    ctx.profile(2)
-    info_b = solve(ie.IE_MIXED)
-    spans = {}
-    for key, kind in (("product_c64", ie.IE_PROF_PRODUCT_C64), ("gram_schmidt_c64", ie.IE_PROF_GS_C64),
-                      ("givens", ie.IE_PROF_GIVENS), ("contraction_c64", ie.IE_C64),
-                      ("contraction_c128", ie.IE_C128)):
-        ms_k, n_k = ctx.profile_read(kind)
-        spans[key] = {"ms_total": ms_k, "records": n_k, "ms_each": ms_k / max(n_k, 1)}
-    ctx.profile(False)
-    breakdown = {"inner_iters": info_b.inner_iters, "outer": info_b.outer_iters, "solve_s": info_b.t_solve,
-                 "spans": spans}
     clk = clocks.stop()
-    t_ms = ev0.elapsed_time(ev1)
+    t_ms = evs[0].elapsed_time(evs[-1])
+    step_s = [evs[k].elapsed_time(evs[k + 1]) / 1e3 for k in range(args.steps)]
     t_max = allreduce_max(t_ms / 1e3, ws)
     units = allreduce_sum(float(n_unk) * R * iters, ws)
     value = units / t_max
 
-    # ---- time-to-solution: mixed (mean of the timed steps) vs plain FP64 ----
-    tts_mixed = t_ms / 1e3 / args.steps
+    # ---- where an inner iteration goes: one more (untimed) solve per mode, every step timed ----
+    def breakdown_of(precision):
+        ctx.profile(2)
+        info_b = solve(ctx, precision)
+        spans = {}
+        for key, kind in (("product_c64", ie.IE_PROF_PRODUCT_C64), ("product_c128", ie.IE_PROF_PRODUCT_C128),
+                          ("gram_schmidt_c64", ie.IE_PROF_GS_C64), ("gram_schmidt_c128", ie.IE_PROF_GS_C128),
+                          ("givens", ie.IE_PROF_GIVENS), ("contraction_c64", ie.IE_C64),
+                          ("contraction_c128", ie.IE_C128)):
+            ms_k, n_k = ctx.profile_read(kind)
+            if n_k:
+                spans[key] = {"ms_total": ms_k, "records": n_k, "ms_each": ms_k / n_k}
+        ctx.profile(False)
+        return {"inner_iters": info_b.inner_iters, "outer": info_b.outer_iters, "solve_s": info_b.t_solve,
+                "spans": spans}
+    breakdown = {"mixed_fp64_krylov": breakdown_of(PREC), "mixed_c64_krylov": breakdown_of(ie.IE_MIXED)}
+
+    # ---- time-to-solution: the timed mode, IE_MIXED and the plain FP64 solve ----
+    def timed_solves(c, precision, n):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+        ex = torch.cuda.ExternalStream(c.stream)
+        uu = torch.zeros_like(b)
+        solve(c, precision, uu)
+        infos = []
+        with torch.cuda.stream(ex):
+            e[0].record()
+        for k in range(n):
+            uu.zero_()
+            torch.cuda.synchronize()
+            with torch.cuda.stream(ex):
+                e[k].record()
+            infos.append(solve(c, precision, uu))
+            with torch.cuda.stream(ex):
+                e[k + 1].record()
+            e[k + 1].synchronize()
+        return [e[k].elapsed_time(e[k + 1]) / 1e3 for k in range(n)], infos
+    mx_s, mx_info = timed_solves(ctx, ie.IE_MIXED, args.tts_repeats)
     # the plain FP64 solve at its own best restart length (longer than the mixed one's),
-    # on a context of its own, after one untimed solve
+    # on a context of its own
     ctx64 = ie.Context(g, model.layers, model.sigma_a, model.freqs[:1], None, max_rhs=R,
                        restart=args.restart_fp64)
-    u64 = torch.zeros_like(b)
-    st64, info64 = ctx64.solve(0, b.data_ptr(), u64.data_ptr(), R, TOL, precision=ie.IE_FP64)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    st64, info64 = ctx64.solve(0, b.data_ptr(), u64.data_ptr(), R, TOL, precision=ie.IE_FP64)
-    torch.cuda.synchronize()
-    tts_fp64 = time.perf_counter() - t1
-    if st64 != ie.IE_OK:
-        raise RuntimeError(f"FP64 solve did not converge: status {st64}")
+    fp_s, fp_info = timed_solves(ctx64, ie.IE_FP64, args.tts_repeats)
     ctx64.close()
-    del u64
-    # the mixed solve with FP64 Krylov vectors, Gram-Schmidt and rotations in its inner
-    # solves and the FP64 contraction in its residuals, on the same context (after one
-    # untimed solve)
-    ufk = torch.zeros_like(b)
-    ctx.solve(0, b.data_ptr(), ufk.data_ptr(), R, TOL, precision=ie.IE_MIXED_FP64K)
-    ufk.zero_()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    stfk, infofk = ctx.solve(0, b.data_ptr(), ufk.data_ptr(), R, TOL, precision=ie.IE_MIXED_FP64K)
-    torch.cuda.synchronize()
-    tts_fp64k = time.perf_counter() - t2
-    if stfk != ie.IE_OK:
-        raise RuntimeError(f"mixed FP64-Krylov solve did not converge: status {stfk}")
-    del ufk
+    tts = {"timed_mode": "IE_MIXED_FP64K",
+           "mixed_fp64_krylov_s": _stats(step_s), "mixed_fp64_krylov_iters": iters / args.steps,
+           "mixed_fp64_krylov_outer": outer / args.steps, "mixed_fp64_krylov_final_rel_res": res,
+           "mixed_c64_krylov_s": _stats(mx_s), "mixed_c64_krylov_iters": mx_info[0].inner_iters,
+           "mixed_c64_krylov_final_rel_res": max(i.final_rel_res for i in mx_info),
+           "fp64_s": _stats(fp_s), "fp64_iters": fp_info[0].inner_iters,
+           "fp64_final_rel_res": max(i.final_rel_res for i in fp_info),
+           "speedup_timed_vs_fp64": float(np.median(fp_s) / np.median(step_s)),
+           "speedup_c64_krylov_vs_fp64": float(np.median(fp_s) / np.median(mx_s))}
 
     # ---- matvec GB/s (c64, both polarisations) ----
     nf = (g.nx + 1) * (g.ny + 1)
@@ -358,50 +464,44 @@ def run_ours(args, rank, ws):
     with torch.cuda.stream(ext):
         e1.record()
     e1.synchronize()
+    if ctx.sync() != ie.IE_OK:
+        raise RuntimeError("a contraction wait ran out during the product timing")
     mv_ms = e0.elapsed_time(e1) / n_mv
     mv_bytes = q_bytes + 2 * 8 * n_unk * R
     kern_ms = ctx.profile_matvec(0, R, ie.IE_C64, 10)
+    hbm_peak, sm_max, peak_src = peaks()
 
     # ---- roofline of the contraction kernel (timed during the steps) ----
-    hbm_peak, sm_max, peak_src = peaks()
     k3_avg_ms = k3_ms / max(k3_n, 1)
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
     # capture of this kernel variant, as it is now, on this workload (profiles/); null for
     # any other variant or workload
-    traffic = CONTRACT_TRAFFIC.get((args.workload, int(tune_v[R - 1]), R))
-    k3_bytes = q_bytes + 2 * 4 * g.nx * g.ny * 3 * g.nz * R * 8
+    variant = int(tune_v[R - 1])
+    traffic = CONTRACT_TRAFFIC.get((args.workload, variant, R))
+    # algorithmic bytes of the contraction: the c64 coefficients once plus the product's
+    # input and output vectors (the spectrum round trip is the kernel's own traffic)
+    k3_alg = q_bytes + 2 * 8 * n_unk * R
+    k3_own = q_bytes + 2 * 4 * g.nx * g.ny * 3 * g.nz * R * 8
     k3_flops = 8.0 * 4 * g.nx * g.ny * R * 9 * g.nz * g.nz
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12            # TFLOP/s, FP32 FMA pipes at max clock
-    variant = int(tune_v[R - 1])
-    t_hbm = k3_bytes / (hbm_peak * 1e9)
-    if variant in (4, 5):
-        # tensor-core variants: 3 TF32 products per FP32 product (3xTF32); TF32 peak =
-        # the measured bf16 peak x the nominal TF32 / bf16 ratio (1.1 / 2.25)
-        bf16 = bf16_peak()
-        tf32_peak = bf16[0] * 1.1 / 2.25
-        t_cmp = 3 * k3_flops / (tf32_peak * 1e12)
-        cmp = {"compute": "tensor, 3xTF32", "flops_per_launch": 3 * k3_flops, "compute_peak_TFLOPs": tf32_peak,
-               "compute_peak_source": f"{bf16[1]} bf16 {bf16[0]:.0f} TFLOP/s x 1.1/2.25",
-               "compute_TFLOPs": 3 * k3_flops / (k3_avg_ms * 1e-3) / 1e12}
-    else:
-        t_cmp = k3_flops / (fp32_peak * 1e12)
-        cmp = {"compute": "FP32 FMA", "flops_per_launch": k3_flops, "compute_peak_TFLOPs": fp32_peak,
-               "compute_peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
-               "compute_TFLOPs": k3_flops / (k3_avg_ms * 1e-3) / 1e12}
-    kname = f"contract (c64, 2 right-hand sides, variant {variant})"
-    if variant not in (4, 5) and t_cmp > t_hbm:
-        achieved = k3_flops / (k3_avg_ms * 1e-3) / 1e12
-        roof = {"kernel": kname, "bound": "alu", "achieved": achieved,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "peak_source": cmp["compute_peak_source"],
-                "hbm_GBs": k3_bytes / (k3_avg_ms * 1e-3) / 1e9, "hbm_frac": k3_bytes / (k3_avg_ms * 1e-3) / 1e9 / hbm_peak,
-                "bytes_per_launch": k3_bytes, "flops_per_launch": k3_flops, "traffic": traffic,
-                "launches": k3_n, "avg_ms": k3_avg_ms}
-    else:
-        achieved = k3_bytes / (k3_avg_ms * 1e-3) / 1e9
-        roof = {"kernel": kname, "bound": "hbm" if t_hbm >= t_cmp else "tensor", "achieved": achieved,
-                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "peak_source": peak_src,
-                "bytes_per_launch": k3_bytes, "traffic": traffic, "launches": k3_n, "avg_ms": k3_avg_ms, **cmp}
+    bf16 = bf16_peak()
+    tf32_peak = bf16[0] * 1.1 / 2.25
+    tensor = variant in TENSOR_VARIANTS
+    achieved = k3_alg / (k3_avg_ms * 1e-3) / 1e9
+    roof = {"kernel": f"contract (c64, 2 right-hand sides, variant {variant})", "bound": "hbm",
+            "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "peak_source": peak_src, "bytes_per_launch": k3_alg,
+            "bytes_definition": "algorithmic: c64 coefficients once + input and output vectors of the product",
+            "kernel_bytes_per_launch": k3_own,
+            "kernel_bytes_definition": "coefficients + the spectrum read and written",
+            "kernel_frac": k3_own / (k3_avg_ms * 1e-3) / 1e9 / hbm_peak,
+            "traffic": traffic, "launches": k3_n, "avg_ms": k3_avg_ms,
+            "compute": "tensor, 3xTF32" if tensor else "FP32 FMA",
+            "flops_per_launch": 3 * k3_flops if tensor else k3_flops,
+            "compute_peak_TFLOPs": tf32_peak if tensor else fp32_peak,
+            "compute_peak_source": (f"{bf16[1]} bf16 {bf16[0]:.0f} TFLOP/s x 1.1/2.25" if tensor else
+                                    f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"),
+            "compute_TFLOPs": (3 if tensor else 1) * k3_flops / (k3_avg_ms * 1e-3) / 1e12}
 
     # ---- e2e: through the ABI with host buffers ----
     bh = b.cpu().pin_memory()
@@ -417,44 +517,57 @@ def run_ours(args, rank, ws):
     for _ in range(n_e2e):
         bd.copy_(bh, non_blocking=True)
         torch.cuda.synchronize()
-        st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), R, TOL, precision=ie.IE_MIXED)
+        st, info = ctx.solve(0, bd.data_ptr(), ud.data_ptr(), R, TOL, precision=PREC)
         uh.copy_(ud, non_blocking=True)
         it_e2e += info.inner_iters
     e1.record()
     e1.synchronize()
     t_e2e = e0.elapsed_time(e1) / 1e3
     e2e_value = allreduce_sum(float(n_unk) * R * it_e2e, ws) / allreduce_max(t_e2e, ws)
+    ctx.close()
+    del xs, ys, bd, ud
+    torch.cuda.empty_cache()
 
-    # ---- cpu baseline (rank 0, N = 1) ----
+    # ---- cpu baseline and the accuracy check against the oracle (rank 0, N = 1) ----
     cpu = None
+    err = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        t_cpu, n_cpu = OracleSample(model).run(args.cpu_iters)
-        cpu = {"value": n_unk * n_cpu / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n_cpu} FP64 GMRES iterations of the numpy oracle (FFT product + CGS2), one right-hand "
-                         f"side, same grid, random coefficient tensor of the same shape; {t_cpu:.1f} s"}
+        err = oracle_check(model, args)
+        ncores = os.cpu_count() or 1
+        legs = [cpu_leg(args.workload, th, args.cpu_iters) for th in (1, ncores)]
+        best = max(legs, key=lambda d: d["iters"] / d["seconds"])
+        cpu = {"value": n_unk * best["iters"] / best["seconds"], "unit": UNIT, "cores": best["threads"],
+               "kind": "oracle",
+               "sample": f"{args.cpu_iters} FP64 GMRES iterations (FFT product + CGS2) of the numpy oracle, one "
+                         "right-hand side, same grid, random coefficient tensor of the same shape; the cycle's "
+                         "initial-residual product timed apart and subtracted; run with BLAS/OpenMP threads capped "
+                         "at 1 and at all host cores (numpy's FFT and einsum use one thread either way)",
+               "legs": [{"threads": d["threads"], "value": n_unk * d["iters"] / d["seconds"],
+                         "seconds": d["seconds"], "iters": d["iters"]} for d in legs]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "c64 inner GMRES (products, Krylov vectors), c128 refinement residual", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "c64 products (FP32 FFTs and contraction) in the inner GMRES, FP64 Krylov vectors, "
+                         "Gram-Schmidt and rotations; c128 refinement residual with the FP64 contraction",
+                "data": "synthetic",
                 "config": {"workload": workload_desc(args.workload, model),
                            "unknowns": n_unk, "rhs": R, "restart": args.restart,
                            "inner_tol": args.inner_tol, "restart_fp64": args.restart_fp64,
+                           "precision": "IE_MIXED_FP64K",
                            "l2": "inputs larger than L2 (c64 coefficients %.0f MB)" % (q_bytes / 1e6),
                            "parallelism": f"replicas x{ws}", "coefficients": "generated on the device",
                            "setup_s": t_setup},
-                "matvec": {"GBs": mv_bytes / (mv_ms * 1e-3) / 1e9, "ms": mv_ms, "bytes": mv_bytes,
+                "matvec": {"GBs": mv_bytes / (mv_ms * 1e-3) / 1e9, "frac": mv_bytes / (mv_ms * 1e-3) / 1e9 / hbm_peak,
+                           "ms": mv_ms, "bytes": mv_bytes,
                            "kernel_ms": {"rows_fwd": kern_ms[0], "cols_fwd": kern_ms[1], "contract": kern_ms[2],
                                          "cols_inv": kern_ms[3], "rows_inv": kern_ms[4]}},
-                "tts": {"mixed_s": tts_mixed, "fp64_s": tts_fp64, "speedup": tts_fp64 / tts_mixed,
-                        "mixed_iters": iters / args.steps, "mixed_outer": outer / args.steps,
-                        "fp64_iters": info64.inner_iters, "final_rel_res": res,
-                        "mixed_fp64_krylov_s": tts_fp64k, "mixed_fp64_krylov_iters": infofk.inner_iters,
-                        "mixed_fp64_krylov_final_rel_res": infofk.final_rel_res},
+                "tts": tts,
                 "roofline": roof,
+                "err_vs_oracle": err,
                 "solve_breakdown": breakdown,
-                "contract_tuning": {"variants": ["tma 1 slot", "tma 3 slots", "panel", "tma 1 slot, 1 row/thread", "3xTF32 mma.sync, producer warp, 2 slots", "3xTF32 mma.sync, 1 slot, unpacked"],
-                                    "chosen_for_2_rhs": int(tune_v[1]),
+                "contract_tuning": {"variants": VARIANT_NAMES, "chosen_for_2_rhs": variant,
                                     "ms_per_launch_2_rhs": [float(v) for v in tune_ms[1]]},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 16),
@@ -462,7 +575,6 @@ def run_ours(args, rank, ws):
                 "gpu_launches": int(l1 - l0),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def run_matvec_only(args):
@@ -608,10 +720,17 @@ def main():
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--restart-fp64", type=int, default=45)
+    ap.add_argument("--tts-repeats", type=int, default=3)
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--threads", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--iters", type=int, default=3, help=argparse.SUPPRESS)
     ap.add_argument("--mode", choices=["solve", "matvec", "batch", "gradient"], default="solve")
     args = ap.parse_args()
+    if args.cpu_sample:
+        run_cpu_sample(args)
+        return
     rank, ws = dist_setup()
     if args.mode == "matvec":
         run_matvec_only(args)

@@ -24,7 +24,11 @@ electromagnetics based on Galerkin method"):
                       compressed tensor Q(i, j) of eq. (matrix_symm).
 * ``normal``       -- the MT plane-wave normal field E^N and U^0 of (slae_matricies).
 * ``operator``     -- A = S + R1 B R2 (eq. (matrix_convolv)): dense apply, FFT
-                      apply (Sect. 3.3), GMRES(m) and dense LU solves.
+                      apply (Sect. 3.3), GMRES(m) and dense LU solves, and the
+                      in-cell field E = U / a (eq. (iEH320op)).
+* ``proxy``        -- full-size synthetic operators (seeded random coefficients
+                      scaled to make GMRES converge) whose GPU solutions the FFT
+                      apply checks by their residual.
 
 Parity status of each function is stated in its module header.
 """

@@ -1,5 +1,8 @@
 """Synthetic operators of full workload size whose solves the oracle can check.
 
+Test infrastructure (see ``oracle/__init__``): used by tests/ and by the CPU-baseline
+leg of bench.py only.
+
 The oracle cannot compute the physical coefficient tensors of the large grids in a
 test's time, so the kernels and solvers are checked at those sizes on a proxy: the
 workload's grid and layers, the anomalous cells at a moderate contrast, and a seeded

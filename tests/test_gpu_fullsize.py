@@ -9,7 +9,7 @@
   at tol 1e-7 the GPU's own residual is below 1e-7 with its c128 operator, which
   agrees with the oracle's to ~1e-15 (FP64) or ~1e-10 (the double-float residual of
   IE_MIXED), so the oracle residual must be below 2e-7.
-The operators are proxies (tests/proxy.py): the workload's grid and layers with a
+The operators are proxies (oracle/proxy.py): the workload's grid and layers with a
 seeded random coefficient tensor scaled to make GMRES converge."""
 import numpy as np
 import pytest
@@ -17,7 +17,7 @@ import pytest
 import workloads as W
 from oracle import normal, operator as O
 from tests.gpu_support import lib_context, need_gpu, rel, to_dev, to_host, torch
-from tests.proxy import contracting_q, moderate_contrast, oracle_residual
+from oracle.proxy import contracting_q, moderate_contrast, oracle_residual
 
 pytestmark = pytest.mark.gpu
 
