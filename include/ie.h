@@ -211,13 +211,15 @@ ie_status ie_solve_batch(ie_ctx *ctx, int n_inst, const int *inst_host, const vo
 /* Contraction variants (no counterpart in the paper): 0 the TMA ring with one slot and
  * two CTAs per SM, 1 the TMA ring with three slots and one CTA per SM (both c64,
  * Nz in {16, 24, 32, 48}, 1-2 right-hand sides), 2 the panel-staged kernel (any case),
- * 3 as 0 with one output row per thread (two right-hand sides), 4 and 5 tensor-core
- * TF32 MMAs with the 3xTF32 split (FP32 accuracy; c64, Nz in {16, 32, 48}, 1-2
- * right-hand sides): 4 a producer warp and a two-slot ring, the fragments read where
- * the copies land; 5 the one-slot ring with an unpacking pass.
+ * 3 as 0 with one output row per thread (two right-hand sides), 4 and 5 warp-level
+ * TF32 MMAs (mma.sync) with the 3xTF32 split (FP32 accuracy; c64, Nz in {16, 32, 48},
+ * 1-2 right-hand sides): 4 a producer warp and a two-slot ring, the fragments read
+ * where the copies land; 5 the one-slot ring with an unpacking pass; 6 the
+ * 5th-generation tensor cores (tcgen05.mma, the block in tensor memory, 3xTF32; c64,
+ * Nz in {16, 32}, 1-2 right-hand sides).
  * ie_contract_tuning reports the c64 variant used for 1..4 right-hand sides per
  * instance (variant_host[4]; -1: built-in choice) and the autotuner's timings
- * (ms_host[4][6], ms per launch, 0 where not timed; may be NULL).
+ * (ms_host[4][7], ms per launch, 0 where not timed; may be NULL).
  * ie_set_contract_variant overrides the choice for one right-hand-side count
  * (-1: built-in choice); IE_ERR_ARG if the variant does not apply to this grid. */
 ie_status ie_contract_tuning(ie_ctx *ctx, int *variant_host, double *ms_host);

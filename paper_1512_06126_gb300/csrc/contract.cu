@@ -14,6 +14,7 @@
 // all right-hand sides.
 #include "contract.cuh"
 #include "contract_mma.cuh"
+#include "contract_tc.cuh"
 #include "contract_tma.cuh"
 
 namespace ie {
@@ -242,6 +243,47 @@ bool try_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, bool unpac
                            err, s);
 }
 
+// The tcgen05 kernel: persistent, as many CTAs per SM as occupancy and tensor memory
+// allow (each holds TcCfg::TCOLS of the SM's 512 columns for its lifetime).
+template <int NZ, int R>
+bool try_tc(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int *err, cudaStream_t s) {
+  using Cfg = TcCfg<NZ, R>;
+  static int per_sm = 0;
+  auto k = contract_tc_kernel<NZ, R>;
+  if (Cfg::SMEM > 227 * 1024) return false;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Cfg::THREADS, Cfg::SMEM) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    if (per_sm > 512 / Cfg::TCOLS) per_sm = 512 / Cfg::TCOLS;
+  }
+  const int nf = (Nx + 1) * (Ny + 1);
+  const int want = per_sm * num_sms();
+  const int grid = nf < want ? nf : want;
+  count_launches(1);
+  k<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(spec, qf, Nx, Ny, ldz, err, g_wait_limit);
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+template <int R>
+bool dispatch_tc(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, int *err, cudaStream_t s) {
+  switch (Nz) {
+    case 16: return try_tc<16, R>(spec, qf, Nx, Ny, ldz, err, s);
+    case 32: return try_tc<32, R>(spec, qf, Nx, Ny, ldz, err, s);
+    default: return false;
+  }
+}
+
 template <int R>
 bool dispatch_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, bool unpack, int *err,
                   cudaStream_t s) {
@@ -298,6 +340,7 @@ bool contract_variant_available(int variant, int Nz, int R, bool c64) {
   if (variant == kContractPanel) return R >= 1 && R <= 4 && 3 * Nz <= 1024;
   if (!c64 || R < 1 || R > 2 || !contract_tma_enabled) return false;
   if (Nz != 16 && Nz != 24 && Nz != 32 && Nz != 48) return false;
+  if (variant == kContractTc) return Nz == 16 || Nz == 32;
   if (variant == kContractMma || variant == kContractMmaUnpack) return Nz % 16 == 0;
   if (variant == kContractTma1) return true;
   if (variant == kContractTma1Row) return R == 2;
@@ -326,6 +369,10 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, i
       const bool unpack = variant == kContractMmaUnpack;
       if (R == 1 && dispatch_mma<1>(spec, qf, Nx, Ny, Nz, ldz, unpack, err, s)) return 0;
       if (R == 2 && dispatch_mma<2>(spec, qf, Nx, Ny, Nz, ldz, unpack, err, s)) return 0;
+    }
+    if (variant == kContractTc && contract_variant_available(variant, Nz, R, true)) {
+      if (R == 1 && dispatch_tc<1>(spec, qf, Nx, Ny, Nz, ldz, err, s)) return 0;
+      if (R == 2 && dispatch_tc<2>(spec, qf, Nx, Ny, Nz, ldz, err, s)) return 0;
     }
     if ((variant == kContractTma1 || variant == kContractTma3 || variant == kContractTma1Row) &&
         contract_variant_available(variant, Nz, R, true)) {

@@ -10,11 +10,13 @@ namespace ie {
 // per thread (two right-hand sides only), and two kernels feeding 3xTF32 tensor-core
 // MMAs (c64, Nz in {16, 32, 48}, R <= 2): a producer warp with a two-slot ring and
 // fragments read in place, or the one-slot ring with an unpacking pass.
+// Variant 6 runs on the 5th-generation tensor cores: tcgen05.mma with the block in
+// tensor memory and FP32 accumulators there (3xTF32; c64, Nz in {16, 32}, R <= 2).
 enum ContractVariant {
   kContractAuto = -1, kContractTma1 = 0, kContractTma3 = 1, kContractPanel = 2, kContractTma1Row = 3,
-  kContractMma = 4, kContractMmaUnpack = 5
+  kContractMma = 4, kContractMmaUnpack = 5, kContractTc = 6
 };
-constexpr int kContractVariants = 6;
+constexpr int kContractVariants = 7;
 bool contract_variant_available(int variant, int Nz, int R, bool c64);
 // Whether the panel kernel, the fallback of every variant, can stage a contraction of
 // Nz layers and R right-hand sides (c64 or c128) in shared memory.

@@ -1,0 +1,456 @@
+// Wavenumber contraction (step 2 of the FFT product, Sect. 3.3) on the 5th-generation
+// tensor cores: tcgen05.mma with the coefficient block in tensor memory (TMEM), the
+// spectrum vectors in shared memory, FP32 accumulators in TMEM.  c64, compile-time Nz
+// with 3 Nz <= 128 (one M = 128 tile of output rows), R <= 2 right-hand sides.
+//
+// Per folded wavenumber the 3Nz x 3Nz complex block M meets at most 8 columns X (4
+// mirrors x R).  As a real product per input component beta (a K-chunk of 2 Nz):
+//   D += [M_r | M_i](:, beta) . [[X_r, X_i], [-X_i, X_r]](beta)
+// so D[:, c] = Y_r and D[:, 8 + c] = Y_i of column c (N = 16).  FP32 accuracy from the
+// 3xTF32 split x = hi + lo (hi = x rounded to TF32, lo = x - hi exactly): D1 += A_hi B_hi
+// and D2 += A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo is ~2^-22 of the product).
+//
+// Warp roles (one CTA per SM; persistent over folded wavenumbers w = blockIdx.x +
+// k gridDim.x):
+//  * warp 0, the producer: 1-D bulk copies (cp.async.bulk) of the packed triangles of
+//    xx, yy, zz, xy, of every row of xz and yz at a padded stride, and of the mirror
+//    spectrum vectors into a ring of NS shared-memory stages;
+//  * warp 1, the MMA issuer: one thread issues the 3 x (2 Nz / 8) x 3 tcgen05.mma of a
+//    wavenumber and commits their completion to mbarriers;
+//  * row warps (TMEM lane quadrant q = warp % 4 holds output rows 32q .. 32q + 31): each
+//    thread unpacks its row of the block chunk by chunk (Lemma 1: zx = -xz^T, zy =
+//    -yz^T), splits it and stores it to a ring of NA chunk buffers in TMEM
+//    (tcgen05.st); after the MMAs of a wavenumber the same warps read the accumulators
+//    (tcgen05.ld), apply the mirror component signs (Lemma 2) and store the outputs;
+//  * B warps: split X (mirror signs applied) into the K-major no-swizzle layout of the
+//    MMA's B operand (core matrices of 8 rows x 16 bytes), double-buffered.
+// Every wait is bounded: on timeout the kernel records an error, each role stops, the
+// producer drains its copies and the issuer its MMAs, and TMEM is released.
+#pragma once
+#include "contract_tma.cuh"
+
+namespace ie {
+namespace tc {
+
+__device__ __forceinline__ void alloc(uint32_t *dst, int ncols) {  // one full warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tma::smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void dealloc(uint32_t taddr, int ncols) {  // one full warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 8 consecutive TMEM columns of this warp's lanes from 8 registers per thread
+__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void st4(uint32_t taddr, const uint32_t (&r)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+               "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+__device__ __forceinline__ void ld2(uint32_t taddr, uint32_t &a, uint32_t &b) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle; lbo = byte distance between
+// core matrices adjacent in K, sbo = between core matrices adjacent in M/N.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// D (+)= A B, A in TMEM, B from a shared-memory descriptor
+__device__ __forceinline__ void mma(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+          d),
+      "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   tma::smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tma::smem_u32(bar)) : "memory");
+}
+// 1-D bulk copy global -> shared with an L2 cache policy (createpolicy)
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          tma::smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(tma::smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+// L2 policy for data read once: evicted first, so that the coefficient stream does not
+// push the spectrum (re-read by the FFT passes around the contraction) out of L2
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// A bounded wait whose outcome is the same in every lane of the warp (all lanes poll;
+// the warp proceeds only if every lane saw the phase complete), so that the warp's
+// .sync.aligned TMEM instructions never run divergently after a timeout.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t phase, long long lim) {
+  return __all_sync(0xffffffffu, tma::mbar_wait_bounded(bar, phase, lim)) != 0;
+}
+// x = hi + lo exactly: hi = x rounded to TF32 (10 fraction bits), lo = x - hi
+__device__ __forceinline__ void split(float x, uint32_t &hi, uint32_t &lo) {
+  const uint32_t h = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+  hi = h;
+  lo = __float_as_uint(__fsub_rn(x, __uint_as_float(h)));
+}
+
+}  // namespace tc
+
+template <int NZ, int R>
+struct TcCfg {
+  static_assert(NZ % 8 == 0 && 3 * NZ <= 128, "one M = 128 tile of 3 Nz output rows; chunks of whole k-steps");
+  static_assert(R >= 1 && R <= 2, "N = 16: 8 complex columns = 4 mirrors x R");
+  static constexpr int N3 = 3 * NZ;
+  static constexpr int CZ = R * N3;
+  static constexpr int P = NZ * (NZ + 1) / 2;
+  static constexpr int BS = 2 * NZ * (2 * NZ + 1);
+  static constexpr int LDF = NZ + 2;  // full-block row stride (complex): 16-byte rows, 2-way banks
+  static constexpr int NQ = (N3 + 31) / 32;        // TMEM lane quadrants holding rows
+  static constexpr int RW = 4;                     // row warps per quadrant
+  static constexpr int EPW = NZ / RW;              // complex entries of a chunk per row warp
+  static constexpr int NROW = 4 * RW;              // warps 4 .. 4 + NROW - 1 (quadrant = warp % 4)
+  static constexpr int NROWA = NQ * RW;            // of them, those with rows
+  static constexpr int NB = 2 + NROW - NROWA;      // B warps: 2, 3 and the row warps without rows
+  static constexpr int WARPS = 4 + NROW;
+  static constexpr int THREADS = 32 * WARPS;
+  static constexpr int NS = 3;                     // shared-memory stages
+  static constexpr int NA = 3;                     // TMEM chunk buffers
+  static constexpr int KC = 2 * NZ;                // K of a chunk (real)
+  static constexpr int ACOLS = 4 * NZ;             // TMEM columns of a chunk buffer (hi, lo)
+  static constexpr int DCOL = NA * ACOLS;          // first accumulator column
+  static constexpr int TCOLS = DCOL + 64 <= 256 ? 256 : 512;
+  static_assert(DCOL + 64 <= 512, "TMEM");
+  // stage layout (bytes)
+  static constexpr size_t TRI = (size_t)4 * P * 8;
+  static constexpr size_t FULL = (size_t)2 * NZ * LDF * 8;
+  static constexpr size_t XR = (size_t)4 * CZ * 8;
+  static constexpr size_t STAGE = ((TRI + FULL + XR + 127) / 128) * 128;
+  // B operand: per chunk and hi / lo, N = 16 rows of K = KC (core matrices 8 x 16 bytes):
+  // byte (n % 8) 16 + (n / 8) SBO + (k / 4) 128 + (k % 4) 4
+  static constexpr uint32_t LBO = 128;
+  static constexpr uint32_t SBO = (uint32_t)(KC / 4) * 128;
+  static constexpr size_t BPART = (size_t)2 * SBO;            // one chunk, hi or lo
+  static constexpr size_t BBUF = (size_t)3 * 2 * BPART;       // one wavenumber
+  static constexpr size_t OFF_BAR = 0;                        // 32 mbarriers + the TMEM address
+  static constexpr size_t OFF_STAGE = 1024;
+  static constexpr size_t OFF_B = OFF_STAGE + NS * STAGE;
+  static constexpr size_t SMEM = OFF_B + 2 * BBUF;
+  static_assert((TRI % 16) == 0 && (LDF * 8) % 16 == 0 && ((TRI + FULL) % 16) == 0, "bulk copy alignment");
+  static constexpr uint32_t IDESC = tc::idesc_tf32(128, 16);
+};
+
+template <int NZ, int R>
+__global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
+    contract_tc_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err,
+                       long long lim) {
+  using Cfg = TcCfg<NZ, R>;
+  constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LDF = Cfg::LDF, NS = Cfg::NS, NA = Cfg::NA;
+  constexpr int KC = Cfg::KC, EPW = Cfg::EPW;
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Cfg::OFF_BAR);
+  uint64_t *full = bars, *empty = bars + 4, *afull = bars + 8, *aempty = bars + 12;
+  uint64_t *bfull = bars + 16, *bempty = bars + 18, *dfull = bars + 20, *dempty = bars + 22, *fin = bars + 24;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Cfg::OFF_BAR + 256);
+  unsigned char *stages = sm + Cfg::OFF_STAGE;
+  unsigned char *bbuf = sm + Cfg::OFF_B;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nf = (Nx + 1) * (Ny + 1);
+  const int w0 = blockIdx.x, gs = gridDim.x;
+  const int n_it = w0 < nf ? (nf - 1 - w0) / gs + 1 : 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int s = 0; s < NS; ++s) {
+        tma::mbar_init(&full[s], 1);
+        tma::mbar_init(&empty[s], Cfg::NROWA + Cfg::NB);
+      }
+      for (int c = 0; c < NA; ++c) {
+        tma::mbar_init(&afull[c], Cfg::NROWA);
+        tma::mbar_init(&aempty[c], 1);
+      }
+      for (int b = 0; b < 2; ++b) {
+        tma::mbar_init(&bfull[b], Cfg::NB);
+        tma::mbar_init(&bempty[b], 1);
+        tma::mbar_init(&dfull[b], 1);
+        tma::mbar_init(&dempty[b], Cfg::NROWA);
+      }
+      tma::mbar_init(fin, 1);
+      tma::fence_mbar_init();
+    }
+    __syncwarp();
+    tc::alloc(tslot, Cfg::TCOLS);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+  // rows beyond 3 Nz must read as zero from every chunk buffer: the row warps zero the
+  // A columns of all their lanes once (the unpacking later overwrites rows < 3 Nz)
+  if (warp >= 4 && warp < 8) {
+    const uint32_t zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint32_t tq = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+    for (int c = 0; c < NA * Cfg::ACOLS; c += 8) tc::st8(tq + c, zero);
+    tc::wait_st();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+
+  bool ok = true;
+  if (warp == 0) {
+    // ---- producer ----
+    const uint64_t once = tc::evict_first_policy();
+    int issued = 0;
+    for (int it = 0; it < n_it; ++it) {
+      const int s = it % NS;
+      if (it >= NS && !tc::warp_wait(&empty[s], (uint32_t)((it / NS - 1) & 1), lim)) {
+        ok = false;
+        break;
+      }
+      const int w = w0 + it * gs;
+      const Mirrors mi = mirrors_of(w, Nx, Ny);
+      const int nm = mi.nmx * mi.nmy;
+      unsigned char *st = stages + (size_t)s * Cfg::STAGE;
+      const float2 *q = qf + (size_t)w * BS;
+      tma::fence_proxy_async();
+      if (lane == 0) tma::mbar_expect_tx(&full[s], (uint32_t)((size_t)BS * 8 + (size_t)nm * CZ * 8));
+      __syncwarp();
+      const int ncopy = 1 + 2 * NZ + nm;
+      for (int j = lane; j < ncopy; j += 32) {
+        if (j == 0) {
+          tc::bulk_g2s_hint(st, q, (uint32_t)Cfg::TRI, &full[s], once);
+        } else if (j <= 2 * NZ) {
+          const int i = j - 1;
+          tc::bulk_g2s_hint(st + Cfg::TRI + (size_t)i * LDF * 8, q + 4 * P + i * NZ, (uint32_t)(NZ * 8), &full[s],
+                            once);
+        } else {
+          const int m = j - 1 - 2 * NZ;
+          const int mx = m % mi.nmx, my = m / mi.nmx;
+          tma::bulk_g2s(st + Cfg::TRI + Cfg::FULL + (size_t)m * CZ * 8, spec + mi.pos(mx, my, Nx) * ldz,
+                        (uint32_t)(CZ * 8), &full[s]);
+        }
+      }
+      ++issued;
+    }
+    // drain: the last NS issues must land before the CTA exits
+    for (int k = issued - NS > 0 ? issued - NS : 0; k < issued; ++k)
+      tma::mbar_wait_bounded(&full[k % NS], (uint32_t)((k / NS) & 1), kWaitLimit);
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      for (int it = 0; it < n_it && ok; ++it) {
+        const int bb = it & 1;
+        if (!tma::mbar_wait_bounded(&bfull[bb], (uint32_t)((it >> 1) & 1), lim) ||
+            (it >= 2 && !tma::mbar_wait_bounded(&dempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim))) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t d1 = tbase + Cfg::DCOL + 32 * bb, d2 = d1 + 16;
+        const uint32_t bsm = tma::smem_u32(bbuf + (size_t)bb * Cfg::BBUF);
+        for (int beta = 0; beta < 3 && ok; ++beta) {
+          const int g = 3 * it + beta, c = g % NA;
+          if (!tma::mbar_wait_bounded(&afull[c], (uint32_t)((g / NA) & 1), lim)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const uint32_t ahi = tbase + c * Cfg::ACOLS, alo = ahi + KC;
+          const uint32_t bhi = bsm + (uint32_t)(2 * beta) * (uint32_t)Cfg::BPART, blo = bhi + (uint32_t)Cfg::BPART;
+#pragma unroll
+          for (int ks = 0; ks < KC / 8; ++ks) {
+            const uint32_t acc = (beta | ks) != 0;
+            const uint64_t dh = tc::sdesc(bhi + 256u * ks, Cfg::LBO, Cfg::SBO);
+            const uint64_t dl = tc::sdesc(blo + 256u * ks, Cfg::LBO, Cfg::SBO);
+            tc::mma(d1, ahi + 8 * ks, dh, Cfg::IDESC, acc);
+            tc::mma(d2, ahi + 8 * ks, dl, Cfg::IDESC, acc);
+            tc::mma(d2, alo + 8 * ks, dh, Cfg::IDESC, 1u);
+          }
+          tc::commit(&aempty[c]);
+        }
+        if (!ok) break;
+        tc::commit(&bempty[bb]);
+        tc::commit(&dfull[bb]);
+      }
+      // drain: every MMA issued above completes before TMEM is released
+      tc::commit(fin);
+      tma::mbar_wait_bounded(fin, 0u, kWaitLimit);
+    }
+  } else if (warp >= 4 && (warp & 3) < Cfg::NQ) {
+    // ---- row warps: unpack, then the epilogue of the previous wavenumber ----
+    const int q = warp & 3, jw = (warp - 4) >> 2;  // quadrant, column share
+    const int row = 32 * q + lane;
+    const bool live = row < N3;
+    const int alpha = live ? row / NZ : 0, a = live ? row - alpha * NZ : 0;
+    const uint32_t tq = tbase + ((uint32_t)(32 * q) << 16);
+    auto epilogue = [&](int e) -> bool {
+      const int bb = e & 1;
+      if (!tc::warp_wait(&dfull[bb], (uint32_t)((e >> 1) & 1), lim)) return false;
+      tc::fence_after();
+      const uint32_t dc = tq + Cfg::DCOL + 32 * bb;
+      uint32_t v[8];
+      tc::ld2(dc + 2 * jw, v[0], v[1]);            // D1 Y_r of columns 2 jw, 2 jw + 1
+      tc::ld2(dc + 8 + 2 * jw, v[2], v[3]);        // D1 Y_i
+      tc::ld2(dc + 16 + 2 * jw, v[4], v[5]);       // D2 Y_r
+      tc::ld2(dc + 24 + 2 * jw, v[6], v[7]);       // D2 Y_i
+      tc::wait_ld();
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::arrive(&dempty[bb]);
+      if (live) {
+        const Mirrors mw = mirrors_of(w0 + e * gs, Nx, Ny);
+        const int ncol = mw.nmx * mw.nmy * R;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = 2 * jw + h;
+          if (col < ncol) {
+            const int m = col / R, r = col - m * R;
+            const int mx = m % mw.nmx, my = m / mw.nmx;
+            float2 y = make_float2(__uint_as_float(v[h]) + __uint_as_float(v[4 + h]),
+                                   __uint_as_float(v[2 + h]) + __uint_as_float(v[6 + h]));
+            if ((alpha == 0 && mx == 1) || (alpha == 1 && my == 1)) { y.x = -y.x; y.y = -y.y; }
+            spec[mw.pos(mx, my, Nx) * ldz + r * N3 + row] = y;
+          }
+        }
+      }
+      return true;
+    };
+    for (int it = 0; it < n_it && ok; ++it) {
+      const int s = it % NS;
+      if (!tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim)) { ok = false; break; }
+      const unsigned char *st = stages + (size_t)s * Cfg::STAGE;
+      const float2 *tri = reinterpret_cast<const float2 *>(st);
+      const float2 *fb = reinterpret_cast<const float2 *>(st + Cfg::TRI);
+      for (int beta = 0; beta < 3; ++beta) {
+        const int g = 3 * it + beta, c = g % NA;
+        if (g >= NA && !tc::warp_wait(&aempty[c], (uint32_t)((g / NA - 1) & 1), lim)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        uint32_t rh[EPW], ih[EPW], rl[EPW], il[EPW];
+#pragma unroll
+        for (int e = 0; e < EPW; ++e) {
+          const int b = jw * EPW + e;
+          float2 m = make_float2(0.f, 0.f);
+          if (live) {
+            const bool fullk = (alpha == 2) != (beta == 2);
+            if (!fullk) {
+              const int kind = alpha == beta ? alpha : 3;
+              const int lo = a < b ? a : b, hi = a < b ? b : a;
+              m = tri[kind * P + ((lo * (2 * NZ - 1) - lo * lo) >> 1) + hi];
+            } else if (beta == 2) {
+              m = fb[(alpha * NZ + a) * LDF + b];
+            } else {
+              m = fb[(beta * NZ + b) * LDF + a];
+              m.x = -m.x;
+              m.y = -m.y;
+            }
+          }
+          tc::split(m.x, rh[e], rl[e]);
+          tc::split(m.y, ih[e], il[e]);
+        }
+        const uint32_t ab = tq + c * Cfg::ACOLS + jw * EPW;
+        if constexpr (EPW == 8) {
+          tc::st8(ab, rh);
+          tc::st8(ab + NZ, ih);
+          tc::st8(ab + KC, rl);
+          tc::st8(ab + KC + NZ, il);
+        } else {
+          tc::st4(ab, rh);
+          tc::st4(ab + NZ, ih);
+          tc::st4(ab + KC, rl);
+          tc::st4(ab + KC + NZ, il);
+        }
+        tc::wait_st();
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::arrive(&afull[c]);
+      }
+      if (!ok) break;
+      __syncwarp();
+      if (lane == 0) tc::arrive(&empty[s]);
+      if (it >= 1 && !epilogue(it - 1)) { ok = false; break; }
+    }
+    if (ok && n_it >= 1) ok = epilogue(n_it - 1);
+  } else {
+    // ---- B warps: warps 2, 3 and the row warps of quadrants without rows ----
+    const int bw = warp < 4 ? warp - 2 : 2 + ((warp - 4) >> 2) * (4 - Cfg::NQ) + ((warp & 3) - Cfg::NQ);
+    const int bt = bw * 32 + lane, nbt = Cfg::NB * 32;
+    for (int it = 0; it < n_it && ok; ++it) {
+      const int s = it % NS, bb = it & 1;
+      if (!tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim) ||
+          (it >= 2 && !tc::warp_wait(&bempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim))) {
+        ok = false;
+        break;
+      }
+      const Mirrors mw = mirrors_of(w0 + it * gs, Nx, Ny);
+      const int ncol = mw.nmx * mw.nmy * R;
+      const float2 *xr = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE + Cfg::TRI + Cfg::FULL);
+      unsigned char *bp = bbuf + (size_t)bb * Cfg::BBUF;
+      // entry e: chunk beta, core-matrix index (k / 4, n / 8), then (n % 8, k % 4) in the
+      // thread index so that a warp writes one 128-byte core matrix
+      for (int e = bt; e < 3 * KC * 16; e += nbt) {
+        const int within = e & 31, cm = e >> 5;
+        const int nn = within >> 2, kk = within & 3;
+        const int cmk = cm % (KC / 4), rest = cm / (KC / 4);
+        const int nh = rest & 1, beta = rest >> 1;
+        const int n = nh * 8 + nn, k = cmk * 4 + kk;
+        const int cc = n & 7;  // complex column
+        const bool second = k >= NZ;
+        const int zrow = beta * NZ + (second ? k - NZ : k);
+        float val = 0.f;
+        if (cc < ncol) {
+          const int m = cc / R, r = cc - m * R;
+          const int mx = m % mw.nmx, my = m / mw.nmx;
+          float2 x = xr[(size_t)m * CZ + r * N3 + zrow];
+          if ((beta == 0 && mx == 1) || (beta == 1 && my == 1)) { x.x = -x.x; x.y = -x.y; }
+          // rows k < Nz multiply M_r: (X_r | X_i); rows k >= Nz multiply M_i: (-X_i | X_r)
+          val = !second ? (n < 8 ? x.x : x.y) : (n < 8 ? -x.y : x.x);
+        }
+        uint32_t h, l;
+        tc::split(val, h, l);
+        const size_t off = (size_t)(2 * beta) * Cfg::BPART + (size_t)nn * 16 + (size_t)nh * Cfg::SBO +
+                           (size_t)cmk * 128 + (size_t)kk * 4;
+        *reinterpret_cast<uint32_t *>(bp + off) = h;
+        *reinterpret_cast<uint32_t *>(bp + off + Cfg::BPART) = l;
+      }
+      tma::fence_proxy_async();  // the MMA reads B through the async proxy
+      __syncwarp();
+      if (lane == 0) {
+        tc::arrive(&bfull[bb]);
+        tc::arrive(&empty[s]);
+      }
+    }
+  }
+  if (!ok && lane == 0) atomicExch(err, kContractTimeout);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::dealloc(tbase, Cfg::TCOLS);
+}
+
+}  // namespace ie

@@ -20,7 +20,7 @@ IE_ERR_ARG = -1
 IE_ERR_SCRATCH = -6
 IE_ERR_TIMEOUT = -7
 IE_C64, IE_C128 = 0, 1
-N_CONTRACT_VARIANTS = 6
+N_CONTRACT_VARIANTS = 7
 IE_C128_DF = 7
 IE_FP64, IE_MIXED, IE_MIXED_FP64K = 0, 1, 2
 IE_PROF_PRODUCT_C64, IE_PROF_PRODUCT_C128, IE_PROF_GS_C64, IE_PROF_GS_C128, IE_PROF_GIVENS = 2, 3, 4, 5, 6
@@ -274,9 +274,9 @@ class Context:
         return s, info
 
     def contract_tuning(self):
-        """(variants for 1..4 right-hand sides per instance, autotuner ms [4][6])."""
+        """(variants for 1..4 right-hand sides per instance, autotuner ms [4][N_CONTRACT_VARIANTS])."""
         v = np.zeros(4, dtype=np.int32)
-        ms = np.zeros((4, 6), dtype=np.float64)
+        ms = np.zeros((4, N_CONTRACT_VARIANTS), dtype=np.float64)
         _check(self._lib.ie_contract_tuning(self.ctx, v.ctypes.data, ms.ctypes.data), "ie_contract_tuning")
         return v, ms
 
