@@ -587,7 +587,10 @@ def run_matvec_only(args):
     model = workload(args.workload)
     g = model.grid
     R = 2
-    ctx = ie.Context(g, model.layers, model.sigma_a, model.freqs[:1], None, max_rhs=R)
+    ctx = ie.Context(g, model.layers, model.sigma_a, model.freqs[:1], None, max_rhs=R,
+                     autotune=args.variant < 0)
+    if args.variant >= 0:
+        ctx.set_contract_variant(R, args.variant)
     xs = torch.randn((R, 3, g.nz, g.ny, g.nx), dtype=torch.complex64, device="cuda")
     ys = torch.empty_like(xs)
     torch.cuda.synchronize()
@@ -602,7 +605,12 @@ def run_matvec_only(args):
     with torch.cuda.stream(ext):
         e1.record()
     e1.synchronize()
-    print(json.dumps({"mode": "matvec", "workload": args.workload, "ms_per_product": e0.elapsed_time(e1) / args.steps}))
+    if ctx.sync() != ie.IE_OK:
+        raise RuntimeError("a contraction wait ran out")
+    kern = ctx.profile_matvec(0, R, ie.IE_C64, max(args.steps, 1))
+    print(json.dumps({"mode": "matvec", "workload": args.workload, "variant": args.variant,
+                      "ms_per_product": e0.elapsed_time(e1) / args.steps,
+                      "kernel_ms": dict(zip(("rows_fwd", "cols_fwd", "contract", "cols_inv", "rows_inv"), kern))}))
     ctx.close()
 
 
@@ -728,6 +736,8 @@ def main():
     ap.add_argument("--threads", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--iters", type=int, default=3, help=argparse.SUPPRESS)
     ap.add_argument("--mode", choices=["solve", "matvec", "batch", "gradient"], default="solve")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="matvec mode: force this contraction variant (default: the autotuner's choice)")
     args = ap.parse_args()
     if args.cpu_sample:
         run_cpu_sample(args)

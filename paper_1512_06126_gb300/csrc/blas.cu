@@ -480,6 +480,197 @@ __global__ void __launch_bounds__(kT) cgs_second_kernel(const C<T> *__restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Gram-Schmidt passes for FP64 vectors in double-float arithmetic (the inner solves of
+// IE_MIXED_FP64K).  GB300 runs FP64 at about 1/64 of the FP32 rate, so the FP64 dot and
+// subtract passes are bound by the FP64 pipe, not by their basis reads.  Here every FP64
+// number x is taken as hi + lo (hi: x's leading 24 significant bits, lo: the next 23,
+// so x = hi + lo up to 2^-46 |x|), split with integer operations on its bits, and the
+// products go through the compensated scheme of Ogita, Rump and Oishi: TwoProduct by
+// FMA, TwoSum into a second FP32 accumulator, the cross terms hi lo added to it (lo lo
+// dropped).  A dot product is then as accurate as one in twice FP32 precision (about
+// 2^-46 relative to the sum of magnitudes, against 2^-53 in FP64); the vectors stay
+// FP64 in memory and the partial sums are combined in FP64.  Same chunking, partial
+// layout and flags as cgs_dot_kernel / cgs_sub_kernel.
+// ---------------------------------------------------------------------------
+struct Df {
+  float s, c;  // value s + c
+};
+
+// x = hi + lo + O(2^-46 |x|) for 2^-103 <= |x| < 2^127 from the bits of x; outside that
+// range (zero included) hi = fl32(x), lo = 0
+__device__ __forceinline__ void dsplit(double x, float &hi, float &lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t uh = (uint32_t)(u >> 32), ul = (uint32_t)u;
+  const uint32_t sgn = uh & 0x80000000u;
+  const uint32_t e = (uh >> 20) & 0x7FFu;  // biased FP64 exponent
+  if (e >= 920u && e <= 1150u) {
+    const uint32_t mh = ((uh & 0xFFFFFu) << 3) | (ul >> 29);  // significand bits 1..23
+    const uint32_t ml = (ul >> 6) & 0x7FFFFFu;                // bits 24..46
+    hi = __uint_as_float(sgn | ((e - 896u) << 23) | mh);
+    // 0.m24..m46 = (1.m24..m46 - 1) exactly, times 2^(e - 1023 - 23) with the sign
+    lo = __fmul_rn(__fsub_rn(__uint_as_float(0x3F800000u | ml), 1.0f), __uint_as_float(sgn | ((e - 919u) << 23)));
+  } else {
+    hi = __double2float_rn(x);
+    lo = 0.0f;
+  }
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+
+// acc += (ah + al)(bh + bl)
+__device__ __forceinline__ void df_fma(Df &acc, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float pe = __fmaf_rn(ah, bh, -p);
+  pe = __fmaf_rn(ah, bl, pe);
+  pe = __fmaf_rn(al, bh, pe);
+  float t, e;
+  two_sum(acc.s, p, t, e);
+  acc.s = t;
+  acc.c = __fadd_rn(acc.c, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ double df_value(const Df &a) { return (double)a.s + (double)a.c; }
+
+constexpr int kDfG = 4;  // basis vectors per unit of the dot pass (the chunk of x is split once per unit)
+
+// part(r, i, c) = sum_chunk conj(V_i) x and, for the first unit of a chunk, npart(r, c)
+// = sum_chunk |x|^2; units (r, c, group of kDfG basis vectors), one warp each
+__global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const double2 *__restrict__ V, const double2 *__restrict__ x,
+                                                        double2 *__restrict__ part, double *__restrict__ npart, int k1,
+                                                        int R, long long n, int nch) {
+  constexpr int CH = GsShape<double>::kCh;
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (kT / 32);
+  const int ng = (k1 + kDfG - 1) / kDfG;
+  const int units = R * nch * ng;
+  for (int u = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); u < units; u += nw) {
+    const int ig = u % ng, rc = u / ng;
+    const int c = rc % nch, r = rc / nch;
+    const long long e0 = (long long)c * CH;
+    const double2 *xr = x + (long long)r * n + e0;
+    const long long lim = n - e0;
+    Df re[kDfG], im[kDfG], nn = {0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < kDfG; ++t) re[t] = im[t] = Df{0.f, 0.f};
+#pragma unroll 2
+    for (int j = 0; j < CH / 32; ++j) {
+      const int l = j * 32 + lane;
+      if (l >= lim) break;
+      const double2 xv = __ldg(xr + l);
+      float xrh, xrl, xih, xil;
+      dsplit(xv.x, xrh, xrl);
+      dsplit(xv.y, xih, xil);
+      if (ig == 0) {
+        df_fma(nn, xrh, xrl, xrh, xrl);
+        df_fma(nn, xih, xil, xih, xil);
+      }
+#pragma unroll
+      for (int t = 0; t < kDfG; ++t) {
+        const int i = ig * kDfG + t;
+        if (i < k1) {
+          const double2 vv = __ldg(V + ((long long)i * R + r) * n + e0 + l);
+          float vrh, vrl, vih, vil;
+          dsplit(vv.x, vrh, vrl);
+          dsplit(vv.y, vih, vil);
+          // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
+          df_fma(re[t], vrh, vrl, xrh, xrl);
+          df_fma(re[t], vih, vil, xih, xil);
+          df_fma(im[t], vrh, vrl, xih, xil);
+          df_fma(im[t], -vih, -vil, xrh, xrl);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kDfG; ++t) {
+      const int i = ig * kDfG + t;
+      const double ax = warp_sum(df_value(re[t])), ay = warp_sum(df_value(im[t]));
+      if (lane == 0 && i < k1) part[((long long)r * k1 + i) * nch + c] = make_double2(ax, ay);
+    }
+    if (ig == 0) {
+      const double s = warp_sum(df_value(nn));
+      if (lane == 0) npart[(long long)r * nch + c] = s;
+    }
+  }
+}
+
+// x[r] -= sum_{i<k1} h[r * ldh + i] V_i[r] in double-float; otherwise as cgs_sub_kernel
+// (vout, nrm, oflag: the normalised next basis vector where no second projection runs)
+__global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restrict__ V, double2 *__restrict__ x,
+                                                        const double2 *__restrict__ h, double *__restrict__ npart,
+                                                        int k1, int R, long long n, int nbs, int ldh,
+                                                        double2 *__restrict__ vout, const double *__restrict__ nrm,
+                                                        const int *__restrict__ oflag) {
+  constexpr int EPT = GsShape<double>::kSubEPT;
+  __shared__ float4 hs[64];  // -h split: (-hr hi, -hr lo, -hi hi, -hi lo)
+  __shared__ double2 shn[kT / 32];
+  const int r = blockIdx.y;
+  const bool scaled = vout && !oflag[r];
+  const int tid = threadIdx.x;
+  if (tid < k1) {
+    const double2 hv = h[(long long)r * ldh + tid];
+    float a, b, c, d;
+    dsplit(-hv.x, a, b);
+    dsplit(-hv.y, c, d);
+    hs[tid] = make_float4(a, b, c, d);
+  }
+  __syncthreads();
+  const double sc = scaled && nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0;
+  double2 *xr = x + (long long)r * n;
+  double2 *vr = vout ? vout + (long long)r * n : nullptr;
+  double nacc = 0.0;
+  for (long long c0 = (long long)blockIdx.x * kT * EPT; c0 < n; c0 += (long long)nbs * kT * EPT) {
+    Df ar[EPT], ai[EPT];
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+      const long long e = c0 + j * kT + tid;
+      const double2 v = e < n ? xr[e] : make_double2(0.0, 0.0);
+      dsplit(v.x, ar[j].s, ar[j].c);
+      dsplit(v.y, ai[j].s, ai[j].c);
+    }
+#pragma unroll 1
+    for (int i = 0; i < k1; ++i) {
+      const float4 hv = hs[i];  // -h
+      const double2 *vi = V + ((long long)i * R + r) * n + c0 + tid;
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) {
+        if (c0 + j * kT + tid < n) {
+          const double2 a = __ldg(vi + j * kT);
+          float vrh, vrl, vih, vil;
+          dsplit(a.x, vrh, vrl);
+          dsplit(a.y, vih, vil);
+          // x += (-h) v: re += (-hr) vr - (-hi) vi, im += (-hr) vi + (-hi) vr
+          df_fma(ar[j], hv.x, hv.y, vrh, vrl);
+          df_fma(ar[j], -hv.z, -hv.w, vih, vil);
+          df_fma(ai[j], hv.x, hv.y, vih, vil);
+          df_fma(ai[j], hv.z, hv.w, vrh, vrl);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+      const long long e = c0 + j * kT + tid;
+      if (e < n) {
+        const double2 v = make_double2(df_value(ar[j]), df_value(ai[j]));
+        if (scaled) {
+          vr[e] = make_double2(v.x * sc, v.y * sc);
+        } else {
+          xr[e] = v;
+          nacc = fma(v.x, v.x, nacc);
+          nacc = fma(v.y, v.y, nacc);
+        }
+      }
+    }
+  }
+  if (scaled) return;
+  const double2 sres = block_reduce(make_double2(nacc, 0.0), shn);
+  if (tid == 0) npart[(long long)r * nbs + blockIdx.x] = sres.x;
+}
+
 // chunks of the dot pass per right-hand side
 template <typename T> int cgs_nch(long long n) {
   return (int)((n + GsShape<T>::kCh - 1) / GsShape<T>::kCh);
@@ -551,6 +742,23 @@ void gmres_norm(const C<T> *w, double *part, double *out, int R, long long n, cu
   norm_final<<<R, kT, 0, s>>>(part, out, nb);
 }
 
+int dot_df_per_sm() {
+  static int v = 0;
+  if (v == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, cgs_dot_df_kernel, kT, 0) != cudaSuccess || v < 1)) {
+    cudaGetLastError();
+    v = 1;
+  }
+  return v;
+}
+int sub_df_per_sm() {
+  static int v = 0;
+  if (v == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, cgs_sub_df_kernel, kT, 0) != cudaSuccess || v < 1)) {
+    cudaGetLastError();
+    v = 1;
+  }
+  return v;
+}
+
 template <typename T> int second_blocks() {
   static int v = 0;
   if (v == 0) {
@@ -569,18 +777,40 @@ template <typename T> int second_blocks() {
 
 template <typename T>
 int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double2 *h2, double2 *part, double *npart,
-                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s) {
+                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s, bool df) {
   if (k1 < 1 || k1 > 64 || R < 1 || R > 16) return -1;
+  df = df && sizeof(T) == 8;
   const int nch = cgs_nch<T>(n), nbs = cgs_nbs<T>(n, R);
   double *np0 = npart, *np1 = npart + (long long)R * nch;
   unsigned *tick = reinterpret_cast<unsigned *>(flag + 16);
-  const int gd = cgs_dot_blocks<T>((long long)R * nch * k1);
   count_launches(4);
   // first projection: h1 = V^H w and ||w||; ||w'|| from the difference of squares
-  cgs_dot_kernel<T><<<gd, kT, 0, s>>>(V, w, part, np0, nullptr, k1, R, n, nch);
+  if constexpr (sizeof(T) == 8) {
+    if (df) {
+      const long long units = (long long)R * nch * ((k1 + kDfG - 1) / kDfG);
+      const long long maxw = (long long)dot_df_per_sm() * sm_count() * (kT / 32);
+      const long long per = (units + maxw - 1) / maxw;
+      const int gd = (int)((((units + per - 1) / per) + kT / 32 - 1) / (kT / 32));
+      cgs_dot_df_kernel<<<gd < 1 ? 1 : gd, kT, 0, s>>>(V, w, part, np0, k1, R, n, nch);
+    }
+  }
+  if (!df) {
+    const int gd = cgs_dot_blocks<T>((long long)R * nch * k1);
+    cgs_dot_kernel<T><<<gd, kT, 0, s>>>(V, w, part, np0, nullptr, k1, R, n, nch);
+  }
   cgs_hsum_kernel<<<dim3(k1 + 1, R), kT, 0, s>>>(part, np0, h1, h2, nrm, flag, tick, k1, R, nch, ldh);
   // w' = w - V h1, written normalised into vnext where no second projection is needed
-  cgs_sub_kernel<T><<<dim3(nbs, R), kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nbs, ldh, vnext, nrm, flag);
+  if constexpr (sizeof(T) == 8) {
+    if (df) {
+      const long long chunks = (n + (long long)kT * GsShape<double>::kSubEPT - 1) / ((long long)kT * GsShape<double>::kSubEPT);
+      long long maxb = ((long long)sub_df_per_sm() * sm_count()) / R;
+      if (maxb < 1) maxb = 1;
+      const long long per = (chunks + maxb - 1) / maxb;
+      const int nbd = (int)((chunks + per - 1) / per);
+      cgs_sub_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(V, w, h1, np1, k1, R, n, nbd, ldh, vnext, nrm, flag);
+    }
+  }
+  if (!df) cgs_sub_kernel<T><<<dim3(nbs, R), kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nbs, ldh, vnext, nrm, flag);
   // second projection where the first cancelled too much (h2 = 0 elsewhere)
   const C<T> *Va = V;
   C<T> *wa = w, *va = vnext;
@@ -804,7 +1034,7 @@ void vec_round(const double2 *x, float2 *y, long long n, cudaStream_t s) {
                                cudaStream_t);                                                                       \
   template void gmres_norm<T>(const C<T> *, double *, double *, int, long long, cudaStream_t);                      \
   template int gmres_orthogonalize<T>(const C<T> *, C<T> *, C<T> *, double2 *, double2 *, double2 *, double *,      \
-                                      double *, int *, int, int, long long, int, cudaStream_t);                     \
+                                      double *, int *, int, int, long long, int, cudaStream_t, bool);               \
   template void gmres_scale<T>(const C<T> *, C<T> *, const double *, int, long long, cudaStream_t);                 \
   template void vec_sub<T>(const C<T> *, const C<T> *, C<T> *, long long, cudaStream_t);                           \
   template void vec_add<T>(const C<T> *, double2 *, long long, cudaStream_t);

@@ -76,6 +76,7 @@ struct ie_ctx {
   int *pin_active = nullptr;                   // pinned: active counts (slot 0: cycle start, 1..4: iterations),
                                                // slot 5: the contraction error word
   int *err = nullptr;                          // device: contraction error word of this context's launches
+  bool gs_df = true;                           // IE_MIXED_FP64K inner Gram-Schmidt in double-float arithmetic
   cudaEvent_t pin_ev[4] = {};
   void *jfac = nullptr, *gdiv = nullptr;       // per cell: 2 s gamma; (dgamma/dln sigma_a) / gamma (0 off the anomaly)
   void *efac = nullptr;                        // per cell: 1 / a = 2 s / (sigma_a + conj sigma_b) (E = U / a)
@@ -576,7 +577,7 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
       sp_op.end();
       ProfSpan sp_gs(c, sizeof(T) == 4 ? IE_PROF_GS_C64 : IE_PROF_GS_C128);
       if (ie::gmres_orthogonalize<T>(Vb, w, Vb + (long long)(k + 1) * nR, h1, h2, c->part, c->nrmpart, c->nrm,
-                                  c->gsflag, k + 1, R, n, ldh, s) != 0)
+                                  c->gsflag, k + 1, R, n, ldh, s, single && c->gs_df) != 0)
         return IE_ERR_ARG;
       sp_gs.end();
       ProfSpan sp_gv(c, IE_PROF_GIVENS);
