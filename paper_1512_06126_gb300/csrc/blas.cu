@@ -497,23 +497,27 @@ struct Df {
   float s, c;  // value s + c
 };
 
-// x = hi + lo + O(2^-46 |x|) for 2^-103 <= |x| < 2^127 from the bits of x; outside that
-// range (zero included) hi = fl32(x), lo = 0
+// x = hi + lo + O(2^-46 |x|) for 2^-103 <= |x| < 2^127, from the bits of x with integer
+// operations only (no FP64 instruction): below that range hi = lo = 0 (a relative
+// contribution below 2^-103 of a unit vector), above it hi = +-Inf, and NaN stays NaN, so
+// that a non-finite vector still fails every test downstream
 __device__ __forceinline__ void dsplit(double x, float &hi, float &lo) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const uint32_t uh = (uint32_t)(u >> 32), ul = (uint32_t)u;
   const uint32_t sgn = uh & 0x80000000u;
-  const uint32_t e = (uh >> 20) & 0x7FFu;  // biased FP64 exponent
-  if (e >= 920u && e <= 1150u) {
-    const uint32_t mh = ((uh & 0xFFFFFu) << 3) | (ul >> 29);  // significand bits 1..23
-    const uint32_t ml = (ul >> 6) & 0x7FFFFFu;                // bits 24..46
-    hi = __uint_as_float(sgn | ((e - 896u) << 23) | mh);
-    // 0.m24..m46 = (1.m24..m46 - 1) exactly, times 2^(e - 1023 - 23) with the sign
-    lo = __fmul_rn(__fsub_rn(__uint_as_float(0x3F800000u | ml), 1.0f), __uint_as_float(sgn | ((e - 919u) << 23)));
-  } else {
-    hi = __double2float_rn(x);
-    lo = 0.0f;
-  }
+  const uint32_t e = (uh >> 20) & 0x7FFu;                    // biased FP64 exponent
+  const uint32_t mh = ((uh & 0xFFFFFu) << 3) | (ul >> 29);  // significand bits 1..23
+  const uint32_t ml = (ul >> 6) & 0x7FFFFFu;                // bits 24..46
+  uint32_t h = sgn | ((e - 896u) << 23) | mh;
+  // 0.m24..m46 = (1.m24..m46 - 1) exactly, times 2^(e - 1023 - 23) with the sign
+  float l = __fmul_rn(__fsub_rn(__uint_as_float(0x3F800000u | ml), 1.0f), __uint_as_float(sgn | ((e - 919u) << 23)));
+  const bool small = e < 920u, big = e > 1150u;
+  const bool nan = e == 0x7FFu && ((uh & 0xFFFFFu) | ul) != 0u;
+  h = small ? sgn : h;
+  h = big ? (sgn | (nan ? 0x7FC00000u : 0x7F800000u)) : h;
+  l = (small || big) ? 0.0f : l;
+  hi = __uint_as_float(h);
+  lo = l;
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {

@@ -104,11 +104,29 @@ __device__ __forceinline__ uint64_t evict_first_policy() {
   return p;
 }
 
+// Bounded wait with a suspend-time hint: a polling thread sleeps until the phase
+// completes or kSuspendNs elapse, instead of spinning (the warps of this kernel wait most
+// of the time and would otherwise take the issue slots of the working ones).  The poll
+// limit of a launch is scaled down accordingly (a poll lasts up to kSuspendNs).
+constexpr uint32_t kSuspendNs = 10000;
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t phase, long long lim) {
+  for (long long i = 0; i < lim; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tma::smem_u32(bar)), "r"(phase), "r"(kSuspendNs)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 // A bounded wait whose outcome is the same in every lane of the warp (all lanes poll;
 // the warp proceeds only if every lane saw the phase complete), so that the warp's
 // .sync.aligned TMEM instructions never run divergently after a timeout.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t phase, long long lim) {
-  return __all_sync(0xffffffffu, tma::mbar_wait_bounded(bar, phase, lim)) != 0;
+  return __all_sync(0xffffffffu, wait(bar, phase, lim)) != 0;
 }
 // x = hi + lo exactly: hi = x rounded to TF32 (10 fraction bits), lo = x - hi
 __device__ __forceinline__ void split(float x, uint32_t &hi, uint32_t &lo) {
@@ -165,7 +183,7 @@ struct TcCfg {
 template <int NZ, int R>
 __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     contract_tc_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err,
-                       long long lim) {
+                       long long lim_polls) {
   using Cfg = TcCfg<NZ, R>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LDF = Cfg::LDF, NS = Cfg::NS, NA = Cfg::NA;
   constexpr int KC = Cfg::KC, EPW = Cfg::EPW;
@@ -180,6 +198,10 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
   const int nf = (Nx + 1) * (Ny + 1);
   const int w0 = blockIdx.x, gs = gridDim.x;
   const int n_it = w0 < nf ? (nf - 1 - w0) / gs + 1 : 0;
+  // a poll lasts up to kSuspendNs: the poll limits are scaled so that the default wait
+  // limit still ends a stuck wait within seconds (0 stays 0: give up at once)
+  const long long lim = lim_polls > 0 ? (lim_polls >> 8 > 0 ? lim_polls >> 8 : 1) : 0;
+  constexpr long long kDrain = kWaitLimit >> 8;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -257,37 +279,39 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     }
     // drain: the last NS issues must land before the CTA exits
     for (int k = issued - NS > 0 ? issued - NS : 0; k < issued; ++k)
-      tma::mbar_wait_bounded(&full[k % NS], (uint32_t)((k / NS) & 1), kWaitLimit);
+      tc::wait(&full[k % NS], (uint32_t)((k / NS) & 1), kDrain);
   } else if (warp == 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
+      // the descriptor's start-address field holds the byte address / 16 (shared memory
+      // addresses stay below 2^18, so adding an offset / 16 never carries out of it): a
+      // k-step (256 bytes further) adds 16
+      const uint64_t bdesc = tc::sdesc(tma::smem_u32(bbuf), Cfg::LBO, Cfg::SBO);
       for (int it = 0; it < n_it && ok; ++it) {
         const int bb = it & 1;
-        if (!tma::mbar_wait_bounded(&bfull[bb], (uint32_t)((it >> 1) & 1), lim) ||
-            (it >= 2 && !tma::mbar_wait_bounded(&dempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim))) {
+        if (!tc::wait(&bfull[bb], (uint32_t)((it >> 1) & 1), lim) ||
+            (it >= 2 && !tc::wait(&dempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim))) {
           ok = false;
           break;
         }
         tc::fence_after();
         const uint32_t d1 = tbase + Cfg::DCOL + 32 * bb, d2 = d1 + 16;
-        const uint32_t bsm = tma::smem_u32(bbuf + (size_t)bb * Cfg::BBUF);
         for (int beta = 0; beta < 3 && ok; ++beta) {
           const int g = 3 * it + beta, c = g % NA;
-          if (!tma::mbar_wait_bounded(&afull[c], (uint32_t)((g / NA) & 1), lim)) {
+          if (!tc::wait(&afull[c], (uint32_t)((g / NA) & 1), lim)) {
             ok = false;
             break;
           }
           tc::fence_after();
           const uint32_t ahi = tbase + c * Cfg::ACOLS, alo = ahi + KC;
-          const uint32_t bhi = bsm + (uint32_t)(2 * beta) * (uint32_t)Cfg::BPART, blo = bhi + (uint32_t)Cfg::BPART;
+          const uint64_t dh0 = bdesc + (((size_t)bb * Cfg::BBUF + (size_t)(2 * beta) * Cfg::BPART) >> 4);
+          const uint64_t dl0 = dh0 + (Cfg::BPART >> 4);
 #pragma unroll
           for (int ks = 0; ks < KC / 8; ++ks) {
             const uint32_t acc = (beta | ks) != 0;
-            const uint64_t dh = tc::sdesc(bhi + 256u * ks, Cfg::LBO, Cfg::SBO);
-            const uint64_t dl = tc::sdesc(blo + 256u * ks, Cfg::LBO, Cfg::SBO);
-            tc::mma(d1, ahi + 8 * ks, dh, Cfg::IDESC, acc);
-            tc::mma(d2, ahi + 8 * ks, dl, Cfg::IDESC, acc);
-            tc::mma(d2, alo + 8 * ks, dh, Cfg::IDESC, 1u);
+            tc::mma(d1, ahi + 8 * ks, dh0 + 16u * ks, Cfg::IDESC, acc);
+            tc::mma(d2, ahi + 8 * ks, dl0 + 16u * ks, Cfg::IDESC, acc);
+            tc::mma(d2, alo + 8 * ks, dh0 + 16u * ks, Cfg::IDESC, 1u);
           }
           tc::commit(&aempty[c]);
         }
@@ -297,7 +321,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
       }
       // drain: every MMA issued above completes before TMEM is released
       tc::commit(fin);
-      tma::mbar_wait_bounded(fin, 0u, kWaitLimit);
+      tc::wait(fin, 0u, kDrain);
     }
   } else if (warp >= 4 && (warp & 3) < Cfg::NQ) {
     // ---- row warps: unpack, then the epilogue of the previous wavenumber ----
@@ -306,6 +330,29 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     const bool live = row < N3;
     const int alpha = live ? row / NZ : 0, a = live ? row - alpha * NZ : 0;
     const uint32_t tq = tbase + ((uint32_t)(32 * q) << 16);
+    // where this thread's entries of a block sit in a stage (complex index; the same for
+    // every wavenumber), two 16-bit offsets per register; entries of zx = -xz^T and
+    // zy = -yz^T are negated (chunks beta < 2 of the rows of z)
+    uint32_t offp[3][EPW / 2];
+#pragma unroll
+    for (int beta = 0; beta < 3; ++beta) {
+#pragma unroll
+      for (int e = 0; e < EPW; ++e) {
+        const int b = jw * EPW + e;
+        int off;
+        if ((alpha == 2) == (beta == 2)) {
+          const int kind = alpha == beta ? alpha : 3;  // xx, yy, zz on the diagonal; xy off it
+          const int lo = a < b ? a : b, hi = a < b ? b : a;
+          off = kind * P + ((lo * (2 * NZ - 1) - lo * lo) >> 1) + hi;
+        } else if (beta == 2) {
+          off = (int)(Cfg::TRI / 8) + (alpha * NZ + a) * LDF + b;
+        } else {
+          off = (int)(Cfg::TRI / 8) + (beta * NZ + b) * LDF + a;
+        }
+        if (e & 1) offp[beta][e >> 1] |= (uint32_t)off << 16;
+        else offp[beta][e >> 1] = (uint32_t)off;
+      }
+    }
     auto epilogue = [&](int e) -> bool {
       const int bb = e & 1;
       if (!tc::warp_wait(&dfull[bb], (uint32_t)((e >> 1) & 1), lim)) return false;
@@ -341,9 +388,8 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     for (int it = 0; it < n_it && ok; ++it) {
       const int s = it % NS;
       if (!tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim)) { ok = false; break; }
-      const unsigned char *st = stages + (size_t)s * Cfg::STAGE;
-      const float2 *tri = reinterpret_cast<const float2 *>(st);
-      const float2 *fb = reinterpret_cast<const float2 *>(st + Cfg::TRI);
+      const float2 *st = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE);
+#pragma unroll
       for (int beta = 0; beta < 3; ++beta) {
         const int g = 3 * it + beta, c = g % NA;
         if (g >= NA && !tc::warp_wait(&aempty[c], (uint32_t)((g / NA - 1) & 1), lim)) {
@@ -351,25 +397,13 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
           break;
         }
         tc::fence_after();
+        const bool neg = alpha == 2 && beta < 2;
         uint32_t rh[EPW], ih[EPW], rl[EPW], il[EPW];
 #pragma unroll
         for (int e = 0; e < EPW; ++e) {
-          const int b = jw * EPW + e;
-          float2 m = make_float2(0.f, 0.f);
-          if (live) {
-            const bool fullk = (alpha == 2) != (beta == 2);
-            if (!fullk) {
-              const int kind = alpha == beta ? alpha : 3;
-              const int lo = a < b ? a : b, hi = a < b ? b : a;
-              m = tri[kind * P + ((lo * (2 * NZ - 1) - lo * lo) >> 1) + hi];
-            } else if (beta == 2) {
-              m = fb[(alpha * NZ + a) * LDF + b];
-            } else {
-              m = fb[(beta * NZ + b) * LDF + a];
-              m.x = -m.x;
-              m.y = -m.y;
-            }
-          }
+          const uint32_t off = (offp[beta][e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+          float2 m = live ? st[off] : make_float2(0.f, 0.f);
+          if (neg) { m.x = -m.x; m.y = -m.y; }
           tc::split(m.x, rh[e], rl[e]);
           tc::split(m.y, ih[e], il[e]);
         }
@@ -398,6 +432,11 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     if (ok && n_it >= 1) ok = epilogue(n_it - 1);
   } else {
     // ---- B warps: warps 2, 3 and the row warps of quadrants without rows ----
+    // One complex value x = X[col][beta Nz + b] (mirror signs applied) per thread and
+    // step; it fills B rows b (which multiply M_r: (X_r | X_i)) and Nz + b (which
+    // multiply M_i: (-X_i | X_r)) of columns col and 8 + col, hi and lo.  Threads of a
+    // warp take (col, b % 4) of one core-matrix row group, so the stores of a warp fill
+    // 128-byte core matrices without bank conflicts.
     const int bw = warp < 4 ? warp - 2 : 2 + ((warp - 4) >> 2) * (4 - Cfg::NQ) + ((warp & 3) - Cfg::NQ);
     const int bt = bw * 32 + lane, nbt = Cfg::NB * 32;
     for (int it = 0; it < n_it && ok; ++it) {
@@ -411,32 +450,33 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
       const int ncol = mw.nmx * mw.nmy * R;
       const float2 *xr = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE + Cfg::TRI + Cfg::FULL);
       unsigned char *bp = bbuf + (size_t)bb * Cfg::BBUF;
-      // entry e: chunk beta, core-matrix index (k / 4, n / 8), then (n % 8, k % 4) in the
-      // thread index so that a warp writes one 128-byte core matrix
-      for (int e = bt; e < 3 * KC * 16; e += nbt) {
-        const int within = e & 31, cm = e >> 5;
-        const int nn = within >> 2, kk = within & 3;
-        const int cmk = cm % (KC / 4), rest = cm / (KC / 4);
-        const int nh = rest & 1, beta = rest >> 1;
-        const int n = nh * 8 + nn, k = cmk * 4 + kk;
-        const int cc = n & 7;  // complex column
-        const bool second = k >= NZ;
-        const int zrow = beta * NZ + (second ? k - NZ : k);
-        float val = 0.f;
-        if (cc < ncol) {
-          const int m = cc / R, r = cc - m * R;
+      // entry e = ((beta * Nz + b) / 4) * 32 + (col * 4 + b % 4)
+      for (int e = bt; e < 3 * NZ * 8; e += nbt) {
+        const int col = (e >> 2) & 7, bq = e & 3, grp = e >> 5;
+        const int zrow = grp * 4 + bq;  // beta * Nz + b
+        const int beta = zrow / NZ, b = zrow - beta * NZ;
+        float2 x = make_float2(0.f, 0.f);
+        if (col < ncol) {
+          const int m = col / R, r = col - m * R;
           const int mx = m % mw.nmx, my = m / mw.nmx;
-          float2 x = xr[(size_t)m * CZ + r * N3 + zrow];
+          x = xr[(size_t)m * CZ + r * N3 + zrow];
           if ((beta == 0 && mx == 1) || (beta == 1 && my == 1)) { x.x = -x.x; x.y = -x.y; }
-          // rows k < Nz multiply M_r: (X_r | X_i); rows k >= Nz multiply M_i: (-X_i | X_r)
-          val = !second ? (n < 8 ? x.x : x.y) : (n < 8 ? -x.y : x.x);
         }
-        uint32_t h, l;
-        tc::split(val, h, l);
-        const size_t off = (size_t)(2 * beta) * Cfg::BPART + (size_t)nn * 16 + (size_t)nh * Cfg::SBO +
-                           (size_t)cmk * 128 + (size_t)kk * 4;
-        *reinterpret_cast<uint32_t *>(bp + off) = h;
-        *reinterpret_cast<uint32_t *>(bp + off + Cfg::BPART) = l;
+        uint32_t rh, rl, ih, il;
+        tc::split(x.x, rh, rl);
+        tc::split(x.y, ih, il);
+        // byte of (row k, column n) in a chunk part: (n % 8) 16 + (n / 8) SBO + (k / 4) 128 + (k % 4) 4
+        unsigned char *p0 = bp + (size_t)(2 * beta) * Cfg::BPART + (size_t)col * 16 + (size_t)(b >> 2) * 128 + bq * 4;
+        unsigned char *p1 = p0 + (size_t)(NZ >> 2) * 128;  // row Nz + b
+        constexpr size_t LO = Cfg::BPART;
+        *reinterpret_cast<uint32_t *>(p0) = rh;                            // (b, col): X_r
+        *reinterpret_cast<uint32_t *>(p0 + LO) = rl;
+        *reinterpret_cast<uint32_t *>(p0 + Cfg::SBO) = ih;                 // (b, 8 + col): X_i
+        *reinterpret_cast<uint32_t *>(p0 + Cfg::SBO + LO) = il;
+        *reinterpret_cast<uint32_t *>(p1) = ih ^ 0x80000000u;              // (Nz + b, col): -X_i
+        *reinterpret_cast<uint32_t *>(p1 + LO) = il ^ 0x80000000u;
+        *reinterpret_cast<uint32_t *>(p1 + Cfg::SBO) = rh;                 // (Nz + b, 8 + col): X_r
+        *reinterpret_cast<uint32_t *>(p1 + Cfg::SBO + LO) = rl;
       }
       tma::fence_proxy_async();  // the MMA reads B through the async proxy
       __syncwarp();
