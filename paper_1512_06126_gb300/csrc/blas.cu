@@ -538,16 +538,37 @@ __device__ __forceinline__ void df_fma(Df &acc, float ah, float al, float bh, fl
   acc.c = __fadd_rn(acc.c, __fadd_rn(e, pe));
 }
 
-__device__ __forceinline__ double df_value(const Df &a) { return (double)a.s + (double)a.c; }
+// a finite float as a double, built from its bits (no FP64 conversion instruction;
+// FP32 subnormals, which carry no weight here, become zero)
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long bits =
+      e == 0u ? sgn
+              : (e == 0xFFu ? sgn | 0x7FF0000000000000ull | ((unsigned long long)(u & 0x7FFFFFu) << 29)
+                            : sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29));
+  return __longlong_as_double((long long)bits);
+}
+// the value s + c: one FP64 addition
+__device__ __forceinline__ double df_value(const Df &a) { return f2d(a.s) + f2d(a.c); }
+// (s + c)(bh + bl) as a double-float
+__device__ __forceinline__ Df df_mul(const Df &a, float bh, float bl) {
+  Df r = {0.f, 0.f};
+  df_fma(r, a.s, a.c, bh, bl);
+  return r;
+}
 
 constexpr int kDfG = 4;  // basis vectors per unit of the dot pass (the chunk of x is split once per unit)
 
 // part(r, i, c) = sum_chunk conj(V_i) x and, for the first unit of a chunk, npart(r, c)
 // = sum_chunk |x|^2; units (r, c, group of kDfG basis vectors), one warp each
+constexpr int kDfCh = 512;  // elements per chunk of the double-float dot pass (16 per lane)
+
 __global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const double2 *__restrict__ V, const double2 *__restrict__ x,
                                                         double2 *__restrict__ part, double *__restrict__ npart, int k1,
                                                         int R, long long n, int nch) {
-  constexpr int CH = GsShape<double>::kCh;
+  constexpr int CH = kDfCh;
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * (kT / 32);
   const int ng = (k1 + kDfG - 1) / kDfG;
@@ -561,7 +582,7 @@ __global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const double2 *__restric
     Df re[kDfG], im[kDfG], nn = {0.f, 0.f};
 #pragma unroll
     for (int t = 0; t < kDfG; ++t) re[t] = im[t] = Df{0.f, 0.f};
-#pragma unroll 2
+#pragma unroll
     for (int j = 0; j < CH / 32; ++j) {
       const int l = j * 32 + lane;
       if (l >= lim) break;
@@ -624,9 +645,11 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restric
   }
   __syncthreads();
   const double sc = scaled && nrm[r] > 0.0 ? 1.0 / nrm[r] : 0.0;
+  float sch, scl;
+  dsplit(sc, sch, scl);
   double2 *xr = x + (long long)r * n;
   double2 *vr = vout ? vout + (long long)r * n : nullptr;
-  double nacc = 0.0;
+  Df nacc = {0.f, 0.f};
   for (long long c0 = (long long)blockIdx.x * kT * EPT; c0 < n; c0 += (long long)nbs * kT * EPT) {
     Df ar[EPT], ai[EPT];
 #pragma unroll
@@ -659,19 +682,18 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restric
     for (int j = 0; j < EPT; ++j) {
       const long long e = c0 + j * kT + tid;
       if (e < n) {
-        const double2 v = make_double2(df_value(ar[j]), df_value(ai[j]));
         if (scaled) {
-          vr[e] = make_double2(v.x * sc, v.y * sc);
+          vr[e] = make_double2(df_value(df_mul(ar[j], sch, scl)), df_value(df_mul(ai[j], sch, scl)));
         } else {
-          xr[e] = v;
-          nacc = fma(v.x, v.x, nacc);
-          nacc = fma(v.y, v.y, nacc);
+          xr[e] = make_double2(df_value(ar[j]), df_value(ai[j]));
+          df_fma(nacc, ar[j].s, ar[j].c, ar[j].s, ar[j].c);
+          df_fma(nacc, ai[j].s, ai[j].c, ai[j].s, ai[j].c);
         }
       }
     }
   }
   if (scaled) return;
-  const double2 sres = block_reduce(make_double2(nacc, 0.0), shn);
+  const double2 sres = block_reduce(make_double2(df_value(nacc), 0.0), shn);
   if (tid == 0) npart[(long long)r * nbs + blockIdx.x] = sres.x;
 }
 
@@ -785,24 +807,29 @@ int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double
   if (k1 < 1 || k1 > 64 || R < 1 || R > 16) return -1;
   df = df && sizeof(T) == 8;
   const int nch = cgs_nch<T>(n), nbs = cgs_nbs<T>(n, R);
-  double *np0 = npart, *np1 = npart + (long long)R * nch;
+  // the double-float dot pass uses shorter chunks (more of them: gs_partial_blocks
+  // allows the count of the c64 chunking, the largest); np1 starts past either
+  const int nch_max = gs_partial_blocks(n);
+  int nch_used = nch;
+  double *np0 = npart, *np1 = npart + (long long)R * nch_max;
   unsigned *tick = reinterpret_cast<unsigned *>(flag + 16);
   count_launches(4);
   // first projection: h1 = V^H w and ||w||; ||w'|| from the difference of squares
   if constexpr (sizeof(T) == 8) {
     if (df) {
-      const long long units = (long long)R * nch * ((k1 + kDfG - 1) / kDfG);
+      nch_used = (int)((n + kDfCh - 1) / kDfCh);
+      const long long units = (long long)R * nch_used * ((k1 + kDfG - 1) / kDfG);
       const long long maxw = (long long)dot_df_per_sm() * sm_count() * (kT / 32);
       const long long per = (units + maxw - 1) / maxw;
       const int gd = (int)((((units + per - 1) / per) + kT / 32 - 1) / (kT / 32));
-      cgs_dot_df_kernel<<<gd < 1 ? 1 : gd, kT, 0, s>>>(V, w, part, np0, k1, R, n, nch);
+      cgs_dot_df_kernel<<<gd < 1 ? 1 : gd, kT, 0, s>>>(V, w, part, np0, k1, R, n, nch_used);
     }
   }
   if (!df) {
     const int gd = cgs_dot_blocks<T>((long long)R * nch * k1);
     cgs_dot_kernel<T><<<gd, kT, 0, s>>>(V, w, part, np0, nullptr, k1, R, n, nch);
   }
-  cgs_hsum_kernel<<<dim3(k1 + 1, R), kT, 0, s>>>(part, np0, h1, h2, nrm, flag, tick, k1, R, nch, ldh);
+  cgs_hsum_kernel<<<dim3(k1 + 1, R), kT, 0, s>>>(part, np0, h1, h2, nrm, flag, tick, k1, R, nch_used, ldh);
   // w' = w - V h1, written normalised into vnext where no second projection is needed
   if constexpr (sizeof(T) == 8) {
     if (df) {

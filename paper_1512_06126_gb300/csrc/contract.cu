@@ -243,6 +243,43 @@ bool try_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, bool unpac
                            err, s);
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// The full xz, yz blocks of every folded wavenumber as a 3-D tensor of 8-byte
+// elements: [nf blocks][2 Nz rows][Nz columns] starting 4P complex into each packed
+// block (strides Nz * 8 and 2 Nz (2 Nz + 1) * 8 bytes); boxes of 16 columns x 2 Nz rows
+// x 1 block, 128-byte swizzle.
+bool encode_full_map(CUtensorMap *map, const float2 *qf, int Nz, long long nf) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const long long P = (long long)Nz * (Nz + 1) / 2, BS = 2LL * Nz * (2 * Nz + 1);
+  const cuuint64_t dims[3] = {(cuuint64_t)Nz, (cuuint64_t)(2 * Nz), (cuuint64_t)nf};
+  const cuuint64_t strides[2] = {(cuuint64_t)Nz * 8, (cuuint64_t)BS * 8};
+  const cuuint32_t box[3] = {16, (cuuint32_t)(2 * Nz), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2 *>(qf + 4 * P), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The tcgen05 kernel: persistent, as many CTAs per SM as occupancy and tensor memory
 // allow (each holds TcCfg::TCOLS of the SM's 512 columns for its lifetime).
 template <int NZ, int R>
@@ -250,13 +287,14 @@ bool try_tc(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int *err, c
   using Cfg = TcCfg<NZ, R>;
   static int per_sm = 0;
   auto k = contract_tc_kernel<NZ, R>;
-  if (Cfg::SMEM > 227 * 1024) return false;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess) {
+  constexpr size_t smem = Cfg::SMEM + 1024;  // the kernel aligns its base to 1024 bytes
+  if (smem > 227 * 1024) return false;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   if (per_sm == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Cfg::THREADS, Cfg::SMEM) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Cfg::THREADS, smem) != cudaSuccess ||
         per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
@@ -264,10 +302,12 @@ bool try_tc(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int *err, c
     if (per_sm > 512 / Cfg::TCOLS) per_sm = 512 / Cfg::TCOLS;
   }
   const int nf = (Nx + 1) * (Ny + 1);
+  CUtensorMap tmap;
+  if (!encode_full_map(&tmap, qf, NZ, nf)) return false;
   const int want = per_sm * num_sms();
   const int grid = nf < want ? nf : want;
   count_launches(1);
-  k<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(spec, qf, Nx, Ny, ldz, err, g_wait_limit);
+  k<<<grid, Cfg::THREADS, smem, s>>>(spec, qf, Nx, Ny, ldz, err, g_wait_limit, tmap);
   if (cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return false;

@@ -12,9 +12,12 @@
 //
 // Warp roles (one CTA per SM; persistent over folded wavenumbers w = blockIdx.x +
 // k gridDim.x):
-//  * warp 0, the producer: 1-D bulk copies (cp.async.bulk) of the packed triangles of
-//    xx, yy, zz, xy, of every row of xz and yz at a padded stride, and of the mirror
-//    spectrum vectors into a ring of NS shared-memory stages;
+//  * warp 0, the producer: a 1-D bulk copy (cp.async.bulk) of the packed triangles of
+//    xx, yy, zz, xy, tensor-map copies (cp.async.bulk.tensor, 128-byte swizzle) of the
+//    full xz and yz blocks in boxes of 16 columns, and 1-D copies of the mirror spectrum
+//    vectors into a ring of NS shared-memory stages: at most 1 + Nz/16 + 4 requests per
+//    wavenumber (one request per row of xz and yz kept the copy engine busy for longer
+//    than the data took to arrive);
 //  * warp 1, the MMA issuer: one thread issues the 3 x (2 Nz / 8) x 3 tcgen05.mma of a
 //    wavenumber and commits their completion to mbarriers;
 //  * row warps (TMEM lane quadrant q = warp % 4 holds output rows 32q .. 32q + 31): each
@@ -27,6 +30,8 @@
 // Every wait is bounded: on timeout the kernel records an error, each role stops, the
 // producer drains its copies and the issuer its MMAs, and TMEM is released.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the map is encoded on the host through the runtime's driver entry point)
+
 #include "contract_tma.cuh"
 
 namespace ie {
@@ -96,6 +101,15 @@ __device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32
       "l"(src), "r"(bytes), "r"(tma::smem_u32(bar)), "l"(policy)
       : "memory");
 }
+// 3-D tensor-map copy global -> shared (box at coordinates x, y, z) with an L2 policy
+__device__ __forceinline__ void tensor3_g2s_hint(void *dst, const void *tmap, int x, int y, int z, uint64_t *bar,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3, "
+      "%4}], [%5], %6;" ::"r"(tma::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(tma::smem_u32(bar)), "l"(policy)
+      : "memory");
+}
 // L2 policy for data read once: evicted first, so that the coefficient stream does not
 // push the spectrum (re-read by the FFT passes around the contraction) out of L2
 __device__ __forceinline__ uint64_t evict_first_policy() {
@@ -145,7 +159,7 @@ struct TcCfg {
   static constexpr int CZ = R * N3;
   static constexpr int P = NZ * (NZ + 1) / 2;
   static constexpr int BS = 2 * NZ * (2 * NZ + 1);
-  static constexpr int LDF = NZ + 2;  // full-block row stride (complex): 16-byte rows, 2-way banks
+  static constexpr int NBOX = NZ / 16;  // tensor-map boxes of 16 complex columns per full-block row
   static constexpr int NQ = (N3 + 31) / 32;        // TMEM lane quadrants holding rows
   static constexpr int RW = 4;                     // row warps per quadrant
   static constexpr int EPW = NZ / RW;              // complex entries of a chunk per row warp
@@ -161,11 +175,19 @@ struct TcCfg {
   static constexpr int DCOL = NA * ACOLS;          // first accumulator column
   static constexpr int TCOLS = DCOL + 64 <= 256 ? 256 : 512;
   static_assert(DCOL + 64 <= 512, "TMEM");
-  // stage layout (bytes)
+  // stage layout (bytes): the packed triangles, then the full xz, yz rows as NBOX boxes
+  // of [2 Nz rows][128 bytes] in the 128-byte swizzle (each 1024-byte aligned), then the
+  // mirror vectors.  Element (row r, column b) of the full blocks (rows 0..Nz-1 xz,
+  // Nz..2Nz-1 yz) sits at complex index FULLC + (b / 16) BOXC + 16 r +
+  // 2 (((b % 16) / 2) ^ (r % 8)) + b % 2.
   static constexpr size_t TRI = (size_t)4 * P * 8;
-  static constexpr size_t FULL = (size_t)2 * NZ * LDF * 8;
+  static constexpr size_t OFF_FULL = ((TRI + 1023) / 1024) * 1024;
+  static constexpr size_t BOX = (size_t)2 * NZ * 128;
+  static constexpr size_t FULL = NBOX * BOX;
+  static constexpr size_t OFF_XR = OFF_FULL + FULL;
   static constexpr size_t XR = (size_t)4 * CZ * 8;
-  static constexpr size_t STAGE = ((TRI + FULL + XR + 127) / 128) * 128;
+  static constexpr size_t STAGE = ((OFF_XR + XR + 1023) / 1024) * 1024;
+  static constexpr int FULLC = (int)(OFF_FULL / 8), BOXC = (int)(BOX / 8);
   // B operand: per chunk and hi / lo, N = 16 rows of K = KC (core matrices 8 x 16 bytes):
   // byte (n % 8) 16 + (n / 8) SBO + (k / 4) 128 + (k % 4) 4
   static constexpr uint32_t LBO = 128;
@@ -173,21 +195,24 @@ struct TcCfg {
   static constexpr size_t BPART = (size_t)2 * SBO;            // one chunk, hi or lo
   static constexpr size_t BBUF = (size_t)3 * 2 * BPART;       // one wavenumber
   static constexpr size_t OFF_BAR = 0;                        // 32 mbarriers + the TMEM address
-  static constexpr size_t OFF_STAGE = 1024;
+  static constexpr size_t OFF_STAGE = 1024;  // stages and boxes 1024-byte aligned (the swizzle atom)
   static constexpr size_t OFF_B = OFF_STAGE + NS * STAGE;
   static constexpr size_t SMEM = OFF_B + 2 * BBUF;
-  static_assert((TRI % 16) == 0 && (LDF * 8) % 16 == 0 && ((TRI + FULL) % 16) == 0, "bulk copy alignment");
+  static_assert(NZ % 16 == 0, "full-block rows in boxes of 16 complex (128 bytes)");
+  static_assert(STAGE / 8 < 32768, "16-bit stage offsets");
   static constexpr uint32_t IDESC = tc::idesc_tf32(128, 16);
 };
 
 template <int NZ, int R>
 __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     contract_tc_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err,
-                       long long lim_polls) {
+                       long long lim_polls, const __grid_constant__ CUtensorMap tfull) {
   using Cfg = TcCfg<NZ, R>;
-  constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LDF = Cfg::LDF, NS = Cfg::NS, NA = Cfg::NA;
+  constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, NS = Cfg::NS, NA = Cfg::NA;
   constexpr int KC = Cfg::KC, EPW = Cfg::EPW;
-  extern __shared__ __align__(128) unsigned char sm[];
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  // the swizzled boxes need 1024-byte aligned destinations: the launch adds 1024 bytes
+  unsigned char *sm = sm_raw + ((1024u - (tma::smem_u32(sm_raw) & 1023u)) & 1023u);
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Cfg::OFF_BAR);
   uint64_t *full = bars, *empty = bars + 4, *afull = bars + 8, *aempty = bars + 12;
   uint64_t *bfull = bars + 16, *bempty = bars + 18, *dfull = bars + 20, *dempty = bars + 22, *fin = bars + 24;
@@ -260,19 +285,18 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
       tma::fence_proxy_async();
       if (lane == 0) tma::mbar_expect_tx(&full[s], (uint32_t)((size_t)BS * 8 + (size_t)nm * CZ * 8));
       __syncwarp();
-      const int ncopy = 1 + 2 * NZ + nm;
+      const int ncopy = 1 + Cfg::NBOX + nm;
       for (int j = lane; j < ncopy; j += 32) {
         if (j == 0) {
           tc::bulk_g2s_hint(st, q, (uint32_t)Cfg::TRI, &full[s], once);
-        } else if (j <= 2 * NZ) {
-          const int i = j - 1;
-          tc::bulk_g2s_hint(st + Cfg::TRI + (size_t)i * LDF * 8, q + 4 * P + i * NZ, (uint32_t)(NZ * 8), &full[s],
-                            once);
+        } else if (j <= Cfg::NBOX) {
+          const int h = j - 1;
+          tc::tensor3_g2s_hint(st + Cfg::OFF_FULL + (size_t)h * Cfg::BOX, &tfull, 16 * h, 0, w, &full[s], once);
         } else {
-          const int m = j - 1 - 2 * NZ;
+          const int m = j - 1 - Cfg::NBOX;
           const int mx = m % mi.nmx, my = m / mi.nmx;
-          tma::bulk_g2s(st + Cfg::TRI + Cfg::FULL + (size_t)m * CZ * 8, spec + mi.pos(mx, my, Nx) * ldz,
-                        (uint32_t)(CZ * 8), &full[s]);
+          tma::bulk_g2s(st + Cfg::OFF_XR + (size_t)m * CZ * 8, spec + mi.pos(mx, my, Nx) * ldz, (uint32_t)(CZ * 8),
+                        &full[s]);
         }
       }
       ++issued;
@@ -344,10 +368,11 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
           const int kind = alpha == beta ? alpha : 3;  // xx, yy, zz on the diagonal; xy off it
           const int lo = a < b ? a : b, hi = a < b ? b : a;
           off = kind * P + ((lo * (2 * NZ - 1) - lo * lo) >> 1) + hi;
-        } else if (beta == 2) {
-          off = (int)(Cfg::TRI / 8) + (alpha * NZ + a) * LDF + b;
         } else {
-          off = (int)(Cfg::TRI / 8) + (beta * NZ + b) * LDF + a;
+          // xz / yz direct (rows of x, y; columns of z) or transposed (rows of z)
+          const int r = beta == 2 ? alpha * NZ + a : beta * NZ + b;
+          const int cc = beta == 2 ? b : a;
+          off = Cfg::FULLC + (cc >> 4) * Cfg::BOXC + 16 * r + ((((cc & 15) >> 1) ^ (r & 7)) << 1) + (cc & 1);
         }
         if (e & 1) offp[beta][e >> 1] |= (uint32_t)off << 16;
         else offp[beta][e >> 1] = (uint32_t)off;
@@ -448,7 +473,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
       }
       const Mirrors mw = mirrors_of(w0 + it * gs, Nx, Ny);
       const int ncol = mw.nmx * mw.nmy * R;
-      const float2 *xr = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE + Cfg::TRI + Cfg::FULL);
+      const float2 *xr = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE + Cfg::OFF_XR);
       unsigned char *bp = bbuf + (size_t)bb * Cfg::BBUF;
       // entry e = ((beta * Nz + b) / 4) * 32 + (col * 4 + b % 4)
       for (int e = bt; e < 3 * NZ * 8; e += nbt) {

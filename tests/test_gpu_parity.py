@@ -154,7 +154,10 @@ def test_full_size_matvec_sampled_rows():
         got = np.array([y[r][:, c[0], c[1], c[2]] for c in cells])
         assert rel(got, ref) <= 1e-11, rel(got, ref)
         got32 = np.array([y32h[r][:, c[0], c[1], c[2]] for c in cells])
-        assert rel(got32, ref) <= 1e-4, rel(got32, ref)
+        # the c64 bound of every other product test, on 15 sampled values: the FFT
+        # round-off spreads evenly over the output, so sampled rows of typical size see
+        # the same relative error as the whole vector
+        assert rel(got32, ref) <= 2e-5, rel(got32, ref)
     ctx.close()
 
 
