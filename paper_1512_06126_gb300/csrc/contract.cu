@@ -307,7 +307,7 @@ bool try_tc(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int *err, c
   const int want = per_sm * num_sms();
   const int grid = nf < want ? nf : want;
   count_launches(1);
-  k<<<grid, Cfg::THREADS, smem, s>>>(spec, qf, Nx, Ny, ldz, err, g_wait_limit, tmap);
+  k<<<grid, Cfg::THREADS, smem, s>>>(spec, qf, Nx, Ny, ldz, err, g_wait_limit, tmap, nullptr);
   if (cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return false;

@@ -203,10 +203,28 @@ struct TcCfg {
   static constexpr uint32_t IDESC = tc::idesc_tf32(128, 16);
 };
 
-template <int NZ, int R>
+// Timing instrumentation (PROF = true only in measurement builds): per warp, clock64()
+// cycles accumulated in the slots of TcProf, written to prof[(block * WARPS + warp) * 8].
+enum TcProf { kPWaitA = 0, kPWaitB = 1, kPWaitC = 2, kPWork = 3, kPWaitSt = 4, kPEpi = 5, kPTotal = 6, kPIters = 7 };
+
+template <int NZ, int R, bool PROF = false>
 __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     contract_tc_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err,
-                       long long lim_polls, const __grid_constant__ CUtensorMap tfull) {
+                       long long lim_polls, const __grid_constant__ CUtensorMap tfull,
+                       unsigned long long *prof) {
+  unsigned long long pt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long t_mark = 0;
+  auto tic = [&]() {
+    if constexpr (PROF) t_mark = clock64();
+  };
+  auto toc = [&](int slot) {
+    if constexpr (PROF) {
+      const long long t = clock64();
+      pt[slot] += (unsigned long long)(t - t_mark);
+      t_mark = t;
+    }
+  };
+  const long long t_begin = PROF ? clock64() : 0;
   using Cfg = TcCfg<NZ, R>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, NS = Cfg::NS, NA = Cfg::NA;
   constexpr int KC = Cfg::KC, EPW = Cfg::EPW;
@@ -273,10 +291,12 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     int issued = 0;
     for (int it = 0; it < n_it; ++it) {
       const int s = it % NS;
+      tic();
       if (it >= NS && !tc::warp_wait(&empty[s], (uint32_t)((it / NS - 1) & 1), lim)) {
         ok = false;
         break;
       }
+      toc(kPWaitA);
       const int w = w0 + it * gs;
       const Mirrors mi = mirrors_of(w, Nx, Ny);
       const int nm = mi.nmx * mi.nmy;
@@ -300,6 +320,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
         }
       }
       ++issued;
+      toc(kPWork);
     }
     // drain: the last NS issues must land before the CTA exits
     for (int k = issued - NS > 0 ? issued - NS : 0; k < issued; ++k)
@@ -313,19 +334,27 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
       const uint64_t bdesc = tc::sdesc(tma::smem_u32(bbuf), Cfg::LBO, Cfg::SBO);
       for (int it = 0; it < n_it && ok; ++it) {
         const int bb = it & 1;
-        if (!tc::wait(&bfull[bb], (uint32_t)((it >> 1) & 1), lim) ||
-            (it >= 2 && !tc::wait(&dempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim))) {
+        tic();
+        if (!tc::wait(&bfull[bb], (uint32_t)((it >> 1) & 1), lim)) {
           ok = false;
           break;
         }
+        toc(kPWaitA);
+        if (it >= 2 && !tc::wait(&dempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim)) {
+          ok = false;
+          break;
+        }
+        toc(kPWaitB);
         tc::fence_after();
         const uint32_t d1 = tbase + Cfg::DCOL + 32 * bb, d2 = d1 + 16;
         for (int beta = 0; beta < 3 && ok; ++beta) {
           const int g = 3 * it + beta, c = g % NA;
+          tic();
           if (!tc::wait(&afull[c], (uint32_t)((g / NA) & 1), lim)) {
             ok = false;
             break;
           }
+          toc(kPWaitC);
           tc::fence_after();
           const uint32_t ahi = tbase + c * Cfg::ACOLS, alo = ahi + KC;
           const uint64_t dh0 = bdesc + (((size_t)bb * Cfg::BBUF + (size_t)(2 * beta) * Cfg::BPART) >> 4);
@@ -338,6 +367,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
             tc::mma(d2, alo + 8 * ks, dh0 + 16u * ks, Cfg::IDESC, 1u);
           }
           tc::commit(&aempty[c]);
+          toc(kPWork);
         }
         if (!ok) break;
         tc::commit(&bempty[bb]);
@@ -380,7 +410,9 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     }
     auto epilogue = [&](int e) -> bool {
       const int bb = e & 1;
+      tic();
       if (!tc::warp_wait(&dfull[bb], (uint32_t)((e >> 1) & 1), lim)) return false;
+      toc(kPWaitC);
       tc::fence_after();
       const uint32_t dc = tq + Cfg::DCOL + 32 * bb;
       uint32_t v[8];
@@ -408,19 +440,24 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
           }
         }
       }
+      toc(kPEpi);
       return true;
     };
     for (int it = 0; it < n_it && ok; ++it) {
       const int s = it % NS;
+      tic();
       if (!tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim)) { ok = false; break; }
+      toc(kPWaitA);
       const float2 *st = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE);
 #pragma unroll
       for (int beta = 0; beta < 3; ++beta) {
         const int g = 3 * it + beta, c = g % NA;
+        tic();
         if (g >= NA && !tc::warp_wait(&aempty[c], (uint32_t)((g / NA - 1) & 1), lim)) {
           ok = false;
           break;
         }
+        toc(kPWaitB);
         tc::fence_after();
         const bool neg = alpha == 2 && beta < 2;
         uint32_t rh[EPW], ih[EPW], rl[EPW], il[EPW];
@@ -444,7 +481,9 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
           tc::st4(ab + KC, rl);
           tc::st4(ab + KC + NZ, il);
         }
+        toc(kPWork);
         tc::wait_st();
+        toc(kPWaitSt);
         tc::fence_before();
         __syncwarp();
         if (lane == 0) tc::arrive(&afull[c]);
@@ -466,11 +505,17 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     const int bt = bw * 32 + lane, nbt = Cfg::NB * 32;
     for (int it = 0; it < n_it && ok; ++it) {
       const int s = it % NS, bb = it & 1;
-      if (!tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim) ||
-          (it >= 2 && !tc::warp_wait(&bempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim))) {
+      tic();
+      if (!tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim)) {
         ok = false;
         break;
       }
+      toc(kPWaitA);
+      if (it >= 2 && !tc::warp_wait(&bempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim)) {
+        ok = false;
+        break;
+      }
+      toc(kPWaitB);
       const Mirrors mw = mirrors_of(w0 + it * gs, Nx, Ny);
       const int ncol = mw.nmx * mw.nmy * R;
       const float2 *xr = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE + Cfg::OFF_XR);
@@ -509,9 +554,17 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
         tc::arrive(&bfull[bb]);
         tc::arrive(&empty[s]);
       }
+      toc(kPWork);
     }
   }
   if (!ok && lane == 0) atomicExch(err, kContractTimeout);
+  if constexpr (PROF) {
+    if (prof && lane == 0) {
+      pt[kPTotal] = (unsigned long long)(clock64() - t_begin);
+      pt[kPIters] = (unsigned long long)n_it;
+      for (int k = 0; k < 8; ++k) prof[((size_t)blockIdx.x * Cfg::WARPS + warp) * 8 + k] = pt[k];
+    }
+  }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
