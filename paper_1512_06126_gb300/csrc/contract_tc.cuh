@@ -7,8 +7,12 @@
 // mirrors x R).  As a real product per input component beta (a K-chunk of 2 Nz):
 //   D += [M_r | M_i](:, beta) . [[X_r, X_i], [-X_i, X_r]](beta)
 // so D[:, c] = Y_r and D[:, 8 + c] = Y_i of column c (N = 16).  FP32 accuracy from the
-// 3xTF32 split x = hi + lo (hi = x rounded to TF32, lo = x - hi exactly): D1 += A_hi B_hi
-// and D2 += A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo is ~2^-22 of the product).
+// 3xTF32 split x = hi + lo (hi = x rounded to TF32, lo = x - hi exactly): one N = 32 MMA
+// D1 += A_hi [B_hi | B_lo] (both parts of B are consecutive core-matrix groups) and one
+// N = 16 MMA D2 += A_lo B_hi per k-step (the dropped A_lo B_lo is ~2^-22 of the
+// product).  The tensor core takes a nearly fixed time per instruction at these small N,
+// so fusing two of the three products into one N = 32 instruction saves a third of the
+// issue time.
 //
 // Warp roles (one CTA per SM; persistent over folded wavenumbers w = blockIdx.x +
 // k gridDim.x):
@@ -173,8 +177,9 @@ struct TcCfg {
   static constexpr int KC = 2 * NZ;                // K of a chunk (real)
   static constexpr int ACOLS = 4 * NZ;             // TMEM columns of a chunk buffer (hi, lo)
   static constexpr int DCOL = NA * ACOLS;          // first accumulator column
-  static constexpr int TCOLS = DCOL + 64 <= 256 ? 256 : 512;
-  static_assert(DCOL + 64 <= 512, "TMEM");
+  static constexpr int DBUF = 64;                  // per buffer: D1 (32 columns) and D2 (16), padded
+  static constexpr int TCOLS = DCOL + 2 * DBUF <= 256 ? 256 : 512;
+  static_assert(DCOL + 2 * DBUF <= 512, "TMEM");
   // stage layout (bytes): the packed triangles, then the full xz, yz rows as NBOX boxes
   // of [2 Nz rows][128 bytes] in the 128-byte swizzle (each 1024-byte aligned), then the
   // mirror vectors.  Element (row r, column b) of the full blocks (rows 0..Nz-1 xz,
@@ -201,6 +206,7 @@ struct TcCfg {
   static_assert(NZ % 16 == 0, "full-block rows in boxes of 16 complex (128 bytes)");
   static_assert(STAGE / 8 < 32768, "16-bit stage offsets");
   static constexpr uint32_t IDESC = tc::idesc_tf32(128, 16);
+  static constexpr uint32_t IDESC32 = tc::idesc_tf32(128, 32);
 };
 
 // Timing instrumentation (PROF = true only in measurement builds): per warp, clock64()
@@ -346,7 +352,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
         }
         toc(kPWaitB);
         tc::fence_after();
-        const uint32_t d1 = tbase + Cfg::DCOL + 32 * bb, d2 = d1 + 16;
+        const uint32_t d1 = tbase + Cfg::DCOL + Cfg::DBUF * bb, d2 = d1 + 32;
         for (int beta = 0; beta < 3 && ok; ++beta) {
           const int g = 3 * it + beta, c = g % NA;
           tic();
@@ -358,13 +364,11 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
           tc::fence_after();
           const uint32_t ahi = tbase + c * Cfg::ACOLS, alo = ahi + KC;
           const uint64_t dh0 = bdesc + (((size_t)bb * Cfg::BBUF + (size_t)(2 * beta) * Cfg::BPART) >> 4);
-          const uint64_t dl0 = dh0 + (Cfg::BPART >> 4);
 #pragma unroll
           for (int ks = 0; ks < KC / 8; ++ks) {
             const uint32_t acc = (beta | ks) != 0;
-            tc::mma(d1, ahi + 8 * ks, dh0 + 16u * ks, Cfg::IDESC, acc);
-            tc::mma(d2, ahi + 8 * ks, dl0 + 16u * ks, Cfg::IDESC, acc);
-            tc::mma(d2, alo + 8 * ks, dh0 + 16u * ks, Cfg::IDESC, 1u);
+            tc::mma(d1, ahi + 8 * ks, dh0 + 16u * ks, Cfg::IDESC32, acc);  // A_hi [B_hi | B_lo]
+            tc::mma(d2, alo + 8 * ks, dh0 + 16u * ks, Cfg::IDESC, acc);    // A_lo B_hi
           }
           tc::commit(&aempty[c]);
           toc(kPWork);
@@ -414,12 +418,14 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
       if (!tc::warp_wait(&dfull[bb], (uint32_t)((e >> 1) & 1), lim)) return false;
       toc(kPWaitC);
       tc::fence_after();
-      const uint32_t dc = tq + Cfg::DCOL + 32 * bb;
-      uint32_t v[8];
-      tc::ld2(dc + 2 * jw, v[0], v[1]);            // D1 Y_r of columns 2 jw, 2 jw + 1
-      tc::ld2(dc + 8 + 2 * jw, v[2], v[3]);        // D1 Y_i
-      tc::ld2(dc + 16 + 2 * jw, v[4], v[5]);       // D2 Y_r
-      tc::ld2(dc + 24 + 2 * jw, v[6], v[7]);       // D2 Y_i
+      const uint32_t dc = tq + Cfg::DCOL + Cfg::DBUF * bb;
+      uint32_t v[12];
+      tc::ld2(dc + 2 * jw, v[0], v[1]);            // A_hi B_hi: Y_r of columns 2 jw, 2 jw + 1
+      tc::ld2(dc + 8 + 2 * jw, v[2], v[3]);        //            Y_i
+      tc::ld2(dc + 16 + 2 * jw, v[4], v[5]);       // A_hi B_lo: Y_r
+      tc::ld2(dc + 24 + 2 * jw, v[6], v[7]);       //            Y_i
+      tc::ld2(dc + 32 + 2 * jw, v[8], v[9]);       // A_lo B_hi: Y_r
+      tc::ld2(dc + 40 + 2 * jw, v[10], v[11]);     //            Y_i
       tc::wait_ld();
       tc::fence_before();
       __syncwarp();
@@ -433,8 +439,8 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
           if (col < ncol) {
             const int m = col / R, r = col - m * R;
             const int mx = m % mw.nmx, my = m / mw.nmx;
-            float2 y = make_float2(__uint_as_float(v[h]) + __uint_as_float(v[4 + h]),
-                                   __uint_as_float(v[2 + h]) + __uint_as_float(v[6 + h]));
+            float2 y = make_float2(__uint_as_float(v[h]) + (__uint_as_float(v[4 + h]) + __uint_as_float(v[8 + h])),
+                                   __uint_as_float(v[2 + h]) + (__uint_as_float(v[6 + h]) + __uint_as_float(v[10 + h])));
             if ((alpha == 0 && mx == 1) || (alpha == 1 && my == 1)) { y.x = -y.x; y.y = -y.y; }
             spec[mw.pos(mx, my, Nx) * ldz + r * N3 + row] = y;
           }
