@@ -80,8 +80,9 @@ def peaks():
 CONTRACT_TRAFFIC = {("C2", 3, 2): 654541312 + 86889728, ("C2", 5, 2): 654550784 + 88402176}
 VARIANT_NAMES = ["tma 1 slot", "tma 3 slots", "panel", "tma 1 slot, 1 row/thread",
                  "3xTF32 mma.sync, producer warp, 2 slots", "3xTF32 mma.sync, 1 slot, unpacked",
-                 "3xTF32 tcgen05.mma, block in TMEM, warp-specialised"]
-TENSOR_VARIANTS = (4, 5, 6)
+                 "3xTF32 tcgen05.mma, block in TMEM, warp-specialised",
+                 "2xFP16 (scaled) tcgen05.mma kind::f16, block in TMEM, warp-specialised"]
+TENSOR_VARIANTS = (4, 5, 6, 7)
 
 
 def bf16_peak():

@@ -282,11 +282,12 @@ bool encode_full_map(CUtensorMap *map, const float2 *qf, int Nz, long long nf) {
 
 // The tcgen05 kernel: persistent, as many CTAs per SM as occupancy and tensor memory
 // allow (each holds TcCfg::TCOLS of the SM's 512 columns for its lifetime).
-template <int NZ, int R>
-bool try_tc(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int *err, cudaStream_t s) {
-  using Cfg = TcCfg<NZ, R>;
+template <int NZ, int R, bool F16>
+bool try_tc(float2 *spec, const float2 *qf, const int *qexp, int Nx, int Ny, int ldz, int *err, cudaStream_t s) {
+  using Cfg = TcCfg<NZ, R, F16>;
   static int per_sm = 0;
-  auto k = contract_tc_kernel<NZ, R>;
+  auto k = contract_tc_kernel<NZ, R, F16, false>;
+  if (F16 && !qexp) return false;
   constexpr size_t smem = Cfg::SMEM + 1024;  // the kernel aligns its base to 1024 bytes
   if (smem > 227 * 1024) return false;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -307,7 +308,7 @@ bool try_tc(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int *err, c
   const int want = per_sm * num_sms();
   const int grid = nf < want ? nf : want;
   count_launches(1);
-  k<<<grid, Cfg::THREADS, smem, s>>>(spec, qf, Nx, Ny, ldz, err, g_wait_limit, tmap, nullptr);
+  k<<<grid, Cfg::THREADS, smem, s>>>(spec, qf, Nx, Ny, ldz, err, g_wait_limit, tmap, qexp, nullptr);
   if (cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -315,12 +316,33 @@ bool try_tc(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int *err, c
   return true;
 }
 
-template <int R>
-bool dispatch_tc(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, int *err, cudaStream_t s) {
+template <int R, bool F16>
+bool dispatch_tc(float2 *spec, const float2 *qf, const int *qexp, int Nx, int Ny, int Nz, int ldz, int *err,
+                 cudaStream_t s) {
   switch (Nz) {
-    case 16: return try_tc<16, R>(spec, qf, Nx, Ny, ldz, err, s);
-    case 32: return try_tc<32, R>(spec, qf, Nx, Ny, ldz, err, s);
+    case 16: return try_tc<16, R, F16>(spec, qf, qexp, Nx, Ny, ldz, err, s);
+    case 32: return try_tc<32, R, F16>(spec, qf, qexp, Nx, Ny, ldz, err, s);
     default: return false;
+  }
+}
+
+// exponent e_w of every folded wavenumber's packed block: max |re|, |im| times 2^e_w in
+// [2^13, 2^14) (0 for a zero block), clamped to [-100, 100]
+__global__ void block_exponent_kernel(const float2 *__restrict__ qf, int *__restrict__ qexp, int BS) {
+  __shared__ float sh[8];
+  const float2 *q = qf + (size_t)blockIdx.x * BS;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < BS; i += blockDim.x) {
+    const float2 v = q[i];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[w]);
+    qexp[blockIdx.x] = tc::scale_exp(m);
   }
 }
 
@@ -380,7 +402,7 @@ bool contract_variant_available(int variant, int Nz, int R, bool c64) {
   if (variant == kContractPanel) return R >= 1 && R <= 4 && 3 * Nz <= 1024;
   if (!c64 || R < 1 || R > 2 || !contract_tma_enabled) return false;
   if (Nz != 16 && Nz != 24 && Nz != 32 && Nz != 48) return false;
-  if (variant == kContractTc) return Nz == 16 || Nz == 32;
+  if (variant == kContractTc || variant == kContractTc16) return Nz == 16 || Nz == 32;
   if (variant == kContractMma || variant == kContractMmaUnpack) return Nz % 16 == 0;
   if (variant == kContractTma1) return true;
   if (variant == kContractTma1Row) return R == 2;
@@ -397,7 +419,7 @@ bool contract_variant_available(int variant, int Nz, int R, bool c64) {
 
 template <typename T>
 int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant, int *err,
-                    cudaStream_t s) {
+                    cudaStream_t s, const int *qexp) {
   if (ldz < R * 3 * Nz) return -1;
   if constexpr (sizeof(T) == 4) {
     if (!err) err = default_err();
@@ -411,8 +433,12 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, i
       if (R == 2 && dispatch_mma<2>(spec, qf, Nx, Ny, Nz, ldz, unpack, err, s)) return 0;
     }
     if (variant == kContractTc && contract_variant_available(variant, Nz, R, true)) {
-      if (R == 1 && dispatch_tc<1>(spec, qf, Nx, Ny, Nz, ldz, err, s)) return 0;
-      if (R == 2 && dispatch_tc<2>(spec, qf, Nx, Ny, Nz, ldz, err, s)) return 0;
+      if (R == 1 && dispatch_tc<1, false>(spec, qf, nullptr, Nx, Ny, Nz, ldz, err, s)) return 0;
+      if (R == 2 && dispatch_tc<2, false>(spec, qf, nullptr, Nx, Ny, Nz, ldz, err, s)) return 0;
+    }
+    if (variant == kContractTc16 && qexp && contract_variant_available(variant, Nz, R, true)) {
+      if (R == 1 && dispatch_tc<1, true>(spec, qf, qexp, Nx, Ny, Nz, ldz, err, s)) return 0;
+      if (R == 2 && dispatch_tc<2, true>(spec, qf, qexp, Nx, Ny, Nz, ldz, err, s)) return 0;
     }
     if ((variant == kContractTma1 || variant == kContractTma3 || variant == kContractTma1Row) &&
         contract_variant_available(variant, Nz, R, true)) {
@@ -426,7 +452,14 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, i
   return -1;
 }
 
-template int launch_contract<float>(float2 *, const float2 *, int, int, int, int, int, int, int *, cudaStream_t);
-template int launch_contract<double>(double2 *, const double2 *, int, int, int, int, int, int, int *, cudaStream_t);
+template int launch_contract<float>(float2 *, const float2 *, int, int, int, int, int, int, int *, cudaStream_t,
+                                    const int *);
+template int launch_contract<double>(double2 *, const double2 *, int, int, int, int, int, int, int *, cudaStream_t,
+                                     const int *);
+
+void launch_block_exponents(const float2 *qf, int *qexp, long long nf, int Nz, cudaStream_t s) {
+  count_launches(1);
+  block_exponent_kernel<<<(unsigned)nf, 256, 0, s>>>(qf, qexp, 2 * Nz * (2 * Nz + 1));
+}
 
 }  // namespace ie

@@ -10,13 +10,16 @@ namespace ie {
 // per thread (two right-hand sides only), and two kernels feeding 3xTF32 tensor-core
 // MMAs (c64, Nz in {16, 32, 48}, R <= 2): a producer warp with a two-slot ring and
 // fragments read in place, or the one-slot ring with an unpacking pass.
-// Variant 6 runs on the 5th-generation tensor cores: tcgen05.mma with the block in
-// tensor memory and FP32 accumulators there (3xTF32; c64, Nz in {16, 32}, R <= 2).
+// Variants 6 and 7 run on the 5th-generation tensor cores: tcgen05.mma with the block in
+// tensor memory and FP32 accumulators there (c64, Nz in {16, 32}, R <= 2): 6 kind::tf32
+// on the 3xTF32 split, 7 kind::f16 on a scaled two-way FP16 split (the same 22
+// significant bits, half the instructions; needs the per-wavenumber exponents of
+// launch_block_exponents).
 enum ContractVariant {
   kContractAuto = -1, kContractTma1 = 0, kContractTma3 = 1, kContractPanel = 2, kContractTma1Row = 3,
-  kContractMma = 4, kContractMmaUnpack = 5, kContractTc = 6
+  kContractMma = 4, kContractMmaUnpack = 5, kContractTc = 6, kContractTc16 = 7
 };
-constexpr int kContractVariants = 7;
+constexpr int kContractVariants = 8;
 bool contract_variant_available(int variant, int Nz, int R, bool c64);
 // Whether the panel kernel, the fallback of every variant, can stage a contraction of
 // Nz layers and R right-hand sides (c64 or c128) in shared memory.
@@ -29,9 +32,14 @@ bool contract_fits(int Nz, int R, bool c64);
 // 3 Nz > 1024, ldz < R 3Nz or a launch fails (nothing is applied then).
 // err: device word in which a kernel records a wait that ran out (kContractTimeout; the
 // wavenumbers it had not reached stay uncontracted); NULL: the library's own word.
+// qexp: the per-wavenumber exponents of launch_block_exponents (variant 7 only; may be
+// NULL, which makes variant 7 fall back).
 template <typename T>
 int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant, int *err,
-                    cudaStream_t s);
+                    cudaStream_t s, const int *qexp = nullptr);
+// qexp[w] = the exponent that scales the largest |re|, |im| of the packed c64 block of
+// folded wavenumber w into [2^13, 2^14) (nf blocks of 2 Nz (2 Nz + 1) complex).
+void launch_block_exponents(const float2 *qf, int *qexp, long long nf, int Nz, cudaStream_t s);
 
 // Double-float copy of packed blocks: qdf[i] = (hi, lo of re, hi, lo of im) of q64[i],
 // hi = fl32(x), lo = fl32(x - hi).

@@ -35,6 +35,7 @@
 // producer drains its copies and the issuer its MMAs, and TMEM is released.
 #pragma once
 #include <cuda.h>  // CUtensorMap (the map is encoded on the host through the runtime's driver entry point)
+#include <cuda_fp16.h>
 
 #include "contract_tma.cuh"
 
@@ -66,6 +67,9 @@ __device__ __forceinline__ void st4(uint32_t taddr, const uint32_t (&r)[4]) {
                "r"(r[2]), "r"(r[3])
                : "memory");
 }
+__device__ __forceinline__ void st2(uint32_t taddr, const uint32_t (&r)[2]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(r[0]), "r"(r[1]) : "memory");
+}
 __device__ __forceinline__ void ld2(uint32_t taddr, uint32_t &a, uint32_t &b) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr) : "memory");
 }
@@ -79,6 +83,26 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 // Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// Instruction descriptor of kind::f16 with FP16 A and B (format 0), FP32 accumulator.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// D (+)= A B, A in TMEM, B from a shared-memory descriptor; kind::tf32 or kind::f16
+template <bool F16>
+__device__ __forceinline__ void mma_k(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  if constexpr (F16)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+            d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+            d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
 }
 // D (+)= A B, A in TMEM, B from a shared-memory descriptor
 __device__ __forceinline__ void mma(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
@@ -146,6 +170,37 @@ __device__ __forceinline__ bool wait(uint64_t *bar, uint32_t phase, long long li
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t phase, long long lim) {
   return __all_sync(0xffffffffu, wait(bar, phase, lim)) != 0;
 }
+// FP16 split of a pair: hi = fp16(x) (11 significant bits), lo = fp16(x - hi); the
+// pairs packed as the two halves of a 32-bit word (first element in the low half)
+__device__ __forceinline__ void split_h2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(__fsub_rn(x0, hf.x), __fsub_rn(x1, hf.y));
+  hi = *reinterpret_cast<const uint32_t *>(&h);
+  lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+// AND of v over the threads of named barrier `id` (count threads), which it also
+// synchronises: every B warp of the FP16 path takes the same decision after its bounded
+// waits, so none is ever left alone at the named barriers that follow
+template <int COUNT>
+__device__ __forceinline__ bool bar_and(int id, bool v) {
+  uint32_t r;
+  asm volatile("{\n .reg .pred q, p;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, %2, %3, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(r)
+               : "r"((uint32_t)v), "r"(id), "n"(COUNT)
+               : "memory");
+  return r != 0;
+}
+// 2^e as a float, e in [-126, 127]
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
+// exponent that scales a maximum m into [2^13, 2^14) (0 for m = 0), clamped to [-100, 100]
+__device__ __forceinline__ int scale_exp(float m) {
+  if (!(m > 0.f)) return 0;
+  const int e = (int)((__float_as_uint(m) >> 23) & 0xFFu) - 127;
+  const int x = 13 - e;
+  return x < -100 ? -100 : (x > 100 ? 100 : x);
+}
+
 // x = hi + lo exactly: hi = x rounded to TF32 (10 fraction bits), lo = x - hi
 __device__ __forceinline__ void split(float x, uint32_t &hi, uint32_t &lo) {
   const uint32_t h = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
@@ -155,7 +210,7 @@ __device__ __forceinline__ void split(float x, uint32_t &hi, uint32_t &lo) {
 
 }  // namespace tc
 
-template <int NZ, int R>
+template <int NZ, int R, bool F16 = false>
 struct TcCfg {
   static_assert(NZ % 8 == 0 && 3 * NZ <= 128, "one M = 128 tile of 3 Nz output rows; chunks of whole k-steps");
   static_assert(R >= 1 && R <= 2, "N = 16: 8 complex columns = 4 mirrors x R");
@@ -173,9 +228,15 @@ struct TcCfg {
   static constexpr int WARPS = 4 + NROW;
   static constexpr int THREADS = 32 * WARPS;
   static constexpr int NS = 3;                     // shared-memory stages
-  static constexpr int NA = 3;                     // TMEM chunk buffers
   static constexpr int KC = 2 * NZ;                // K of a chunk (real)
-  static constexpr int ACOLS = 4 * NZ;             // TMEM columns of a chunk buffer (hi, lo)
+  // kind::tf32: one element per TMEM column and K = 8 per instruction; kind::f16: two per
+  // column and K = 16, so a chunk takes half the columns and the ring can be twice as deep
+  static constexpr int EPC = F16 ? 2 : 1;
+  static constexpr int KSTEP = F16 ? 16 : 8;
+  static constexpr int NKS = KC / KSTEP;           // k-steps of a chunk
+  static constexpr int AHALF = KC / EPC;           // TMEM columns of the hi (or lo) part of a chunk
+  static constexpr int ACOLS = 2 * AHALF;          // TMEM columns of a chunk buffer (hi, lo)
+  static constexpr int NA = F16 ? 6 : 3;           // TMEM chunk buffers
   static constexpr int DCOL = NA * ACOLS;          // first accumulator column
   static constexpr int DBUF = 64;                  // per buffer: D1 (32 columns) and D2 (16), padded
   static constexpr int TCOLS = DCOL + 2 * DBUF <= 256 ? 256 : 512;
@@ -193,10 +254,11 @@ struct TcCfg {
   static constexpr size_t XR = (size_t)4 * CZ * 8;
   static constexpr size_t STAGE = ((OFF_XR + XR + 1023) / 1024) * 1024;
   static constexpr int FULLC = (int)(OFF_FULL / 8), BOXC = (int)(BOX / 8);
-  // B operand: per chunk and hi / lo, N = 16 rows of K = KC (core matrices 8 x 16 bytes):
-  // byte (n % 8) 16 + (n / 8) SBO + (k / 4) 128 + (k % 4) 4
+  // B operand: per chunk and hi / lo, N = 16 rows of K = KC (core matrices 8 rows x 16
+  // bytes of KPC elements): byte (n % 8) 16 + (n / 8) SBO + (k / KPC) 128 + (k % KPC) esz
+  static constexpr int KPC = F16 ? 8 : 4;
   static constexpr uint32_t LBO = 128;
-  static constexpr uint32_t SBO = (uint32_t)(KC / 4) * 128;
+  static constexpr uint32_t SBO = (uint32_t)(KC / KPC) * 128;
   static constexpr size_t BPART = (size_t)2 * SBO;            // one chunk, hi or lo
   static constexpr size_t BBUF = (size_t)3 * 2 * BPART;       // one wavenumber
   static constexpr size_t OFF_BAR = 0;                        // 32 mbarriers + the TMEM address
@@ -205,19 +267,24 @@ struct TcCfg {
   static constexpr size_t SMEM = OFF_B + 2 * BBUF;
   static_assert(NZ % 16 == 0, "full-block rows in boxes of 16 complex (128 bytes)");
   static_assert(STAGE / 8 < 32768, "16-bit stage offsets");
-  static constexpr uint32_t IDESC = tc::idesc_tf32(128, 16);
-  static constexpr uint32_t IDESC32 = tc::idesc_tf32(128, 32);
+  static constexpr uint32_t IDESC = F16 ? tc::idesc_f16(128, 16) : tc::idesc_tf32(128, 16);
+  static constexpr uint32_t IDESC32 = F16 ? tc::idesc_f16(128, 32) : tc::idesc_tf32(128, 32);
 };
 
 // Timing instrumentation (PROF = true only in measurement builds): per warp, clock64()
 // cycles accumulated in the slots of TcProf, written to prof[(block * WARPS + warp) * 8].
 enum TcProf { kPWaitA = 0, kPWaitB = 1, kPWaitC = 2, kPWork = 3, kPWaitSt = 4, kPEpi = 5, kPTotal = 6, kPIters = 7 };
 
-template <int NZ, int R, bool PROF = false>
-__global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
+// F16: the kind::f16 instructions on a scaled two-way FP16 split (11 + 11 significant bits,
+// as in the TF32 split): the block of wavenumber w is scaled by 2^qexp[w] and column c of
+// X by 2^xe[c] (powers of two that bring the largest magnitudes into [2^13, 2^14), so
+// that FP16 keeps every entry whose size matters to the product), and the outputs are
+// scaled back exactly.
+template <int NZ, int R, bool F16 = false, bool PROF = false>
+__global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     contract_tc_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err,
                        long long lim_polls, const __grid_constant__ CUtensorMap tfull,
-                       unsigned long long *prof) {
+                       const int *__restrict__ qexp, unsigned long long *prof) {
   unsigned long long pt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long t_mark = 0;
   auto tic = [&]() {
@@ -231,16 +298,22 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     }
   };
   const long long t_begin = PROF ? clock64() : 0;
-  using Cfg = TcCfg<NZ, R>;
+  using Cfg = TcCfg<NZ, R, F16>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, NS = Cfg::NS, NA = Cfg::NA;
   constexpr int KC = Cfg::KC, EPW = Cfg::EPW;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   // the swizzled boxes need 1024-byte aligned destinations: the launch adds 1024 bytes
   unsigned char *sm = sm_raw + ((1024u - (tma::smem_u32(sm_raw) & 1023u)) & 1023u);
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Cfg::OFF_BAR);
-  uint64_t *full = bars, *empty = bars + 4, *afull = bars + 8, *aempty = bars + 12;
-  uint64_t *bfull = bars + 16, *bempty = bars + 18, *dfull = bars + 20, *dempty = bars + 22, *fin = bars + 24;
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Cfg::OFF_BAR + 256);
+  // barrier block: full[4] empty[4] afull[8] aempty[8] bfull[2] bempty[2] dfull[2] dempty[2]
+  // fin (33 x 8 bytes), the TMEM address at 384, the FP16 column exponents at 512..639 and
+  // maxima at 640..671 of the 1024-byte block
+  static_assert(NS <= 4 && NA <= 8, "barrier block");
+  uint64_t *full = bars, *empty = bars + 4, *afull = bars + 8, *aempty = bars + 16;
+  uint64_t *bfull = bars + 24, *bempty = bars + 26, *dfull = bars + 28, *dempty = bars + 30, *fin = bars + 32;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Cfg::OFF_BAR + 384);
+  int *xexp = reinterpret_cast<int *>(sm + Cfg::OFF_BAR + 512);              // F16: [4][8] column exponents
+  uint32_t *xmax = reinterpret_cast<uint32_t *>(sm + Cfg::OFF_BAR + 640);    // F16: [8] column maxima
   unsigned char *stages = sm + Cfg::OFF_STAGE;
   unsigned char *bbuf = sm + Cfg::OFF_B;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -362,13 +435,13 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
           }
           toc(kPWaitC);
           tc::fence_after();
-          const uint32_t ahi = tbase + c * Cfg::ACOLS, alo = ahi + KC;
+          const uint32_t ahi = tbase + c * Cfg::ACOLS, alo = ahi + Cfg::AHALF;
           const uint64_t dh0 = bdesc + (((size_t)bb * Cfg::BBUF + (size_t)(2 * beta) * Cfg::BPART) >> 4);
 #pragma unroll
-          for (int ks = 0; ks < KC / 8; ++ks) {
+          for (int ks = 0; ks < Cfg::NKS; ++ks) {
             const uint32_t acc = (beta | ks) != 0;
-            tc::mma(d1, ahi + 8 * ks, dh0 + 16u * ks, Cfg::IDESC32, acc);  // A_hi [B_hi | B_lo]
-            tc::mma(d2, alo + 8 * ks, dh0 + 16u * ks, Cfg::IDESC, acc);    // A_lo B_hi
+            tc::mma_k<F16>(d1, ahi + 8 * ks, dh0 + 16u * ks, Cfg::IDESC32, acc);  // A_hi [B_hi | B_lo]
+            tc::mma_k<F16>(d2, alo + 8 * ks, dh0 + 16u * ks, Cfg::IDESC, acc);    // A_lo B_hi
           }
           tc::commit(&aempty[c]);
           toc(kPWork);
@@ -412,7 +485,8 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
         else offp[beta][e >> 1] = (uint32_t)off;
       }
     }
-    auto epilogue = [&](int e) -> bool {
+    int ea_cur = 0, ea_prev = 0;  // F16: block exponents of the current and the previous wavenumber
+    auto epilogue = [&](int e, int ea) -> bool {
       const int bb = e & 1;
       tic();
       if (!tc::warp_wait(&dfull[bb], (uint32_t)((e >> 1) & 1), lim)) return false;
@@ -427,6 +501,11 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
       tc::ld2(dc + 32 + 2 * jw, v[8], v[9]);       // A_lo B_hi: Y_r
       tc::ld2(dc + 40 + 2 * jw, v[10], v[11]);     //            Y_i
       tc::wait_ld();
+      int xe0 = 0, xe1 = 0;
+      if constexpr (F16) {  // read before dempty is released (the B warps reuse the ring later)
+        xe0 = xexp[(e & 3) * 8 + 2 * jw];
+        xe1 = xexp[(e & 3) * 8 + 2 * jw + 1];
+      }
       tc::fence_before();
       __syncwarp();
       if (lane == 0) tc::arrive(&dempty[bb]);
@@ -442,6 +521,11 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
             float2 y = make_float2(__uint_as_float(v[h]) + (__uint_as_float(v[4 + h]) + __uint_as_float(v[8 + h])),
                                    __uint_as_float(v[2 + h]) + (__uint_as_float(v[6 + h]) + __uint_as_float(v[10 + h])));
             if ((alpha == 0 && mx == 1) || (alpha == 1 && my == 1)) { y.x = -y.x; y.y = -y.y; }
+            if constexpr (F16) {  // undo the scalings (exact powers of two)
+              const float sc = tc::pow2f(-ea) * tc::pow2f(-(h ? xe1 : xe0));
+              y.x *= sc;
+              y.y *= sc;
+            }
             spec[mw.pos(mx, my, Nx) * ldz + r * N3 + row] = y;
           }
         }
@@ -455,6 +539,9 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
       if (!tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim)) { ok = false; break; }
       toc(kPWaitA);
       const float2 *st = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE);
+      ea_prev = ea_cur;
+      if constexpr (F16) ea_cur = __ldg(qexp + w0 + it * gs);
+      const float ascale = F16 ? tc::pow2f(ea_cur) : 1.f;
 #pragma unroll
       for (int beta = 0; beta < 3; ++beta) {
         const int g = 3 * it + beta, c = g % NA;
@@ -466,26 +553,54 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
         toc(kPWaitB);
         tc::fence_after();
         const bool neg = alpha == 2 && beta < 2;
-        uint32_t rh[EPW], ih[EPW], rl[EPW], il[EPW];
+        if constexpr (F16) {
+          // entries (b, b + 1) as one word: re parts at K = b (columns AHALF-relative b / 2),
+          // im parts at K = Nz + b
+          constexpr int HW = EPW / 2;
+          uint32_t rh[HW], ih[HW], rl[HW], il[HW];
+          const float sg = neg ? -ascale : ascale;
 #pragma unroll
-        for (int e = 0; e < EPW; ++e) {
-          const uint32_t off = (offp[beta][e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
-          float2 m = live ? st[off] : make_float2(0.f, 0.f);
-          if (neg) { m.x = -m.x; m.y = -m.y; }
-          tc::split(m.x, rh[e], rl[e]);
-          tc::split(m.y, ih[e], il[e]);
-        }
-        const uint32_t ab = tq + c * Cfg::ACOLS + jw * EPW;
-        if constexpr (EPW == 8) {
-          tc::st8(ab, rh);
-          tc::st8(ab + NZ, ih);
-          tc::st8(ab + KC, rl);
-          tc::st8(ab + KC + NZ, il);
+          for (int e2 = 0; e2 < HW; ++e2) {
+            const uint32_t o = offp[beta][e2];
+            float2 m0 = live ? st[o & 0xFFFFu] : make_float2(0.f, 0.f);
+            float2 m1 = live ? st[o >> 16] : make_float2(0.f, 0.f);
+            tc::split_h2(m0.x * sg, m1.x * sg, rh[e2], rl[e2]);
+            tc::split_h2(m0.y * sg, m1.y * sg, ih[e2], il[e2]);
+          }
+          const uint32_t ab = tq + c * Cfg::ACOLS + jw * HW;
+          if constexpr (HW == 4) {
+            tc::st4(ab, rh);
+            tc::st4(ab + NZ / 2, ih);
+            tc::st4(ab + Cfg::AHALF, rl);
+            tc::st4(ab + Cfg::AHALF + NZ / 2, il);
+          } else {
+            tc::st2(ab, rh);
+            tc::st2(ab + NZ / 2, ih);
+            tc::st2(ab + Cfg::AHALF, rl);
+            tc::st2(ab + Cfg::AHALF + NZ / 2, il);
+          }
         } else {
-          tc::st4(ab, rh);
-          tc::st4(ab + NZ, ih);
-          tc::st4(ab + KC, rl);
-          tc::st4(ab + KC + NZ, il);
+          uint32_t rh[EPW], ih[EPW], rl[EPW], il[EPW];
+#pragma unroll
+          for (int e = 0; e < EPW; ++e) {
+            const uint32_t off = (offp[beta][e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+            float2 m = live ? st[off] : make_float2(0.f, 0.f);
+            if (neg) { m.x = -m.x; m.y = -m.y; }
+            tc::split(m.x, rh[e], rl[e]);
+            tc::split(m.y, ih[e], il[e]);
+          }
+          const uint32_t ab = tq + c * Cfg::ACOLS + jw * EPW;
+          if constexpr (EPW == 8) {
+            tc::st8(ab, rh);
+            tc::st8(ab + NZ, ih);
+            tc::st8(ab + KC, rl);
+            tc::st8(ab + KC + NZ, il);
+          } else {
+            tc::st4(ab, rh);
+            tc::st4(ab + NZ, ih);
+            tc::st4(ab + KC, rl);
+            tc::st4(ab + KC + NZ, il);
+          }
         }
         toc(kPWork);
         tc::wait_st();
@@ -497,9 +612,9 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
       if (!ok) break;
       __syncwarp();
       if (lane == 0) tc::arrive(&empty[s]);
-      if (it >= 1 && !epilogue(it - 1)) { ok = false; break; }
+      if (it >= 1 && !epilogue(it - 1, ea_prev)) { ok = false; break; }
     }
-    if (ok && n_it >= 1) ok = epilogue(n_it - 1);
+    if (ok && n_it >= 1) ok = epilogue(n_it - 1, ea_cur);
   } else {
     // ---- B warps: warps 2, 3 and the row warps of quadrants without rows ----
     // One complex value x = X[col][beta Nz + b] (mirror signs applied) per thread and
@@ -512,20 +627,97 @@ __global__ void __launch_bounds__(TcCfg<NZ, R>::THREADS, 1)
     for (int it = 0; it < n_it && ok; ++it) {
       const int s = it % NS, bb = it & 1;
       tic();
-      if (!tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim)) {
-        ok = false;
-        break;
-      }
+      bool got = tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim);
       toc(kPWaitA);
-      if (it >= 2 && !tc::warp_wait(&bempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim)) {
+      if (got && it >= 2) got = tc::warp_wait(&bempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim);
+      toc(kPWaitB);
+      if constexpr (F16) got = tc::bar_and<Cfg::NB * 32>(1, got);
+      if (!got) {
         ok = false;
         break;
       }
-      toc(kPWaitB);
       const Mirrors mw = mirrors_of(w0 + it * gs, Nx, Ny);
       const int ncol = mw.nmx * mw.nmy * R;
       const float2 *xr = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE + Cfg::OFF_XR);
       unsigned char *bp = bbuf + (size_t)bb * Cfg::BBUF;
+      if constexpr (F16) {
+        // (1) the largest |re|, |im| of every column, (2) its scale exponent, (3) the
+        // columns scaled, split and stored 8 rows (16 bytes of a core-matrix row) at a
+        // time.  Named barrier 1 orders the phases among the B warps only.
+        constexpr int NBT = Cfg::NB * 32;
+        if (bt < 8) xmax[bt] = 0u;
+        asm volatile("bar.sync 1, %0;" ::"n"(NBT) : "memory");
+        constexpr int QPC = N3 / 4;  // 4-row groups per column
+        for (int e = bt; e < 8 * QPC; e += nbt) {
+          const int col = e / QPC, z0 = (e - col * QPC) * 4;
+          if (col < ncol) {
+            const int m = col / R, r = col - m * R;
+            const float4 *x4 = reinterpret_cast<const float4 *>(xr + (size_t)m * CZ + r * N3 + z0);
+            const float4 u = x4[0], v = x4[1];
+            float mx = fmaxf(fmaxf(fabsf(u.x), fabsf(u.y)), fmaxf(fabsf(u.z), fabsf(u.w)));
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            atomicMax(&xmax[col], __float_as_uint(mx));
+          }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(NBT) : "memory");
+        if (bt < 8) xexp[(it & 3) * 8 + bt] = tc::scale_exp(__uint_as_float(xmax[bt]));
+        int myexp[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) myexp[c] = tc::scale_exp(__uint_as_float(xmax[c]));
+        asm volatile("bar.sync 1, %0;" ::"n"(NBT) : "memory");
+        constexpr int OPC = N3 / 8;  // 8-row groups per column (never across a component: Nz % 8 == 0)
+        for (int e = bt; e < 8 * OPC; e += nbt) {
+          const int col = e & 7, oct = e >> 3;
+          const int z0 = oct * 8, beta = z0 / NZ, b0 = z0 - beta * NZ;
+          float xs[8], ys[8];
+          if (col < ncol) {
+            const int m = col / R, r = col - m * R;
+            const int mx = m % mw.nmx, my = m / mw.nmx;
+            const bool flip = (beta == 0 && mx == 1) || (beta == 1 && my == 1);
+            float sc = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (c == col) sc = tc::pow2f(myexp[c]);
+            if (flip) sc = -sc;
+            const float4 *x4 = reinterpret_cast<const float4 *>(xr + (size_t)m * CZ + r * N3 + z0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float4 u = x4[j];
+              xs[2 * j] = u.x * sc;
+              ys[2 * j] = u.y * sc;
+              xs[2 * j + 1] = u.z * sc;
+              ys[2 * j + 1] = u.w * sc;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) xs[j] = ys[j] = 0.f;
+          }
+          uint4 rh, rl, ih, il;
+          tc::split_h2(xs[0], xs[1], rh.x, rl.x);
+          tc::split_h2(xs[2], xs[3], rh.y, rl.y);
+          tc::split_h2(xs[4], xs[5], rh.z, rl.z);
+          tc::split_h2(xs[6], xs[7], rh.w, rl.w);
+          tc::split_h2(ys[0], ys[1], ih.x, il.x);
+          tc::split_h2(ys[2], ys[3], ih.y, il.y);
+          tc::split_h2(ys[4], ys[5], ih.z, il.z);
+          tc::split_h2(ys[6], ys[7], ih.w, il.w);
+          const uint4 nih = make_uint4(ih.x ^ 0x80008000u, ih.y ^ 0x80008000u, ih.z ^ 0x80008000u, ih.w ^ 0x80008000u);
+          const uint4 nil = make_uint4(il.x ^ 0x80008000u, il.y ^ 0x80008000u, il.z ^ 0x80008000u, il.w ^ 0x80008000u);
+          // rows k = b0 .. b0 + 7 (multiply M_r) and Nz + b0 .. (multiply M_i) of columns col
+          // (Y_r) and 8 + col (Y_i): byte (n % 8) 16 + (n / 8) SBO + (k / 8) 128
+          unsigned char *p0 = bp + (size_t)(2 * beta) * Cfg::BPART + (size_t)col * 16 + (size_t)(b0 >> 3) * 128;
+          unsigned char *p1 = p0 + (size_t)(NZ >> 3) * 128;
+          constexpr size_t LO = Cfg::BPART;
+          *reinterpret_cast<uint4 *>(p0) = rh;
+          *reinterpret_cast<uint4 *>(p0 + LO) = rl;
+          *reinterpret_cast<uint4 *>(p0 + Cfg::SBO) = ih;
+          *reinterpret_cast<uint4 *>(p0 + Cfg::SBO + LO) = il;
+          *reinterpret_cast<uint4 *>(p1) = nih;
+          *reinterpret_cast<uint4 *>(p1 + LO) = nil;
+          *reinterpret_cast<uint4 *>(p1 + Cfg::SBO) = rh;
+          *reinterpret_cast<uint4 *>(p1 + Cfg::SBO + LO) = rl;
+        }
+      } else
       // entry e = ((beta * Nz + b) / 4) * 32 + (col * 4 + b % 4)
       for (int e = bt; e < 3 * NZ * 8; e += nbt) {
         const int col = (e >> 2) & 7, bq = e & 3, grp = e >> 5;

@@ -41,6 +41,7 @@ struct Instance {
   double2 *q64 = nullptr;
   float2 *q32 = nullptr;
   float4 *qdf = nullptr;           // double-float copy of q64 (residuals of the mixed solver)
+  int *qexp = nullptr;             // per folded wavenumber: the scale exponent of its c64 block
   double2 *rtab = nullptr;         // receiver kernels [Ny][Nx][Nz][10] (after ie_set_receivers)
   double2 en{0.0, 0.0}, hn{0.0, 0.0};  // normal E^N and E^N'/(i w mu0) at the receiver depth
 };
@@ -279,6 +280,8 @@ ie_status build_spectral(ie_ctx *c, Instance &in, const double *q_host) {
   IE_TRY(cuda_status(e));
   IE_TRY(dalloc(c, &in.qdf, nf * BS * sizeof(float4)));
   ie::launch_split_df(in.q64, in.qdf, nf * BS, c->stream);
+  IE_TRY(dalloc(c, &in.qexp, nf * sizeof(int)));
+  ie::launch_block_exponents(in.q32, in.qexp, nf, Nz, c->stream);
   return cuda_status(cudaGetLastError());
 }
 
@@ -318,8 +321,8 @@ ie_status contract_group(ie_ctx *c, const Group &g, ie::C<T> *spec, cudaStream_t
     if constexpr (sizeof(T) == 8) {
       if (df && ie::launch_contract_df(sk, c->inst[g.inst[k]].qdf, c->nx, c->ny, c->nz, g.rpi, CZ, s) == 0) continue;
     }
-    if (ie::launch_contract<T>(sk, qf<T>(c->inst[g.inst[k]]), c->nx, c->ny, c->nz, g.rpi, CZ, variant, c->err, s) !=
-        0)
+    if (ie::launch_contract<T>(sk, qf<T>(c->inst[g.inst[k]]), c->nx, c->ny, c->nz, g.rpi, CZ, variant, c->err, s,
+                               c->inst[g.inst[k]].qexp) != 0)
       return IE_ERR_CUDA;
   }
   if (c->prof) {
@@ -937,7 +940,8 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
       cudaEventRecord(ev[1], s);
       ie::launch_fft_axis<float, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[2], s);
-      bad |= ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, CZ, c->cvar[nrhs], c->err, s);
+      bad |= ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, CZ, c->cvar[nrhs], c->err, s,
+                                        c->inst[inst].qexp);
       cudaEventRecord(ev[3], s);
       ie::launch_fft_axis<float, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[4], s);
@@ -982,10 +986,11 @@ ie_status autotune_contraction(ie_ctx *c) {
       if (ie::contract_variant_available(v, Nz, rpi, true)) ++n_avail;
     for (int v = 0; v < ie::kContractVariants && n_avail > 1; ++v) {
       if (!ie::contract_variant_available(v, Nz, rpi, true)) continue;
-      bool ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream) == 0;
+      const int *qe = c->inst[0].qexp;
+      bool ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream, qe) == 0;
       cudaEventRecord(e0, c->stream);
       for (int k = 0; k < 3 && ok; ++k)
-        ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream) == 0;
+        ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream, qe) == 0;
       cudaEventRecord(e1, c->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) { st = IE_ERR_CUDA; break; }
       float ms = 0.f;

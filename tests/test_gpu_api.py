@@ -45,7 +45,7 @@ def _ctx_nz16():
     return m, q, lib_context(m, [q], max_rhs=2)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 3, 4, 5, 6, 7])
 def test_timed_out_contraction_is_reported_by_sync(variant):
     need_gpu()
     from paper_1512_06126_gb300 import ie

@@ -55,7 +55,7 @@ def test_forced_contraction_variants_against_oracle(shape):
     # Nz in {16, 32}
     assert (2, 5) in tried and (1, 2) in tried, tried
     if nz in (16, 32):
-        assert (1, 6) in tried and (2, 6) in tried, tried
+        assert {(1, 6), (2, 6), (1, 7), (2, 7)} <= set(tried), tried
     ctx.close()
 
 
@@ -80,11 +80,11 @@ def _solve_all_modes(m, q, qt, variant=None, restart=16):
     return out, tuned
 
 
-@pytest.mark.parametrize("variant", [None, 5, 6])
+@pytest.mark.parametrize("variant", [None, 5, 6, 7])
 def test_fast_path_solves_against_oracle(variant):
     """64 x 64 x 32 cells (the C2 background and anomaly layout cut to 64 x 64):
     register-blocked FFTs of length 128 and the tensor-core contraction (the
-    autotuner's choice, then the mma.sync and the tcgen05 kernels forced)."""
+    autotuner's choice, then the mma.sync and the two tcgen05 kernels forced)."""
     need_gpu()
     c2 = W.config2()
     g = W.Grid(64, 64, 32, c2.grid.hx, c2.grid.hy, c2.grid.z_edges)
