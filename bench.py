@@ -64,6 +64,7 @@ if ROOT not in sys.path:
 import workloads as W  # noqa: E402
 
 METRIC = "IE matvec GB/s & unknowns*iters/s; GMRES time-to-solution at 1e-7, mixed vs FP64"
+PRECISIONS_BY_NAME = {"fp64": 0, "mixed": 1, "fp64k": 2}  # ie.IE_FP64, IE_MIXED, IE_MIXED_FP64K
 UNIT = "unknowns*iters/s"
 TOL = 1e-7
 
@@ -433,19 +434,22 @@ def run_ours(args, rank, ws):
     mx_s, mx_info = timed_solves(ctx, ie.IE_MIXED, args.tts_repeats)
     # the plain FP64 solve at its own best restart length (longer than the mixed one's),
     # on a context of its own
-    ctx64 = ie.Context(g, model.layers, model.sigma_a, model.freqs[:1], None, max_rhs=R,
-                       restart=args.restart_fp64)
-    fp_s, fp_info = timed_solves(ctx64, ie.IE_FP64, args.tts_repeats)
-    ctx64.close()
+    if not args.skip_fp64:
+        ctx64 = ie.Context(g, model.layers, model.sigma_a, model.freqs[:1], None, max_rhs=R,
+                           restart=args.restart_fp64)
+        fp_s, fp_info = timed_solves(ctx64, ie.IE_FP64, args.tts_repeats)
+        ctx64.close()
     tts = {"timed_mode": "IE_MIXED_FP64K",
            "mixed_fp64_krylov_s": _stats(step_s), "mixed_fp64_krylov_iters": iters / args.steps,
            "mixed_fp64_krylov_outer": outer / args.steps, "mixed_fp64_krylov_final_rel_res": res,
            "mixed_c64_krylov_s": _stats(mx_s), "mixed_c64_krylov_iters": mx_info[0].inner_iters,
            "mixed_c64_krylov_final_rel_res": max(i.final_rel_res for i in mx_info),
-           "fp64_s": _stats(fp_s), "fp64_iters": fp_info[0].inner_iters,
-           "fp64_final_rel_res": max(i.final_rel_res for i in fp_info),
-           "speedup_timed_vs_fp64": float(np.median(fp_s) / np.median(step_s)),
-           "speedup_c64_krylov_vs_fp64": float(np.median(fp_s) / np.median(mx_s))}
+           "speedup_c64_krylov_vs_timed": float(np.median(step_s) / np.median(mx_s))}
+    if not args.skip_fp64:
+        tts.update({"fp64_s": _stats(fp_s), "fp64_iters": fp_info[0].inner_iters,
+                    "fp64_final_rel_res": max(i.final_rel_res for i in fp_info),
+                    "speedup_timed_vs_fp64": float(np.median(fp_s) / np.median(step_s)),
+                    "speedup_c64_krylov_vs_fp64": float(np.median(fp_s) / np.median(mx_s))})
 
     # ---- matvec GB/s (c64, both polarisations) ----
     nf = (g.nx + 1) * (g.ny + 1)
@@ -533,7 +537,11 @@ def run_ours(args, rank, ws):
     # ---- cpu baseline and the accuracy check against the oracle (rank 0, N = 1) ----
     cpu = None
     err = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
+    # the oracle holds the full spectral blocks, 4 Nx Ny (3 Nz)^2 complex128
+    oracle_bytes = 4 * g.nx * g.ny * (3 * g.nz) ** 2 * 16
+    if oracle_bytes > 20e9:
+        err = cpu = {"skipped": f"the oracle's spectral blocks would take {oracle_bytes / 1e9:.0f} GB of host memory"}
+    elif rank == 0 and ws == 1 and not args.no_cpu:
         err = oracle_check(model, args)
         ncores = os.cpu_count() or 1
         legs = [cpu_leg(args.workload, th, args.cpu_iters) for th in (1, ncores)]
@@ -615,17 +623,32 @@ def run_matvec_only(args):
     ctx.close()
 
 
-def run_batch(args):
+def c3_summary(args, precision, with_fp64=True):
     """The batched configuration: 16 frequencies x 2 polarisations over four grids
-    (64^2x16, 96^2x24, 128^2x32, 192^2x48; frequency k on grid k mod 4).  Per grid,
-    its four frequencies (8 right-hand sides) are solved in one batched mixed-precision
-    solve (ie_solve_batch), then one instance at a time for comparison.  Device time
-    with CUDA events on the library stream, after one untimed batched solve."""
+    (64^2x16, 96^2x24, 128^2x32, 192^2x48; frequency k on grid k mod 4).  Per grid, its
+    four frequencies (8 right-hand sides) are solved in one batched solve
+    (ie_solve_batch) in `precision`, then one instance at a time in the same precision,
+    then (with_fp64) batched in plain FP64 on a context of its own (restart
+    --restart-fp64).  Device time with CUDA events on the library stream, after one
+    untimed solve of each kind."""
     import torch
     from paper_1512_06126_gb300 import build, ie
     build.build()
     out = []
-    t_b = t_s = 0.0
+    t_b = t_s = t_64 = 0.0
+
+    def timed(ctx, fn):
+        ext = torch.cuda.ExternalStream(ctx.stream)
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(ext):
+            e0.record()
+        r = fn()
+        with torch.cuda.stream(ext):
+            e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3, r
+
     for m in W.config3():
         g = m.grid
         nf = len(m.freqs)
@@ -637,42 +660,56 @@ def run_batch(args):
                 ctx.rhs_mt(k, p, b[k, p].data_ptr())
         u = torch.zeros_like(b)
         torch.cuda.synchronize()
-        ext = torch.cuda.ExternalStream(ctx.stream)
         insts = list(range(nf))
-        ctx.solve_batch(insts, b.data_ptr(), u.data_ptr(), 2, TOL, precision=ie.IE_MIXED)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(ext):
-            e0.record()
-        st, info = ctx.solve_batch(insts, b.data_ptr(), u.data_ptr(), 2, TOL, precision=ie.IE_MIXED)
-        with torch.cuda.stream(ext):
-            e1.record()
-        e1.synchronize()
-        tb = e0.elapsed_time(e1) / 1e3
+
+        def batched(c=ctx, prec=precision, uu=u):
+            uu.zero_()
+            return c.solve_batch(insts, b.data_ptr(), uu.data_ptr(), 2, TOL, precision=prec)
+        tb, (st, info) = timed(ctx, batched)
         u1 = torch.zeros_like(b[0])
-        with torch.cuda.stream(ext):
-            e0.record()
-        it_single = 0
-        res1 = 0.0
-        for k in range(nf):
-            st1, i1 = ctx.solve(k, b[k].data_ptr(), u1.data_ptr(), 2, TOL, precision=ie.IE_MIXED)
-            it_single += i1.inner_iters
-            res1 = max(res1, i1.final_rel_res)
-        with torch.cuda.stream(ext):
-            e1.record()
-        e1.synchronize()
-        ts = e0.elapsed_time(e1) / 1e3
-        out.append({"grid": f"{g.nx}x{g.ny}x{g.nz}", "instances": 2 * nf, "batched_s": tb,
-                    "batched_iters": info.inner_iters, "batched_res": info.final_rel_res, "one_at_a_time_s": ts,
-                    "one_at_a_time_iters": it_single, "one_at_a_time_res": res1, "status": [st, st1]})
+
+        def singles():
+            its, res, sts = 0, 0.0, []
+            for k in range(nf):
+                u1.zero_()
+                st1, i1 = ctx.solve(k, b[k].data_ptr(), u1.data_ptr(), 2, TOL, precision=precision)
+                its += i1.inner_iters
+                res = max(res, i1.final_rel_res)
+                sts.append(st1)
+            return its, res, sts
+        ts, (it_single, res1, st1) = timed(ctx, singles)
+        ctx.close()
+        rec = {"grid": f"{g.nx}x{g.ny}x{g.nz}", "instances": 2 * nf, "batched_s": tb,
+               "batched_iters": info.inner_iters, "batched_res": info.final_rel_res, "one_at_a_time_s": ts,
+               "one_at_a_time_iters": it_single, "one_at_a_time_res": res1, "status": [st] + st1}
+        if with_fp64:
+            ctx64 = ie.Context(g, m.layers, m.sigma_a, m.freqs, None, max_rhs=2 * nf, restart=args.restart_fp64)
+            t64, (st64, info64) = timed(ctx64, lambda: batched(ctx64, ie.IE_FP64))
+            ctx64.close()
+            rec.update({"fp64_batched_s": t64, "fp64_iters": info64.inner_iters, "fp64_res": info64.final_rel_res,
+                        "fp64_status": st64})
+            t_64 += t64
+        out.append(rec)
         t_b += tb
         t_s += ts
-        ctx.close()
         del b, u, u1
         torch.cuda.empty_cache()
-    print(json.dumps({"mode": "batch", "workload": "C3: 32 instances (16 frequencies x 2 polarisations) over 4 grids",
-                      "metric": "solved instances/s (mixed precision, tol 1e-7)",
-                      "batched": 32 / t_b, "one_at_a_time": 32 / t_s, "batched_s": t_b, "one_at_a_time_s": t_s,
-                      "tol": TOL, "per_grid": out}), flush=True)
+    res = {"workload": "C3: 32 instances (16 frequencies x 2 polarisations) over 4 grids",
+           "metric": "solved instances/s (tol 1e-7)", "precision": {ie.IE_MIXED: "IE_MIXED",
+                                                                     ie.IE_MIXED_FP64K: "IE_MIXED_FP64K",
+                                                                     ie.IE_FP64: "IE_FP64"}[precision],
+           "batched": 32 / t_b, "one_at_a_time": 32 / t_s, "batched_s": t_b, "one_at_a_time_s": t_s,
+           "tol": TOL, "per_grid": out}
+    if with_fp64:
+        res.update({"fp64_batched_s": t_64, "fp64": 32 / t_64, "speedup_batched_vs_fp64": t_64 / t_b,
+                    "speedup_batched_vs_one_at_a_time": t_s / t_b})
+    return res
+
+
+def run_batch(args):
+    print(json.dumps({"mode": "batch", **c3_summary(args, PRECISIONS_BY_NAME[args.precision],
+                                                    with_fp64=not args.skip_fp64)}),
+          flush=True)
 
 
 def run_gradient(args):
@@ -737,6 +774,9 @@ def main():
     ap.add_argument("--threads", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--iters", type=int, default=3, help=argparse.SUPPRESS)
     ap.add_argument("--mode", choices=["solve", "matvec", "batch", "gradient"], default="solve")
+    ap.add_argument("--precision", choices=list(PRECISIONS_BY_NAME), default="fp64k",
+                    help="batch mode: the precision of the batched and one-at-a-time solves")
+    ap.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 comparisons")
     ap.add_argument("--variant", type=int, default=-1,
                     help="matvec mode: force this contraction variant (default: the autotuner's choice)")
     args = ap.parse_args()

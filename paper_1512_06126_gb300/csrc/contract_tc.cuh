@@ -603,13 +603,17 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
           }
         }
         toc(kPWork);
-        tc::wait_st();
-        toc(kPWaitSt);
-        tc::fence_before();
-        __syncwarp();
-        if (lane == 0) tc::arrive(&afull[c]);
       }
       if (!ok) break;
+      // one wait for the stores of the three chunks, then the MMAs may read them
+      tc::wait_st();
+      toc(kPWaitSt);
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) {
+#pragma unroll
+        for (int beta = 0; beta < 3; ++beta) tc::arrive(&afull[(3 * it + beta) % NA]);
+      }
       __syncwarp();
       if (lane == 0) tc::arrive(&empty[s]);
       if (it >= 1 && !epilogue(it - 1, ea_prev)) { ok = false; break; }
@@ -645,19 +649,20 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
         // columns scaled, split and stored 8 rows (16 bytes of a core-matrix row) at a
         // time.  Named barrier 1 orders the phases among the B warps only.
         constexpr int NBT = Cfg::NB * 32;
-        if (bt < 8) xmax[bt] = 0u;
-        asm volatile("bar.sync 1, %0;" ::"n"(NBT) : "memory");
-        constexpr int QPC = N3 / 4;  // 4-row groups per column
-        for (int e = bt; e < 8 * QPC; e += nbt) {
-          const int col = e / QPC, z0 = (e - col * QPC) * 4;
+        // column col by B warp col % NB: lanes take 2-complex pairs of its 3 Nz rows,
+        // then a warp reduction (non-negative floats order like their bit patterns)
+        for (int col = bw; col < 8; col += Cfg::NB) {
+          uint32_t mx = 0u;
           if (col < ncol) {
             const int m = col / R, r = col - m * R;
-            const float4 *x4 = reinterpret_cast<const float4 *>(xr + (size_t)m * CZ + r * N3 + z0);
-            const float4 u = x4[0], v = x4[1];
-            float mx = fmaxf(fmaxf(fabsf(u.x), fabsf(u.y)), fmaxf(fabsf(u.z), fabsf(u.w)));
-            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-            atomicMax(&xmax[col], __float_as_uint(mx));
+            const float4 *x4 = reinterpret_cast<const float4 *>(xr + (size_t)m * CZ + r * N3);
+            for (int j = lane; j < N3 / 2; j += 32) {
+              const float4 u = x4[j];
+              mx = max(mx, __float_as_uint(fmaxf(fmaxf(fabsf(u.x), fabsf(u.y)), fmaxf(fabsf(u.z), fabsf(u.w)))));
+            }
           }
+          mx = __reduce_max_sync(0xffffffffu, mx);
+          if (lane == 0) xmax[col] = mx;
         }
         asm volatile("bar.sync 1, %0;" ::"n"(NBT) : "memory");
         if (bt < 8) xexp[(it & 3) * 8 + bt] = tc::scale_exp(__uint_as_float(xmax[bt]));
