@@ -179,18 +179,6 @@ __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t &hi, uint3
   hi = *reinterpret_cast<const uint32_t *>(&h);
   lo = *reinterpret_cast<const uint32_t *>(&l);
 }
-// AND of v over the threads of named barrier `id` (count threads), which it also
-// synchronises: every B warp of the FP16 path takes the same decision after its bounded
-// waits, so none is ever left alone at the named barriers that follow
-template <int COUNT>
-__device__ __forceinline__ bool bar_and(int id, bool v) {
-  uint32_t r;
-  asm volatile("{\n .reg .pred q, p;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, %2, %3, q;\n selp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(r)
-               : "r"((uint32_t)v), "r"(id), "n"(COUNT)
-               : "memory");
-  return r != 0;
-}
 // 2^e as a float, e in [-126, 127]
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
 // exponent that scales a maximum m into [2^13, 2^14) (0 for m = 0), clamped to [-100, 100]
@@ -306,14 +294,13 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
   unsigned char *sm = sm_raw + ((1024u - (tma::smem_u32(sm_raw) & 1023u)) & 1023u);
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Cfg::OFF_BAR);
   // barrier block: full[4] empty[4] afull[8] aempty[8] bfull[2] bempty[2] dfull[2] dempty[2]
-  // fin (33 x 8 bytes), the TMEM address at 384, the FP16 column exponents at 512..639 and
-  // maxima at 640..671 of the 1024-byte block
+  // fin (33 x 8 bytes), the TMEM address at 384 and the FP16 column exponents at 512..639
+  // of the 1024-byte block
   static_assert(NS <= 4 && NA <= 8, "barrier block");
   uint64_t *full = bars, *empty = bars + 4, *afull = bars + 8, *aempty = bars + 16;
   uint64_t *bfull = bars + 24, *bempty = bars + 26, *dfull = bars + 28, *dempty = bars + 30, *fin = bars + 32;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Cfg::OFF_BAR + 384);
   int *xexp = reinterpret_cast<int *>(sm + Cfg::OFF_BAR + 512);              // F16: [4][8] column exponents
-  uint32_t *xmax = reinterpret_cast<uint32_t *>(sm + Cfg::OFF_BAR + 640);    // F16: [8] column maxima
   unsigned char *stages = sm + Cfg::OFF_STAGE;
   unsigned char *bbuf = sm + Cfg::OFF_B;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -635,7 +622,6 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       toc(kPWaitA);
       if (got && it >= 2) got = tc::warp_wait(&bempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim);
       toc(kPWaitB);
-      if constexpr (F16) got = tc::bar_and<Cfg::NB * 32>(1, got);
       if (!got) {
         ok = false;
         break;
@@ -645,82 +631,63 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       const float2 *xr = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE + Cfg::OFF_XR);
       unsigned char *bp = bbuf + (size_t)bb * Cfg::BBUF;
       if constexpr (F16) {
-        // (1) the largest |re|, |im| of every column, (2) its scale exponent, (3) the
-        // columns scaled, split and stored 8 rows (16 bytes of a core-matrix row) at a
-        // time.  Named barrier 1 orders the phases among the B warps only.
-        constexpr int NBT = Cfg::NB * 32;
-        // column col by B warp col % NB: lanes take 2-complex pairs of its 3 Nz rows,
-        // then a warp reduction (non-negative floats order like their bit patterns)
+        // Each B warp owns whole columns (col = bw, bw + NB, ...): lane l < 3 Nz / 8 takes
+        // rows 8 l .. 8 l + 7 (one component: Nz % 8 == 0), a warp reduction of the
+        // largest |re|, |im| gives the column's scale exponent, and the scaled, split
+        // rows go out as 16-byte core-matrix rows of hi and lo.
+        constexpr int OPC = N3 / 8;  // 8-row groups per column
+        static_assert(OPC <= 32, "one 8-row group per lane");
         for (int col = bw; col < 8; col += Cfg::NB) {
-          uint32_t mx = 0u;
-          if (col < ncol) {
-            const int m = col / R, r = col - m * R;
-            const float4 *x4 = reinterpret_cast<const float4 *>(xr + (size_t)m * CZ + r * N3);
-            for (int j = lane; j < N3 / 2; j += 32) {
-              const float4 u = x4[j];
-              mx = max(mx, __float_as_uint(fmaxf(fmaxf(fabsf(u.x), fabsf(u.y)), fmaxf(fabsf(u.z), fabsf(u.w)))));
-            }
-          }
-          mx = __reduce_max_sync(0xffffffffu, mx);
-          if (lane == 0) xmax[col] = mx;
-        }
-        asm volatile("bar.sync 1, %0;" ::"n"(NBT) : "memory");
-        if (bt < 8) xexp[(it & 3) * 8 + bt] = tc::scale_exp(__uint_as_float(xmax[bt]));
-        int myexp[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) myexp[c] = tc::scale_exp(__uint_as_float(xmax[c]));
-        asm volatile("bar.sync 1, %0;" ::"n"(NBT) : "memory");
-        constexpr int OPC = N3 / 8;  // 8-row groups per column (never across a component: Nz % 8 == 0)
-        for (int e = bt; e < 8 * OPC; e += nbt) {
-          const int col = e & 7, oct = e >> 3;
-          const int z0 = oct * 8, beta = z0 / NZ, b0 = z0 - beta * NZ;
+          const bool have = lane < OPC;
+          const int z0 = have ? lane * 8 : 0, beta = z0 / NZ, b0 = z0 - beta * NZ;
           float xs[8], ys[8];
-          if (col < ncol) {
-            const int m = col / R, r = col - m * R;
-            const int mx = m % mw.nmx, my = m / mw.nmx;
-            const bool flip = (beta == 0 && mx == 1) || (beta == 1 && my == 1);
-            float sc = 0.f;
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-              if (c == col) sc = tc::pow2f(myexp[c]);
-            if (flip) sc = -sc;
+          for (int j = 0; j < 8; ++j) xs[j] = ys[j] = 0.f;
+          uint32_t mx = 0u;
+          if (have && col < ncol) {
+            const int m = col / R, r = col - m * R;
+            const int mxm = m % mw.nmx, mym = m / mw.nmx;
+            const bool flip = (beta == 0 && mxm == 1) || (beta == 1 && mym == 1);
             const float4 *x4 = reinterpret_cast<const float4 *>(xr + (size_t)m * CZ + r * N3 + z0);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const float4 u = x4[j];
-              xs[2 * j] = u.x * sc;
-              ys[2 * j] = u.y * sc;
-              xs[2 * j + 1] = u.z * sc;
-              ys[2 * j + 1] = u.w * sc;
+              xs[2 * j] = flip ? -u.x : u.x;
+              ys[2 * j] = flip ? -u.y : u.y;
+              xs[2 * j + 1] = flip ? -u.z : u.z;
+              ys[2 * j + 1] = flip ? -u.w : u.w;
+              mx = max(mx, __float_as_uint(fmaxf(fmaxf(fabsf(u.x), fabsf(u.y)), fmaxf(fabsf(u.z), fabsf(u.w)))));
             }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) xs[j] = ys[j] = 0.f;
           }
-          uint4 rh, rl, ih, il;
-          tc::split_h2(xs[0], xs[1], rh.x, rl.x);
-          tc::split_h2(xs[2], xs[3], rh.y, rl.y);
-          tc::split_h2(xs[4], xs[5], rh.z, rl.z);
-          tc::split_h2(xs[6], xs[7], rh.w, rl.w);
-          tc::split_h2(ys[0], ys[1], ih.x, il.x);
-          tc::split_h2(ys[2], ys[3], ih.y, il.y);
-          tc::split_h2(ys[4], ys[5], ih.z, il.z);
-          tc::split_h2(ys[6], ys[7], ih.w, il.w);
-          const uint4 nih = make_uint4(ih.x ^ 0x80008000u, ih.y ^ 0x80008000u, ih.z ^ 0x80008000u, ih.w ^ 0x80008000u);
-          const uint4 nil = make_uint4(il.x ^ 0x80008000u, il.y ^ 0x80008000u, il.z ^ 0x80008000u, il.w ^ 0x80008000u);
-          // rows k = b0 .. b0 + 7 (multiply M_r) and Nz + b0 .. (multiply M_i) of columns col
-          // (Y_r) and 8 + col (Y_i): byte (n % 8) 16 + (n / 8) SBO + (k / 8) 128
-          unsigned char *p0 = bp + (size_t)(2 * beta) * Cfg::BPART + (size_t)col * 16 + (size_t)(b0 >> 3) * 128;
-          unsigned char *p1 = p0 + (size_t)(NZ >> 3) * 128;
-          constexpr size_t LO = Cfg::BPART;
-          *reinterpret_cast<uint4 *>(p0) = rh;
-          *reinterpret_cast<uint4 *>(p0 + LO) = rl;
-          *reinterpret_cast<uint4 *>(p0 + Cfg::SBO) = ih;
-          *reinterpret_cast<uint4 *>(p0 + Cfg::SBO + LO) = il;
-          *reinterpret_cast<uint4 *>(p1) = nih;
-          *reinterpret_cast<uint4 *>(p1 + LO) = nil;
-          *reinterpret_cast<uint4 *>(p1 + Cfg::SBO) = rh;
-          *reinterpret_cast<uint4 *>(p1 + Cfg::SBO + LO) = rl;
+          const int ex = tc::scale_exp(__uint_as_float(__reduce_max_sync(0xffffffffu, mx)));
+          if (lane == 0) xexp[(it & 3) * 8 + col] = ex;
+          if (have) {
+            const float sc = tc::pow2f(ex);
+            uint4 rh, rl, ih, il;
+            tc::split_h2(xs[0] * sc, xs[1] * sc, rh.x, rl.x);
+            tc::split_h2(xs[2] * sc, xs[3] * sc, rh.y, rl.y);
+            tc::split_h2(xs[4] * sc, xs[5] * sc, rh.z, rl.z);
+            tc::split_h2(xs[6] * sc, xs[7] * sc, rh.w, rl.w);
+            tc::split_h2(ys[0] * sc, ys[1] * sc, ih.x, il.x);
+            tc::split_h2(ys[2] * sc, ys[3] * sc, ih.y, il.y);
+            tc::split_h2(ys[4] * sc, ys[5] * sc, ih.z, il.z);
+            tc::split_h2(ys[6] * sc, ys[7] * sc, ih.w, il.w);
+            const uint4 nih = make_uint4(ih.x ^ 0x80008000u, ih.y ^ 0x80008000u, ih.z ^ 0x80008000u, ih.w ^ 0x80008000u);
+            const uint4 nil = make_uint4(il.x ^ 0x80008000u, il.y ^ 0x80008000u, il.z ^ 0x80008000u, il.w ^ 0x80008000u);
+            // rows k = b0 .. b0 + 7 (multiply M_r) and Nz + b0 .. (multiply M_i) of columns
+            // col (Y_r) and 8 + col (Y_i): byte (n % 8) 16 + (n / 8) SBO + (k / 8) 128
+            unsigned char *p0 = bp + (size_t)(2 * beta) * Cfg::BPART + (size_t)col * 16 + (size_t)(b0 >> 3) * 128;
+            unsigned char *p1 = p0 + (size_t)(NZ >> 3) * 128;
+            constexpr size_t LO = Cfg::BPART;
+            *reinterpret_cast<uint4 *>(p0) = rh;
+            *reinterpret_cast<uint4 *>(p0 + LO) = rl;
+            *reinterpret_cast<uint4 *>(p0 + Cfg::SBO) = ih;
+            *reinterpret_cast<uint4 *>(p0 + Cfg::SBO + LO) = il;
+            *reinterpret_cast<uint4 *>(p1) = nih;
+            *reinterpret_cast<uint4 *>(p1 + LO) = nil;
+            *reinterpret_cast<uint4 *>(p1 + Cfg::SBO) = rh;
+            *reinterpret_cast<uint4 *>(p1 + Cfg::SBO + LO) = rl;
+          }
         }
       } else
       // entry e = ((beta * Nz + b) / 4) * 32 + (col * 4 + b % 4)
