@@ -244,9 +244,16 @@ struct TcCfg {
   static constexpr int FULLC = (int)(OFF_FULL / 8), BOXC = (int)(BOX / 8);
   // B operand: per chunk and hi / lo, N = 16 rows of K = KC (core matrices 8 rows x 16
   // bytes of KPC elements): byte (n % 8) 16 + (n / 8) SBO + (k / KPC) 128 + (k % KPC) esz
+  // FP16 at Nz = 32: a chunk's K row is 64 halves = 128 bytes, one atom of the 128-byte
+  // swizzle (row n of an 8-row group at (n % 8) 128, its 16-byte chunk j at position
+  // j ^ (n % 8); groups 1024 bytes apart; a k-step moves the start address by 32 bytes),
+  // in which the column-at-a-time stores of the B warps hit distinct banks
   static constexpr int KPC = F16 ? 8 : 4;
-  static constexpr uint32_t LBO = 128;
-  static constexpr uint32_t SBO = (uint32_t)(KC / KPC) * 128;
+  static constexpr bool SWZ = F16 && KC * 2 == 128;
+  static constexpr uint32_t LBO = SWZ ? 16 : 128;
+  static constexpr uint32_t SBO = SWZ ? 1024 : (uint32_t)(KC / KPC) * 128;
+  static constexpr uint32_t KADV = SWZ ? 2 : 16;  // descriptor units (16 bytes) per k-step
+  static constexpr uint64_t DESC_LAYOUT = SWZ ? (2ull << 61) : 0ull;
   static constexpr size_t BPART = (size_t)2 * SBO;            // one chunk, hi or lo
   static constexpr size_t BBUF = (size_t)3 * 2 * BPART;       // one wavenumber
   static constexpr size_t OFF_BAR = 0;                        // 32 mbarriers + the TMEM address
@@ -368,7 +375,8 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       const int nm = mi.nmx * mi.nmy;
       unsigned char *st = stages + (size_t)s * Cfg::STAGE;
       const float2 *q = qf + (size_t)w * BS;
-      tma::fence_proxy_async();
+      // (no proxy fence: nothing writes the stages through the generic proxy; their readers
+      // hand them back through the empty barrier)
       if (lane == 0) tma::mbar_expect_tx(&full[s], (uint32_t)((size_t)BS * 8 + (size_t)nm * CZ * 8));
       __syncwarp();
       const int ncopy = 1 + Cfg::NBOX + nm;
@@ -397,7 +405,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       // the descriptor's start-address field holds the byte address / 16 (shared memory
       // addresses stay below 2^18, so adding an offset / 16 never carries out of it): a
       // k-step (256 bytes further) adds 16
-      const uint64_t bdesc = tc::sdesc(tma::smem_u32(bbuf), Cfg::LBO, Cfg::SBO);
+      const uint64_t bdesc = tc::sdesc(tma::smem_u32(bbuf), Cfg::LBO, Cfg::SBO) | Cfg::DESC_LAYOUT;
       for (int it = 0; it < n_it && ok; ++it) {
         const int bb = it & 1;
         tic();
@@ -427,8 +435,8 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
 #pragma unroll
           for (int ks = 0; ks < Cfg::NKS; ++ks) {
             const uint32_t acc = (beta | ks) != 0;
-            tc::mma_k<F16>(d1, ahi + 8 * ks, dh0 + 16u * ks, Cfg::IDESC32, acc);  // A_hi [B_hi | B_lo]
-            tc::mma_k<F16>(d2, alo + 8 * ks, dh0 + 16u * ks, Cfg::IDESC, acc);    // A_lo B_hi
+            tc::mma_k<F16>(d1, ahi + 8 * ks, dh0 + Cfg::KADV * ks, Cfg::IDESC32, acc);  // A_hi [B_hi | B_lo]
+            tc::mma_k<F16>(d2, alo + 8 * ks, dh0 + Cfg::KADV * ks, Cfg::IDESC, acc);    // A_lo B_hi
           }
           tc::commit(&aempty[c]);
           toc(kPWork);
@@ -488,6 +496,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       tc::ld2(dc + 32 + 2 * jw, v[8], v[9]);       // A_lo B_hi: Y_r
       tc::ld2(dc + 40 + 2 * jw, v[10], v[11]);     //            Y_i
       tc::wait_ld();
+      toc(kPWaitSt);
       int xe0 = 0, xe1 = 0;
       if constexpr (F16) {  // read before dempty is released (the B warps reuse the ring later)
         xe0 = xexp[(e & 3) * 8 + 2 * jw];
@@ -594,7 +603,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       if (!ok) break;
       // one wait for the stores of the three chunks, then the MMAs may read them
       tc::wait_st();
-      toc(kPWaitSt);
+      toc(kPWork);
       tc::fence_before();
       __syncwarp();
       if (lane == 0) {
@@ -675,9 +684,16 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
             const uint4 nih = make_uint4(ih.x ^ 0x80008000u, ih.y ^ 0x80008000u, ih.z ^ 0x80008000u, ih.w ^ 0x80008000u);
             const uint4 nil = make_uint4(il.x ^ 0x80008000u, il.y ^ 0x80008000u, il.z ^ 0x80008000u, il.w ^ 0x80008000u);
             // rows k = b0 .. b0 + 7 (multiply M_r) and Nz + b0 .. (multiply M_i) of columns
-            // col (Y_r) and 8 + col (Y_i): byte (n % 8) 16 + (n / 8) SBO + (k / 8) 128
-            unsigned char *p0 = bp + (size_t)(2 * beta) * Cfg::BPART + (size_t)col * 16 + (size_t)(b0 >> 3) * 128;
-            unsigned char *p1 = p0 + (size_t)(NZ >> 3) * 128;
+            // col (Y_r) and 8 + col (Y_i, one SBO further)
+            unsigned char *cb = bp + (size_t)(2 * beta) * Cfg::BPART;
+            unsigned char *p0, *p1;
+            if constexpr (Cfg::SWZ) {
+              p0 = cb + (size_t)col * 128 + (size_t)(((b0 >> 3) ^ col) << 4);
+              p1 = cb + (size_t)col * 128 + (size_t)((((NZ >> 3) + (b0 >> 3)) ^ col) << 4);
+            } else {  // byte (n % 8) 16 + (n / 8) SBO + (k / 8) 128
+              p0 = cb + (size_t)col * 16 + (size_t)(b0 >> 3) * 128;
+              p1 = p0 + (size_t)(NZ >> 3) * 128;
+            }
             constexpr size_t LO = Cfg::BPART;
             *reinterpret_cast<uint4 *>(p0) = rh;
             *reinterpret_cast<uint4 *>(p0 + LO) = rl;
@@ -718,13 +734,14 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
         *reinterpret_cast<uint32_t *>(p1 + Cfg::SBO) = rh;                 // (Nz + b, 8 + col): X_r
         *reinterpret_cast<uint32_t *>(p1 + Cfg::SBO + LO) = rl;
       }
+      toc(kPWork);
       tma::fence_proxy_async();  // the MMA reads B through the async proxy
       __syncwarp();
       if (lane == 0) {
         tc::arrive(&bfull[bb]);
         tc::arrive(&empty[s]);
       }
-      toc(kPWork);
+      toc(kPEpi);
     }
   }
   if (!ok && lane == 0) atomicExch(err, kContractTimeout);
