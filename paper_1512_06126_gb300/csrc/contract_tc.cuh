@@ -151,6 +151,21 @@ __device__ __forceinline__ uint64_t evict_first_policy() {
 // of the time and would otherwise take the issue slots of the working ones).  The poll
 // limit of a launch is scaled down accordingly (a poll lasts up to kSuspendNs).
 constexpr uint32_t kSuspendNs = 10000;
+// the same, counting the polls into *polls when COUNT (measurement builds)
+template <bool COUNT>
+__device__ __forceinline__ bool wait_c(uint64_t *bar, uint32_t phase, long long lim, unsigned long long *polls) {
+  for (long long i = 0; i < lim; ++i) {
+    if constexpr (COUNT) ++*polls;
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tma::smem_u32(bar)), "r"(phase), "r"(kSuspendNs)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 __device__ __forceinline__ bool wait(uint64_t *bar, uint32_t phase, long long lim) {
   for (long long i = 0; i < lim; ++i) {
     uint32_t ok;
@@ -267,7 +282,8 @@ struct TcCfg {
 };
 
 // Timing instrumentation (PROF = true only in measurement builds): per warp, clock64()
-// cycles accumulated in the slots of TcProf, written to prof[(block * WARPS + warp) * 8].
+// cycles accumulated in the slots of TcProf, written to prof[(block * WARPS + warp) * 16],
+// and the number of barrier polls of lane 0 in slot 8.
 enum TcProf { kPWaitA = 0, kPWaitB = 1, kPWaitC = 2, kPWork = 3, kPWaitSt = 4, kPEpi = 5, kPTotal = 6, kPIters = 7 };
 
 // F16: the kind::f16 instructions on a scaled two-way FP16 split (11 + 11 significant bits,
@@ -293,6 +309,11 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     }
   };
   const long long t_begin = PROF ? clock64() : 0;
+  unsigned long long polls = 0;
+  auto wt = [&](uint64_t *bar, uint32_t ph, long long l) -> bool { return tc::wait_c<PROF>(bar, ph, l, &polls); };
+  auto wwt = [&](uint64_t *bar, uint32_t ph, long long l) -> bool {
+    return __all_sync(0xffffffffu, tc::wait_c<PROF>(bar, ph, l, &polls)) != 0;
+  };
   using Cfg = TcCfg<NZ, R, F16>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, NS = Cfg::NS, NA = Cfg::NA;
   constexpr int KC = Cfg::KC, EPW = Cfg::EPW;
@@ -365,7 +386,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     for (int it = 0; it < n_it; ++it) {
       const int s = it % NS;
       tic();
-      if (it >= NS && !tc::warp_wait(&empty[s], (uint32_t)((it / NS - 1) & 1), lim)) {
+      if (it >= NS && !wwt(&empty[s], (uint32_t)((it / NS - 1) & 1), lim)) {
         ok = false;
         break;
       }
@@ -398,7 +419,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     }
     // drain: the last NS issues must land before the CTA exits
     for (int k = issued - NS > 0 ? issued - NS : 0; k < issued; ++k)
-      tc::wait(&full[k % NS], (uint32_t)((k / NS) & 1), kDrain);
+      wt(&full[k % NS], (uint32_t)((k / NS) & 1), kDrain);
   } else if (warp == 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
@@ -409,12 +430,12 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       for (int it = 0; it < n_it && ok; ++it) {
         const int bb = it & 1;
         tic();
-        if (!tc::wait(&bfull[bb], (uint32_t)((it >> 1) & 1), lim)) {
+        if (!wt(&bfull[bb], (uint32_t)((it >> 1) & 1), lim)) {
           ok = false;
           break;
         }
         toc(kPWaitA);
-        if (it >= 2 && !tc::wait(&dempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim)) {
+        if (it >= 2 && !wt(&dempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim)) {
           ok = false;
           break;
         }
@@ -424,7 +445,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
         for (int beta = 0; beta < 3 && ok; ++beta) {
           const int g = 3 * it + beta, c = g % NA;
           tic();
-          if (!tc::wait(&afull[c], (uint32_t)((g / NA) & 1), lim)) {
+          if (!wt(&afull[c], (uint32_t)((g / NA) & 1), lim)) {
             ok = false;
             break;
           }
@@ -447,7 +468,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       }
       // drain: every MMA issued above completes before TMEM is released
       tc::commit(fin);
-      tc::wait(fin, 0u, kDrain);
+      wt(fin, 0u, kDrain);
     }
   } else if (warp >= 4 && (warp & 3) < Cfg::NQ) {
     // ---- row warps: unpack, then the epilogue of the previous wavenumber ----
@@ -484,7 +505,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     auto epilogue = [&](int e, int ea) -> bool {
       const int bb = e & 1;
       tic();
-      if (!tc::warp_wait(&dfull[bb], (uint32_t)((e >> 1) & 1), lim)) return false;
+      if (!wwt(&dfull[bb], (uint32_t)((e >> 1) & 1), lim)) return false;
       toc(kPWaitC);
       tc::fence_after();
       const uint32_t dc = tq + Cfg::DCOL + Cfg::DBUF * bb;
@@ -532,7 +553,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     for (int it = 0; it < n_it && ok; ++it) {
       const int s = it % NS;
       tic();
-      if (!tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim)) { ok = false; break; }
+      if (!wwt(&full[s], (uint32_t)((it / NS) & 1), lim)) { ok = false; break; }
       toc(kPWaitA);
       const float2 *st = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE);
       ea_prev = ea_cur;
@@ -542,7 +563,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       for (int beta = 0; beta < 3; ++beta) {
         const int g = 3 * it + beta, c = g % NA;
         tic();
-        if (g >= NA && !tc::warp_wait(&aempty[c], (uint32_t)((g / NA - 1) & 1), lim)) {
+        if (g >= NA && !wwt(&aempty[c], (uint32_t)((g / NA - 1) & 1), lim)) {
           ok = false;
           break;
         }
@@ -627,9 +648,9 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     for (int it = 0; it < n_it && ok; ++it) {
       const int s = it % NS, bb = it & 1;
       tic();
-      bool got = tc::warp_wait(&full[s], (uint32_t)((it / NS) & 1), lim);
+      bool got = wwt(&full[s], (uint32_t)((it / NS) & 1), lim);
       toc(kPWaitA);
-      if (got && it >= 2) got = tc::warp_wait(&bempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim);
+      if (got && it >= 2) got = wwt(&bempty[bb], (uint32_t)(((it >> 1) - 1) & 1), lim);
       toc(kPWaitB);
       if (!got) {
         ok = false;
@@ -749,7 +770,8 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     if (prof && lane == 0) {
       pt[kPTotal] = (unsigned long long)(clock64() - t_begin);
       pt[kPIters] = (unsigned long long)n_it;
-      for (int k = 0; k < 8; ++k) prof[((size_t)blockIdx.x * Cfg::WARPS + warp) * 8 + k] = pt[k];
+      for (int k = 0; k < 8; ++k) prof[((size_t)blockIdx.x * Cfg::WARPS + warp) * 16 + k] = pt[k];
+      prof[((size_t)blockIdx.x * Cfg::WARPS + warp) * 16 + 8] = polls;
     }
   }
   tc::fence_before();
