@@ -191,7 +191,9 @@ ie_status ie_fields(ie_ctx *ctx, const void *u_dev, void *e_dev, int nrhs, void 
  * from GMRES in c64 (c64 operator, c64 Krylov vectors, FP32 rotations; Hessenberg
  * entries and cross-thread sums in FP64).  IE_MIXED_FP64K: the same refinement with the
  * FP64 contraction in the residual and inner GMRES on the c64 operator with FP64 Krylov
- * vectors, Gram-Schmidt and rotations.
+ * vectors and FP64 rotations; its Gram-Schmidt dot products and updates of the FP64
+ * vectors run in double-float arithmetic (FP32 pairs, about 2^-46 relative to the sum
+ * of magnitudes; the Hessenberg entries and norms are FP64).
  * Stops when ||b - A u|| <= tol ||b|| for every right-hand side.
  * b_dev, u_dev: device c128 [nrhs][3][Nz][Ny][Nx]; if use_x0 the initial guess is
  * read from u_dev, otherwise it is zero. */

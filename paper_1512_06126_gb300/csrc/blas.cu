@@ -499,8 +499,10 @@ struct Df {
 
 // x = hi + lo + O(2^-46 |x|) for 2^-103 <= |x| < 2^127, from the bits of x with integer
 // operations only (no FP64 instruction): below that range hi = lo = 0 (a relative
-// contribution below 2^-103 of a unit vector), above it hi = +-Inf, and NaN stays NaN, so
-// that a non-finite vector still fails every test downstream
+// contribution below 2^-103 of a unit vector); above it, and for Inf and NaN, hi is
+// non-finite (Inf, or NaN where the leading 20 + 3 significand bits are not all zero,
+// as in every NaN that arithmetic produces) and lo = 0, so that a non-finite vector
+// still fails every test downstream
 __device__ __forceinline__ void dsplit(double x, float &hi, float &lo) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const uint32_t uh = (uint32_t)(u >> 32), ul = (uint32_t)u;
@@ -512,9 +514,8 @@ __device__ __forceinline__ void dsplit(double x, float &hi, float &lo) {
   // 0.m24..m46 = (1.m24..m46 - 1) exactly, times 2^(e - 1023 - 23) with the sign
   float l = __fmul_rn(__fsub_rn(__uint_as_float(0x3F800000u | ml), 1.0f), __uint_as_float(sgn | ((e - 919u) << 23)));
   const bool small = e < 920u, big = e > 1150u;
-  const bool nan = e == 0x7FFu && ((uh & 0xFFFFFu) | ul) != 0u;
   h = small ? sgn : h;
-  h = big ? (sgn | (nan ? 0x7FC00000u : 0x7F800000u)) : h;
+  h = big ? (sgn | 0x7F800000u | mh) : h;
   l = (small || big) ? 0.0f : l;
   hi = __uint_as_float(h);
   lo = l;
@@ -559,67 +560,103 @@ __device__ __forceinline__ Df df_mul(const Df &a, float bh, float bl) {
   return r;
 }
 
-constexpr int kDfG = 4;  // basis vectors per unit of the dot pass (the chunk of x is split once per unit)
+// a += b for double-floats (b given by its two parts)
+__device__ __forceinline__ void df_add(Df &a, float bs, float bc) {
+  float t, e;
+  two_sum(a.s, bs, t, e);
+  a.s = t;
+  a.c = __fadd_rn(a.c, __fadd_rn(bc, e));
+}
+// sum over the warp in double-float (FP32 shuffles; the total in every lane)
+__device__ __forceinline__ void df_warp_sum(Df &a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bs = __shfl_xor_sync(0xffffffffu, a.s, o), bc = __shfl_xor_sync(0xffffffffu, a.c, o);
+    df_add(a, bs, bc);
+  }
+}
 
-// part(r, i, c) = sum_chunk conj(V_i) x and, for the first unit of a chunk, npart(r, c)
-// = sum_chunk |x|^2; units (r, c, group of kDfG basis vectors), one warp each
-constexpr int kDfCh = 512;  // elements per chunk of the double-float dot pass (16 per lane)
+// Both double-float passes take chunks of kT * kDfEPT elements, kDfEPT per thread, and
+// walk the basis one vector at a time with the next vector's loads already in flight
+// (the dot pass keeps its chunk of x split in registers).  At 128 x 128 x 32 with two
+// right-hand sides this ran the dot pass at 3.2-3.4 TB/s and the subtract pass at
+// 4.3-4.4 TB/s for basis sizes 4-20, against 2.0-2.4 and 3.2-3.3 TB/s for groups of
+// four basis vectors per warp (dot) and eight elements per thread without the
+// pipelining (subtract); at that rate both are bound by the issue of the double-float
+// arithmetic (about 100 instructions per complex element and basis vector).
+constexpr int kDfEPT = 4;
+constexpr int kDfCh = kT * kDfEPT;  // elements per chunk
 
+// part(r, i, c) = sum_chunk conj(V_i) x and npart(r, c) = sum_chunk |x|^2, chunk c of
+// kDfCh elements; grid (nbs, R), each block the same number of chunks
 __global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const double2 *__restrict__ V, const double2 *__restrict__ x,
                                                         double2 *__restrict__ part, double *__restrict__ npart, int k1,
-                                                        int R, long long n, int nch) {
-  constexpr int CH = kDfCh;
-  const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * (kT / 32);
-  const int ng = (k1 + kDfG - 1) / kDfG;
-  const int units = R * nch * ng;
-  for (int u = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); u < units; u += nw) {
-    const int ig = u % ng, rc = u / ng;
-    const int c = rc % nch, r = rc / nch;
-    const long long e0 = (long long)c * CH;
-    const double2 *xr = x + (long long)r * n + e0;
-    const long long lim = n - e0;
-    Df re[kDfG], im[kDfG], nn = {0.f, 0.f};
+                                                        int R, long long n, int nbs, int nch) {
+  constexpr int EPT = kDfEPT;
+  __shared__ double2 red[kT / 32][65];  // per warp: the k1 dot products, then |x|^2 in slot 64
+  const int r = blockIdx.y, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const double2 *xr = x + (long long)r * n;
+  const double2 z2 = make_double2(0.0, 0.0);
+  for (long long c0 = (long long)blockIdx.x * kDfCh; c0 < n; c0 += (long long)nbs * kDfCh) {
+    const int c = (int)(c0 / kDfCh);
+    float xs[EPT][4];  // (re hi, re lo, im hi, im lo)
+    Df nn = {0.f, 0.f};
 #pragma unroll
-    for (int t = 0; t < kDfG; ++t) re[t] = im[t] = Df{0.f, 0.f};
+    for (int j = 0; j < EPT; ++j) {
+      const long long e = c0 + j * kT + tid;
+      const double2 v = e < n ? __ldg(xr + e) : z2;
+      dsplit(v.x, xs[j][0], xs[j][1]);
+      dsplit(v.y, xs[j][2], xs[j][3]);
+      df_fma(nn, xs[j][0], xs[j][1], xs[j][0], xs[j][1]);
+      df_fma(nn, xs[j][2], xs[j][3], xs[j][2], xs[j][3]);
+    }
+    df_warp_sum(nn);
+    if (lane == 0) red[wid][64] = make_double2(df_value(nn), 0.0);
+    double2 vn[EPT];
+    {
+      const double2 *v0 = V + (long long)r * n + c0 + tid;
 #pragma unroll
-    for (int j = 0; j < CH / 32; ++j) {
-      const int l = j * 32 + lane;
-      if (l >= lim) break;
-      const double2 xv = __ldg(xr + l);
-      float xrh, xrl, xih, xil;
-      dsplit(xv.x, xrh, xrl);
-      dsplit(xv.y, xih, xil);
-      if (ig == 0) {
-        df_fma(nn, xrh, xrl, xrh, xrl);
-        df_fma(nn, xih, xil, xih, xil);
+      for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v0 + j * kT) : z2;
+    }
+#pragma unroll 1
+    for (int i = 0; i < k1; ++i) {
+      double2 vc[EPT];
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) vc[j] = vn[j];
+      if (i + 1 < k1) {
+        const double2 *v1 = V + ((long long)(i + 1) * R + r) * n + c0 + tid;
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v1 + j * kT) : z2;
       }
+      Df are = {0.f, 0.f}, aim = {0.f, 0.f};
 #pragma unroll
-      for (int t = 0; t < kDfG; ++t) {
-        const int i = ig * kDfG + t;
-        if (i < k1) {
-          const double2 vv = __ldg(V + ((long long)i * R + r) * n + e0 + l);
-          float vrh, vrl, vih, vil;
-          dsplit(vv.x, vrh, vrl);
-          dsplit(vv.y, vih, vil);
-          // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
-          df_fma(re[t], vrh, vrl, xrh, xrl);
-          df_fma(re[t], vih, vil, xih, xil);
-          df_fma(im[t], vrh, vrl, xih, xil);
-          df_fma(im[t], -vih, -vil, xrh, xrl);
-        }
+      for (int j = 0; j < EPT; ++j) {
+        float vrh, vrl, vih, vil;
+        dsplit(vc[j].x, vrh, vrl);
+        dsplit(vc[j].y, vih, vil);
+        // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
+        df_fma(are, vrh, vrl, xs[j][0], xs[j][1]);
+        df_fma(are, vih, vil, xs[j][2], xs[j][3]);
+        df_fma(aim, vrh, vrl, xs[j][2], xs[j][3]);
+        df_fma(aim, -vih, -vil, xs[j][0], xs[j][1]);
       }
+      df_warp_sum(are);
+      df_warp_sum(aim);
+      if (lane == 0) red[wid][i] = make_double2(df_value(are), df_value(aim));
     }
+    __syncthreads();
+    if (tid <= k1) {
+      const int i = tid < k1 ? tid : 64;
+      double sx = 0.0, sy = 0.0;
 #pragma unroll
-    for (int t = 0; t < kDfG; ++t) {
-      const int i = ig * kDfG + t;
-      const double ax = warp_sum(df_value(re[t])), ay = warp_sum(df_value(im[t]));
-      if (lane == 0 && i < k1) part[((long long)r * k1 + i) * nch + c] = make_double2(ax, ay);
+      for (int w = 0; w < kT / 32; ++w) {
+        sx += red[w][i].x;
+        sy += red[w][i].y;
+      }
+      if (tid < k1) part[((long long)r * k1 + tid) * nch + c] = make_double2(sx, sy);
+      else npart[(long long)r * nch + c] = sx;
     }
-    if (ig == 0) {
-      const double s = warp_sum(df_value(nn));
-      if (lane == 0) npart[(long long)r * nch + c] = s;
-    }
+    __syncthreads();
   }
 }
 
@@ -630,7 +667,7 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restric
                                                         int k1, int R, long long n, int nbs, int ldh,
                                                         double2 *__restrict__ vout, const double *__restrict__ nrm,
                                                         const int *__restrict__ oflag) {
-  constexpr int EPT = GsShape<double>::kSubEPT;
+  constexpr int EPT = kDfEPT;
   __shared__ float4 hs[64];  // -h split: (-hr hi, -hr lo, -hi hi, -hi lo)
   __shared__ double2 shn[kT / 32];
   const int r = blockIdx.y;
@@ -650,7 +687,7 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restric
   double2 *xr = x + (long long)r * n;
   double2 *vr = vout ? vout + (long long)r * n : nullptr;
   Df nacc = {0.f, 0.f};
-  for (long long c0 = (long long)blockIdx.x * kT * EPT; c0 < n; c0 += (long long)nbs * kT * EPT) {
+  for (long long c0 = (long long)blockIdx.x * kDfCh; c0 < n; c0 += (long long)nbs * kDfCh) {
     Df ar[EPT], ai[EPT];
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
@@ -659,23 +696,33 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restric
       dsplit(v.x, ar[j].s, ar[j].c);
       dsplit(v.y, ai[j].s, ai[j].c);
     }
+    double2 vn[EPT];
+    {
+      const double2 *v0 = V + (long long)r * n + c0 + tid;
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v0 + j * kT) : make_double2(0.0, 0.0);
+    }
 #pragma unroll 1
     for (int i = 0; i < k1; ++i) {
       const float4 hv = hs[i];  // -h
-      const double2 *vi = V + ((long long)i * R + r) * n + c0 + tid;
+      double2 vc[EPT];
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) vc[j] = vn[j];
+      if (i + 1 < k1) {
+        const double2 *v1 = V + ((long long)(i + 1) * R + r) * n + c0 + tid;
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v1 + j * kT) : make_double2(0.0, 0.0);
+      }
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
-        if (c0 + j * kT + tid < n) {
-          const double2 a = __ldg(vi + j * kT);
-          float vrh, vrl, vih, vil;
-          dsplit(a.x, vrh, vrl);
-          dsplit(a.y, vih, vil);
-          // x += (-h) v: re += (-hr) vr - (-hi) vi, im += (-hr) vi + (-hi) vr
-          df_fma(ar[j], hv.x, hv.y, vrh, vrl);
-          df_fma(ar[j], -hv.z, -hv.w, vih, vil);
-          df_fma(ai[j], hv.x, hv.y, vih, vil);
-          df_fma(ai[j], hv.z, hv.w, vrh, vrl);
-        }
+        float vrh, vrl, vih, vil;
+        dsplit(vc[j].x, vrh, vrl);
+        dsplit(vc[j].y, vih, vil);
+        // x += (-h) v: re += (-hr) vr - (-hi) vi, im += (-hr) vi + (-hi) vr
+        df_fma(ar[j], hv.x, hv.y, vrh, vrl);
+        df_fma(ar[j], -hv.z, -hv.w, vih, vil);
+        df_fma(ai[j], hv.x, hv.y, vih, vil);
+        df_fma(ai[j], hv.z, hv.w, vrh, vrl);
       }
     }
 #pragma unroll
@@ -768,21 +815,26 @@ void gmres_norm(const C<T> *w, double *part, double *out, int R, long long n, cu
   norm_final<<<R, kT, 0, s>>>(part, out, nb);
 }
 
-int dot_df_per_sm() {
-  static int v = 0;
-  if (v == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, cgs_dot_df_kernel, kT, 0) != cudaSuccess || v < 1)) {
-    cudaGetLastError();
-    v = 1;
+// blocks per right-hand side of the double-float passes: at most one wave of the GPU
+// over all R (at the smaller occupancy of the two kernels), every block the same
+// number of kDfCh-element chunks
+int df_blocks(long long n, int R) {
+  static int per = 0;
+  if (per == 0) {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cgs_dot_df_kernel, kT, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cgs_sub_df_kernel, kT, 0) != cudaSuccess) {
+      cudaGetLastError();
+      a = b = 1;
+    }
+    per = a < b ? a : b;
+    if (per < 1) per = 1;
   }
-  return v;
-}
-int sub_df_per_sm() {
-  static int v = 0;
-  if (v == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, cgs_sub_df_kernel, kT, 0) != cudaSuccess || v < 1)) {
-    cudaGetLastError();
-    v = 1;
-  }
-  return v;
+  const long long chunks = (n + kDfCh - 1) / kDfCh;
+  long long maxb = ((long long)per * sm_count()) / R;
+  if (maxb < 1) maxb = 1;
+  const long long each = (chunks + maxb - 1) / maxb;
+  return (int)((chunks + each - 1) / each);
 }
 
 template <typename T> int second_blocks() {
@@ -818,11 +870,8 @@ int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double
   if constexpr (sizeof(T) == 8) {
     if (df) {
       nch_used = (int)((n + kDfCh - 1) / kDfCh);
-      const long long units = (long long)R * nch_used * ((k1 + kDfG - 1) / kDfG);
-      const long long maxw = (long long)dot_df_per_sm() * sm_count() * (kT / 32);
-      const long long per = (units + maxw - 1) / maxw;
-      const int gd = (int)((((units + per - 1) / per) + kT / 32 - 1) / (kT / 32));
-      cgs_dot_df_kernel<<<gd < 1 ? 1 : gd, kT, 0, s>>>(V, w, part, np0, k1, R, n, nch_used);
+      const int nbd = df_blocks(n, R);
+      cgs_dot_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(V, w, part, np0, k1, R, n, nbd, nch_used);
     }
   }
   if (!df) {
@@ -833,11 +882,7 @@ int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double
   // w' = w - V h1, written normalised into vnext where no second projection is needed
   if constexpr (sizeof(T) == 8) {
     if (df) {
-      const long long chunks = (n + (long long)kT * GsShape<double>::kSubEPT - 1) / ((long long)kT * GsShape<double>::kSubEPT);
-      long long maxb = ((long long)sub_df_per_sm() * sm_count()) / R;
-      if (maxb < 1) maxb = 1;
-      const long long per = (chunks + maxb - 1) / maxb;
-      const int nbd = (int)((chunks + per - 1) / per);
+      const int nbd = df_blocks(n, R);
       cgs_sub_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(V, w, h1, np1, k1, R, n, nbd, ldh, vnext, nrm, flag);
     }
   }
