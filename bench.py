@@ -25,6 +25,9 @@ Printed (one JSON line, rank 0):
                 one thread and all threads
   e2e           the same metric through the C ABI with host buffers (H2D of the
                 right-hand sides and D2H of the solution inside the timed region)
+  c3_batch      the batched configuration (16 frequencies x 2 polarisations over four
+                grids) in the timed precision: batched and one-at-a-time solved
+                instances/s (--skip-c3 leaves it out; --mode batch adds plain FP64)
 
 --impl reference runs the oracle (the reference implementation of this tier) on the
 host cores for the same workload and metric.
@@ -83,8 +86,9 @@ CONTRACT_TRAFFIC = {("C2", 3, 2): 654541312 + 86889728, ("C2", 5, 2): 654550784 
 VARIANT_NAMES = ["tma 1 slot", "tma 3 slots", "panel", "tma 1 slot, 1 row/thread",
                  "3xTF32 mma.sync, producer warp, 2 slots", "3xTF32 mma.sync, 1 slot, unpacked",
                  "3xTF32 tcgen05.mma, block in TMEM, warp-specialised",
-                 "2xFP16 (scaled) tcgen05.mma kind::f16, block in TMEM, warp-specialised"]
-TENSOR_VARIANTS = (4, 5, 6, 7)
+                 "2xFP16 (scaled) tcgen05.mma kind::f16, block in TMEM, warp-specialised",
+                 "3xTF32 mma.sync, one output component per sub-step"]
+TENSOR_VARIANTS = (4, 5, 6, 7, 8)
 
 
 def bf16_peak():
@@ -558,6 +562,11 @@ def run_ours(args, rank, ws):
                "legs": [{"threads": d["threads"], "value": n_unk * d["iters"] / d["seconds"],
                          "seconds": d["seconds"], "iters": d["iters"]} for d in legs]}
 
+    # ---- the batched configuration (four grids, 32 instances) in the timed precision ----
+    c3 = None
+    if rank == 0 and ws == 1 and args.workload == "C2" and not args.skip_c3:
+        c3 = c3_summary(args, ie.IE_MIXED_FP64K, with_fp64=False)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
@@ -583,6 +592,7 @@ def run_ours(args, rank, ws):
                 "solve_breakdown": breakdown,
                 "contract_tuning": {"variants": VARIANT_NAMES, "chosen_for_2_rhs": variant,
                                     "ms_per_launch_2_rhs": [float(v) for v in tune_ms[1]]},
+                "c3_batch": c3,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 16),
                         "d2h_bytes_per_step": int(b.numel() * 16)},
@@ -781,6 +791,7 @@ def main():
     ap.add_argument("--precision", choices=list(PRECISIONS_BY_NAME), default="fp64k",
                     help="batch mode: the precision of the batched and one-at-a-time solves")
     ap.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 comparisons")
+    ap.add_argument("--skip-c3", action="store_true", help="leave the batched four-grid summary out of the solve line")
     ap.add_argument("--variant", type=int, default=-1,
                     help="matvec mode: force this contraction variant (default: the autotuner's choice)")
     args = ap.parse_args()

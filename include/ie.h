@@ -220,10 +220,13 @@ ie_status ie_solve_batch(ie_ctx *ctx, int n_inst, const int *inst_host, const vo
  * 5th-generation tensor cores (tcgen05.mma with the block in tensor memory; c64,
  * Nz in {16, 32}, 1-2 right-hand sides): 6 kind::tf32 on the 3xTF32 split, 7 kind::f16
  * on a two-way FP16 split of the block and of the vectors, each scaled by a power of two
- * (the same 22 significant bits as 6, half the MMA instructions).
+ * (the same 22 significant bits as 6, half the MMA instructions); 8 the mma.sync path of
+ * 5 one output component at a time, three of the six matrices unpacked per sub-step
+ * (c64, Nz in {16, 32, 48, 64}, 1-2 right-hand sides; the tensor-core variant for
+ * Nz = 64).
  * ie_contract_tuning reports the c64 variant used for 1..4 right-hand sides per
  * instance (variant_host[4]; -1: built-in choice) and the autotuner's timings
- * (ms_host[4][8], ms per launch, 0 where not timed; may be NULL).
+ * (ms_host[4][9], ms per launch, 0 where not timed; may be NULL).
  * ie_set_contract_variant overrides the choice for one right-hand-side count
  * (-1: built-in choice); IE_ERR_ARG if the variant does not apply to this grid. */
 ie_status ie_contract_tuning(ie_ctx *ctx, int *variant_host, double *ms_host);

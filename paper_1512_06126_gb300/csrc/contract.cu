@@ -346,6 +346,25 @@ __global__ void block_exponent_kernel(const float2 *__restrict__ qf, int *__rest
   }
 }
 
+template <int NZ, int R>
+bool try_mma_comp(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int *err, cudaStream_t s) {
+  static int per_sm = 0;
+  using Cfg = MmaCompCfg<NZ, R>;
+  return launch_persistent(contract_mma_comp_kernel<NZ, R>, Cfg::THREADS, Cfg::SMEM, &per_sm, spec, qf, Nx, Ny, ldz,
+                           err, s);
+}
+
+template <int R>
+bool dispatch_mma_comp(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, int *err, cudaStream_t s) {
+  switch (Nz) {
+    case 16: return try_mma_comp<16, R>(spec, qf, Nx, Ny, ldz, err, s);
+    case 32: return try_mma_comp<32, R>(spec, qf, Nx, Ny, ldz, err, s);
+    case 48: return try_mma_comp<48, R>(spec, qf, Nx, Ny, ldz, err, s);
+    case 64: return try_mma_comp<64, R>(spec, qf, Nx, Ny, ldz, err, s);
+    default: return false;
+  }
+}
+
 template <int R>
 bool dispatch_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, bool unpack, int *err,
                   cudaStream_t s) {
@@ -401,6 +420,7 @@ bool contract_fits(int Nz, int R, bool c64) {
 bool contract_variant_available(int variant, int Nz, int R, bool c64) {
   if (variant == kContractPanel) return R >= 1 && R <= 4 && 3 * Nz <= 1024;
   if (!c64 || R < 1 || R > 2 || !contract_tma_enabled) return false;
+  if (variant == kContractMmaComp) return Nz == 16 || Nz == 32 || Nz == 48 || Nz == 64;
   if (Nz != 16 && Nz != 24 && Nz != 32 && Nz != 48) return false;
   if (variant == kContractTc || variant == kContractTc16) return Nz == 16 || Nz == 32;
   if (variant == kContractMma || variant == kContractMmaUnpack) return Nz % 16 == 0;
@@ -431,6 +451,10 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, i
       const bool unpack = variant == kContractMmaUnpack;
       if (R == 1 && dispatch_mma<1>(spec, qf, Nx, Ny, Nz, ldz, unpack, err, s)) return 0;
       if (R == 2 && dispatch_mma<2>(spec, qf, Nx, Ny, Nz, ldz, unpack, err, s)) return 0;
+    }
+    if (variant == kContractMmaComp && contract_variant_available(variant, Nz, R, true)) {
+      if (R == 1 && dispatch_mma_comp<1>(spec, qf, Nx, Ny, Nz, ldz, err, s)) return 0;
+      if (R == 2 && dispatch_mma_comp<2>(spec, qf, Nx, Ny, Nz, ldz, err, s)) return 0;
     }
     if (variant == kContractTc && contract_variant_available(variant, Nz, R, true)) {
       if (R == 1 && dispatch_tc<1, false>(spec, qf, nullptr, Nx, Ny, Nz, ldz, err, s)) return 0;

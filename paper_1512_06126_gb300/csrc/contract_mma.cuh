@@ -507,4 +507,288 @@ __global__ void __launch_bounds__(MmaUnpackCfg<NZ, R>::THREADS)
   }
 }
 
+// contract_mma_comp_kernel: the block of a wavenumber in three sub-steps, one per output
+// component alpha, so that only the three Nz x Nz matrices M[alpha][0..2] are unpacked
+// at a time (at Nz = 64 the whole unpacked block, 6 x 64 x 68 complex, does not fit in
+// shared memory with its staging; three matrices do).  Per sub-step one thread copies
+// the three packed matrices (bulk copies, the next sub-step's issued as soon as the
+// current one is unpacked), all warps unpack them, and warp (row tile, beta) applies
+// M[alpha][beta] to the X of component beta with the 3xTF32 MMAs; the three beta
+// partial sums meet in shared memory.  X is staged once per wavenumber.  Across the
+// three sub-steps xy, xz, yz are read twice (the second time mostly from L2).
+template <int NZ, int R>
+struct MmaCompCfg {
+  static_assert(NZ % 16 == 0 && NZ <= 64, "row tiles of 16; at most 64 layers");
+  static_assert(R >= 1 && R <= 2, "one n-tile of 8 columns: 4 mirrors x R <= 8");
+  static constexpr int N3 = 3 * NZ;
+  static constexpr int CZ = R * N3;
+  static constexpr int P = NZ * (NZ + 1) / 2;
+  static constexpr int BS = 2 * NZ * (2 * NZ + 1);
+  static constexpr int LD = NZ + 4;     // = 4 (mod 16)
+  static constexpr int RT = NZ / 16;    // row tiles per component
+  static constexpr int WARPS = 3 * RT;  // (row tile, beta)
+  static constexpr int THREADS = WARPS * 32;
+  static constexpr int KS = N3 / 8;     // k-steps of the staged X
+  static constexpr int RAWMAX = 2 * NZ * NZ + P;  // complex: two full matrices + a triangle
+  static constexpr int LDXR = CZ + 4;
+  static constexpr size_t OFF_BAR = 0;  // [0]: the block's copies, [1]: X's copies
+  static constexpr size_t OFF_RAW = 128;
+  static constexpr size_t RAW_BYTES = (size_t)RAWMAX * 8;
+  static constexpr size_t OFF_XRAW = OFF_RAW + RAW_BYTES;
+  static constexpr size_t XRAW_BYTES = (size_t)4 * LDXR * 8;
+  static constexpr size_t OFF_BLK = OFF_XRAW + XRAW_BYTES;
+  static constexpr size_t BLK_BYTES = (size_t)3 * NZ * LD * 8;
+  static constexpr size_t OFF_XS = OFF_BLK + BLK_BYTES;
+  static constexpr size_t XS_PLANE = (size_t)KS * 32 * 16;
+  static constexpr size_t OFF_TRI = OFF_XS + 2 * XS_PLANE;
+  static constexpr size_t SMEM = OFF_TRI + (((size_t)P * 2 + 15) / 16) * 16;
+  // the beta partial sums (8 floats per thread of the beta = 1, 2 warps) reuse the
+  // unpacked matrices' space once the MMAs are done
+  static_assert((size_t)2 * RT * 32 * 8 * 4 <= BLK_BYTES, "partial sums fit the block space");
+  static_assert(((size_t)P * 8) % 16 == 0 && RAW_BYTES % 16 == 0 && OFF_XRAW % 16 == 0 && (LDXR * 8) % 16 == 0,
+                "bulk copy alignment");
+};
+
+template <int NZ, int R>
+__global__ void __launch_bounds__(MmaCompCfg<NZ, R>::THREADS, 1)
+    contract_mma_comp_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz,
+                             int *err, long long lim) {
+  using Cfg = MmaCompCfg<NZ, R>;
+  constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LD = Cfg::LD, RT = Cfg::RT;
+  constexpr int THREADS = Cfg::THREADS, NN = NZ * NZ;
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Cfg::OFF_BAR);
+  float2 *raw = reinterpret_cast<float2 *>(sm + Cfg::OFF_RAW);
+  float2 *xraw = reinterpret_cast<float2 *>(sm + Cfg::OFF_XRAW);
+  float2 *blk = reinterpret_cast<float2 *>(sm + Cfg::OFF_BLK);
+  float *red = reinterpret_cast<float *>(sm + Cfg::OFF_BLK);
+  uint4 *xs = reinterpret_cast<uint4 *>(sm + Cfg::OFF_XS);
+  uint16_t *tri = reinterpret_cast<uint16_t *>(sm + Cfg::OFF_TRI);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nf = (Nx + 1) * (Ny + 1);
+
+  // triangle entries (a, a + d) in diagonal order, so that the two stores of each spread
+  // over the banks
+  for (int d = tid; d < NZ; d += THREADS) {
+    const int s0 = d * NZ - d * (d - 1) / 2;
+    for (int a = 0; a + d < NZ; ++a) tri[s0 + a] = (uint16_t)(a << 8 | (a + d));
+  }
+  if (tid == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::fence_mbar_init();
+  }
+  __syncthreads();
+
+  // the packed matrices of M[alpha][0..2] into raw: alpha 0: xx, xy (triangles), xz;
+  // alpha 1: xy, yy (triangles), yz; alpha 2: xz, yz (full), zz (triangle)
+  auto issue_block = [&](int w, int alpha) {
+    const float2 *q = qf + (size_t)w * BS;
+    tma::fence_proxy_async();
+    if (alpha < 2) {
+      tma::mbar_expect_tx(&bar[0], (uint32_t)((2 * P + NN) * 8));
+      tma::bulk_g2s(raw, q + (alpha == 0 ? 0 : 3) * (size_t)P, (uint32_t)(P * 8), &bar[0]);
+      tma::bulk_g2s(raw + P, q + (alpha == 0 ? 3 : 1) * (size_t)P, (uint32_t)(P * 8), &bar[0]);
+      tma::bulk_g2s(raw + 2 * P, q + 4 * (size_t)P + (size_t)alpha * NN, (uint32_t)(NN * 8), &bar[0]);
+    } else {
+      tma::mbar_expect_tx(&bar[0], (uint32_t)((P + 2 * NN) * 8));
+      tma::bulk_g2s(raw, q + 4 * (size_t)P, (uint32_t)(2 * NN * 8), &bar[0]);
+      tma::bulk_g2s(raw + 2 * NN, q + 2 * (size_t)P, (uint32_t)(P * 8), &bar[0]);
+    }
+  };
+  auto issue_x = [&](int w) {
+    const Mirrors mi = mirrors_of(w, Nx, Ny);
+    const int nm = mi.nmx * mi.nmy;
+    tma::fence_proxy_async();
+    tma::mbar_expect_tx(&bar[1], (uint32_t)(nm * CZ * 8));
+    for (int m = 0; m < nm; ++m) {
+      const int mx = m % mi.nmx, my = m / mi.nmx;
+      tma::bulk_g2s(xraw + (size_t)m * Cfg::LDXR, spec + mi.pos(mx, my, Nx) * ldz, (uint32_t)(CZ * 8), &bar[1]);
+    }
+  };
+
+  // copies issued and waited for, per barrier (thread 0 issues; every thread waits)
+  int nb_issued = 0, nx_issued = 0, nb_done = 0, nx_done = 0;
+  const int w0 = blockIdx.x;
+  if (tid == 0 && w0 < nf) {
+    issue_x(w0);
+    issue_block(w0, 0);
+    nx_issued = nb_issued = 1;
+  }
+  // on a wait that ran out: record it, let thread 0 wait for its copies still in
+  // flight, and stop (the decision is collective, so no thread is left at a barrier)
+  auto give_up = [&]() {
+    if (tid == 0) {
+      atomicExch(err, kContractTimeout);
+      for (; nb_done < nb_issued; ++nb_done) tma::mbar_wait_bounded(&bar[0], (uint32_t)(nb_done & 1), kWaitLimit);
+      for (; nx_done < nx_issued; ++nx_done) tma::mbar_wait_bounded(&bar[1], (uint32_t)(nx_done & 1), kWaitLimit);
+    }
+  };
+
+  const int g = lane >> 2, t = lane & 3;
+  const int rt = warp % RT, beta = warp / RT;
+  const int a0 = rt * 16;
+  for (int w = w0; w < nf; w += gridDim.x) {
+    const Mirrors mw = mirrors_of(w, Nx, Ny);
+    const int nmx = mw.nmx;
+    const int ncol = mw.nmx * mw.nmy * R;
+    // X of this wavenumber, split and in fragment order (as in contract_mma_unpack_kernel)
+    if (!__syncthreads_and(tma::mbar_wait_bounded(&bar[1], (uint32_t)(nx_done & 1), lim))) {
+      give_up();
+      return;
+    }
+    ++nx_done;
+    for (int e = tid; e < Cfg::KS * 32; e += THREADS) {
+      const int ks = e >> 5, col = (e >> 2) & 7, tt = e & 3;
+      const int k0 = ks * 8 + tt;
+      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+      if (col < ncol) {
+        const int m = col / R, r = col - m * R;
+        const int mx = m % nmx, my = m / nmx;
+        const int comp = k0 / NZ;
+        const float2 *xp = xraw + (size_t)m * Cfg::LDXR + r * N3 + k0;
+        v0 = xp[0];
+        v1 = xp[4];
+        if ((comp == 0 && mx == 1) || (comp == 1 && my == 1)) {
+          v0 = make_float2(-v0.x, -v0.y);
+          v1 = make_float2(-v1.x, -v1.y);
+        }
+      }
+      uint4 h, l;
+      mma::split(v0.x, h.x, l.x);
+      mma::split(v0.y, h.y, l.y);
+      mma::split(v1.x, h.z, l.z);
+      mma::split(v1.y, h.w, l.w);
+      xs[e] = h;
+      xs[Cfg::KS * 32 + e] = l;
+    }
+    for (int alpha = 0; alpha < 3; ++alpha) {
+      if (!__syncthreads_and(tma::mbar_wait_bounded(&bar[0], (uint32_t)(nb_done & 1), lim))) {
+        give_up();
+        return;
+      }
+      ++nb_done;
+      // unpack M[alpha][0..2] into blk[0..2] (rows a, columns b at a LD + b)
+      const int ntri = alpha < 2 ? 2 : 1;
+      const int total = ntri * P + (3 - ntri) * NN;
+      for (int e = tid; e < total; e += THREADS) {
+        if (alpha < 2) {
+          if (e < 2 * P) {
+            const int slot = e >= P, ee = e - slot * P;
+            const int ab = tri[ee], a = ab >> 8, b = ab & 255;
+            const float2 v = raw[slot * P + a * NZ - a * (a - 1) / 2 + (b - a)];
+            float2 *m = blk + slot * NZ * LD;
+            m[a * LD + b] = v;
+            m[b * LD + a] = v;
+          } else {
+            const int ee = e - 2 * P, a = ee / NZ, b = ee - a * NZ;
+            blk[2 * NZ * LD + a * LD + b] = raw[e];
+          }
+        } else {
+          if (e < 2 * NN) {
+            const int slot = e >= NN, ee = e - slot * NN, a = ee / NZ, b = ee - a * NZ;
+            blk[slot * NZ * LD + a * LD + b] = raw[e];
+          } else {
+            const int ab = tri[e - 2 * NN], a = ab >> 8, b = ab & 255;
+            const float2 v = raw[2 * NN + a * NZ - a * (a - 1) / 2 + (b - a)];
+            float2 *m = blk + 2 * NZ * LD;
+            m[a * LD + b] = v;
+            m[b * LD + a] = v;
+          }
+        }
+      }
+      __syncthreads();  // blk (and on alpha 0 xs) ready; raw (and xraw) consumed
+      if (tid == 0) {
+        if (alpha < 2) {
+          issue_block(w, alpha + 1);
+          ++nb_issued;
+        } else if (w + (int)gridDim.x < nf) {
+          issue_block(w + gridDim.x, 0);
+          ++nb_issued;
+        }
+        if (alpha == 0 && w + (int)gridDim.x < nf) {
+          issue_x(w + gridDim.x);
+          ++nx_issued;
+        }
+      }
+      float acc[2][2][2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][j][h][c] = 0.f;
+      {
+        // M[2][0] = -xz^T, M[2][1] = -yz^T: read transposed, the minus on X
+        const bool trb = alpha == 2 && beta < 2;
+        const uint32_t neg = trb ? 0x80000000u : 0u;
+        const int rs = trb ? 1 : LD, cs = trb ? LD : 1;
+        const float2 *p0 = blk + beta * NZ * LD + (a0 + g) * rs + t * cs;
+        const uint4 *xfh = xs, *xfl = xs + Cfg::KS * 32;
+#pragma unroll 4
+        for (int bb = 0; bb < NZ; bb += 8) {
+          const float2 *p = p0 + bb * cs;
+          float2 m[4];
+          m[0] = p[0];
+          m[1] = p[8 * rs];
+          m[2] = p[4 * cs];
+          m[3] = p[8 * rs + 4 * cs];
+          const int ks = beta * (NZ / 8) + bb / 8;
+          const uint4 xh = xfh[ks * 32 + lane], xl = xfl[ks * 32 + lane];
+          const uint32_t brh[2] = {xh.x ^ neg, xh.z ^ neg}, bih[2] = {xh.y ^ neg, xh.w ^ neg};
+          const uint32_t brl[2] = {xl.x ^ neg, xl.z ^ neg}, bil[2] = {xl.y ^ neg, xl.w ^ neg};
+          uint32_t arh[4], arl[4], aih[4], ail[4];
+          mma::split_a(m, arh, arl, aih, ail);
+          mma::mma12(acc, arh, arl, aih, ail, brh, brl, bih, bil);
+        }
+      }
+      float part[4][2];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float rr = acc[0][0][0][c] + acc[0][0][1][c], ii = acc[1][1][0][c] + acc[1][1][1][c];
+        const float ri = acc[0][1][0][c] + acc[0][1][1][c], ir = acc[1][0][0][c] + acc[1][0][1][c];
+        part[c][0] = rr - ii;
+        part[c][1] = ri + ir;
+      }
+      __syncthreads();  // every warp is done with blk: its space takes the partial sums
+      if (beta > 0) {
+        float4 *rp = reinterpret_cast<float4 *>(red + (((beta - 1) * RT + rt) * 32 + lane) * 8);
+        rp[0] = make_float4(part[0][0], part[0][1], part[1][0], part[1][1]);
+        rp[1] = make_float4(part[2][0], part[2][1], part[3][0], part[3][1]);
+      }
+      __syncthreads();
+      if (beta == 0) {
+#pragma unroll
+        for (int bt = 0; bt < 2; ++bt) {
+          const float4 *rp = reinterpret_cast<const float4 *>(red + ((bt * RT + rt) * 32 + lane) * 8);
+          const float4 u0 = rp[0], u1 = rp[1];
+          part[0][0] += u0.x;
+          part[0][1] += u0.y;
+          part[1][0] += u0.z;
+          part[1][1] += u0.w;
+          part[2][0] += u1.x;
+          part[2][1] += u1.y;
+          part[3][0] += u1.z;
+          part[3][1] += u1.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int col = 2 * t + (c & 1);
+          if (col < ncol) {
+            const int row = alpha * NZ + a0 + g + 8 * (c >> 1);
+            const int m = col / R, r = col - m * R;
+            const int mx = m % nmx, my = m / nmx;
+            float2 v = make_float2(part[c][0], part[c][1]);
+            if ((alpha == 0 && mx == 1) || (alpha == 1 && my == 1)) { v.x = -v.x; v.y = -v.y; }
+            spec[mw.pos(mx, my, Nx) * ldz + r * N3 + row] = v;
+          }
+        }
+      }
+      __syncthreads();  // the partial sums are read before the next unpacking
+    }
+  }
+}
+
 }  // namespace ie

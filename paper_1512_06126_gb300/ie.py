@@ -20,7 +20,7 @@ IE_ERR_ARG = -1
 IE_ERR_SCRATCH = -6
 IE_ERR_TIMEOUT = -7
 IE_C64, IE_C128 = 0, 1
-N_CONTRACT_VARIANTS = 8
+N_CONTRACT_VARIANTS = 9
 IE_C128_DF = 7
 IE_FP64, IE_MIXED, IE_MIXED_FP64K = 0, 1, 2
 IE_PROF_PRODUCT_C64, IE_PROF_PRODUCT_C128, IE_PROF_GS_C64, IE_PROF_GS_C128, IE_PROF_GIVENS = 2, 3, 4, 5, 6

@@ -1,7 +1,7 @@
 """The kernels the large workloads run, checked against the oracle.
 
 * every c64 contraction variant, forced, against the oracle's FFT product for
-  Nz in {16, 32, 48} and one and two right-hand sides (2e-5 relative, the c64 bound of
+  Nz in {16, 32, 48, 64} and one and two right-hand sides (2e-5 relative, the c64 bound of
   the other product tests: FP32 FFTs and FP32 accumulation over 3 Nz terms);
 * solves on a 64 x 64 x 32 grid (register-blocked FFTs of length 128, tensor-core
   contraction) and on the 128 x 128 x 32 single-solve grid, in all three precision
@@ -22,7 +22,7 @@ from oracle.proxy import contracting_q, moderate_contrast, oracle_residual
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("shape", [(24, 20, 16), (20, 18, 32), (12, 10, 48)])
+@pytest.mark.parametrize("shape", [(24, 20, 16), (20, 18, 32), (12, 10, 48), (10, 8, 64)])
 def test_forced_contraction_variants_against_oracle(shape):
     need_gpu()
     from paper_1512_06126_gb300 import ie
@@ -51,9 +51,11 @@ def test_forced_contraction_variants_against_oracle(shape):
                 assert err <= 2e-5, (shape, R, v, r, err)
             tried.append((R, v))
         ctx.set_contract_variant(R, -1)
-    # the tensor-core variants run wherever Nz is a multiple of 16, the tcgen05 one for
-    # Nz in {16, 32}
-    assert (2, 5) in tried and (1, 2) in tried, tried
+    # the mma.sync variants run wherever Nz is a multiple of 16 (the one-component form
+    # up to 64, the others up to 48), the tcgen05 ones for Nz in {16, 32}
+    assert (1, 2) in tried and {(1, 8), (2, 8)} <= set(tried), tried
+    if nz <= 48:
+        assert (2, 5) in tried, tried
     if nz in (16, 32):
         assert {(1, 6), (2, 6), (1, 7), (2, 7)} <= set(tried), tried
     ctx.close()
