@@ -87,7 +87,7 @@ VARIANT_NAMES = ["tma 1 slot", "tma 3 slots", "panel", "tma 1 slot, 1 row/thread
                  "3xTF32 mma.sync, producer warp, 2 slots", "3xTF32 mma.sync, 1 slot, unpacked",
                  "3xTF32 tcgen05.mma, block in TMEM, warp-specialised",
                  "2xFP16 (scaled) tcgen05.mma kind::f16, block in TMEM, warp-specialised",
-                 "3xTF32 mma.sync, one output component per sub-step"]
+                 "3xTF32 mma.sync, one Nz x Nz matrix per sub-step"]
 TENSOR_VARIANTS = (4, 5, 6, 7, 8)
 
 

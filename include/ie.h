@@ -221,9 +221,9 @@ ie_status ie_solve_batch(ie_ctx *ctx, int n_inst, const int *inst_host, const vo
  * Nz in {16, 32}, 1-2 right-hand sides): 6 kind::tf32 on the 3xTF32 split, 7 kind::f16
  * on a two-way FP16 split of the block and of the vectors, each scaled by a power of two
  * (the same 22 significant bits as 6, half the MMA instructions); 8 the mma.sync path of
- * 5 one output component at a time, three of the six matrices unpacked per sub-step
- * (c64, Nz in {16, 32, 48, 64}, 1-2 right-hand sides; the tensor-core variant for
- * Nz = 64).
+ * 5 one Nz x Nz matrix of the block at a time, one matrix staged and unpacked per
+ * sub-step (c64, Nz in {16, 32, 48, 64}, 1-2 right-hand sides; the tensor-core variant
+ * for Nz = 64).
  * ie_contract_tuning reports the c64 variant used for 1..4 right-hand sides per
  * instance (variant_host[4]; -1: built-in choice) and the autotuner's timings
  * (ms_host[4][9], ms per launch, 0 where not timed; may be NULL).

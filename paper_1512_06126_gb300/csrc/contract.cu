@@ -349,8 +349,8 @@ __global__ void block_exponent_kernel(const float2 *__restrict__ qf, int *__rest
 template <int NZ, int R>
 bool try_mma_comp(float2 *spec, const float2 *qf, int Nx, int Ny, int ldz, int *err, cudaStream_t s) {
   static int per_sm = 0;
-  using Cfg = MmaCompCfg<NZ, R>;
-  return launch_persistent(contract_mma_comp_kernel<NZ, R>, Cfg::THREADS, Cfg::SMEM, &per_sm, spec, qf, Nx, Ny, ldz,
+  using Cfg = MmaMatCfg<NZ, R>;
+  return launch_persistent(contract_mma_mat_kernel<NZ, R>, Cfg::THREADS, Cfg::SMEM, &per_sm, spec, qf, Nx, Ny, ldz,
                            err, s);
 }
 

@@ -14,9 +14,9 @@ namespace ie {
 // tensor memory and FP32 accumulators there (c64, Nz in {16, 32}, R <= 2): 6 kind::tf32
 // on the 3xTF32 split, 7 kind::f16 on a scaled two-way FP16 split (the same 22
 // significant bits, half the instructions; needs the per-wavenumber exponents of
-// launch_block_exponents).  Variant 8 takes the 3xTF32 mma.sync path a component of
-// the output at a time, unpacking three of the six matrices per sub-step (c64, Nz in
-// {16, 32, 48, 64}, R <= 2): the tensor-core variant for Nz = 64.
+// launch_block_exponents).  Variant 8 takes the 3xTF32 mma.sync path one Nz x Nz
+// matrix of the block at a time, staging and unpacking one matrix per sub-step (c64,
+// Nz in {16, 32, 48, 64}, R <= 2): the tensor-core variant for Nz = 64.
 enum ContractVariant {
   kContractAuto = -1, kContractTma1 = 0, kContractTma3 = 1, kContractPanel = 2, kContractTma1Row = 3,
   kContractMma = 4, kContractMmaUnpack = 5, kContractTc = 6, kContractTc16 = 7, kContractMmaComp = 8

@@ -507,17 +507,19 @@ __global__ void __launch_bounds__(MmaUnpackCfg<NZ, R>::THREADS)
   }
 }
 
-// contract_mma_comp_kernel: the block of a wavenumber in three sub-steps, one per output
-// component alpha, so that only the three Nz x Nz matrices M[alpha][0..2] are unpacked
-// at a time (at Nz = 64 the whole unpacked block, 6 x 64 x 68 complex, does not fit in
-// shared memory with its staging; three matrices do).  Per sub-step one thread copies
-// the three packed matrices (bulk copies, the next sub-step's issued as soon as the
-// current one is unpacked), all warps unpack them, and warp (row tile, beta) applies
-// M[alpha][beta] to the X of component beta with the 3xTF32 MMAs; the three beta
-// partial sums meet in shared memory.  X is staged once per wavenumber.  Across the
-// three sub-steps xy, xz, yz are read twice (the second time mostly from L2).
+// contract_mma_mat_kernel: the block of a wavenumber one Nz x Nz matrix M[alpha][beta]
+// at a time (nine sub-steps; the symmetric xy and the full xz, yz serve two of them
+// each and are copied twice, the second time mostly from L2), so that a CTA stages
+// one packed matrix and one unpacked one: at Nz = 64 the whole unpacked block (6 x 64 x
+// 68 complex) does not fit in shared memory with its staging, one matrix does, twice
+// per SM.  Per sub-step one thread copies the packed matrix (a bulk copy, the next
+// sub-step's issued as soon as the current one is unpacked), all warps unpack it, and
+// warp (row tile, K half) applies it to its half of X's component beta with the
+// 3xTF32 MMAs, accumulating over beta in registers; after beta = 2 the two K halves
+// meet in shared memory and component alpha of Y is stored.  X is staged once per
+// wavenumber.
 template <int NZ, int R>
-struct MmaCompCfg {
+struct MmaMatCfg {
   static_assert(NZ % 16 == 0 && NZ <= 64, "row tiles of 16; at most 64 layers");
   static_assert(R >= 1 && R <= 2, "one n-tile of 8 columns: 4 mirrors x R <= 8");
   static constexpr int N3 = 3 * NZ;
@@ -526,34 +528,33 @@ struct MmaCompCfg {
   static constexpr int BS = 2 * NZ * (2 * NZ + 1);
   static constexpr int LD = NZ + 4;     // = 4 (mod 16)
   static constexpr int RT = NZ / 16;    // row tiles per component
-  static constexpr int WARPS = 3 * RT;  // (row tile, beta)
+  static constexpr int WARPS = 2 * RT;  // (row tile, K half)
   static constexpr int THREADS = WARPS * 32;
   static constexpr int KS = N3 / 8;     // k-steps of the staged X
-  static constexpr int RAWMAX = 2 * NZ * NZ + P;  // complex: two full matrices + a triangle
   static constexpr int LDXR = CZ + 4;
-  static constexpr size_t OFF_BAR = 0;  // [0]: the block's copies, [1]: X's copies
+  static constexpr size_t OFF_BAR = 0;  // [0]: the matrix copies, [1]: X's copies
   static constexpr size_t OFF_RAW = 128;
-  static constexpr size_t RAW_BYTES = (size_t)RAWMAX * 8;
+  static constexpr size_t RAW_BYTES = (size_t)NZ * NZ * 8;
   static constexpr size_t OFF_XRAW = OFF_RAW + RAW_BYTES;
   static constexpr size_t XRAW_BYTES = (size_t)4 * LDXR * 8;
   static constexpr size_t OFF_BLK = OFF_XRAW + XRAW_BYTES;
-  static constexpr size_t BLK_BYTES = (size_t)3 * NZ * LD * 8;
+  static constexpr size_t BLK_BYTES = (size_t)NZ * LD * 8;
   static constexpr size_t OFF_XS = OFF_BLK + BLK_BYTES;
   static constexpr size_t XS_PLANE = (size_t)KS * 32 * 16;
   static constexpr size_t OFF_TRI = OFF_XS + 2 * XS_PLANE;
   static constexpr size_t SMEM = OFF_TRI + (((size_t)P * 2 + 15) / 16) * 16;
-  // the beta partial sums (8 floats per thread of the beta = 1, 2 warps) reuse the
-  // unpacked matrices' space once the MMAs are done
-  static_assert((size_t)2 * RT * 32 * 8 * 4 <= BLK_BYTES, "partial sums fit the block space");
-  static_assert(((size_t)P * 8) % 16 == 0 && RAW_BYTES % 16 == 0 && OFF_XRAW % 16 == 0 && (LDXR * 8) % 16 == 0,
-                "bulk copy alignment");
+  // the K-half partial sums (8 floats per thread of the second-half warps) reuse the
+  // unpacked matrix's space once the MMAs are done
+  static_assert((size_t)RT * 32 * 8 * 4 <= BLK_BYTES, "partial sums fit the matrix space");
+  static_assert(((size_t)P * 8) % 16 == 0 && OFF_XRAW % 16 == 0 && (LDXR * 8) % 16 == 0 && OFF_XS % 16 == 0,
+                "bulk copy and vector alignment");
 };
 
 template <int NZ, int R>
-__global__ void __launch_bounds__(MmaCompCfg<NZ, R>::THREADS, 1)
-    contract_mma_comp_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz,
-                             int *err, long long lim) {
-  using Cfg = MmaCompCfg<NZ, R>;
+__global__ void __launch_bounds__(MmaMatCfg<NZ, R>::THREADS)
+    contract_mma_mat_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz,
+                            int *err, long long lim) {
+  using Cfg = MmaMatCfg<NZ, R>;
   constexpr int N3 = Cfg::N3, CZ = Cfg::CZ, P = Cfg::P, BS = Cfg::BS, LD = Cfg::LD, RT = Cfg::RT;
   constexpr int THREADS = Cfg::THREADS, NN = NZ * NZ;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -580,21 +581,18 @@ __global__ void __launch_bounds__(MmaCompCfg<NZ, R>::THREADS, 1)
   }
   __syncthreads();
 
-  // the packed matrices of M[alpha][0..2] into raw: alpha 0: xx, xy (triangles), xz;
-  // alpha 1: xy, yy (triangles), yz; alpha 2: xz, yz (full), zz (triangle)
-  auto issue_block = [&](int w, int alpha) {
-    const float2 *q = qf + (size_t)w * BS;
+  // packed kind of M[alpha][beta]: xx, yy, zz, xy (triangles 0-3), xz, yz (full 4, 5);
+  // M[1][0] = xy, M[2][0] = -xz^T, M[2][1] = -yz^T
+  auto kind_of = [](int alpha, int beta) -> int {
+    return alpha == beta ? alpha : (alpha + beta == 1 ? 3 : (alpha + beta == 2 ? 4 : 5));
+  };
+  auto issue_mat = [&](int w, int step) {
+    const int kind = kind_of(step / 3, step % 3);
+    const float2 *q = qf + (size_t)w * BS + (kind < 4 ? (size_t)kind * P : 4 * (size_t)P + (size_t)(kind - 4) * NN);
+    const uint32_t bytes = (uint32_t)((kind < 4 ? P : NN) * 8);
     tma::fence_proxy_async();
-    if (alpha < 2) {
-      tma::mbar_expect_tx(&bar[0], (uint32_t)((2 * P + NN) * 8));
-      tma::bulk_g2s(raw, q + (alpha == 0 ? 0 : 3) * (size_t)P, (uint32_t)(P * 8), &bar[0]);
-      tma::bulk_g2s(raw + P, q + (alpha == 0 ? 3 : 1) * (size_t)P, (uint32_t)(P * 8), &bar[0]);
-      tma::bulk_g2s(raw + 2 * P, q + 4 * (size_t)P + (size_t)alpha * NN, (uint32_t)(NN * 8), &bar[0]);
-    } else {
-      tma::mbar_expect_tx(&bar[0], (uint32_t)((P + 2 * NN) * 8));
-      tma::bulk_g2s(raw, q + 4 * (size_t)P, (uint32_t)(2 * NN * 8), &bar[0]);
-      tma::bulk_g2s(raw + 2 * NN, q + 2 * (size_t)P, (uint32_t)(P * 8), &bar[0]);
-    }
+    tma::mbar_expect_tx(&bar[0], bytes);
+    tma::bulk_g2s(raw, q, bytes, &bar[0]);
   };
   auto issue_x = [&](int w) {
     const Mirrors mi = mirrors_of(w, Nx, Ny);
@@ -612,7 +610,7 @@ __global__ void __launch_bounds__(MmaCompCfg<NZ, R>::THREADS, 1)
   const int w0 = blockIdx.x;
   if (tid == 0 && w0 < nf) {
     issue_x(w0);
-    issue_block(w0, 0);
+    issue_mat(w0, 0);
     nx_issued = nb_issued = 1;
   }
   // on a wait that ran out: record it, let thread 0 wait for its copies still in
@@ -626,7 +624,7 @@ __global__ void __launch_bounds__(MmaCompCfg<NZ, R>::THREADS, 1)
   };
 
   const int g = lane >> 2, t = lane & 3;
-  const int rt = warp % RT, beta = warp / RT;
+  const int rt = warp % RT, kh = warp / RT;
   const int a0 = rt * 16;
   for (int w = w0; w < nf; w += gridDim.x) {
     const Mirrors mw = mirrors_of(w, Nx, Ny);
@@ -662,80 +660,70 @@ __global__ void __launch_bounds__(MmaCompCfg<NZ, R>::THREADS, 1)
       xs[e] = h;
       xs[Cfg::KS * 32 + e] = l;
     }
-    for (int alpha = 0; alpha < 3; ++alpha) {
+    float acc[2][2][2][4];
+    for (int step = 0; step < 9; ++step) {
+      const int alpha = step / 3, beta = step - 3 * alpha;
+      const int kind = kind_of(alpha, beta);
       if (!__syncthreads_and(tma::mbar_wait_bounded(&bar[0], (uint32_t)(nb_done & 1), lim))) {
         give_up();
         return;
       }
       ++nb_done;
-      // unpack M[alpha][0..2] into blk[0..2] (rows a, columns b at a LD + b)
-      const int ntri = alpha < 2 ? 2 : 1;
-      const int total = ntri * P + (3 - ntri) * NN;
-      for (int e = tid; e < total; e += THREADS) {
-        if (alpha < 2) {
-          if (e < 2 * P) {
-            const int slot = e >= P, ee = e - slot * P;
-            const int ab = tri[ee], a = ab >> 8, b = ab & 255;
-            const float2 v = raw[slot * P + a * NZ - a * (a - 1) / 2 + (b - a)];
-            float2 *m = blk + slot * NZ * LD;
-            m[a * LD + b] = v;
-            m[b * LD + a] = v;
-          } else {
-            const int ee = e - 2 * P, a = ee / NZ, b = ee - a * NZ;
-            blk[2 * NZ * LD + a * LD + b] = raw[e];
-          }
-        } else {
-          if (e < 2 * NN) {
-            const int slot = e >= NN, ee = e - slot * NN, a = ee / NZ, b = ee - a * NZ;
-            blk[slot * NZ * LD + a * LD + b] = raw[e];
-          } else {
-            const int ab = tri[e - 2 * NN], a = ab >> 8, b = ab & 255;
-            const float2 v = raw[2 * NN + a * NZ - a * (a - 1) / 2 + (b - a)];
-            float2 *m = blk + 2 * NZ * LD;
-            m[a * LD + b] = v;
-            m[b * LD + a] = v;
-          }
+      // unpack: rows a, columns b at a LD + b
+      if (kind < 4) {
+        for (int e = tid; e < P; e += THREADS) {
+          const int ab = tri[e], a = ab >> 8, b = ab & 255;
+          const float2 v = raw[a * NZ - a * (a - 1) / 2 + (b - a)];
+          blk[a * LD + b] = v;
+          blk[b * LD + a] = v;
+        }
+      } else {
+        for (int e = tid; e < NN; e += THREADS) {
+          const int a = e / NZ, b = e - a * NZ;
+          blk[a * LD + b] = raw[e];
         }
       }
-      __syncthreads();  // blk (and on alpha 0 xs) ready; raw (and xraw) consumed
+      __syncthreads();  // blk (and in the first step xs) ready; raw (and xraw) consumed
       if (tid == 0) {
-        if (alpha < 2) {
-          issue_block(w, alpha + 1);
+        if (step < 8) {
+          issue_mat(w, step + 1);
           ++nb_issued;
         } else if (w + (int)gridDim.x < nf) {
-          issue_block(w + gridDim.x, 0);
+          issue_mat(w + gridDim.x, 0);
           ++nb_issued;
         }
-        if (alpha == 0 && w + (int)gridDim.x < nf) {
+        if (step == 0 && w + (int)gridDim.x < nf) {
           issue_x(w + gridDim.x);
           ++nx_issued;
         }
       }
-      float acc[2][2][2][4];
+      if (beta == 0) {
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+          for (int j = 0; j < 2; ++j)
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[i][j][h][c] = 0.f;
+              for (int c = 0; c < 4; ++c) acc[i][j][h][c] = 0.f;
+      }
       {
         // M[2][0] = -xz^T, M[2][1] = -yz^T: read transposed, the minus on X
         const bool trb = alpha == 2 && beta < 2;
         const uint32_t neg = trb ? 0x80000000u : 0u;
         const int rs = trb ? 1 : LD, cs = trb ? LD : 1;
-        const float2 *p0 = blk + beta * NZ * LD + (a0 + g) * rs + t * cs;
+        const int b0 = kh * (NZ / 2);
+        const float2 *p0 = blk + (a0 + g) * rs + (b0 + t) * cs;
         const uint4 *xfh = xs, *xfl = xs + Cfg::KS * 32;
-#pragma unroll 4
-        for (int bb = 0; bb < NZ; bb += 8) {
+#pragma unroll
+        for (int bb = 0; bb < NZ / 2; bb += 8) {
           const float2 *p = p0 + bb * cs;
           float2 m[4];
           m[0] = p[0];
           m[1] = p[8 * rs];
           m[2] = p[4 * cs];
           m[3] = p[8 * rs + 4 * cs];
-          const int ks = beta * (NZ / 8) + bb / 8;
+          const int ks = (beta * NZ + b0 + bb) / 8;
           const uint4 xh = xfh[ks * 32 + lane], xl = xfl[ks * 32 + lane];
           const uint32_t brh[2] = {xh.x ^ neg, xh.z ^ neg}, bih[2] = {xh.y ^ neg, xh.w ^ neg};
           const uint32_t brl[2] = {xl.x ^ neg, xl.z ^ neg}, bil[2] = {xl.y ^ neg, xl.w ^ neg};
@@ -744,6 +732,9 @@ __global__ void __launch_bounds__(MmaCompCfg<NZ, R>::THREADS, 1)
           mma::mma12(acc, arh, arl, aih, ail, brh, brl, bih, bil);
         }
       }
+      __syncthreads();  // every warp is done with blk
+      if (beta < 2) continue;
+      // component alpha of Y: the two K halves meet in blk's space
       float part[4][2];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -752,27 +743,23 @@ __global__ void __launch_bounds__(MmaCompCfg<NZ, R>::THREADS, 1)
         part[c][0] = rr - ii;
         part[c][1] = ri + ir;
       }
-      __syncthreads();  // every warp is done with blk: its space takes the partial sums
-      if (beta > 0) {
-        float4 *rp = reinterpret_cast<float4 *>(red + (((beta - 1) * RT + rt) * 32 + lane) * 8);
+      if (kh == 1) {
+        float4 *rp = reinterpret_cast<float4 *>(red + (rt * 32 + lane) * 8);
         rp[0] = make_float4(part[0][0], part[0][1], part[1][0], part[1][1]);
         rp[1] = make_float4(part[2][0], part[2][1], part[3][0], part[3][1]);
       }
       __syncthreads();
-      if (beta == 0) {
-#pragma unroll
-        for (int bt = 0; bt < 2; ++bt) {
-          const float4 *rp = reinterpret_cast<const float4 *>(red + ((bt * RT + rt) * 32 + lane) * 8);
-          const float4 u0 = rp[0], u1 = rp[1];
-          part[0][0] += u0.x;
-          part[0][1] += u0.y;
-          part[1][0] += u0.z;
-          part[1][1] += u0.w;
-          part[2][0] += u1.x;
-          part[2][1] += u1.y;
-          part[3][0] += u1.z;
-          part[3][1] += u1.w;
-        }
+      if (kh == 0) {
+        const float4 *rp = reinterpret_cast<const float4 *>(red + (rt * 32 + lane) * 8);
+        const float4 u0 = rp[0], u1 = rp[1];
+        part[0][0] += u0.x;
+        part[0][1] += u0.y;
+        part[1][0] += u0.z;
+        part[1][1] += u0.w;
+        part[2][0] += u1.x;
+        part[2][1] += u1.y;
+        part[3][0] += u1.z;
+        part[3][1] += u1.w;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int col = 2 * t + (c & 1);
