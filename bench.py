@@ -27,7 +27,7 @@ Printed (one JSON line, rank 0):
                 right-hand sides and D2H of the solution inside the timed region)
   c3_batch      the batched configuration (16 frequencies x 2 polarisations over four
                 grids) in the timed precision: batched and one-at-a-time solved
-                instances/s (--skip-c3 leaves it out; --mode batch adds plain FP64)
+                instances/s, and batched plain FP64 (--skip-c3 leaves it out)
 
 --impl reference runs the oracle (the reference implementation of this tier) on the
 host cores for the same workload and metric.
@@ -566,7 +566,7 @@ def run_ours(args, rank, ws):
     # ---- the batched configuration (four grids, 32 instances) in the timed precision ----
     c3 = None
     if rank == 0 and ws == 1 and args.workload == "C2" and not args.skip_c3:
-        c3 = c3_summary(args, ie.IE_MIXED_FP64K, with_fp64=False)
+        c3 = c3_summary(args, ie.IE_MIXED_FP64K, with_fp64=not args.skip_fp64)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -230,6 +230,20 @@ ie_status ie_solve_batch(ie_ctx *ctx, int n_inst, const int *inst_host, const vo
  * ie_set_contract_variant overrides the choice for one right-hand-side count
  * (-1: built-in choice); IE_ERR_ARG if the variant does not apply to this grid. */
 ie_status ie_contract_tuning(ie_ctx *ctx, int *variant_host, double *ms_host);
+
+/* Stage order (radices) of the FFT plan of one axis (0: the 2Nx row transforms, 1: the
+ * 2Ny column transforms), used by the mixed-radix Stockham kernels of the c128 product
+ * and of every c64 length without a register-blocked kernel (Sect. 3.3, steps 1 and 3).
+ * With the autotuner on, ie_setup times the candidate orders of each length (radix-4
+ * stages first, radix-8 first, odd factors first, a radix-2 stage first) in the c128
+ * forward passes and keeps the fastest.  radix_host: at least 20 ints; *n_stages the
+ * count; *ms (may be NULL): the chosen plan's time per pass for one right-hand side
+ * (0 if not tuned).  IE_ERR_ARG for an axis other than 0 or 1. */
+ie_status ie_fft_plan(ie_ctx *ctx, int axis, int *radix_host, int *n_stages, double *ms);
+/* Override the plan of one axis with n_stages radices from {2, 3, 4, 5, 7, 8, 11, 13}
+ * whose product is the axis's transform length (2Nx or 2Ny); IE_ERR_ARG otherwise
+ * (the plan is left unchanged). */
+ie_status ie_set_fft_plan(ie_ctx *ctx, int axis, const int *radix_host, int n_stages);
 ie_status ie_set_contract_variant(ie_ctx *ctx, int nrhs, int variant);
 
 /* Solve the transposed system A^T w = b (same arguments as ie_solve).  The

@@ -30,6 +30,68 @@ FftPlan make_plan(int L) {
   return p;
 }
 
+std::vector<FftPlan> candidate_plans(int L) {
+  std::vector<FftPlan> out;
+  FftPlan base;
+  try {
+    base = make_plan(L);
+  } catch (...) {
+    return out;
+  }
+  int n2 = 0, rest = L;
+  while (rest % 2 == 0) { ++n2; rest /= 2; }
+  std::vector<int> odd;
+  for (int st = 0; st < base.n_stages; ++st)
+    if (base.radix[st] % 2) odd.push_back(base.radix[st]);
+  auto build = [&](const std::vector<int> &r) {
+    FftPlan p{};
+    p.L = L;
+    if ((int)r.size() > kMaxStages) return;
+    for (int v : r) p.radix[p.n_stages++] = v;
+    for (const FftPlan &q : out) {
+      if (q.n_stages != p.n_stages) continue;
+      bool same = true;
+      for (int k = 0; k < p.n_stages; ++k) same = same && q.radix[k] == p.radix[k];
+      if (same) return;
+    }
+    out.push_back(p);
+  };
+  auto pow2_stages = [&](int first8, bool two_first) {
+    std::vector<int> r;
+    int m = n2;
+    if (two_first && m % 2 == 1) { r.push_back(2); --m; }
+    if (first8) while (m >= 3) { r.push_back(8); m -= 3; }
+    while (m >= 2) { r.push_back(4); m -= 2; }
+    if (m == 1) r.push_back(2);
+    return r;
+  };
+  {
+    std::vector<int> r(base.radix, base.radix + base.n_stages);
+    build(r);
+  }
+  {
+    std::vector<int> r = pow2_stages(1, false);
+    r.insert(r.end(), odd.begin(), odd.end());
+    build(r);
+  }
+  {
+    std::vector<int> r = odd, t = pow2_stages(0, false);
+    r.insert(r.end(), t.begin(), t.end());
+    build(r);
+  }
+  {
+    std::vector<int> r = odd, t = pow2_stages(1, false);
+    r.insert(r.end(), t.begin(), t.end());
+    build(r);
+  }
+  {
+    std::vector<int> r = pow2_stages(0, true);
+    r.insert(r.end(), odd.begin(), odd.end());
+    build(r);
+  }
+  return out;
+}
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -156,8 +218,17 @@ template <typename K> void set_smem(K kern, size_t bytes) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Register-blocked FP32 kernels for L = 16 Q, Q in {8, 16, 32} (0: not applicable).
-int fast_q(int L) { return (L == 128 || L == 256 || L == 512) ? L / 16 : 0; }
+// Register-blocked FP32 kernels for L = 16 Q, Q in {8, 12, 16, 24, 32} (0: not applicable).
+int fast_q(int L) { return (L == 128 || L == 192 || L == 256 || L == 384 || L == 512) ? L / 16 : 0; }
+
+#define IE_FAST_Q_DISPATCH(q, CALL) \
+  switch (q) {                      \
+    case 8: CALL(8); break;         \
+    case 12: CALL(12); break;       \
+    case 16: CALL(16); break;       \
+    case 24: CALL(24); break;       \
+    default: CALL(32); break;       \
+  }
 
 template <int Q, bool INV>
 void axis_fast(const float2 *in, float2 *out, int outer, int Lin, int Lout, long long inner, float scale,
@@ -195,9 +266,9 @@ void launch_fft_axis(const C<T> *in, C<T> *out, int outer, int Lin, int Lout, lo
     const int q = fast_q(plan.L);
     if (q) {
       count_launches(1);
-      if (q == 8) axis_fast<8, INV>(in, out, outer, Lin, Lout, inner, scale, s);
-      else if (q == 16) axis_fast<16, INV>(in, out, outer, Lin, Lout, inner, scale, s);
-      else axis_fast<32, INV>(in, out, outer, Lin, Lout, inner, scale, s);
+#define IE_CALL(Q) axis_fast<Q, INV>(in, out, outer, Lin, Lout, inner, scale, s)
+      IE_FAST_Q_DISPATCH(q, IE_CALL)
+#undef IE_CALL
       return;
     }
   }
@@ -217,9 +288,9 @@ void launch_fft_rows_fwd(const C<TX> *x, const C<TX> *in_scale, C<T> *t1, int CZ
     const int q = fast_q(plan.L);
     if (q && plan.L == 2 * Nx) {
       count_launches(1);
-      if (q == 8) rows_fwd_fast<8, TX>(x, in_scale, t1, CZ, Nz, Ny, Nx, s);
-      else if (q == 16) rows_fwd_fast<16, TX>(x, in_scale, t1, CZ, Nz, Ny, Nx, s);
-      else rows_fwd_fast<32, TX>(x, in_scale, t1, CZ, Nz, Ny, Nx, s);
+#define IE_CALL(Q) rows_fwd_fast<Q, TX>(x, in_scale, t1, CZ, Nz, Ny, Nx, s)
+      IE_FAST_Q_DISPATCH(q, IE_CALL)
+#undef IE_CALL
       return;
     }
   }
@@ -239,9 +310,9 @@ void launch_fft_rows_inv(const C<T> *t1, const C<TX> *x, const C<TX> *diag, cons
     const int q = fast_q(plan.L);
     if (q && plan.L == 2 * Nx) {
       count_launches(1);
-      if (q == 8) rows_inv_fast<8, TX>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx, s);
-      else if (q == 16) rows_inv_fast<16, TX>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx, s);
-      else rows_inv_fast<32, TX>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx, s);
+#define IE_CALL(Q) rows_inv_fast<Q, TX>(t1, x, diag, out_scale, y, CZ, Nz, Ny, Nx, s)
+      IE_FAST_Q_DISPATCH(q, IE_CALL)
+#undef IE_CALL
       return;
     }
   }

@@ -6,12 +6,18 @@
 // [l][ti] (ti contiguous), so that global loads and stores move whole 128-byte
 // rows and butterflies touch consecutive shared-memory words.
 #pragma once
+#include <vector>
+
 #include "ie_common.cuh"
 
 namespace ie {
 
 // Host: factor L into radices 4, 2, 3, 5 and any remaining prime factors.
 FftPlan make_plan(int L);
+// Host: the distinct stage orders the plan autotuner times for length L: the default
+// (4s, a 2, odd factors), radix-8 stages first, the odd factors first, a radix-2 stage
+// first (empty if L has a prime factor above 13).
+std::vector<FftPlan> candidate_plans(int L);
 
 // Number of transforms per CTA for element type T (one 128-byte row of them).
 template <typename T> __host__ __device__ constexpr int fft_ti() { return 128 / (int)sizeof(C<T>); }
@@ -37,11 +43,43 @@ __device__ __forceinline__ C<T> twid(const C<T> *tw, int idx) {
   return w;
 }
 
-// In-register DFT of compile-time radix R (2 and 4 closed form, others by the direct sum
-// with the length-L twiddle table).
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(C<T> &a0, C<T> &a1, C<T> &a2, C<T> &a3) {
+  C<T> t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  C<T> t2 = cadd(a1, a3), d = csub(a1, a3);
+  // forward: -i * d ; inverse: +i * d
+  C<T> t3 = INV ? mk<T>(-d.y, d.x) : mk<T>(d.y, -d.x);
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+// In-register DFT of compile-time radix R (2, 4 and 8 closed form, others by the direct
+// sum with the length-L twiddle table).
 template <typename T, bool INV, int R>
 __device__ __forceinline__ void dft_small(C<T> (&v)[R], const C<T> *tw, int L) {
-  if constexpr (R == 2) {
+  if constexpr (R == 8) {
+    // even and odd halves by 4-point DFTs, then X[k] = E[k] + w_8^k O[k], X[k + 4] =
+    // E[k] - w_8^k O[k] (w_8 = (1 -+ i) / sqrt 2, w_8^2 = -+ i)
+    C<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<T, INV>(e0, e1, e2, e3);
+    dft4<T, INV>(o0, o1, o2, o3);
+    const T h = (T)0.70710678118654752440;
+    // w_8 o1, w_8^2 o2, w_8^3 o3 (forward; the inverse takes the conjugates)
+    C<T> p1 = INV ? mk<T>(h * (o1.x - o1.y), h * (o1.x + o1.y)) : mk<T>(h * (o1.x + o1.y), h * (o1.y - o1.x));
+    C<T> p2 = INV ? mk<T>(-o2.y, o2.x) : mk<T>(o2.y, -o2.x);
+    C<T> p3 = INV ? mk<T>(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : mk<T>(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, p1);
+    v[5] = csub(e1, p1);
+    v[2] = cadd(e2, p2);
+    v[6] = csub(e2, p2);
+    v[3] = cadd(e3, p3);
+    v[7] = csub(e3, p3);
+  } else if constexpr (R == 2) {
     C<T> a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
@@ -96,7 +134,7 @@ __device__ __forceinline__ void fft_stage(const C<T> *src, C<T> *dst, int ld, in
 
 // Run the plan on ntr sequences stored as buf[l * ld + t] (t < ntr).  A holds the
 // input; B is scratch of the same shape.  Returns the buffer with the result.
-// Supported radices: 2, 3, 4, 5, 7, 11, 13 (make_plan rejects other prime factors).
+// Supported radices: 2, 3, 4, 5, 7, 8, 11, 13 (make_plan rejects other prime factors).
 template <typename T, bool INV>
 __device__ C<T> *fft_smem(C<T> *A, C<T> *B, int ld, int ntr, const C<T> *tw, const FftPlan &p, int tid,
                           int nthr) {
@@ -106,6 +144,7 @@ __device__ C<T> *fft_smem(C<T> *A, C<T> *B, int ld, int ntr, const C<T> *tw, con
   for (int st = 0; st < p.n_stages; ++st) {
     const int R = p.radix[st];
     switch (R) {
+      case 8: fft_stage<T, INV, 8>(src, dst, ld, ntr, tw, L, Ns, tid, nthr); break;
       case 4: fft_stage<T, INV, 4>(src, dst, ld, ntr, tw, L, Ns, tid, nthr); break;
       case 2: fft_stage<T, INV, 2>(src, dst, ld, ntr, tw, L, Ns, tid, nthr); break;
       case 3: fft_stage<T, INV, 3>(src, dst, ld, ntr, tw, L, Ns, tid, nthr); break;

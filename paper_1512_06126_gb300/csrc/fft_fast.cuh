@@ -1,11 +1,13 @@
-// Register-blocked FP32 FFTs for transform lengths L = 16 Q, Q in {8, 16, 32}
-// (L = 128, 256, 512: the zero-padded lengths 2N of 64-, 128- and 256-cell grids).
+// Register-blocked FP32 FFTs for transform lengths L = 16 Q, Q in {8, 12, 16, 24, 32}
+// (L = 128, 192, 256, 384, 512: the zero-padded lengths 2N of 64-, 96-, 128-, 192- and
+// 256-cell grids).
 //
 // A length-L DFT is split as L = 16 x Q: with l = q + Q p and k = k1 + 16 k2,
 //   X[k1 + 16 k2] = sum_q w_Q^(q k2) w_L^(q k1) sum_p x[q + Q p] w_16^(p k1),
 // so one thread per (sequence, q) does a 16-point DFT in registers, multiplies by the
 // twiddles w_L^(q k1), and after one exchange through shared memory one thread per
-// (sequence, k1) does a Q-point DFT in registers.  TI = 16 sequences share a CTA and
+// (sequence, k1) does a Q-point DFT in registers (radix 2, and one radix-3 step where
+// Q = 3 M).  TI = 16 sequences share a CTA and
 // sit in the lowest thread-index bits, so every global load or store of a half-warp
 // moves 16 consecutive elements of the sequence index (128 bytes).  The in-register
 // DFTs are radix-2 decimation in time, the input permutation resolved at compile time
@@ -96,13 +98,50 @@ __device__ __forceinline__ void step1(float2 (&v)[16], const float2 *tw, float2 
   }
 }
 
-// Step 2 for one (sequence t, k1): returns X[k1 + 16 k2] in w[k2].
+// Step 2 for one (sequence t, k1): returns X[k1 + 16 k2] in w[k2].  Q a power of two:
+// one radix-2 DFT in registers.  Q = 3 M (M a power of two): with q = r + 3 m and
+// k2 = k + M s, X = sum_r w_3^(r s) w_Q^(r k) Z_r[k], Z_r the M-point DFT of the inputs
+// r, r + 3, ...: three M-point DFTs, the twiddles w_Q^(r k), M 3-point DFTs.
 template <int Q, bool INV>
 __device__ __forceinline__ void step2(float2 (&w)[Q], const float2 *tw, const float2 *Y, int k1, int t) {
   constexpr int L = 16 * Q;
+  if constexpr ((Q & (Q - 1)) == 0) {
 #pragma unroll
-  for (int q = 0; q < Q; ++q) w[bitrev<Q>(q)] = Y[(q * 16 + k1) * kTI + t];
-  dft_br<Q, INV>(w, tw, L / Q);
+    for (int q = 0; q < Q; ++q) w[bitrev<Q>(q)] = Y[(q * 16 + k1) * kTI + t];
+    dft_br<Q, INV>(w, tw, L / Q);
+  } else {
+    constexpr int M = Q / 3;
+    static_assert(3 * M == Q && (M & (M - 1)) == 0, "Q = 3 M with M a power of two");
+    float2 z[3][M];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) z[r][bitrev<M>(m)] = Y[((r + 3 * m) * 16 + k1) * kTI + t];
+      dft_br<M, INV>(z[r], tw, L / M);
+    }
+    // sin(2 pi / 3); w_3 = -1/2 -+ i s (forward / inverse)
+    const float s3 = INV ? -0.86602540378443865f : 0.86602540378443865f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const float2 a = z[0][k];
+      float2 b = z[1][k], c = z[2][k];
+      if (k != 0) {
+        float2 w1 = tw[k * (L / Q)], w2 = tw[2 * k * (L / Q)];
+        if (INV) {
+          w1.y = -w1.y;
+          w2.y = -w2.y;
+        }
+        b = fmul(b, w1);
+        c = fmul(c, w2);
+      }
+      const float2 sp = make_float2(b.x + c.x, b.y + c.y), sm = make_float2(b.x - c.x, b.y - c.y);
+      const float2 h = make_float2(a.x - 0.5f * sp.x, a.y - 0.5f * sp.y);
+      w[k] = make_float2(a.x + sp.x, a.y + sp.y);
+      // w_3 b + w_3^2 c = -(b + c) / 2 - i s (b - c); the conjugate pair for s = 2
+      w[k + M] = make_float2(h.x + s3 * sm.y, h.y - s3 * sm.x);
+      w[k + 2 * M] = make_float2(h.x - s3 * sm.y, h.y + s3 * sm.x);
+    }
+  }
 }
 
 template <typename TX>

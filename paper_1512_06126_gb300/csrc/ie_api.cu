@@ -55,6 +55,7 @@ struct ie_ctx {
   std::vector<cd> sig, sigma_a;
   std::vector<int> lay;
   ie::FftPlan px{}, py{};
+  double fft_ms[2] = {0.0, 0.0};  // plan autotuner: ms of the chosen c128 pass (x rows, y columns)
   int max_rhs = 1;
   int cvar[5] = {-1, -1, -1, -1, -1};          // c64 contraction variant per right-hand sides per instance
   double tune_ms[5][ie::kContractVariants] = {};  // autotuner timings (ms per launch, 0: not timed)
@@ -965,6 +966,53 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
 }
 long long ie_ctx_device_bytes(ie_ctx *c) { return c ? c->dev_bytes : 0; }
 
+// FFT plan autotuner: time every candidate stage order (candidate_plans) of the two
+// transform lengths in the c128 passes the refinement residuals and FP64 solves run (the
+// forward row pass over x, the column pass over y; four launches each on the context's
+// workspaces, zeroed) and keep the fastest.  The c64 passes use the same plans where no
+// register-blocked kernel applies.
+ie_status autotune_fft(ie_ctx *c) {
+  const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
+  const int CZ = 3 * Nz;  // one right-hand side
+  cudaEvent_t e0, e1;
+  IE_CUDA(cudaEventCreate(&e0));
+  IE_CUDA(cudaEventCreate(&e1));
+  const double2 *x = (const double2 *)c->w;
+  double2 *t1 = (double2 *)c->t1, *spec = (double2 *)c->spec;
+  cudaMemsetAsync(c->w, 0, (size_t)c->nvec() * sizeof(double2), c->stream);
+  cudaMemsetAsync(c->t1, 0, (size_t)Ny * 2 * Nx * CZ * sizeof(double2), c->stream);
+  ie_status st = IE_OK;
+  for (int axis = 0; axis < 2 && st == IE_OK; ++axis) {
+    const std::vector<ie::FftPlan> cand = ie::candidate_plans(axis == 0 ? 2 * Nx : 2 * Ny);
+    if (cand.size() < 2) continue;
+    double best_ms = 1e300;
+    ie::FftPlan best = axis == 0 ? c->px : c->py;
+    for (const ie::FftPlan &p : cand) {
+      auto run = [&]() {
+        if (axis == 0)
+          ie::launch_fft_rows_fwd<double>(x, nullptr, t1, CZ, Nz, Ny, Nx, p, c->stream);
+        else
+          ie::launch_fft_axis<double, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, p, 1.0, c->stream);
+      };
+      run();
+      cudaEventRecord(e0, c->stream);
+      for (int k = 0; k < 4; ++k) run();
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = IE_ERR_CUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / 4.0 < best_ms) { best_ms = ms / 4.0; best = p; }
+    }
+    if (st != IE_OK) break;
+    if (axis == 0) c->px = best; else c->py = best;
+    c->fft_ms[axis] = best_ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == IE_OK) st = cuda_status(cudaGetLastError());
+  return st;
+}
+
 // Autotuner: time every contraction variant that applies to this grid (c64, one and two
 // right-hand sides per instance) on the context's own coefficients and workspaces, and
 // keep the fastest.  The spectrum workspace is zeroed first; the values do not change
@@ -1094,7 +1142,10 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
     for (int k = 0; k < kPinSlots; ++k) IE_CUDA(cudaEventCreateWithFlags(&c->pin_ev[k], cudaEventDisableTiming));
   }
   IE_CUDA(cudaStreamSynchronize(c->stream));
-  if (c->autotune) IE_TRY(autotune_contraction(c));
+  if (c->autotune) {
+    IE_TRY(autotune_fft(c));
+    IE_TRY(autotune_contraction(c));
+  }
   return IE_OK;
 }
 
@@ -1174,6 +1225,33 @@ ie_status ie_contract_tuning(ie_ctx *c, int *variant_host, double *ms_host) {
     if (ms_host)
       for (int v = 0; v < ie::kContractVariants; ++v) ms_host[(r - 1) * ie::kContractVariants + v] = c->tune_ms[r][v];
   }
+  return IE_OK;
+}
+
+ie_status ie_fft_plan(ie_ctx *c, int axis, int *radix_host, int *n_stages, double *ms) {
+  if (!c || axis < 0 || axis > 1 || !radix_host || !n_stages) return IE_ERR_ARG;
+  const ie::FftPlan &p = axis == 0 ? c->px : c->py;
+  *n_stages = p.n_stages;
+  for (int k = 0; k < p.n_stages; ++k) radix_host[k] = p.radix[k];
+  if (ms) *ms = c->fft_ms[axis];
+  return IE_OK;
+}
+
+ie_status ie_set_fft_plan(ie_ctx *c, int axis, const int *radix_host, int n_stages) {
+  if (!c || axis < 0 || axis > 1 || !radix_host || n_stages < 1 || n_stages > ie::kMaxStages) return IE_ERR_ARG;
+  ie::FftPlan p{};
+  p.L = axis == 0 ? 2 * c->nx : 2 * c->ny;
+  long long prod = 1;
+  for (int k = 0; k < n_stages; ++k) {
+    const int r = radix_host[k];
+    if (r != 2 && r != 3 && r != 4 && r != 5 && r != 7 && r != 8 && r != 11 && r != 13) return IE_ERR_ARG;
+    prod *= r;
+    p.radix[k] = r;
+  }
+  if (prod != p.L) return IE_ERR_ARG;
+  p.n_stages = n_stages;
+  if (axis == 0) c->px = p; else c->py = p;
+  c->fft_ms[axis] = 0.0;
   return IE_OK;
 }
 

@@ -27,7 +27,7 @@ IE_PROF_PRODUCT_C64, IE_PROF_PRODUCT_C128, IE_PROF_GS_C64, IE_PROF_GS_C128, IE_P
 
 EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_noalloc_sync", "ie_matvec", "ie_sync",
            "ie_fields", "ie_debug_set_wait_limit", "ie_solve", "ie_adjoint_solve", "ie_solve_batch",
-           "ie_contract_tuning", "ie_set_contract_variant", "ie_rhs_mt", "ie_set_sigma", "ie_set_receivers",
+           "ie_contract_tuning", "ie_fft_plan", "ie_set_fft_plan", "ie_set_contract_variant", "ie_rhs_mt", "ie_set_sigma", "ie_set_receivers",
            "ie_receiver_fields", "ie_mt_misfit", "ie_receiver_adjoint", "ie_gradient_accumulate", "ie_ctx_stream",
            "ie_ctx_device_bytes", "ie_profile", "ie_profile_read", "ie_profile_matvec", "ie_kernel_launches",
            "ie_destroy", "ie_status_str")
@@ -101,6 +101,10 @@ def load(path: str = LIB_PATH):
     lib.ie_solve_batch.restype = I
     lib.ie_contract_tuning.argtypes = [VP, VP, VP]
     lib.ie_contract_tuning.restype = I
+    lib.ie_fft_plan.argtypes = [VP, I, VP, VP, VP]
+    lib.ie_fft_plan.restype = I
+    lib.ie_set_fft_plan.argtypes = [VP, I, VP, I]
+    lib.ie_set_fft_plan.restype = I
     lib.ie_set_contract_variant.argtypes = [VP, I, I]
     lib.ie_set_contract_variant.restype = I
     lib.ie_set_sigma.argtypes = [VP, VP]
@@ -279,6 +283,19 @@ class Context:
         ms = np.zeros((4, N_CONTRACT_VARIANTS), dtype=np.float64)
         _check(self._lib.ie_contract_tuning(self.ctx, v.ctypes.data, ms.ctypes.data), "ie_contract_tuning")
         return v, ms
+
+    def fft_plan(self, axis):
+        """(radices of the FFT plan of axis 0 (x) or 1 (y), ms per c128 pass or 0)."""
+        r = np.zeros(20, dtype=np.int32)
+        n = ctypes.c_int(0)
+        ms = ctypes.c_double(0.0)
+        _check(self._lib.ie_fft_plan(self.ctx, axis, r.ctypes.data, ctypes.addressof(n), ctypes.addressof(ms)),
+               "ie_fft_plan")
+        return [int(v) for v in r[:n.value]], ms.value
+
+    def set_fft_plan(self, axis, radices):
+        r = np.ascontiguousarray(radices, dtype=np.int32)
+        _check(self._lib.ie_set_fft_plan(self.ctx, axis, r.ctypes.data, len(r)), "ie_set_fft_plan")
 
     def set_contract_variant(self, nrhs, variant):
         _check(self._lib.ie_set_contract_variant(self.ctx, nrhs, variant), "ie_set_contract_variant")

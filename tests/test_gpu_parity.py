@@ -327,22 +327,27 @@ def test_solve_nan_rhs_is_not_converged(precision):
     ctx.close()
 
 
-@pytest.mark.parametrize("shape", [(64, 64, 6), (128, 64, 4), (256, 32, 3), (64, 128, 5)])
+@pytest.mark.parametrize("shape", [(64, 64, 6), (128, 64, 4), (256, 32, 3), (64, 128, 5), (96, 96, 3),
+                                   (192, 96, 2), (96, 192, 2)])
 def test_fast_fft_lengths_against_c128(shape):
-    """Grids whose padded lengths 2N are 128, 256 or 512 take the register-blocked FP32
-    FFTs; the c64 product (one and two right-hand sides) must match the c128 product,
-    which uses the generic Stockham FFTs in FP64.  The mixed-precision solve (inner
-    GMRES in c64 through the same FFTs) must reach the FP64 solve's solution."""
+    """Grids whose padded lengths 2N are 128, 192, 256, 384 or 512 take the
+    register-blocked FP32 FFTs (192 and 384 with a radix-3 step); the c64 product (one
+    and two right-hand sides) must match the oracle's FFT product (2e-5) and the c128
+    product, which uses the generic Stockham FFTs in FP64 (2e-6).  The mixed-precision
+    solve (inner GMRES in c64 through the same FFTs) must reach the FP64 solve's
+    solution."""
     need_gpu()
     nx, ny, nz = shape
     m0 = W.small_model(nx=nx, ny=ny, nz=nz, seed=7, freq=1.0)
     g = m0.grid
     q = W.random_compressed_q(ny, nx, nz, seed=41, decay=0.02)
+    qt = O.full_spectrum_blocks(O.embed_spectrum(q))
     ctx = lib_context(m0, [q], max_rhs=2)
     s = torch.cuda.current_stream().cuda_stream
     for R in (1, 2):
         x = W.random_field((R, 3, nz, ny, nx), 60 + R)
-        x128 = to_dev(x.astype(np.complex64).astype(np.complex128))
+        xr = x.astype(np.complex64).astype(np.complex128)
+        x128 = to_dev(xr)
         y128 = torch.empty_like(x128)
         ctx.matvec(0, x128.data_ptr(), y128.data_ptr(), R, dtype=1, stream=s)
         x64 = x128.to(torch.complex64)
@@ -351,6 +356,10 @@ def test_fast_fft_lengths_against_c128(shape):
         torch.cuda.synchronize()
         err = float((y64.to(torch.complex128) - y128).norm() / y128.norm())
         assert err <= 2e-6, (shape, R, err)
+        y = to_host(y64).astype(np.complex128)
+        for r in range(R):
+            err = rel(y[r], O.fft_apply(m0, qt, xr[r]))
+            assert err <= 2e-5, (shape, R, r, err)
     b = to_dev(np.stack([normal.rhs_U0(m0, 1.0, "x"), normal.rhs_U0(m0, 1.0, "y")]))
     u64 = torch.zeros_like(b)
     umx = torch.zeros_like(b)
@@ -360,4 +369,44 @@ def test_fast_fft_lengths_against_c128(shape):
     st, _ = ctx.solve(0, b.data_ptr(), umx.data_ptr(), 2, 1e-7, precision=1)
     assert st == 0
     assert rel(to_host(umx), to_host(u64)) <= 1e-5
+    ctx.close()
+
+
+def test_fft_plans_against_oracle():
+    """The plan autotuner's choice multiplies out to each transform length, and every
+    stage order (radix 8, 4, 2, 3, 5 stages, odd factors first or last), set by hand,
+    gives the oracle's FFT product: c128 at 1e-12, c64 (generic FP32 Stockham: 2Nx = 96
+    and 2Ny = 80 have no register-blocked kernel) at 2e-5."""
+    need_gpu()
+    from paper_1512_06126_gb300 import ie
+    nx, ny, nz = 48, 40, 2
+    m = W.small_model(nx=nx, ny=ny, nz=nz, seed=5, freq=1.0)
+    q = W.random_compressed_q(ny, nx, nz, seed=43, decay=0.02)
+    qt = O.full_spectrum_blocks(O.embed_spectrum(q))
+    ctx = lib_context(m, [q], max_rhs=1)
+    for axis, L in ((0, 2 * nx), (1, 2 * ny)):
+        r, ms = ctx.fft_plan(axis)
+        assert int(np.prod(r)) == L and set(r) <= {2, 3, 4, 5, 8}, (axis, r)
+        assert ms > 0
+    with pytest.raises(ie.IEError):
+        ctx.set_fft_plan(0, [16, 6])  # 16 is not a radix of the kernels
+    with pytest.raises(ie.IEError):
+        ctx.set_fft_plan(1, [4, 4, 4])  # 64 != 2 Ny
+    x = W.random_field((1, 3, nz, ny, nx), 71).astype(np.complex64).astype(np.complex128)
+    ref = O.fft_apply(m, qt, x[0])
+    xd = to_dev(x)
+    s = torch.cuda.current_stream().cuda_stream
+    plans_x = [[4, 4, 2, 3], [8, 4, 3], [3, 8, 4], [2, 4, 4, 3], [3, 2, 2, 2, 2, 2]]
+    plans_y = [[4, 4, 5], [8, 2, 5], [5, 4, 4], [5, 8, 2], [2, 8, 5]]
+    for px, py in zip(plans_x, plans_y):
+        ctx.set_fft_plan(0, px)
+        ctx.set_fft_plan(1, py)
+        assert ctx.fft_plan(0)[0] == px and ctx.fft_plan(1)[0] == py
+        yd = torch.empty_like(xd)
+        ctx.matvec(0, xd.data_ptr(), yd.data_ptr(), 1, dtype=ie.IE_C128, stream=s)
+        assert rel(to_host(yd)[0], ref) <= 1e-12, (px, py)
+        x64 = xd.to(torch.complex64)
+        y64 = torch.empty_like(x64)
+        ctx.matvec(0, x64.data_ptr(), y64.data_ptr(), 1, dtype=ie.IE_C64, stream=s)
+        assert rel(to_host(y64)[0].astype(np.complex128), ref) <= 2e-5, (px, py)
     ctx.close()
