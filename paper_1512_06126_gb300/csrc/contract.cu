@@ -365,6 +365,22 @@ bool dispatch_mma_comp(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, i
   }
 }
 
+// the FP16 pairs of variant 7's A operand: hi = fp16(x 2^e), lo = fp16(x 2^e - hi), for
+// the real and the imaginary part, hi in the low half
+__global__ void split_f16_kernel(const float2 *__restrict__ qf, const int *__restrict__ qexp, uint2 *__restrict__ qh,
+                                 long long n, int BS) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float sc = tc::pow2f(qexp[i / BS]);
+    const float2 v = qf[i];
+    const float xr = v.x * sc, xi = v.y * sc;
+    const __half hr = __float2half_rn(xr), hi = __float2half_rn(xi);
+    const __half lr = __float2half_rn(__fsub_rn(xr, __half2float(hr)));
+    const __half li = __float2half_rn(__fsub_rn(xi, __half2float(hi)));
+    qh[i] = make_uint2((uint32_t)__half_as_ushort(hr) | (uint32_t)__half_as_ushort(lr) << 16,
+                       (uint32_t)__half_as_ushort(hi) | (uint32_t)__half_as_ushort(li) << 16);
+  }
+}
+
 template <int R>
 bool dispatch_mma(float2 *spec, const float2 *qf, int Nx, int Ny, int Nz, int ldz, bool unpack, int *err,
                   cudaStream_t s) {
@@ -439,7 +455,7 @@ bool contract_variant_available(int variant, int Nz, int R, bool c64) {
 
 template <typename T>
 int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant, int *err,
-                    cudaStream_t s, const int *qexp) {
+                    cudaStream_t s, const int *qexp, const void *qh) {
   if (ldz < R * 3 * Nz) return -1;
   if constexpr (sizeof(T) == 4) {
     if (!err) err = default_err();
@@ -460,9 +476,10 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, i
       if (R == 1 && dispatch_tc<1, false>(spec, qf, nullptr, Nx, Ny, Nz, ldz, err, s)) return 0;
       if (R == 2 && dispatch_tc<2, false>(spec, qf, nullptr, Nx, Ny, Nz, ldz, err, s)) return 0;
     }
-    if (variant == kContractTc16 && qexp && contract_variant_available(variant, Nz, R, true)) {
-      if (R == 1 && dispatch_tc<1, true>(spec, qf, qexp, Nx, Ny, Nz, ldz, err, s)) return 0;
-      if (R == 2 && dispatch_tc<2, true>(spec, qf, qexp, Nx, Ny, Nz, ldz, err, s)) return 0;
+    if (variant == kContractTc16 && qexp && qh && contract_variant_available(variant, Nz, R, true)) {
+      const float2 *q16 = reinterpret_cast<const float2 *>(qh);  // 8 bytes per complex, as qf
+      if (R == 1 && dispatch_tc<1, true>(spec, q16, qexp, Nx, Ny, Nz, ldz, err, s)) return 0;
+      if (R == 2 && dispatch_tc<2, true>(spec, q16, qexp, Nx, Ny, Nz, ldz, err, s)) return 0;
     }
     if ((variant == kContractTma1 || variant == kContractTma3 || variant == kContractTma1Row) &&
         contract_variant_available(variant, Nz, R, true)) {
@@ -477,9 +494,17 @@ int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, i
 }
 
 template int launch_contract<float>(float2 *, const float2 *, int, int, int, int, int, int, int *, cudaStream_t,
-                                    const int *);
+                                    const int *, const void *);
 template int launch_contract<double>(double2 *, const double2 *, int, int, int, int, int, int, int *, cudaStream_t,
-                                     const int *);
+                                     const int *, const void *);
+
+void launch_split_f16(const float2 *qf, const int *qexp, void *qh, long long nf, int Nz, cudaStream_t s) {
+  const long long n = nf * 2LL * Nz * (2 * Nz + 1);
+  const long long blocks = (n + 255) / 256;
+  count_launches(1);
+  split_f16_kernel<<<(unsigned)(blocks < 65535LL * 64 ? blocks : 65535LL * 64), 256, 0, s>>>(
+      qf, qexp, reinterpret_cast<uint2 *>(qh), n, 2 * Nz * (2 * Nz + 1));
+}
 
 void launch_block_exponents(const float2 *qf, int *qexp, long long nf, int Nz, cudaStream_t s) {
   count_launches(1);

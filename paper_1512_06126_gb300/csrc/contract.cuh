@@ -34,14 +34,19 @@ bool contract_fits(int Nz, int R, bool c64);
 // 3 Nz > 1024, ldz < R 3Nz or a launch fails (nothing is applied then).
 // err: device word in which a kernel records a wait that ran out (kContractTimeout; the
 // wavenumbers it had not reached stay uncontracted); NULL: the library's own word.
-// qexp: the per-wavenumber exponents of launch_block_exponents (variant 7 only; may be
-// NULL, which makes variant 7 fall back).
+// qexp, qh: the per-wavenumber exponents of launch_block_exponents and the FP16-split
+// blocks of launch_split_f16 (variant 7 only; either NULL makes variant 7 fall back).
 template <typename T>
 int launch_contract(C<T> *spec, const C<T> *qf, int Nx, int Ny, int Nz, int R, int ldz, int variant, int *err,
-                    cudaStream_t s, const int *qexp = nullptr);
+                    cudaStream_t s, const int *qexp = nullptr, const void *qh = nullptr);
 // qexp[w] = the exponent that scales the largest |re|, |im| of the packed c64 block of
 // folded wavenumber w into [2^13, 2^14) (nf blocks of 2 Nz (2 Nz + 1) complex).
 void launch_block_exponents(const float2 *qf, int *qexp, long long nf, int Nz, cudaStream_t s);
+// The packed c64 blocks scaled by 2^qexp[w] and split into FP16 pairs, the layout of qf
+// with 8 bytes per complex: (hi(re) | lo(re) << 16, hi(im) | lo(im) << 16), hi =
+// fp16(x 2^e), lo = fp16(x 2^e - hi) (round to nearest): the A operand of variant 7,
+// split once at set-up instead of in every product.
+void launch_split_f16(const float2 *qf, const int *qexp, void *qh, long long nf, int Nz, cudaStream_t s);
 
 // Double-float copy of packed blocks: qdf[i] = (hi, lo of re, hi, lo of im) of q64[i],
 // hi = fl32(x), lo = fl32(x - hi).

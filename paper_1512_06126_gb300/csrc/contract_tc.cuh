@@ -290,7 +290,8 @@ enum TcProf { kPWaitA = 0, kPWaitB = 1, kPWaitC = 2, kPWork = 3, kPWaitSt = 4, k
 // as in the TF32 split): the block of wavenumber w is scaled by 2^qexp[w] and column c of
 // X by 2^xe[c] (powers of two that bring the largest magnitudes into [2^13, 2^14), so
 // that FP16 keeps every entry whose size matters to the product), and the outputs are
-// scaled back exactly.
+// scaled back exactly.  With F16, qf holds the blocks already scaled and split
+// (launch_split_f16, 8 bytes per complex like the c64 blocks); the B warps split X.
 template <int NZ, int R, bool F16 = false, bool PROF = false>
 __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     contract_tc_kernel(float2 *__restrict__ spec, const float2 *__restrict__ qf, int Nx, int Ny, int ldz, int *err,
@@ -558,7 +559,6 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       const float2 *st = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE);
       ea_prev = ea_cur;
       if constexpr (F16) ea_cur = __ldg(qexp + w0 + it * gs);
-      const float ascale = F16 ? tc::pow2f(ea_cur) : 1.f;
 #pragma unroll
       for (int beta = 0; beta < 3; ++beta) {
         const int g = 3 * it + beta, c = g % NA;
@@ -572,17 +572,22 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
         const bool neg = alpha == 2 && beta < 2;
         if constexpr (F16) {
           // entries (b, b + 1) as one word: re parts at K = b (columns AHALF-relative b / 2),
-          // im parts at K = Nz + b
+          // im parts at K = Nz + b.  The stage holds the blocks already scaled and split
+          // (launch_split_f16: per complex (hi | lo << 16) of re, then of im), so a word is
+          // two halves picked from two entries; the minus of zx, zy flips the sign bits.
           constexpr int HW = EPW / 2;
           uint32_t rh[HW], ih[HW], rl[HW], il[HW];
-          const float sg = neg ? -ascale : ascale;
+          const uint2 *st2 = reinterpret_cast<const uint2 *>(st);
+          const uint32_t sgn = neg ? 0x80008000u : 0u;
 #pragma unroll
           for (int e2 = 0; e2 < HW; ++e2) {
             const uint32_t o = offp[beta][e2];
-            float2 m0 = live ? st[o & 0xFFFFu] : make_float2(0.f, 0.f);
-            float2 m1 = live ? st[o >> 16] : make_float2(0.f, 0.f);
-            tc::split_h2(m0.x * sg, m1.x * sg, rh[e2], rl[e2]);
-            tc::split_h2(m0.y * sg, m1.y * sg, ih[e2], il[e2]);
+            const uint2 m0 = live ? st2[o & 0xFFFFu] : make_uint2(0u, 0u);
+            const uint2 m1 = live ? st2[o >> 16] : make_uint2(0u, 0u);
+            rh[e2] = __byte_perm(m0.x, m1.x, 0x5410) ^ sgn;
+            rl[e2] = __byte_perm(m0.x, m1.x, 0x7632) ^ sgn;
+            ih[e2] = __byte_perm(m0.y, m1.y, 0x5410) ^ sgn;
+            il[e2] = __byte_perm(m0.y, m1.y, 0x7632) ^ sgn;
           }
           const uint32_t ab = tq + c * Cfg::ACOLS + jw * HW;
           if constexpr (HW == 4) {

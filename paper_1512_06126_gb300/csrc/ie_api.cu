@@ -42,6 +42,7 @@ struct Instance {
   float2 *q32 = nullptr;
   float4 *qdf = nullptr;           // double-float copy of q64 (residuals of the mixed solver)
   int *qexp = nullptr;             // per folded wavenumber: the scale exponent of its c64 block
+  void *qh = nullptr;              // the c64 blocks scaled and split into FP16 pairs (Nz in {16, 32})
   double2 *rtab = nullptr;         // receiver kernels [Ny][Nx][Nz][10] (after ie_set_receivers)
   double2 en{0.0, 0.0}, hn{0.0, 0.0};  // normal E^N and E^N'/(i w mu0) at the receiver depth
 };
@@ -283,6 +284,10 @@ ie_status build_spectral(ie_ctx *c, Instance &in, const double *q_host) {
   ie::launch_split_df(in.q64, in.qdf, nf * BS, c->stream);
   IE_TRY(dalloc(c, &in.qexp, nf * sizeof(int)));
   ie::launch_block_exponents(in.q32, in.qexp, nf, Nz, c->stream);
+  if (ie::contract_variant_available(ie::kContractTc16, Nz, 1, true)) {
+    IE_TRY(dalloc(c, &in.qh, nf * BS * sizeof(uint2)));
+    ie::launch_split_f16(in.q32, in.qexp, in.qh, nf, Nz, c->stream);
+  }
   return cuda_status(cudaGetLastError());
 }
 
@@ -323,7 +328,7 @@ ie_status contract_group(ie_ctx *c, const Group &g, ie::C<T> *spec, cudaStream_t
       if (df && ie::launch_contract_df(sk, c->inst[g.inst[k]].qdf, c->nx, c->ny, c->nz, g.rpi, CZ, s) == 0) continue;
     }
     if (ie::launch_contract<T>(sk, qf<T>(c->inst[g.inst[k]]), c->nx, c->ny, c->nz, g.rpi, CZ, variant, c->err, s,
-                               c->inst[g.inst[k]].qexp) != 0)
+                               c->inst[g.inst[k]].qexp, c->inst[g.inst[k]].qh) != 0)
       return IE_ERR_CUDA;
   }
   if (c->prof) {
@@ -942,7 +947,7 @@ ie_status ie_profile_matvec(ie_ctx *c, int inst, int nrhs, int dtype, int n_iter
       ie::launch_fft_axis<float, false>(t1, sp, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[2], s);
       bad |= ie::launch_contract<float>(sp, c->inst[inst].q32, Nx, Ny, Nz, nrhs, CZ, c->cvar[nrhs], c->err, s,
-                                        c->inst[inst].qexp);
+                                        c->inst[inst].qexp, c->inst[inst].qh);
       cudaEventRecord(ev[3], s);
       ie::launch_fft_axis<float, true>(sp, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
       cudaEventRecord(ev[4], s);
@@ -1035,10 +1040,13 @@ ie_status autotune_contraction(ie_ctx *c) {
     for (int v = 0; v < ie::kContractVariants && n_avail > 1; ++v) {
       if (!ie::contract_variant_available(v, Nz, rpi, true)) continue;
       const int *qe = c->inst[0].qexp;
-      bool ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream, qe) == 0;
+      const void *qh = c->inst[0].qh;
+      bool ok =
+          ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream, qe, qh) == 0;
       cudaEventRecord(e0, c->stream);
       for (int k = 0; k < 3 && ok; ++k)
-        ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream, qe) == 0;
+        ok = ie::launch_contract<float>(spec, c->inst[0].q32, Nx, Ny, Nz, rpi, CZ, v, c->err, c->stream, qe, qh) ==
+             0;
       cudaEventRecord(e1, c->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) { st = IE_ERR_CUDA; break; }
       float ms = 0.f;
