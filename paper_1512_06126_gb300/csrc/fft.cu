@@ -124,15 +124,23 @@ __global__ void __launch_bounds__(kThreads) fft_axis_kernel(const C<T> *__restri
   }
 }
 
+// a value of the vectors' type TX in the transform's arithmetic T (FP64 -> FP32 from the
+// bits, see d2f_bits)
 template <typename T, typename TX>
 __device__ __forceinline__ C<T> to_t(C<TX> v) {
-  return mk<T>((T)v.x, (T)v.y);
+  if constexpr (sizeof(T) == 4 && sizeof(TX) == 8) return to_f32(v);
+  else return mk<T>((T)v.x, (T)v.y);
+}
+template <typename TX, typename T>
+__device__ __forceinline__ C<TX> from_t(C<T> v) {
+  if constexpr (sizeof(T) == 4 && sizeof(TX) == 8) return to_prec<double>(v);
+  else return mk<TX>((TX)v.x, (TX)v.y);
 }
 
 // T: arithmetic type of the transform; TX: element type of the vectors and scales.
 template <typename T, typename TX>
 __global__ void __launch_bounds__(kThreads) fft_rows_fwd_kernel(const C<TX> *__restrict__ x,
-                                                                const C<TX> *__restrict__ in_scale,
+                                                                const C<T> *__restrict__ in_scale,
                                                                 C<T> *__restrict__ t1, int CZ, int Nz, int Ny,
                                                                 int Nx, FftPlan plan) {
   extern __shared__ unsigned char smem_raw[];
@@ -151,9 +159,8 @@ __global__ void __launch_bounds__(kThreads) fft_rows_fwd_kernel(const C<TX> *__r
     const int cz = cz0 + t;
     C<T> v = mk<T>(0, 0);
     if (cz < CZ) {
-      C<TX> u = x[((long long)cz * Ny + y) * Nx + xx];
-      if (in_scale) u = cmul(u, in_scale[((long long)(cz % Nz) * Ny + y) * Nx + xx]);
-      v = to_t<T, TX>(u);
+      v = to_t<T, TX>(x[((long long)cz * Ny + y) * Nx + xx]);
+      if (in_scale) v = cmul(v, in_scale[((long long)(cz % Nz) * Ny + y) * Nx + xx]);
     }
     A[xx * LD + t] = v;
   }
@@ -172,8 +179,8 @@ __global__ void __launch_bounds__(kThreads) fft_rows_fwd_kernel(const C<TX> *__r
 template <typename T, typename TX>
 __global__ void __launch_bounds__(kThreads) fft_rows_inv_kernel(const C<T> *__restrict__ t1,
                                                                 const C<TX> *__restrict__ x,
-                                                                const C<TX> *__restrict__ diag,
-                                                                const C<TX> *__restrict__ out_scale,
+                                                                const C<T> *__restrict__ diag,
+                                                                const C<T> *__restrict__ out_scale,
                                                                 C<TX> *__restrict__ y_out, int CZ, int Nz, int Ny,
                                                                 int Nx, FftPlan plan) {
   extern __shared__ unsigned char smem_raw[];
@@ -201,10 +208,9 @@ __global__ void __launch_bounds__(kThreads) fft_rows_inv_kernel(const C<T> *__re
     if (cz < CZ) {
       const long long cell = ((long long)(cz % Nz) * Ny + y) * Nx + xx;
       const long long gi = ((long long)cz * Ny + y) * Nx + xx;
-      const C<T> r = res[xx * LD + t];
-      C<TX> v = cmul(mk<TX>((TX)r.x, (TX)r.y), out_scale[cell]);
-      if (diag) cfma(v, diag[cell], x[gi]);
-      y_out[gi] = v;
+      C<T> v = cmul(res[xx * LD + t], out_scale[cell]);
+      if (diag) cfma(v, diag[cell], to_t<T, TX>(x[gi]));
+      y_out[gi] = from_t<TX, T>(v);
     }
   }
 }
@@ -240,7 +246,7 @@ void axis_fast(const float2 *in, float2 *out, int outer, int Lin, int Lout, long
 }
 
 template <int Q, typename TX>
-void rows_fwd_fast(const C<TX> *x, const C<TX> *in_scale, float2 *t1, int CZ, int Nz, int Ny, int Nx,
+void rows_fwd_fast(const C<TX> *x, const float2 *in_scale, float2 *t1, int CZ, int Nz, int Ny, int Nx,
                    cudaStream_t s) {
   auto k = fftfast::rows_fwd_kernel<Q, TX>;
   set_smem(k, fftfast::smem_bytes(Q));
@@ -249,7 +255,7 @@ void rows_fwd_fast(const C<TX> *x, const C<TX> *in_scale, float2 *t1, int CZ, in
 }
 
 template <int Q, typename TX>
-void rows_inv_fast(const float2 *t1, const C<TX> *x, const C<TX> *diag, const C<TX> *out_scale, C<TX> *y, int CZ,
+void rows_inv_fast(const float2 *t1, const C<TX> *x, const float2 *diag, const float2 *out_scale, C<TX> *y, int CZ,
                    int Nz, int Ny, int Nx, cudaStream_t s) {
   auto k = fftfast::rows_inv_kernel<Q, TX>;
   set_smem(k, fftfast::smem_bytes(Q));
@@ -282,7 +288,7 @@ void launch_fft_axis(const C<T> *in, C<T> *out, int outer, int Lin, int Lout, lo
 }
 
 template <typename T, typename TX>
-void launch_fft_rows_fwd(const C<TX> *x, const C<TX> *in_scale, C<T> *t1, int CZ, int Nz, int Ny, int Nx,
+void launch_fft_rows_fwd(const C<TX> *x, const C<T> *in_scale, C<T> *t1, int CZ, int Nz, int Ny, int Nx,
                          const FftPlan &plan, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
     const int q = fast_q(plan.L);
@@ -304,7 +310,7 @@ void launch_fft_rows_fwd(const C<TX> *x, const C<TX> *in_scale, C<T> *t1, int CZ
 }
 
 template <typename T, typename TX>
-void launch_fft_rows_inv(const C<T> *t1, const C<TX> *x, const C<TX> *diag, const C<TX> *out_scale, C<TX> *y,
+void launch_fft_rows_inv(const C<T> *t1, const C<TX> *x, const C<T> *diag, const C<T> *out_scale, C<TX> *y,
                          int CZ, int Nz, int Ny, int Nx, const FftPlan &plan, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
     const int q = fast_q(plan.L);
@@ -337,14 +343,14 @@ template void launch_fft_rows_fwd<float, float>(const float2 *, const float2 *, 
                                                 const FftPlan &, cudaStream_t);
 template void launch_fft_rows_fwd<double, double>(const double2 *, const double2 *, double2 *, int, int, int, int,
                                                   const FftPlan &, cudaStream_t);
-template void launch_fft_rows_fwd<float, double>(const double2 *, const double2 *, float2 *, int, int, int, int,
+template void launch_fft_rows_fwd<float, double>(const double2 *, const float2 *, float2 *, int, int, int, int,
                                                  const FftPlan &, cudaStream_t);
 template void launch_fft_rows_inv<float, float>(const float2 *, const float2 *, const float2 *, const float2 *,
                                                 float2 *, int, int, int, int, const FftPlan &, cudaStream_t);
 template void launch_fft_rows_inv<double, double>(const double2 *, const double2 *, const double2 *,
                                                   const double2 *, double2 *, int, int, int, int, const FftPlan &,
                                                   cudaStream_t);
-template void launch_fft_rows_inv<float, double>(const float2 *, const double2 *, const double2 *, const double2 *,
+template void launch_fft_rows_inv<float, double>(const float2 *, const double2 *, const float2 *, const float2 *,
                                                  double2 *, int, int, int, int, const FftPlan &, cudaStream_t);
 
 }  // namespace ie

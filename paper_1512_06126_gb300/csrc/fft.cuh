@@ -174,17 +174,17 @@ void launch_fft_axis(const C<T> *in, C<T> *out, int outer, int Lin, int Lout, lo
 
 // Forward row pass: x[CZ][Ny][Nx] times in_scale[Nz][Ny][Nx] (cz -> z = cz % Nz), zero-padded
 // to 2Nx and transformed along x -> T1[Ny][2Nx][CZ].
-// T: arithmetic of the transform; TX: element type of x and in_scale (TX = double with
-// T = float reads FP64 vectors and rounds the scaled values to FP32 on load).
+// T: arithmetic of the transform and of the scales; TX: element type of x (TX = double
+// with T = float: FP64 vectors rounded to FP32 on load, then scaled in FP32).
 template <typename T, typename TX = T>
-void launch_fft_rows_fwd(const C<TX> *x, const C<TX> *in_scale, C<T> *t1, int CZ, int Nz, int Ny, int Nx,
+void launch_fft_rows_fwd(const C<TX> *x, const C<T> *in_scale, C<T> *t1, int CZ, int Nz, int Ny, int Nx,
                          const FftPlan &plan, cudaStream_t s);
 
 // Inverse row pass: T1[Ny][2Nx][CZ] -> inverse along kx, keep x < Nx, and write
-// y[CZ][Ny][Nx] = diag[cell] * x[CZ][cell] + out_scale[cell] * value.
-// (TX = double with T = float: the diagonal term and the output are FP64.)
+// y[CZ][Ny][Nx] = diag[cell] * x[CZ][cell] + out_scale[cell] * value, in the arithmetic of
+// T (TX = double with T = float: x rounded to FP32, the result stored as FP64).
 template <typename T, typename TX = T>
-void launch_fft_rows_inv(const C<T> *t1, const C<TX> *x, const C<TX> *diag, const C<TX> *out_scale, C<TX> *y,
+void launch_fft_rows_inv(const C<T> *t1, const C<TX> *x, const C<T> *diag, const C<T> *out_scale, C<TX> *y,
                          int CZ, int Nz, int Ny, int Nx, const FftPlan &plan, cudaStream_t s);
 
 }  // namespace ie

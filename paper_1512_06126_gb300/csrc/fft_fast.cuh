@@ -144,11 +144,6 @@ __device__ __forceinline__ void step2(float2 (&w)[Q], const float2 *tw, const fl
   }
 }
 
-template <typename TX>
-__device__ __forceinline__ float2 to_f(typename cplx<TX>::type u) {
-  return make_float2((float)u.x, (float)u.y);
-}
-
 // Transform along the middle axis of in[outer][Lin][inner] (rows >= Lin are zero) ->
 // out[outer][Lout][inner] (rows >= Lout dropped), times scale.
 template <int Q, bool INV>
@@ -189,7 +184,7 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) axis_kernel(const floa
 // transformed along x -> T1[Ny][L][CZ].
 template <int Q, typename TX>
 __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_fwd_kernel(
-    const typename cplx<TX>::type *__restrict__ x, const typename cplx<TX>::type *__restrict__ in_scale,
+    const typename cplx<TX>::type *__restrict__ x, const float2 *__restrict__ in_scale,
     float2 *__restrict__ t1, int CZ, int Nz, int Ny, int Nx) {
   constexpr int L = 16 * Q;
   constexpr int LD = kTI + 1;
@@ -210,9 +205,8 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_fwd_kernel(
       const int cz = cz0 + tt;
       float2 v = make_float2(0.f, 0.f);
       if (cz < CZ) {
-        typename cplx<TX>::type u = x[((long long)cz * Ny + y) * NXC + xx];
-        if (in_scale) u = cmul(u, in_scale[((long long)(cz % Nz) * Ny + y) * NXC + xx]);
-        v = to_f<TX>(u);
+        v = to_f32(x[((long long)cz * Ny + y) * NXC + xx]);
+        if (in_scale) v = cmul(v, in_scale[((long long)(cz % Nz) * Ny + y) * NXC + xx]);
       }
       Y[xx * LD + tt] = v;
     }
@@ -244,9 +238,8 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_fwd_kernel(
 template <int Q, typename TX>
 __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_inv_kernel(
     const float2 *__restrict__ t1, const typename cplx<TX>::type *__restrict__ x,
-    const typename cplx<TX>::type *__restrict__ diag, const typename cplx<TX>::type *__restrict__ out_scale,
+    const float2 *__restrict__ diag, const float2 *__restrict__ out_scale,
     typename cplx<TX>::type *__restrict__ y_out, int CZ, int Nz, int Ny, int Nx) {
-  using V = typename cplx<TX>::type;
   constexpr int L = 16 * Q;
   constexpr int LD = kTI + 1;
   extern __shared__ float2 smf[];
@@ -285,10 +278,9 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_inv_kernel(
     if (e < NXC * kTI && cz < CZ) {
       const long long cell = ((long long)(cz % Nz) * Ny + y) * NXC + xx;
       const long long gi = ((long long)cz * Ny + y) * NXC + xx;
-      const float2 r = Y[xx * LD + tt];
-      V val = cmul(mk<TX>((TX)r.x, (TX)r.y), out_scale[cell]);
-      if (diag) cfma(val, diag[cell], x[gi]);
-      y_out[gi] = val;
+      float2 val = cmul(Y[xx * LD + tt], out_scale[cell]);
+      if (diag) cfma(val, diag[cell], to_f32(x[gi]));
+      y_out[gi] = to_prec<TX>(val);
     }
   }
 }

@@ -359,22 +359,22 @@ ie_status apply(ie_ctx *c, const Group &g, const ie::C<T> *x, ie::C<T> *y, int t
   return cuda_status(cudaGetLastError());
 }
 
-// c64 product on FP64 vectors (the inner solves of IE_MIXED_FP64K): the row passes
-// read and write FP64 (rounding the scaled input to FP32 on load; the diagonal term and
-// the output in FP64), the FFTs and the contraction run in FP32.
+// c64 product on FP64 vectors (the inner solves of IE_MIXED_FP64K): the c64 operator
+// applied in FP32 arithmetic throughout (the FP32 scales), the row passes reading the
+// FP64 vector (rounded to FP32 on load) and writing the FP64 result.
 ie_status apply_mixed(ie_ctx *c, const Group &g, const double2 *x, double2 *y, int transpose, cudaStream_t s) {
   const int Nx = c->nx, Ny = c->ny, Nz = c->nz;
   const int CZ = g.R() * 3 * Nz;
-  const DiagSet &D = c->d64;
-  const double2 *in_s = (const double2 *)(transpose ? D.in_t : D.in_f);
-  const double2 *out_s = (const double2 *)(transpose ? D.out_t : D.out_f);
+  const DiagSet &D = c->d32;
+  const float2 *in_s = (const float2 *)(transpose ? D.in_t : D.in_f);
+  const float2 *out_s = (const float2 *)(transpose ? D.out_t : D.out_f);
   float2 *t1 = (float2 *)c->t1;
   float2 *spec = (float2 *)c->spec;
   ie::launch_fft_rows_fwd<float, double>(x, in_s, t1, CZ, Nz, Ny, Nx, c->px, s);
   ie::launch_fft_axis<float, false>(t1, spec, 1, Ny, 2 * Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
   IE_TRY(contract_group<float>(c, g, spec, s));
   ie::launch_fft_axis<float, true>(spec, t1, 1, 2 * Ny, Ny, 2LL * Nx * CZ, c->py, 1.0f, s);
-  ie::launch_fft_rows_inv<float, double>(t1, x, (const double2 *)D.diag, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
+  ie::launch_fft_rows_inv<float, double>(t1, x, (const float2 *)D.diag, out_s, y, CZ, Nz, Ny, Nx, c->px, s);
   return cuda_status(cudaGetLastError());
 }
 
