@@ -13,6 +13,8 @@
 // DFTs are radix-2 decimation in time, the input permutation resolved at compile time
 // by loading the inputs permuted; their twiddles and the w_L^(q k1) come from one table w_L^m per CTA.
 #pragma once
+#include <utility>
+
 #include "ie_common.cuh"
 
 namespace ie {
@@ -34,30 +36,60 @@ __host__ __device__ constexpr int bitrev(int i) {
   return r;
 }
 
-// In-register DFT of length N (power of two): the input in bit-reversed order
+// cos(2 pi j / 32) for j = 0 .. 8
+__device__ __forceinline__ constexpr float cos32(int j) {
+  return j == 0 ? 1.0f
+       : j == 1 ? 0.98078528040323044913f
+       : j == 2 ? 0.92387953251128675613f
+       : j == 3 ? 0.83146961230254523708f
+       : j == 4 ? 0.70710678118654752440f
+       : j == 5 ? 0.55557023301960222474f
+       : j == 6 ? 0.38268343236508977173f
+       : j == 7 ? 0.19509032201612826785f
+                : 0.0f;
+}
+// v times w_32^J (forward sign) or its conjugate, J a compile-time constant: the
+// twiddles of the in-register DFTs (w_N^j = w_32^(32 j / N) for N <= 32), so that no
+// table is read, the trivial factors (1, -+i) cost no multiplication and the others
+// two multiplications and two fused multiply-adds with immediate operands
+template <int J, bool INV>
+__device__ __forceinline__ float2 twiddle32(float2 v) {
+  static_assert(J >= 0 && J < 16, "half a turn at most");
+  if constexpr (J == 0) {
+    return v;
+  } else if constexpr (J == 8) {  // -i (forward), +i (inverse)
+    return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+  } else {
+    // w = c - i s (forward): c = cos(2 pi J / 32), s = sin(2 pi J / 32)
+    constexpr float c = J < 8 ? cos32(J) : -cos32(16 - J);
+    constexpr float sn = J < 8 ? cos32(8 - J) : cos32(J - 8);
+    constexpr float s = INV ? -sn : sn;
+    return make_float2(fmaf(v.x, c, v.y * s), fmaf(v.y, c, -(v.x * s)));
+  }
+}
+
+// In-register DFT of length N (power of two, N <= 32): the input in bit-reversed order
 // (b[bitrev(i)] = x[i], so callers load it permuted at compile time), the output in
-// natural order, in place.  tw[m] = w_L^m (forward sign), stride = L / N so that
-// w_N^j = tw[j * stride].
+// natural order, in place.  The twiddles are compile-time constants (twiddle32).
 // One butterfly stage of span LEN, then the next (one template instance per stage, so
 // every register index is a compile-time constant).
 template <int N, int LEN, bool INV>
 struct BrStage {
+  template <int J>
+  static __device__ __forceinline__ void bfly(float2 (&b)[N], int i) {
+    const float2 u = b[i + J];
+    const float2 v = twiddle32<J * (32 / LEN), INV>(b[i + J + LEN / 2]);
+    b[i + J] = make_float2(u.x + v.x, u.y + v.y);
+    b[i + J + LEN / 2] = make_float2(u.x - v.x, u.y - v.y);
+  }
+  template <int... J>
+  static __device__ __forceinline__ void group(float2 (&b)[N], int i, std::integer_sequence<int, J...>) {
+    (bfly<J>(b, i), ...);
+  }
   static __device__ __forceinline__ void run(float2 (&b)[N], const float2 *tw, int stride) {
+    static_assert(N <= 32 && LEN <= N, "twiddles from w_32");
 #pragma unroll
-    for (int i = 0; i < N; i += LEN) {
-#pragma unroll
-      for (int j = 0; j < LEN / 2; ++j) {
-        const float2 u = b[i + j];
-        float2 v = b[i + j + LEN / 2];
-        if (j != 0) {
-          float2 w = tw[j * (N / LEN) * stride];
-          if (INV) w.y = -w.y;
-          v = fmul(v, w);
-        }
-        b[i + j] = make_float2(u.x + v.x, u.y + v.y);
-        b[i + j + LEN / 2] = make_float2(u.x - v.x, u.y - v.y);
-      }
-    }
+    for (int i = 0; i < N; i += LEN) group(b, i, std::make_integer_sequence<int, LEN / 2>{});
     BrStage<N, 2 * LEN, INV>::run(b, tw, stride);
   }
 };
