@@ -395,12 +395,16 @@ __global__ void __launch_bounds__(kT) cgs_hsum_kernel(const double2 *__restrict_
 // (the grid is co-resident), which returns at once when no flag is set:
 //   h2 = V^H w' (dot units), w'' = w' - V h2, nrm = ||w''||, vnext = w'' / nrm.
 // The per-block norm partials go to npart[r * gridDim.x + block] (gridDim.x <= 1024).
+// the split copy of one basis entry (defined with the double-float helpers below)
+__device__ __forceinline__ float4 dsplit4(double2 v);
+
 template <typename T>
 __global__ void __launch_bounds__(kT) cgs_second_kernel(const C<T> *__restrict__ V, C<T> *__restrict__ w,
                                                         C<T> *__restrict__ vnext, double2 *__restrict__ h2,
                                                         double2 *__restrict__ part, double *__restrict__ npart,
                                                         double *__restrict__ nrm, const int *__restrict__ flag,
-                                                        int k1, int R, long long n, int ldh, int nch) {
+                                                        int k1, int R, long long n, int ldh, int nch,
+                                                        float4 *__restrict__ vsnext) {
   int any = 0;
   for (int r = 0; r < R; ++r) any |= flag[r];
   if (!any) return;  // the same decision in every block: no block reaches a grid barrier
@@ -475,7 +479,11 @@ __global__ void __launch_bounds__(kT) cgs_second_kernel(const C<T> *__restrict__
     const T sc = (T)(nr > 0.0 ? 1.0 / nr : 0.0);
     for (long long e = (long long)blockIdx.x * kT + tid; e < n; e += (long long)gridDim.x * kT) {
       const C<T> v = w[(long long)r * n + e];
-      vnext[(long long)r * n + e] = mk<T>(v.x * sc, v.y * sc);
+      const C<T> vs = mk<T>(v.x * sc, v.y * sc);
+      vnext[(long long)r * n + e] = vs;
+      if constexpr (sizeof(T) == 8) {
+        if (vsnext) vsnext[(long long)r * n + e] = dsplit4(vs);
+      }
     }
   }
 }
@@ -519,6 +527,15 @@ __device__ __forceinline__ void dsplit(double x, float &hi, float &lo) {
   l = (small || big) ? 0.0f : l;
   hi = __uint_as_float(h);
   lo = l;
+}
+
+// (re hi, re lo, im hi, im lo) of a complex FP64 value: its entry in the split copy of
+// the Krylov basis that the double-float passes read
+__device__ __forceinline__ float4 dsplit4(double2 v) {
+  float4 q;
+  dsplit(v.x, q.x, q.y);
+  dsplit(v.y, q.z, q.w);
+  return q;
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -589,7 +606,7 @@ constexpr int kDfCh = kT * kDfEPT;  // elements per chunk
 
 // part(r, i, c) = sum_chunk conj(V_i) x and npart(r, c) = sum_chunk |x|^2, chunk c of
 // kDfCh elements; grid (nbs, R), each block the same number of chunks
-__global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const double2 *__restrict__ V, const double2 *__restrict__ x,
+__global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const float4 *__restrict__ Vs, const double2 *__restrict__ x,
                                                         double2 *__restrict__ part, double *__restrict__ npart, int k1,
                                                         int R, long long n, int nbs, int nch) {
   constexpr int EPT = kDfEPT;
@@ -612,28 +629,27 @@ __global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const double2 *__restric
     }
     df_warp_sum(nn);
     if (lane == 0) red[wid][64] = make_double2(df_value(nn), 0.0);
-    double2 vn[EPT];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 vn[EPT];
     {
-      const double2 *v0 = V + (long long)r * n + c0 + tid;
+      const float4 *v0 = Vs + (long long)r * n + c0 + tid;
 #pragma unroll
-      for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v0 + j * kT) : z2;
+      for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v0 + j * kT) : z4;
     }
 #pragma unroll 1
     for (int i = 0; i < k1; ++i) {
-      double2 vc[EPT];
+      float4 vc[EPT];
 #pragma unroll
       for (int j = 0; j < EPT; ++j) vc[j] = vn[j];
       if (i + 1 < k1) {
-        const double2 *v1 = V + ((long long)(i + 1) * R + r) * n + c0 + tid;
+        const float4 *v1 = Vs + ((long long)(i + 1) * R + r) * n + c0 + tid;
 #pragma unroll
-        for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v1 + j * kT) : z2;
+        for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v1 + j * kT) : z4;
       }
       Df are = {0.f, 0.f}, aim = {0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
-        float vrh, vrl, vih, vil;
-        dsplit(vc[j].x, vrh, vrl);
-        dsplit(vc[j].y, vih, vil);
+        const float vrh = vc[j].x, vrl = vc[j].y, vih = vc[j].z, vil = vc[j].w;
         // conj(v) x = (vr xr + vi xi) + i (vr xi - vi xr)
         df_fma(are, vrh, vrl, xs[j][0], xs[j][1]);
         df_fma(are, vih, vil, xs[j][2], xs[j][3]);
@@ -662,10 +678,11 @@ __global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const double2 *__restric
 
 // x[r] -= sum_{i<k1} h[r * ldh + i] V_i[r] in double-float; otherwise as cgs_sub_kernel
 // (vout, nrm, oflag: the normalised next basis vector where no second projection runs)
-__global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restrict__ V, double2 *__restrict__ x,
+__global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const float4 *__restrict__ Vs, double2 *__restrict__ x,
                                                         const double2 *__restrict__ h, double *__restrict__ npart,
                                                         int k1, int R, long long n, int nbs, int ldh,
-                                                        double2 *__restrict__ vout, const double *__restrict__ nrm,
+                                                        double2 *__restrict__ vout, float4 *__restrict__ vsout,
+                                                        const double *__restrict__ nrm,
                                                         const int *__restrict__ oflag) {
   constexpr int EPT = kDfEPT;
   __shared__ float4 hs[64];  // -h split: (-hr hi, -hr lo, -hi hi, -hi lo)
@@ -696,28 +713,27 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restric
       dsplit(v.x, ar[j].s, ar[j].c);
       dsplit(v.y, ai[j].s, ai[j].c);
     }
-    double2 vn[EPT];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 vn[EPT];
     {
-      const double2 *v0 = V + (long long)r * n + c0 + tid;
+      const float4 *v0 = Vs + (long long)r * n + c0 + tid;
 #pragma unroll
-      for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v0 + j * kT) : make_double2(0.0, 0.0);
+      for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v0 + j * kT) : z4;
     }
 #pragma unroll 1
     for (int i = 0; i < k1; ++i) {
       const float4 hv = hs[i];  // -h
-      double2 vc[EPT];
+      float4 vc[EPT];
 #pragma unroll
       for (int j = 0; j < EPT; ++j) vc[j] = vn[j];
       if (i + 1 < k1) {
-        const double2 *v1 = V + ((long long)(i + 1) * R + r) * n + c0 + tid;
+        const float4 *v1 = Vs + ((long long)(i + 1) * R + r) * n + c0 + tid;
 #pragma unroll
-        for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v1 + j * kT) : make_double2(0.0, 0.0);
+        for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v1 + j * kT) : z4;
       }
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
-        float vrh, vrl, vih, vil;
-        dsplit(vc[j].x, vrh, vrl);
-        dsplit(vc[j].y, vih, vil);
+        const float vrh = vc[j].x, vrl = vc[j].y, vih = vc[j].z, vil = vc[j].w;
         // x += (-h) v: re += (-hr) vr - (-hi) vi, im += (-hr) vi + (-hi) vr
         df_fma(ar[j], hv.x, hv.y, vrh, vrl);
         df_fma(ar[j], -hv.z, -hv.w, vih, vil);
@@ -730,7 +746,9 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restric
       const long long e = c0 + j * kT + tid;
       if (e < n) {
         if (scaled) {
-          vr[e] = make_double2(df_value(df_mul(ar[j], sch, scl)), df_value(df_mul(ai[j], sch, scl)));
+          const double2 v = make_double2(df_value(df_mul(ar[j], sch, scl)), df_value(df_mul(ai[j], sch, scl)));
+          vr[e] = v;
+          if (vsout) vsout[(long long)r * n + e] = dsplit4(v);
         } else {
           xr[e] = make_double2(df_value(ar[j]), df_value(ai[j]));
           df_fma(nacc, ar[j].s, ar[j].c, ar[j].s, ar[j].c);
@@ -742,6 +760,13 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const double2 *__restric
   if (scaled) return;
   const double2 sres = block_reduce(make_double2(df_value(nacc), 0.0), shn);
   if (tid == 0) npart[(long long)r * nbs + blockIdx.x] = sres.x;
+}
+
+// vs = the split copy of v (dsplit4 of every entry)
+__global__ void __launch_bounds__(kT) split_vec_kernel(const double2 *__restrict__ v, float4 *__restrict__ vs,
+                                                       long long n) {
+  for (long long e = blockIdx.x * (long long)kT + threadIdx.x; e < n; e += (long long)gridDim.x * kT)
+    vs[e] = dsplit4(v[e]);
 }
 
 // chunks of the dot pass per right-hand side
@@ -855,9 +880,10 @@ template <typename T> int second_blocks() {
 
 template <typename T>
 int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double2 *h2, double2 *part, double *npart,
-                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s, bool df) {
+                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s, bool df,
+                        const float4 *Vs, float4 *vs_next) {
   if (k1 < 1 || k1 > 64 || R < 1 || R > 16) return -1;
-  df = df && sizeof(T) == 8;
+  df = df && sizeof(T) == 8 && Vs && vs_next;
   const int nch = cgs_nch<T>(n), nbs = cgs_nbs<T>(n, R);
   // the double-float dot pass uses shorter chunks (more of them: gs_partial_blocks
   // allows the count of the c64 chunking, the largest); np1 starts past either
@@ -871,7 +897,7 @@ int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double
     if (df) {
       nch_used = (int)((n + kDfCh - 1) / kDfCh);
       const int nbd = df_blocks(n, R);
-      cgs_dot_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(V, w, part, np0, k1, R, n, nbd, nch_used);
+      cgs_dot_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(Vs, w, part, np0, k1, R, n, nbd, nch_used);
     }
   }
   if (!df) {
@@ -883,7 +909,7 @@ int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double
   if constexpr (sizeof(T) == 8) {
     if (df) {
       const int nbd = df_blocks(n, R);
-      cgs_sub_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(V, w, h1, np1, k1, R, n, nbd, ldh, vnext, nrm, flag);
+      cgs_sub_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(Vs, w, h1, np1, k1, R, n, nbd, ldh, vnext, vs_next, nrm, flag);
     }
   }
   if (!df) cgs_sub_kernel<T><<<dim3(nbs, R), kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nbs, ldh, vnext, nrm, flag);
@@ -895,7 +921,8 @@ int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double
   const int *fa = flag;
   int k1a = k1, Ra = R, ldha = ldh, ncha = nch;
   long long na = n;
-  void *args[] = {&Va, &wa, &va, &h2a, &pa, &npa, &nrma, &fa, &k1a, &Ra, &na, &ldha, &ncha};
+  float4 *vsa = df ? vs_next : nullptr;
+  void *args[] = {&Va, &wa, &va, &h2a, &pa, &npa, &nrma, &fa, &k1a, &Ra, &na, &ldha, &ncha, &vsa};
   if (cudaLaunchCooperativeKernel((const void *)cgs_second_kernel<T>, dim3(second_blocks<T>()), dim3(kT), args, 0, s) !=
       cudaSuccess)
     return -1;
@@ -1082,6 +1109,11 @@ void givens_solve(const GivensState &st, double2 *yd, int R, int m, int ldh, cud
   backsub_kernel<<<1, 32, 0, s>>>(st, yd, R, m, ldh);
 }
 
+void gmres_split(const double2 *v, float4 *vs, long long n, cudaStream_t s) {
+  count_launches(1);
+  split_vec_kernel<<<blocks_for(n), kT, 0, s>>>(v, vs, n);
+}
+
 template <typename T>
 void gmres_scale(const C<T> *src, C<T> *dst, const double *nrm, int R, long long n, cudaStream_t s) {
   count_launches(1);
@@ -1110,7 +1142,8 @@ void vec_round(const double2 *x, float2 *y, long long n, cudaStream_t s) {
                                cudaStream_t);                                                                       \
   template void gmres_norm<T>(const C<T> *, double *, double *, int, long long, cudaStream_t);                      \
   template int gmres_orthogonalize<T>(const C<T> *, C<T> *, C<T> *, double2 *, double2 *, double2 *, double *,      \
-                                      double *, int *, int, int, long long, int, cudaStream_t, bool);               \
+                                      double *, int *, int, int, long long, int, cudaStream_t, bool, const float4 *, \
+                                      float4 *);                                                                   \
   template void gmres_scale<T>(const C<T> *, C<T> *, const double *, int, long long, cudaStream_t);                 \
   template void vec_sub<T>(const C<T> *, const C<T> *, C<T> *, long long, cudaStream_t);                           \
   template void vec_add<T>(const C<T> *, double2 *, long long, cudaStream_t);

@@ -24,13 +24,20 @@ void gmres_norm(const C<T> *w, double *part, double *out, int R, long long n, cu
 // + R * 1024 doubles; nrm: 2 R doubles; flag: 48 ints, zero before the first call (flags
 // [0, R): 1 where the second projection ran; [16, 16 + R): reduction tickets, left zero;
 // [32]: incremented by every second projection).
-// df (FP64 vectors only): the dot and subtract passes of the first projection in
-// double-float arithmetic on the FP32 pipe (about 2^-46 relative to the sums of
-// magnitudes; the second projection, the norms and all cross-thread sums stay FP64).
+// df (FP64 vectors only, with Vs and vs_next): the dot and subtract passes of the first
+// projection in double-float arithmetic on the FP32 pipe (about 2^-46 relative to the
+// sums of magnitudes; the second projection, the norms and all cross-thread sums stay
+// FP64).  They read the basis from its split copy Vs (same layout as V, one float4 per
+// complex entry: gmres_split of it, so the same numbers the FP64 basis would give when
+// split on the fly) and write the split copy of vnext to vs_next.
 // Returns -1 (nothing launched) for arguments out of range or a failed launch.
 template <typename T>
 int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double2 *h2, double2 *part, double *npart,
-                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s, bool df = false);
+                        double *nrm, int *flag, int k1, int R, long long n, int ldh, cudaStream_t s, bool df = false,
+                        const float4 *Vs = nullptr, float4 *vs_next = nullptr);
+// vs[e] = (re hi, re lo, im hi, im lo) of v[e] (hi: the leading 24 significant bits, lo
+// the next 23), the split copy of a basis vector for the double-float passes
+void gmres_split(const double2 *v, float4 *vs, long long n, cudaStream_t s);
 int gs_partial_blocks(long long n);
 
 // GMRES least-squares state on the device, per right-hand side r (m < 64):

@@ -80,6 +80,7 @@ struct ie_ctx {
                                                // slot 5: the contraction error word
   int *err = nullptr;                          // device: contraction error word of this context's launches
   bool gs_df = true;                           // IE_MIXED_FP64K inner Gram-Schmidt in double-float arithmetic
+  float4 *Vs = nullptr;                        // split copy of the FP64 basis [restart + 1][R][3N] (gs_df)
   cudaEvent_t pin_ev[4] = {};
   void *jfac = nullptr, *gdiv = nullptr;       // per cell: 2 s gamma; (dgamma/dln sigma_a) / gamma (0 off the anomaly)
   void *efac = nullptr;                        // per cell: 1 / a = 2 s / (sigma_a + conj sigma_b) (E = U / a)
@@ -522,6 +523,9 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
     have_res = false;
     ie::gmres_norm<T>(w, c->nrmpart, c->nrm, R, n, s);
     ie::gmres_scale<T>(w, Vb, c->nrm, R, n, s);
+    if constexpr (sizeof(T) == 8) {
+      if (single && c->gs_df) ie::gmres_split((const double2 *)Vb, c->Vs, nR, s);
+    }
     ie::givens_init(st, c->nrm, R, ldh, s);
     IE_CUDA(cudaMemcpyAsync(c->pin_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (compact) IE_CUDA(cudaMemcpyAsync(act.data(), st.active, R * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -586,7 +590,8 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
       sp_op.end();
       ProfSpan sp_gs(c, sizeof(T) == 4 ? IE_PROF_GS_C64 : IE_PROF_GS_C128);
       if (ie::gmres_orthogonalize<T>(Vb, w, Vb + (long long)(k + 1) * nR, h1, h2, c->part, c->nrmpart, c->nrm,
-                                  c->gsflag, k + 1, R, n, ldh, s, single && c->gs_df) != 0)
+                                  c->gsflag, k + 1, R, n, ldh, s, single && c->gs_df, c->Vs,
+                                  c->Vs + (long long)(k + 1) * nR) != 0)
         return IE_ERR_ARG;
       sp_gs.end();
       ProfSpan sp_gv(c, IE_PROF_GIVENS);
@@ -1124,6 +1129,8 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
   IE_TRY(dalloc(c, &c->w, nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->r, nv * sizeof(double2)));
   IE_TRY(dalloc(c, &c->dx, nv * sizeof(double2)));  // correction of IE_MIXED_FP64K inner solves
+  // the split copy of the FP64 Krylov basis read by the double-float Gram-Schmidt passes
+  IE_TRY(dalloc(c, &c->Vs, (size_t)(c->restart + 1) * nv * sizeof(float4)));
   if (c->restart > 63) return IE_ERR_ARG;
   const long long nbp = std::max<long long>(ie::mdot_nb(c->nvec()), ie::gs_partial_blocks(c->nvec()));
   IE_TRY(dalloc(c, &c->part, (size_t)max_rhs * (c->restart + 1) * nbp * sizeof(double2)));
