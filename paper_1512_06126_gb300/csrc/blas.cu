@@ -676,14 +676,15 @@ __global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const float4 *__restrict
   }
 }
 
-// x[r] -= sum_{i<k1} h[r * ldh + i] V_i[r] in double-float; otherwise as cgs_sub_kernel
-// (vout, nrm, oflag: the normalised next basis vector where no second projection runs)
+// x[r] -= sum_{i<k1} h[r * ldh + i] V_i[r] in double-float (neg = 0: x += ...); otherwise
+// as cgs_sub_kernel (vout, nrm, oflag: the normalised next basis vector where no second
+// projection runs; npart may be NULL when no norm is wanted)
 __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const float4 *__restrict__ Vs, double2 *__restrict__ x,
                                                         const double2 *__restrict__ h, double *__restrict__ npart,
                                                         int k1, int R, long long n, int nbs, int ldh,
                                                         double2 *__restrict__ vout, float4 *__restrict__ vsout,
                                                         const double *__restrict__ nrm,
-                                                        const int *__restrict__ oflag) {
+                                                        const int *__restrict__ oflag, int neg) {
   constexpr int EPT = kDfEPT;
   __shared__ float4 hs[64];  // -h split: (-hr hi, -hr lo, -hi hi, -hi lo)
   __shared__ double2 shn[kT / 32];
@@ -693,8 +694,8 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const float4 *__restrict
   if (tid < k1) {
     const double2 hv = h[(long long)r * ldh + tid];
     float a, b, c, d;
-    dsplit(-hv.x, a, b);
-    dsplit(-hv.y, c, d);
+    dsplit(neg ? -hv.x : hv.x, a, b);
+    dsplit(neg ? -hv.y : hv.y, c, d);
     hs[tid] = make_float4(a, b, c, d);
   }
   __syncthreads();
@@ -757,7 +758,7 @@ __global__ void __launch_bounds__(kT) cgs_sub_df_kernel(const float4 *__restrict
       }
     }
   }
-  if (scaled) return;
+  if (scaled || !npart) return;
   const double2 sres = block_reduce(make_double2(df_value(nacc), 0.0), shn);
   if (tid == 0) npart[(long long)r * nbs + blockIdx.x] = sres.x;
 }
@@ -909,7 +910,7 @@ int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double
   if constexpr (sizeof(T) == 8) {
     if (df) {
       const int nbd = df_blocks(n, R);
-      cgs_sub_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(Vs, w, h1, np1, k1, R, n, nbd, ldh, vnext, vs_next, nrm, flag);
+      cgs_sub_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(Vs, w, h1, np1, k1, R, n, nbd, ldh, vnext, vs_next, nrm, flag, 1);
     }
   }
   if (!df) cgs_sub_kernel<T><<<dim3(nbs, R), kT, 0, s>>>(V, w, h1, np1, nullptr, k1, R, n, nbs, ldh, vnext, nrm, flag);
@@ -1107,6 +1108,15 @@ void givens_residual(const GivensState &st, double2 *z, int R, int m, int ldh, c
 void givens_solve(const GivensState &st, double2 *yd, int R, int m, int ldh, cudaStream_t s) {
   count_launches(1);
   backsub_kernel<<<1, 32, 0, s>>>(st, yd, R, m, ldh);
+}
+
+void gmres_maxpy_df(const float4 *Vs, const double2 *h, double2 *x, int k1, int R, long long n, int ldh,
+                    cudaStream_t s) {
+  if (k1 < 0 || k1 > 64) return;
+  const int nbd = df_blocks(n, R);
+  count_launches(1);
+  cgs_sub_df_kernel<<<dim3(nbd, R), kT, 0, s>>>(Vs, x, h, nullptr, k1, R, n, nbd, ldh, nullptr, nullptr, nullptr,
+                                                nullptr, 0);
 }
 
 void gmres_split(const double2 *v, float4 *vs, long long n, cudaStream_t s) {

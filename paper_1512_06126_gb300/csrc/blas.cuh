@@ -38,6 +38,10 @@ int gmres_orthogonalize(const C<T> *V, C<T> *w, C<T> *vnext, double2 *h1, double
 // vs[e] = (re hi, re lo, im hi, im lo) of v[e] (hi: the leading 24 significant bits, lo
 // the next 23), the split copy of a basis vector for the double-float passes
 void gmres_split(const double2 *v, float4 *vs, long long n, cudaStream_t s);
+// x[r] += sum_{i<k1} h[r * ldh + i] V_i[r] for FP64 vectors in double-float arithmetic,
+// V read from its split copy Vs (k1 <= 64; gmres_maxpy with sign +1, on the FP32 pipe)
+void gmres_maxpy_df(const float4 *Vs, const double2 *h, double2 *x, int k1, int R, long long n, int ldh,
+                    cudaStream_t s);
 int gs_partial_blocks(long long n);
 
 // GMRES least-squares state on the device, per right-hand side r (m < 64):

@@ -603,14 +603,19 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
       ++it;
       kmax = k + 1;
     }
-    // x += V y with y from the rotated least-squares problem (zero beyond each kr)
+    // x += V y with y from the rotated least-squares problem (zero beyond each kr); the
+    // FP64 vectors of the IE_MIXED_FP64K inner solves in double-float from the split basis
+    const bool dfk = sizeof(T) == 8 && single && c->gs_df;
     ie::givens_solve(st, yd, R, m, ldh, s);
-    ie::gmres_maxpy<T>(Vb, yd, x, kmax, R, n, ldh, 1.0, s);
-    if (sizeof(T) == 4) {
-      // the next cycle's residual from the basis: w = V_0..V_kmax z
+    if (dfk) ie::gmres_maxpy_df(c->Vs, yd, (double2 *)x, kmax, R, n, ldh, s);
+    else ie::gmres_maxpy<T>(Vb, yd, x, kmax, R, n, ldh, 1.0, s);
+    if (sizeof(T) == 4 || dfk) {
+      // the next cycle's residual from the basis (the inner solves of both mixed modes):
+      // w = V_0..V_kmax z
       ie::givens_residual(st, h1, R, m, ldh, s);
       IE_CUDA(cudaMemsetAsync(w, 0, nR * sizeof(Vt), s));
-      ie::gmres_maxpy<T>(Vb, h1, w, kmax + 1, R, n, ldh, 1.0, s);
+      if (dfk) ie::gmres_maxpy_df(c->Vs, h1, (double2 *)w, kmax + 1, R, n, ldh, s);
+      else ie::gmres_maxpy<T>(Vb, h1, w, kmax + 1, R, n, ldh, 1.0, s);
       have_res = true;
     }
     IE_CUDA(cudaMemcpyAsync(kr.data(), st.kr, R * sizeof(int), cudaMemcpyDeviceToHost, s));
