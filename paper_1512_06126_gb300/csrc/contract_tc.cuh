@@ -227,8 +227,12 @@ struct TcCfg {
   static constexpr int EPW = NZ / RW;              // complex entries of a chunk per row warp
   static constexpr int NROW = 4 * RW;              // warps 4 .. 4 + NROW - 1 (quadrant = warp % 4)
   static constexpr int NROWA = NQ * RW;            // of them, those with rows
-  static constexpr int NB = 2 + NROW - NROWA;      // B warps: 2, 3 and the row warps without rows
-  static constexpr int WARPS = 4 + NROW;
+  // B warps: 2, 3, the row warps without rows and (FP16) extra warps up to 8, one per
+  // column, so that no B warp stages two columns of X while others stage one
+  static constexpr int NB0 = 2 + NROW - NROWA;
+  static constexpr int NXB = F16 && NB0 < 8 ? 8 - NB0 : 0;  // extra warps 4 + NROW ..
+  static constexpr int NB = NB0 + NXB;
+  static constexpr int WARPS = 4 + NROW + NXB;
   static constexpr int THREADS = 32 * WARPS;
   static constexpr int NS = 3;                     // shared-memory stages
   static constexpr int KC = 2 * NZ;                // K of a chunk (real)
@@ -281,6 +285,15 @@ struct TcCfg {
   static constexpr uint32_t IDESC32 = F16 ? tc::idesc_f16(128, 32) : tc::idesc_tf32(128, 32);
 };
 
+// Written by the B warps for every column c of X of a wavenumber (before they release the
+// B buffer), read by the row warps' epilogue (before they release the accumulators):
+// output element (row) of column c at spec[off + row] (off < 0: no such column), its mirror
+// sign flips (bit 0: the x component, bit 1: the y component) and, FP16, its exponent.
+struct ColInfo {
+  long long off;
+  int flags, xe;
+};
+
 // Timing instrumentation (PROF = true only in measurement builds): per warp, clock64()
 // cycles accumulated in the slots of TcProf, written to prof[(block * WARPS + warp) * 16],
 // and the number of barrier polls of lane 0 in slot 8.
@@ -323,13 +336,14 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
   unsigned char *sm = sm_raw + ((1024u - (tma::smem_u32(sm_raw) & 1023u)) & 1023u);
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Cfg::OFF_BAR);
   // barrier block: full[4] empty[4] afull[8] aempty[8] bfull[2] bempty[2] dfull[2] dempty[2]
-  // fin (33 x 8 bytes), the TMEM address at 384 and the FP16 column exponents at 512..639
-  // of the 1024-byte block
+  // fin (33 x 8 bytes), the TMEM address at 384 and the column records at 512..1023 of
+  // the 1024-byte block
   static_assert(NS <= 4 && NA <= 8, "barrier block");
   uint64_t *full = bars, *empty = bars + 4, *afull = bars + 8, *aempty = bars + 16;
   uint64_t *bfull = bars + 24, *bempty = bars + 26, *dfull = bars + 28, *dempty = bars + 30, *fin = bars + 32;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Cfg::OFF_BAR + 384);
-  int *xexp = reinterpret_cast<int *>(sm + Cfg::OFF_BAR + 512);              // F16: [4][8] column exponents
+  // per wavenumber (ring of 4) and column of X: where its output goes and its scale
+  ColInfo *cinfo = reinterpret_cast<ColInfo *>(sm + Cfg::OFF_BAR + 512);      // [4][8]
   unsigned char *stages = sm + Cfg::OFF_STAGE;
   unsigned char *bbuf = sm + Cfg::OFF_B;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -471,7 +485,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       tc::commit(fin);
       wt(fin, 0u, kDrain);
     }
-  } else if (warp >= 4 && (warp & 3) < Cfg::NQ) {
+  } else if (warp >= 4 && warp < 4 + Cfg::NROW && (warp & 3) < Cfg::NQ) {
     // ---- row warps: unpack, then the epilogue of the previous wavenumber ----
     const int q = warp & 3, jw = (warp - 4) >> 2;  // quadrant, column share
     const int row = 32 * q + lane;
@@ -519,32 +533,25 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       tc::ld2(dc + 40 + 2 * jw, v[10], v[11]);     //            Y_i
       tc::wait_ld();
       toc(kPWaitSt);
-      int xe0 = 0, xe1 = 0;
-      if constexpr (F16) {  // read before dempty is released (the B warps reuse the ring later)
-        xe0 = xexp[(e & 3) * 8 + 2 * jw];
-        xe1 = xexp[(e & 3) * 8 + 2 * jw + 1];
-      }
+      // read before dempty is released (the B warps reuse the ring later)
+      const ColInfo ci[2] = {cinfo[(e & 3) * 8 + 2 * jw], cinfo[(e & 3) * 8 + 2 * jw + 1]};
       tc::fence_before();
       __syncwarp();
       if (lane == 0) tc::arrive(&dempty[bb]);
       if (live) {
-        const Mirrors mw = mirrors_of(w0 + e * gs, Nx, Ny);
-        const int ncol = mw.nmx * mw.nmy * R;
+        const int fbit = alpha == 0 ? 1 : (alpha == 1 ? 2 : 0);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int col = 2 * jw + h;
-          if (col < ncol) {
-            const int m = col / R, r = col - m * R;
-            const int mx = m % mw.nmx, my = m / mw.nmx;
+          if (ci[h].off >= 0) {
             float2 y = make_float2(__uint_as_float(v[h]) + (__uint_as_float(v[4 + h]) + __uint_as_float(v[8 + h])),
                                    __uint_as_float(v[2 + h]) + (__uint_as_float(v[6 + h]) + __uint_as_float(v[10 + h])));
-            if ((alpha == 0 && mx == 1) || (alpha == 1 && my == 1)) { y.x = -y.x; y.y = -y.y; }
+            if (ci[h].flags & fbit) { y.x = -y.x; y.y = -y.y; }
             if constexpr (F16) {  // undo the scalings (exact powers of two)
-              const float sc = tc::pow2f(-ea) * tc::pow2f(-(h ? xe1 : xe0));
+              const float sc = tc::pow2f(-ea) * tc::pow2f(-ci[h].xe);
               y.x *= sc;
               y.y *= sc;
             }
-            spec[mw.pos(mx, my, Nx) * ldz + r * N3 + row] = y;
+            spec[ci[h].off + row] = y;
           }
         }
       }
@@ -648,7 +655,9 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     // multiply M_i: (-X_i | X_r)) of columns col and 8 + col, hi and lo.  Threads of a
     // warp take (col, b % 4) of one core-matrix row group, so the stores of a warp fill
     // 128-byte core matrices without bank conflicts.
-    const int bw = warp < 4 ? warp - 2 : 2 + ((warp - 4) >> 2) * (4 - Cfg::NQ) + ((warp & 3) - Cfg::NQ);
+    const int bw = warp < 4 ? warp - 2
+                 : warp >= 4 + Cfg::NROW ? Cfg::NB0 + (warp - 4 - Cfg::NROW)
+                                         : 2 + ((warp - 4) >> 2) * (4 - Cfg::NQ) + ((warp & 3) - Cfg::NQ);
     const int bt = bw * 32 + lane, nbt = Cfg::NB * 32;
     for (int it = 0; it < n_it && ok; ++it) {
       const int s = it % NS, bb = it & 1;
@@ -666,26 +675,28 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       const float2 *xr = reinterpret_cast<const float2 *>(stages + (size_t)s * Cfg::STAGE + Cfg::OFF_XR);
       unsigned char *bp = bbuf + (size_t)bb * Cfg::BBUF;
       if constexpr (F16) {
-        // Each B warp owns whole columns (col = bw, bw + NB, ...): lane l < 3 Nz / 8 takes
-        // rows 8 l .. 8 l + 7 (one component: Nz % 8 == 0), a warp reduction of the
-        // largest |re|, |im| gives the column's scale exponent, and the scaled, split
-        // rows go out as 16-byte core-matrix rows of hi and lo.
+        // Each B warp owns whole columns (col = bw, bw + NB, ...): lanes 2 g and 2 g + 1 take
+        // the two halves (rows 8 g .. 8 g + 3 and 8 g + 4 .. 8 g + 7) of 8-row group g
+        // (one component: Nz % 8 == 0), a warp reduction of the largest |re|, |im| gives
+        // the column's scale exponent, and the scaled, split rows go out as 8-byte halves
+        // of the 16-byte core-matrix rows of hi and lo.
         constexpr int OPC = N3 / 8;  // 8-row groups per column
-        static_assert(OPC <= 32, "one 8-row group per lane");
+        static_assert(2 * OPC <= 32, "two lanes per 8-row group");
         for (int col = bw; col < 8; col += Cfg::NB) {
-          const bool have = lane < OPC;
-          const int z0 = have ? lane * 8 : 0, beta = z0 / NZ, b0 = z0 - beta * NZ;
-          float xs[8], ys[8];
+          const bool have = lane < 2 * OPC;
+          const int g8 = have ? lane >> 1 : 0, half = lane & 1;
+          const int beta = (g8 * 8) / NZ, b0 = g8 * 8 - beta * NZ;
+          float xs[4], ys[4];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) xs[j] = ys[j] = 0.f;
+          for (int j = 0; j < 4; ++j) xs[j] = ys[j] = 0.f;
           uint32_t mx = 0u;
           if (have && col < ncol) {
             const int m = col / R, r = col - m * R;
             const int mxm = m % mw.nmx, mym = m / mw.nmx;
             const bool flip = (beta == 0 && mxm == 1) || (beta == 1 && mym == 1);
-            const float4 *x4 = reinterpret_cast<const float4 *>(xr + (size_t)m * CZ + r * N3 + z0);
+            const float4 *x4 = reinterpret_cast<const float4 *>(xr + (size_t)m * CZ + r * N3 + g8 * 8 + half * 4);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 2; ++j) {
               const float4 u = x4[j];
               xs[2 * j] = flip ? -u.x : u.x;
               ys[2 * j] = flip ? -u.y : u.y;
@@ -695,23 +706,28 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
             }
           }
           const int ex = tc::scale_exp(__uint_as_float(__reduce_max_sync(0xffffffffu, mx)));
-          if (lane == 0) xexp[(it & 3) * 8 + col] = ex;
+          if (lane == 0) {
+            ColInfo ci = {-1, 0, ex};
+            if (col < ncol) {
+              const int m = col / R, r = col - m * R;
+              const int mxm = m % mw.nmx, mym = m / mw.nmx;
+              ci.off = (long long)mw.pos(mxm, mym, Nx) * ldz + r * N3;
+              ci.flags = (mxm == 1 ? 1 : 0) | (mym == 1 ? 2 : 0);
+            }
+            cinfo[(it & 3) * 8 + col] = ci;
+          }
           if (have) {
             const float sc = tc::pow2f(ex);
-            uint4 rh, rl, ih, il;
+            uint2 rh, rl, ih, il;
             tc::split_h2(xs[0] * sc, xs[1] * sc, rh.x, rl.x);
             tc::split_h2(xs[2] * sc, xs[3] * sc, rh.y, rl.y);
-            tc::split_h2(xs[4] * sc, xs[5] * sc, rh.z, rl.z);
-            tc::split_h2(xs[6] * sc, xs[7] * sc, rh.w, rl.w);
             tc::split_h2(ys[0] * sc, ys[1] * sc, ih.x, il.x);
             tc::split_h2(ys[2] * sc, ys[3] * sc, ih.y, il.y);
-            tc::split_h2(ys[4] * sc, ys[5] * sc, ih.z, il.z);
-            tc::split_h2(ys[6] * sc, ys[7] * sc, ih.w, il.w);
-            const uint4 nih = make_uint4(ih.x ^ 0x80008000u, ih.y ^ 0x80008000u, ih.z ^ 0x80008000u, ih.w ^ 0x80008000u);
-            const uint4 nil = make_uint4(il.x ^ 0x80008000u, il.y ^ 0x80008000u, il.z ^ 0x80008000u, il.w ^ 0x80008000u);
+            const uint2 nih = make_uint2(ih.x ^ 0x80008000u, ih.y ^ 0x80008000u);
+            const uint2 nil = make_uint2(il.x ^ 0x80008000u, il.y ^ 0x80008000u);
             // rows k = b0 .. b0 + 7 (multiply M_r) and Nz + b0 .. (multiply M_i) of columns
-            // col (Y_r) and 8 + col (Y_i, one SBO further)
-            unsigned char *cb = bp + (size_t)(2 * beta) * Cfg::BPART;
+            // col (Y_r) and 8 + col (Y_i, one SBO further); this lane's half at 8 half
+            unsigned char *cb = bp + (size_t)(2 * beta) * Cfg::BPART + 8 * half;
             unsigned char *p0, *p1;
             if constexpr (Cfg::SWZ) {
               p0 = cb + (size_t)col * 128 + (size_t)(((b0 >> 3) ^ col) << 4);
@@ -721,17 +737,28 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
               p1 = p0 + (size_t)(NZ >> 3) * 128;
             }
             constexpr size_t LO = Cfg::BPART;
-            *reinterpret_cast<uint4 *>(p0) = rh;
-            *reinterpret_cast<uint4 *>(p0 + LO) = rl;
-            *reinterpret_cast<uint4 *>(p0 + Cfg::SBO) = ih;
-            *reinterpret_cast<uint4 *>(p0 + Cfg::SBO + LO) = il;
-            *reinterpret_cast<uint4 *>(p1) = nih;
-            *reinterpret_cast<uint4 *>(p1 + LO) = nil;
-            *reinterpret_cast<uint4 *>(p1 + Cfg::SBO) = rh;
-            *reinterpret_cast<uint4 *>(p1 + Cfg::SBO + LO) = rl;
+            *reinterpret_cast<uint2 *>(p0) = rh;
+            *reinterpret_cast<uint2 *>(p0 + LO) = rl;
+            *reinterpret_cast<uint2 *>(p0 + Cfg::SBO) = ih;
+            *reinterpret_cast<uint2 *>(p0 + Cfg::SBO + LO) = il;
+            *reinterpret_cast<uint2 *>(p1) = nih;
+            *reinterpret_cast<uint2 *>(p1 + LO) = nil;
+            *reinterpret_cast<uint2 *>(p1 + Cfg::SBO) = rh;
+            *reinterpret_cast<uint2 *>(p1 + Cfg::SBO + LO) = rl;
           }
         }
-      } else
+      } else {
+        if (bt < 8) {
+          const int col = bt;
+          ColInfo ci = {-1, 0, 0};
+          if (col < ncol) {
+            const int m = col / R, r = col - m * R;
+            const int mxm = m % mw.nmx, mym = m / mw.nmx;
+            ci.off = (long long)mw.pos(mxm, mym, Nx) * ldz + r * N3;
+            ci.flags = (mxm == 1 ? 1 : 0) | (mym == 1 ? 2 : 0);
+          }
+          cinfo[(it & 3) * 8 + col] = ci;
+        }
       // entry e = ((beta * Nz + b) / 4) * 32 + (col * 4 + b % 4)
       for (int e = bt; e < 3 * NZ * 8; e += nbt) {
         const int col = (e >> 2) & 7, bq = e & 3, grp = e >> 5;
@@ -759,6 +786,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
         *reinterpret_cast<uint32_t *>(p1 + LO) = il ^ 0x80000000u;
         *reinterpret_cast<uint32_t *>(p1 + Cfg::SBO) = rh;                 // (Nz + b, 8 + col): X_r
         *reinterpret_cast<uint32_t *>(p1 + Cfg::SBO + LO) = rl;
+      }
       }
       toc(kPWork);
       tma::fence_proxy_async();  // the MMA reads B through the async proxy
