@@ -727,6 +727,75 @@ def run_batch(args):
           flush=True)
 
 
+def run_maps(args):
+    """Field recovery at sites and the MT maps of the COMMEMI3D-3-like model (Sect. 4):
+    both polarisations solved in IE_MIXED_FP64K (tol 1e-7), the fields recovered at
+    two profiles of sites off the cell centres (x = 1.9 km and y = 3.83 km of the model,
+    a site every 100 m), the impedances and the apparent resistivity / phase; device
+    time of each stage (set-up of the site kernels: host clock, synchronous)."""
+    import torch
+    from paper_1512_06126_gb300 import build, ie
+    build.build()
+    m = W.commemi3d3_like()
+    g = m.grid
+    ox, oy = W.COMMEMI3D3_ORIGIN
+    t0 = time.perf_counter()
+    ctx = ie.Context(g, m.layers, m.sigma_a, m.freqs, None, max_rhs=2, restart=args.restart,
+                     inner_tol=args.inner_tol)
+    t_setup = time.perf_counter() - t0
+    b = torch.empty((2, 3, g.nz, g.ny, g.nx), dtype=torch.complex128, device="cuda")
+    for p in range(2):
+        ctx.rhs_mt(0, p, b[p].data_ptr())
+    u = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    ext = torch.cuda.ExternalStream(ctx.stream)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(ext):
+            e0.record()
+        r = fn()
+        with torch.cuda.stream(ext):
+            e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    ms_solve, (st, info) = timed(lambda: ctx.solve(0, b.data_ptr(), u.data_ptr(), 2, TOL,
+                                                   precision=ie.IE_MIXED_FP64K))
+    # profile A along y at x = 1.9 km (a cell face), profile B along x at y = 3.83 km
+    ys = (np.arange(g.ny) + 0.5) * g.hy
+    xs = (np.arange(g.nx) + 0.5) * g.hx
+    sx = np.concatenate([np.full(g.ny, 1900.0 + ox), xs])
+    sy = np.concatenate([ys, np.full(g.nx, 3830.0 + oy)])
+    n_rec = sx.size
+    t0 = time.perf_counter()
+    ctx.set_receivers_xy(sx, sy, 0.0)
+    t_sites = time.perf_counter() - t0
+    f = torch.empty((2, n_rec, 4), dtype=torch.complex128, device="cuda")
+    z = torch.empty((n_rec, 4), dtype=torch.complex128, device="cuda")
+    c = torch.empty((2, n_rec, 4), dtype=torch.complex128, device="cuda")
+    zobs = torch.zeros_like(z)
+    rho = torch.empty((n_rec, 4), dtype=torch.float64, device="cuda")
+    ph = torch.empty_like(rho)
+    ms_fields, _ = timed(lambda: ctx.receiver_fields(0, u.data_ptr(), 2, (0, 1), f.data_ptr()))
+    ms_z, _ = timed(lambda: ctx.mt_misfit(f.data_ptr(), zobs.data_ptr(), z.data_ptr(), c.data_ptr()))
+    ms_maps, _ = timed(lambda: ctx.mt_apparent(0, z.data_ptr(), n_rec, rho.data_ptr(), ph.data_ptr()))
+    rho_h, ph_h = rho.cpu().numpy(), ph.cpu().numpy()
+    ctx.close()
+    a, bb = slice(0, g.ny), slice(g.ny, n_rec)
+    print(json.dumps({
+        "mode": "maps", "workload": f"COMMEMI3D-3-like: {g.nx}x{g.ny}x{g.nz} cells, 7 blocks (max contrast "
+                                    f"3.3e4), period 1 s, 2 polarisations, tol {TOL}",
+        "setup_s": t_setup, "status": st, "inner_iters": info.inner_iters, "outer": info.outer_iters,
+        "final_rel_res": info.final_rel_res, "solve_s": ms_solve / 1e3, "sites": int(n_rec),
+        "site_kernels_s": t_sites, "fields_ms": ms_fields, "impedance_ms": ms_z, "maps_ms": ms_maps,
+        "profile_x1.9km": {"y_km": list(np.round(ys / 1000 - oy / 1000, 3)),
+                           "rho_xy": list(np.round(rho_h[a, 1], 4)), "phase_xy": list(np.round(ph_h[a, 1], 3))},
+        "profile_y3.83km": {"x_km": list(np.round(xs / 1000 - ox / 1000, 3)),
+                            "rho_yx": list(np.round(rho_h[bb, 2], 4)), "phase_yx": list(np.round(ph_h[bb, 2], 3))},
+    }), flush=True)
+
+
 def run_gradient(args):
     """MT misfit and its gradient on the 64x64x24 workload: 8 frequencies x 2
     polarisations, 16 x 16 receivers every second cell over the centre, observed
@@ -788,7 +857,7 @@ def main():
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--threads", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--iters", type=int, default=3, help=argparse.SUPPRESS)
-    ap.add_argument("--mode", choices=["solve", "matvec", "batch", "gradient"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "matvec", "batch", "gradient", "maps"], default="solve")
     ap.add_argument("--precision", choices=list(PRECISIONS_BY_NAME), default="fp64k",
                     help="batch mode: the precision of the batched and one-at-a-time solves")
     ap.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 comparisons")
@@ -806,6 +875,8 @@ def main():
         run_batch(args)
     elif args.mode == "gradient":
         run_gradient(args)
+    elif args.mode == "maps":
+        run_maps(args)
     elif args.impl == "reference":
         run_reference(args, rank, ws)
     else:

@@ -276,6 +276,23 @@ ie_status ie_set_sigma(ie_ctx *ctx, const double *sigma_a_host);
  * IE_ERR_GEOMETRY.  Synchronous. */
 ie_status ie_set_receivers(ie_ctx *ctx, int n_rec, const int *ix_host, const int *iy_host, double z_rec);
 
+/* Receivers at arbitrary lateral sites (x_host[r], y_host[r]) in metres, in the grid's
+ * frame (cell j spans [x0 + j hx, x0 + (j + 1) hx]), within the grid's lateral extent,
+ * all at depth z_rec as for ie_set_receivers (eq. (APR_lab), field recovery at any
+ * point outside the domain).  Sites that share their position relative to the cell
+ * centres (a profile or map on a lattice of the cell size) share one table of kernels
+ * over every receiver-minus-cell offset: c128 [group][2 Ny][2 Nx][Nz][10] per instance,
+ * generated on the device, 4 Nx Ny Nz 160 bytes per group.  ie_receiver_fields,
+ * ie_mt_misfit and ie_receiver_adjoint then act on these sites.  IE_ERR_ARG for a site
+ * outside the grid's extent; IE_ERR_GEOMETRY as for ie_set_receivers.  Synchronous. */
+ie_status ie_set_receivers_xy(ie_ctx *ctx, int n_rec, const double *x_host, const double *y_host, double z_rec);
+
+/* The MT maps from impedances: for the n_rec 2 x 2 impedances z_dev (c128 [n_rec][4],
+ * as written by ie_mt_misfit) of instance inst, rho_dev[r][k] = |Z_k|^2 / (omega mu0)
+ * (apparent resistivity, ohm m) and phase_dev[r][k] = arg Z_k (degrees), k = xx, xy, yx,
+ * yy (device FP64 arrays [n_rec][4]).  Synchronous. */
+ie_status ie_mt_apparent(ie_ctx *ctx, int inst, const void *z_dev, int n_rec, void *rho_dev, void *phase_dev);
+
 /* Fields at the receivers for nrhs solutions U of instance inst, whose sources are
  * the plane waves pol_host[p] (0: x, 1: y): f_dev c128 [nrhs][n_rec][4] =
  * (E_x, E_y, H_x, H_y), the normal field plus sum over cells of the kernels times the

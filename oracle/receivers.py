@@ -218,6 +218,38 @@ def receiver_operator(grid, layers, freq, z_r, receivers):
     return G
 
 
+def receiver_operator_sites(grid, layers, freq, z_r, sites):
+    """Dense receiver operator G [n_rec][4][3 N] for receivers at arbitrary lateral
+    sites (x, y) in metres, the grid's frame (cell j spans [j hx, (j + 1) hx]): every
+    (site, cell) offset from the site to the cell centre computed directly (field
+    recovery at any point, eq. (APR_lab))."""
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    N = nx * ny * nz
+    G = np.zeros((len(sites), 4, 3 * N), dtype=np.complex128)
+    cache = {}
+    for ir, (x, y) in enumerate(sites):
+        for i in range(ny):
+            for j in range(nx):
+                Dx, Dy = x - (j + 0.5) * grid.hx, y - (i + 0.5) * grid.hy
+                key = (round(Dx, 9), round(Dy, 9))
+                if key not in cache:
+                    cache[key] = receiver_kernels_offset(grid, layers, freq, z_r, Dx, Dy)
+                GE, GH = cache[key]
+                for b in range(nz):
+                    cell = (b * ny + i) * nx + j
+                    for c in range(3):
+                        G[ir, 0:2, c * N + cell] = GE[b, :, c]
+                        G[ir, 2:4, c * N + cell] = GH[b, :, c]
+    return G
+
+
+def apparent(Z, freq):
+    """The MT maps of impedances Z [...][2][2]: apparent resistivity |Z|^2 / (w mu0) in
+    ohm m and phase arg Z in degrees."""
+    omega = 2.0 * np.pi * freq
+    return np.abs(Z) ** 2 / (omega * MU0), np.degrees(np.angle(Z))
+
+
 def normal_at(layers, freq, z_r):
     """(E^N(z_r), E^N'(z_r) / (i w mu0)) of the 1-D profile."""
     omega = 2.0 * np.pi * freq

@@ -352,12 +352,15 @@ __device__ __forceinline__ double box_hat(double k, double h) {
   return h * sin(x) / x;
 }
 
-__global__ void weights_kernel(WParams P, const int *offs, int n_off, double *W, double *edges_ws) {
+// doffs (may be NULL): real offsets (Dy, Dx) in metres per offset in place of the cell
+// offsets offs (i, j) -> (i hy, j hx) (receivers at arbitrary lateral sites)
+__global__ void weights_kernel(WParams P, const int *offs, int n_off, double *W, double *edges_ws,
+                               const double *doffs = nullptr) {
   extern __shared__ double smw[];  // [kNW][T]
   const int o = blockIdx.x;
   if (o >= n_off) return;
-  const int i = offs[2 * o], j = offs[2 * o + 1];
-  const double Dx = j * P.hx, Dy = i * P.hy;
+  const double Dx = doffs ? doffs[2 * o + 1] : offs[2 * o + 1] * P.hx;
+  const double Dy = doffs ? doffs[2 * o] : offs[2 * o] * P.hy;
   const int T = P.T;
   for (int q = threadIdx.x; q < kNW * T; q += blockDim.x) smw[q] = 0.0;
   const double rmax = hypot(fabs(Dx) + P.hx, fabs(Dy) + P.hy);
@@ -801,7 +804,7 @@ CoefGenStatus generate_coefficients(const CoefGenInput &in, double2 *q_dev, cuda
 }
 
 CoefGenStatus generate_receiver_tables(const CoefGenInput &in, double z_r, int r_layer, double2 *tab_dev,
-                                       cudaStream_t s) {
+                                       cudaStream_t s, const double *offs_host, int n_off_host) {
   const int nx = in.nx, ny = in.ny, nz = in.nz;
   if (in.n_interfaces < 1 || in.n_interfaces > kMaxLay || nz > 256) return CoefGenStatus::kUnsupported;
   LayDev L{};
@@ -831,11 +834,13 @@ CoefGenStatus generate_receiver_tables(const CoefGenInput &in, double z_r, int r
   std::vector<int> offs;
   for (int i = 0; i < ny; ++i)
     for (int j = 0; j < nx; ++j) { offs.push_back(i); offs.push_back(j); }
-  const int n_off = nx * ny;
+  const bool real_offs = offs_host != nullptr;
+  if (real_offs && n_off_host < 1) return CoefGenStatus::kUnsupported;
+  const int n_off = real_offs ? n_off_host : nx * ny;
   const int max_panels = 4000;
   const long long ncol = (long long)kNRP * 2 * nz;
   zc *spec = nullptr, *F = nullptr;
-  double *W = nullptr, *edges = nullptr, *Pm = nullptr;
+  double *W = nullptr, *edges = nullptr, *Pm = nullptr, *d_doffs = nullptr;
   int *d_offs = nullptr;
   ck(cudaMalloc(&spec, sizeof(zc) * 2 * T * (L.L + 1) * 5));
   ck(cudaMalloc(&F, sizeof(zc) * kNR * (size_t)T * nz));
@@ -843,10 +848,13 @@ CoefGenStatus generate_receiver_tables(const CoefGenInput &in, double z_r, int r
   ck(cudaMalloc(&edges, sizeof(double) * (size_t)n_off * (max_panels + 1)));
   ck(cudaMalloc(&Pm, sizeof(double) * (size_t)n_off * ncol));
   ck(cudaMalloc(&d_offs, sizeof(int) * offs.size()));
+  if (real_offs) ck(cudaMalloc(&d_doffs, sizeof(double) * 2 * (size_t)n_off));
   cublasHandle_t hb = nullptr;
   if (st == CoefGenStatus::kOk && cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) st = CoefGenStatus::kCuda;
   if (st == CoefGenStatus::kOk) {
     ck(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice, s));
+    if (real_offs)
+      ck(cudaMemcpyAsync(d_doffs, offs_host, sizeof(double) * 2 * (size_t)n_off, cudaMemcpyHostToDevice, s));
     double gx[kGL], gw[kGL];
     gauss_legendre(kGL, gx, gw);
     ck(cudaMemcpyToSymbolAsync(c_glx, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, s));
@@ -857,7 +865,7 @@ CoefGenStatus generate_receiver_tables(const CoefGenInput &in, double z_r, int r
     WParams P{nx, ny, in.hx, in.hy, hmin, T, t0, dt, near_lh, 80.0, 10.0, 0.25, lam_low, max_panels, 1};
     const size_t smw = sizeof(double) * kNW * T;
     cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
-    weights_kernel<<<n_off, 256, smw, s>>>(P, d_offs, n_off, W, edges);
+    weights_kernel<<<n_off, 256, smw, s>>>(P, d_offs, n_off, W, edges, d_doffs);
     ck(cudaGetLastError());
     cublasSetStream(hb, s);
     const double one = 1.0, zero = 0.0;
@@ -879,7 +887,7 @@ CoefGenStatus generate_receiver_tables(const CoefGenInput &in, double z_r, int r
     ck(cudaStreamSynchronize(s));
   }
   if (hb) cublasDestroy(hb);
-  cudaFree(spec); cudaFree(F); cudaFree(W); cudaFree(edges); cudaFree(Pm); cudaFree(d_offs);
+  cudaFree(spec); cudaFree(F); cudaFree(W); cudaFree(edges); cudaFree(Pm); cudaFree(d_offs); cudaFree(d_doffs);
   return st;
 }
 

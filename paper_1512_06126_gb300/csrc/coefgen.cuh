@@ -23,8 +23,10 @@ CoefGenStatus generate_coefficients(const CoefGenInput &in, double2 *q_dev, cuda
 // every lateral offset i in [0, Ny), j in [0, Nx) (receiver minus cell) and source
 // z-cell b: tab_dev c128 [Ny][Nx][Nz][10], entries E_xx, E_yy, E_xy, E_xz, E_yz,
 // H_xx, H_yx, H_xy, H_xz, H_yz (E_yx = E_xy, H_yy = -H_xx).  Cells not strictly
-// below z_r get zeros.
+// below z_r get zeros.  offs_host (optional): n_off_host real offsets (Dy, Dx) in metres
+// (receiver minus cell centre) in place of the quadrant of cell offsets: tab_dev then
+// holds [n_off_host][Nz][10].
 CoefGenStatus generate_receiver_tables(const CoefGenInput &in, double z_r, int r_layer, double2 *tab_dev,
-                                       cudaStream_t s);
+                                       cudaStream_t s, const double *offs_host = nullptr, int n_off_host = 0);
 
 }  // namespace ie

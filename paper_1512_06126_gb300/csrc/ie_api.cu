@@ -43,7 +43,9 @@ struct Instance {
   float4 *qdf = nullptr;           // double-float copy of q64 (residuals of the mixed solver)
   int *qexp = nullptr;             // per folded wavenumber: the scale exponent of its c64 block
   void *qh = nullptr;              // the c64 blocks scaled and split into FP16 pairs (Nz in {16, 32})
-  double2 *rtab = nullptr;         // receiver kernels [Ny][Nx][Nz][10] (after ie_set_receivers)
+  double2 *rtab = nullptr;         // receiver kernels [Ny][Nx][Nz][10] (ie_set_receivers) or, for sites,
+                                   // [group][2 Ny][2 Nx][Nz][10] (ie_set_receivers_xy)
+  size_t rtab_cap = 0;             // its allocated elements
   double2 en{0.0, 0.0}, hn{0.0, 0.0};  // normal E^N and E^N'/(i w mu0) at the receiver depth
 };
 
@@ -86,6 +88,8 @@ struct ie_ctx {
   void *efac = nullptr;                        // per cell: 1 / a = 2 s / (sigma_a + conj sigma_b) (E = U / a)
   int n_rec = 0;                               // receivers (ie_set_receivers)
   int *rec_ix = nullptr, *rec_iy = nullptr;
+  int *rec_grp = nullptr;                      // sites (ie_set_receivers_xy): table group of every receiver
+  bool rec_sites = false;                      // the receivers are arbitrary sites
   double z_rec = 0.0;
   double *phi_r = nullptr;                     // per-receiver misfit terms
   std::vector<void *> allocs;
@@ -1296,6 +1300,111 @@ ie_status ie_set_sigma(ie_ctx *c, const double *sigma_a_host) {
   return build_diagonals(c);
 }
 
+namespace {
+// layer of the receiver depth and the layer stack as (re, im) pairs for the generator
+int receiver_layer_of(const ie_ctx *c, double z_rec) {
+  int r_layer = 0;
+  for (size_t k = 0; k < c->d.size(); ++k)
+    if (z_rec >= c->d[k]) r_layer = (int)k + 1;
+  return r_layer;
+}
+std::vector<double> sigma_pairs(const ie_ctx *c) {
+  std::vector<double> sg(2 * c->sig.size());
+  for (size_t k = 0; k < c->sig.size(); ++k) { sg[2 * k] = c->sig[k].real(); sg[2 * k + 1] = c->sig[k].imag(); }
+  return sg;
+}
+ie_status ensure_rtab(ie_ctx *c, Instance &in, size_t elems) {
+  if (in.rtab && in.rtab_cap >= elems) return IE_OK;
+  IE_TRY(dalloc(c, &in.rtab, elems * sizeof(double2)));
+  in.rtab_cap = elems;
+  return IE_OK;
+}
+}  // namespace
+
+ie_status ie_set_receivers_xy(ie_ctx *c, int n_rec, const double *x, const double *y, double z_rec) {
+  if (!c || n_rec < 1 || n_rec > (1 << 16) || !x || !y) return IE_ERR_ARG;
+  if (z_rec > c->ze[0] || z_rec < c->d[0]) return IE_ERR_ARG;
+  const int nx = c->nx, ny = c->ny, nz = c->nz;
+  std::vector<int> ix(n_rec), iy(n_rec), grp(n_rec);
+  std::vector<double> gfx, gfy;
+  for (int r = 0; r < n_rec; ++r) {
+    const double ux = (x[r] - c->x0) / c->hx - 0.5, uy = (y[r] - c->y0) / c->hy - 0.5;
+    if (!(ux >= -0.5 && ux <= nx - 0.5 && uy >= -0.5 && uy <= ny - 0.5)) return IE_ERR_ARG;
+    // the cell centre at or before the site, and the site's position beyond it in cells
+    const int jr = (int)std::floor(ux), ir = (int)std::floor(uy);
+    const double fx = ux - jr, fy = uy - ir;
+    int gsel = -1;
+    for (size_t g = 0; g < gfx.size(); ++g)
+      if (std::fabs(gfx[g] - fx) < 1e-9 && std::fabs(gfy[g] - fy) < 1e-9) { gsel = (int)g; break; }
+    if (gsel < 0) {
+      gsel = (int)gfx.size();
+      gfx.push_back(fx);
+      gfy.push_back(fy);
+    }
+    ix[r] = jr;
+    iy[r] = ir;
+    grp[r] = gsel;
+  }
+  const int n_grp = (int)gfx.size();
+  const int old_n = c->n_rec;
+  const double old_z = c->z_rec;
+  c->n_rec = n_rec;
+  c->z_rec = z_rec;
+  if (check_receiver_geometry(c) != IE_OK) {
+    c->n_rec = old_n;
+    c->z_rec = old_z;
+    return IE_ERR_GEOMETRY;
+  }
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  if (old_n < n_rec || !c->rec_grp) {
+    IE_TRY(dalloc(c, &c->rec_ix, (size_t)n_rec * sizeof(int)));
+    IE_TRY(dalloc(c, &c->rec_iy, (size_t)n_rec * sizeof(int)));
+    IE_TRY(dalloc(c, &c->rec_grp, (size_t)n_rec * sizeof(int)));
+    IE_TRY(dalloc(c, &c->phi_r, (size_t)n_rec * sizeof(double)));
+  }
+  IE_CUDA(cudaMemcpy(c->rec_ix, ix.data(), (size_t)n_rec * sizeof(int), cudaMemcpyHostToDevice));
+  IE_CUDA(cudaMemcpy(c->rec_iy, iy.data(), (size_t)n_rec * sizeof(int), cudaMemcpyHostToDevice));
+  IE_CUDA(cudaMemcpy(c->rec_grp, grp.data(), (size_t)n_rec * sizeof(int), cudaMemcpyHostToDevice));
+  c->rec_sites = true;
+  const int r_layer = receiver_layer_of(c, z_rec);
+  std::vector<double> sg = sigma_pairs(c);
+  const int n_off = 4 * nx * ny;
+  const size_t gstride = (size_t)n_off * nz * 10;
+  std::vector<double> offs(2 * (size_t)n_off);
+  for (auto &in : c->inst) {
+    IE_TRY(ensure_rtab(c, in, gstride * n_grp));
+    ie::CoefGenInput gi{nx, ny, nz, c->hx, c->hy, c->ze.data(), c->lay.data(), (int)c->d.size(), c->d.data(),
+                        sg.data(), in.freq};
+    for (int g = 0; g < n_grp; ++g) {
+      // offsets (receiver minus cell centre) of the group: row di + Ny, column dj + Nx
+      for (int di = -ny; di < ny; ++di)
+        for (int dj = -nx; dj < nx; ++dj) {
+          const size_t o = (size_t)(di + ny) * 2 * nx + (dj + nx);
+          offs[2 * o] = (di + gfy[g]) * c->hy;
+          offs[2 * o + 1] = (dj + gfx[g]) * c->hx;
+        }
+      const ie::CoefGenStatus gs =
+          ie::generate_receiver_tables(gi, z_rec, r_layer, in.rtab + g * gstride, c->stream, offs.data(), n_off);
+      if (gs != ie::CoefGenStatus::kOk) return gs == ie::CoefGenStatus::kUnsupported ? IE_ERR_ARG : IE_ERR_CUDA;
+    }
+    cd E, H;
+    mt_point(c, 2.0 * M_PI * in.freq, z_rec, &E, &H);
+    in.en = make_double2(E.real(), E.imag());
+    in.hn = make_double2(H.real(), H.imag());
+  }
+  return IE_OK;
+}
+
+ie_status ie_mt_apparent(ie_ctx *c, int inst, const void *z_dev, int n_rec, void *rho_dev, void *phase_dev) {
+  if (!c || !z_dev || !rho_dev || !phase_dev || inst < 0 || inst >= (int)c->inst.size() || n_rec < 1)
+    return IE_ERR_ARG;
+  ie::launch_mt_apparent((const double2 *)z_dev, 4 * n_rec, 2.0 * M_PI * c->inst[inst].freq, (double *)rho_dev,
+                         (double *)phase_dev, c->stream);
+  IE_CUDA(cudaGetLastError());
+  IE_CUDA(cudaStreamSynchronize(c->stream));
+  return IE_OK;
+}
+
 ie_status ie_set_receivers(ie_ctx *c, int n_rec, const int *ix, const int *iy, double z_rec) {
   if (!c || n_rec < 1 || n_rec > (1 << 16) || !ix || !iy) return IE_ERR_ARG;
   if (z_rec > c->ze[0] || z_rec < c->d[0]) return IE_ERR_ARG;
@@ -1318,14 +1427,12 @@ ie_status ie_set_receivers(ie_ctx *c, int n_rec, const int *ix, const int *iy, d
   }
   IE_CUDA(cudaMemcpy(c->rec_ix, ix, (size_t)n_rec * sizeof(int), cudaMemcpyHostToDevice));
   IE_CUDA(cudaMemcpy(c->rec_iy, iy, (size_t)n_rec * sizeof(int), cudaMemcpyHostToDevice));
-  int r_layer = 0;
-  for (size_t k = 0; k < c->d.size(); ++k)
-    if (z_rec >= c->d[k]) r_layer = (int)k + 1;
-  std::vector<double> sg(2 * c->sig.size());
-  for (size_t k = 0; k < c->sig.size(); ++k) { sg[2 * k] = c->sig[k].real(); sg[2 * k + 1] = c->sig[k].imag(); }
+  c->rec_sites = false;
+  const int r_layer = receiver_layer_of(c, z_rec);
+  std::vector<double> sg = sigma_pairs(c);
   const size_t tab_elems = (size_t)c->nx * c->ny * c->nz * 10;
   for (auto &in : c->inst) {
-    if (!in.rtab) IE_TRY(dalloc(c, &in.rtab, tab_elems * sizeof(double2)));
+    IE_TRY(ensure_rtab(c, in, tab_elems));
     ie::CoefGenInput gi{c->nx, c->ny, c->nz, c->hx, c->hy, c->ze.data(), c->lay.data(), (int)c->d.size(),
                         c->d.data(), sg.data(), in.freq};
     const ie::CoefGenStatus gs = ie::generate_receiver_tables(gi, z_rec, r_layer, in.rtab, c->stream);
@@ -1348,9 +1455,9 @@ ie_status ie_receiver_fields(ie_ctx *c, int inst, const void *u_dev, int nrhs, c
     pol[p] = pol_host[p];
   }
   const Instance &in = c->inst[inst];
-  ie::launch_receiver_fields(in.rtab, c->rec_ix, c->rec_iy, c->n_rec, (const double2 *)u_dev,
-                             (const double2 *)c->jfac, nrhs, c->nx, c->ny, c->nz, pol[0], pol[1], pol[2], pol[3],
-                             in.en, in.hn, (double2 *)f_dev, c->stream);
+  ie::launch_receiver_fields(in.rtab, c->rec_ix, c->rec_iy, c->rec_sites ? c->rec_grp : nullptr, c->n_rec,
+                             (const double2 *)u_dev, (const double2 *)c->jfac, nrhs, c->nx, c->ny, c->nz, pol[0],
+                             pol[1], pol[2], pol[3], in.en, in.hn, (double2 *)f_dev, c->stream);
   IE_CUDA(cudaGetLastError());
   IE_CUDA(cudaStreamSynchronize(c->stream));
   return IE_OK;
@@ -1375,8 +1482,9 @@ ie_status ie_receiver_adjoint(ie_ctx *c, int inst, const void *c_dev, int nrhs, 
   if (!c || !c_dev || !rhs_dev || inst < 0 || inst >= (int)c->inst.size() || nrhs < 1 || nrhs > 4)
     return IE_ERR_ARG;
   if (c->n_rec == 0 || !c->inst[inst].rtab) return IE_ERR_ARG;
-  ie::launch_receiver_adjoint(c->inst[inst].rtab, c->rec_ix, c->rec_iy, c->n_rec, (const double2 *)c_dev,
-                              (const double2 *)c->jfac, nrhs, c->nx, c->ny, c->nz, (double2 *)rhs_dev, c->stream);
+  ie::launch_receiver_adjoint(c->inst[inst].rtab, c->rec_ix, c->rec_iy, c->rec_sites ? c->rec_grp : nullptr,
+                              c->n_rec, (const double2 *)c_dev, (const double2 *)c->jfac, nrhs, c->nx, c->ny, c->nz,
+                              (double2 *)rhs_dev, c->stream);
   IE_CUDA(cudaGetLastError());
   IE_CUDA(cudaStreamSynchronize(c->stream));
   return IE_OK;

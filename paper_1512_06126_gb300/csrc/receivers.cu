@@ -54,10 +54,35 @@ __device__ __forceinline__ Kern load_kern(const double2 *tab, int di, int dj, in
   return K;
 }
 
+// Kernels of receiver r for the cell at (i, j, b): di = rec_iy[r] - i, dj = rec_ix[r] - j.
+// grp == NULL: the quadrant table above.  Otherwise receivers at arbitrary sites: tab
+// holds one table per group of sites that share a sub-cell position,
+// [group][2 Ny][2 Nx][Nz][10] over di in [-Ny, Ny), dj in [-Nx, Nx), signs included.
+__device__ __forceinline__ Kern load_kern_r(const double2 *tab, const int *grp, int r, int di, int dj, int b, int nx,
+                                            int ny, int nz) {
+  if (!grp) return load_kern(tab, di, dj, b, nx, nz);
+  const double2 *t =
+      tab + (((((size_t)__ldg(grp + r) * 2 * ny + (di + ny)) * 2 * nx + (dj + nx)) * nz + b) * kE);
+  Kern K;
+  K.e[0][0] = __ldg(t + 0);
+  K.e[0][1] = K.e[1][0] = __ldg(t + 2);
+  K.e[0][2] = __ldg(t + 3);
+  K.e[1][1] = __ldg(t + 1);
+  K.e[1][2] = __ldg(t + 4);
+  K.h[0][0] = __ldg(t + 5);
+  K.h[0][1] = __ldg(t + 7);
+  K.h[0][2] = __ldg(t + 8);
+  K.h[1][0] = __ldg(t + 6);
+  K.h[1][1] = cs(K.h[0][0], -1.0);
+  K.h[1][2] = __ldg(t + 9);
+  return K;
+}
+
 // One CTA per receiver; 4 * nrhs complex sums reduced over the CTA.
 __global__ void __launch_bounds__(kRT) receiver_fields_kernel(const double2 *__restrict__ tab,
                                                               const int *__restrict__ rec_ix,
                                                               const int *__restrict__ rec_iy,
+                                                              const int *__restrict__ rec_grp,
                                                               const double2 *__restrict__ u,
                                                               const double2 *__restrict__ jfac, int nrhs, int nx,
                                                               int ny, int nz, int4 pols, double2 en, double2 hn,
@@ -75,7 +100,7 @@ __global__ void __launch_bounds__(kRT) receiver_fields_kernel(const double2 *__r
     const double2 jf = jfac[m];
     if (jf.x == 0.0 && jf.y == 0.0) continue;
     const int j = (int)(m % nx), i = (int)((m / nx) % ny), b = (int)(m / ((long long)nx * ny));
-    const Kern K = load_kern(tab, ry - i, rx - j, b, nx, nz);
+    const Kern K = load_kern_r(tab, rec_grp, r, ry - i, rx - j, b, nx, ny, nz);
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       if (p >= nrhs) break;
@@ -124,7 +149,8 @@ __global__ void __launch_bounds__(kRT) receiver_fields_kernel(const double2 *__r
 // One thread per cell: the transpose of the receiver operator, scaled by jfac.
 __global__ void __launch_bounds__(kRT) receiver_adjoint_kernel(const double2 *__restrict__ tab,
                                                                const int *__restrict__ rec_ix,
-                                                               const int *__restrict__ rec_iy, int n_rec,
+                                                               const int *__restrict__ rec_iy,
+                                                               const int *__restrict__ rec_grp, int n_rec,
                                                                const double2 *__restrict__ cvec,
                                                                const double2 *__restrict__ jfac, int nrhs, int nx,
                                                                int ny, int nz, double2 *__restrict__ rhs) {
@@ -139,7 +165,7 @@ __global__ void __launch_bounds__(kRT) receiver_adjoint_kernel(const double2 *__
     if (!(jf.x == 0.0 && jf.y == 0.0)) {
       const int j = (int)(m % nx), i = (int)((m / nx) % ny), b = (int)(m / ((long long)nx * ny));
       for (int r = 0; r < n_rec; ++r) {
-        const Kern K = load_kern(tab, __ldg(rec_iy + r) - i, __ldg(rec_ix + r) - j, b, nx, nz);
+        const Kern K = load_kern_r(tab, rec_grp, r, __ldg(rec_iy + r) - i, __ldg(rec_ix + r) - j, b, nx, ny, nz);
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           if (p >= nrhs) break;
@@ -162,6 +188,18 @@ __global__ void __launch_bounds__(kRT) receiver_adjoint_kernel(const double2 *__
       for (int c = 0; c < 3; ++c) rhs[((long long)p * 3 + c) * N + m] = cm(jf, q[p][c]);
     }
   }
+}
+
+// Apparent resistivity |Z|^2 / (w mu0) (ohm m) and phase arg Z (degrees) of n impedance
+// entries (the MT maps)
+__global__ void mt_apparent_kernel(const double2 *__restrict__ z, int n, double omega, double *__restrict__ rho,
+                                   double *__restrict__ phase) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double2 v = z[k];
+  const double mu0 = 4.0e-7 * 3.14159265358979323846;
+  rho[k] = (v.x * v.x + v.y * v.y) / (omega * mu0);
+  phase[k] = atan2(v.y, v.x) * (180.0 / 3.14159265358979323846);
 }
 
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
@@ -243,19 +281,26 @@ int grid_for(long long n) {
 
 }  // namespace
 
-void launch_receiver_fields(const double2 *tab, const int *rec_ix, const int *rec_iy, int n_rec, const double2 *u,
-                            const double2 *jfac, int nrhs, int nx, int ny, int nz, int pol0, int pol1, int pol2,
-                            int pol3, double2 en, double2 hn, double2 *f, cudaStream_t s) {
+void launch_receiver_fields(const double2 *tab, const int *rec_ix, const int *rec_iy, const int *rec_grp,
+                            int n_rec, const double2 *u, const double2 *jfac, int nrhs, int nx, int ny, int nz,
+                            int pol0, int pol1, int pol2, int pol3, double2 en, double2 hn, double2 *f,
+                            cudaStream_t s) {
   count_launches(1);
-  receiver_fields_kernel<<<n_rec, kRT, 0, s>>>(tab, rec_ix, rec_iy, u, jfac, nrhs, nx, ny, nz,
+  receiver_fields_kernel<<<n_rec, kRT, 0, s>>>(tab, rec_ix, rec_iy, rec_grp, u, jfac, nrhs, nx, ny, nz,
                                                make_int4(pol0, pol1, pol2, pol3), en, hn, f, n_rec);
 }
 
-void launch_receiver_adjoint(const double2 *tab, const int *rec_ix, const int *rec_iy, int n_rec, const double2 *c,
-                             const double2 *jfac, int nrhs, int nx, int ny, int nz, double2 *rhs, cudaStream_t s) {
+void launch_receiver_adjoint(const double2 *tab, const int *rec_ix, const int *rec_iy, const int *rec_grp,
+                             int n_rec, const double2 *c, const double2 *jfac, int nrhs, int nx, int ny, int nz,
+                             double2 *rhs, cudaStream_t s) {
   count_launches(1);
-  receiver_adjoint_kernel<<<grid_for((long long)nx * ny * nz), kRT, 0, s>>>(tab, rec_ix, rec_iy, n_rec, c, jfac,
-                                                                           nrhs, nx, ny, nz, rhs);
+  receiver_adjoint_kernel<<<grid_for((long long)nx * ny * nz), kRT, 0, s>>>(tab, rec_ix, rec_iy, rec_grp, n_rec, c,
+                                                                           jfac, nrhs, nx, ny, nz, rhs);
+}
+
+void launch_mt_apparent(const double2 *z, int n, double omega, double *rho, double *phase, cudaStream_t s) {
+  count_launches(1);
+  mt_apparent_kernel<<<(n + 127) / 128, 128, 0, s>>>(z, n, omega, rho, phase);
 }
 
 void launch_mt_misfit(const double2 *f, const double2 *zobs, int n_rec, double2 *z, double *phi_r, double2 *c,

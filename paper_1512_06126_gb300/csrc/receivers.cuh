@@ -12,13 +12,21 @@ namespace ie {
 // f[p][r][4] = (Ex, Ey, Hx, Hy) at receiver r for solution p: the normal field of
 // polarisation pol[p] (0: x, E_x = en, H_y = hn; 1: y, E_y = en, H_x = -hn) plus
 // sum over cells of the kernels times the current jfac * u (jfac = 2 s gamma).
-void launch_receiver_fields(const double2 *tab, const int *rec_ix, const int *rec_iy, int n_rec, const double2 *u,
-                            const double2 *jfac, int nrhs, int nx, int ny, int nz, int pol0, int pol1, int pol2,
-                            int pol3, double2 en, double2 hn, double2 *f, cudaStream_t s);
+// rec_grp: NULL for receivers at cell centres (tab: the quadrant table above); otherwise
+// the group of every receiver, tab [group][2 Ny][2 Nx][Nz][10] over offsets (rec_iy - i,
+// rec_ix - j) in [-Ny, Ny) x [-Nx, Nx), signs included (arbitrary sites).
+void launch_receiver_fields(const double2 *tab, const int *rec_ix, const int *rec_iy, const int *rec_grp,
+                            int n_rec, const double2 *u, const double2 *jfac, int nrhs, int nx, int ny, int nz,
+                            int pol0, int pol1, int pol2, int pol3, double2 en, double2 hn, double2 *f,
+                            cudaStream_t s);
 
 // rhs[p] = jfac * (G^T c[p]): c[p][r][4] are receiver sources for (Ex, Ey, Hx, Hy).
-void launch_receiver_adjoint(const double2 *tab, const int *rec_ix, const int *rec_iy, int n_rec, const double2 *c,
-                             const double2 *jfac, int nrhs, int nx, int ny, int nz, double2 *rhs, cudaStream_t s);
+void launch_receiver_adjoint(const double2 *tab, const int *rec_ix, const int *rec_iy, const int *rec_grp,
+                             int n_rec, const double2 *c, const double2 *jfac, int nrhs, int nx, int ny, int nz,
+                             double2 *rhs, cudaStream_t s);
+
+// rho[k] = |z[k]|^2 / (omega mu0), phase[k] = arg z[k] in degrees (k < n)
+void launch_mt_apparent(const double2 *z, int n, double omega, double *rho, double *phase, cudaStream_t s);
 
 // Per receiver: Z = E H^-1 from f[2][n_rec][4] (x then y polarisation), phi_r =
 // 1/2 sum |Z - Zobs|^2, and the adjoint sources c[2][n_rec][4] of dPhi.

@@ -27,7 +27,8 @@ IE_PROF_PRODUCT_C64, IE_PROF_PRODUCT_C128, IE_PROF_GS_C64, IE_PROF_GS_C128, IE_P
 
 EXPORTS = ("ie_setup", "ie_generate_coefficients", "ie_matvec_noalloc", "ie_noalloc_sync", "ie_matvec", "ie_sync",
            "ie_fields", "ie_debug_set_wait_limit", "ie_solve", "ie_adjoint_solve", "ie_solve_batch",
-           "ie_contract_tuning", "ie_fft_plan", "ie_set_fft_plan", "ie_set_contract_variant", "ie_rhs_mt", "ie_set_sigma", "ie_set_receivers",
+           "ie_contract_tuning", "ie_fft_plan", "ie_set_fft_plan", "ie_set_contract_variant", "ie_rhs_mt",
+           "ie_set_sigma", "ie_set_receivers", "ie_set_receivers_xy", "ie_mt_apparent",
            "ie_receiver_fields", "ie_mt_misfit", "ie_receiver_adjoint", "ie_gradient_accumulate", "ie_ctx_stream",
            "ie_ctx_device_bytes", "ie_profile", "ie_profile_read", "ie_profile_matvec", "ie_kernel_launches",
            "ie_destroy", "ie_status_str")
@@ -111,6 +112,10 @@ def load(path: str = LIB_PATH):
     lib.ie_set_sigma.restype = I
     lib.ie_set_receivers.argtypes = [VP, I, VP, VP, D]
     lib.ie_set_receivers.restype = I
+    lib.ie_set_receivers_xy.argtypes = [VP, I, VP, VP, D]
+    lib.ie_set_receivers_xy.restype = I
+    lib.ie_mt_apparent.argtypes = [VP, I, VP, I, VP, VP]
+    lib.ie_mt_apparent.restype = I
     lib.ie_receiver_fields.argtypes = [VP, I, VP, I, VP, VP]
     lib.ie_receiver_fields.restype = I
     lib.ie_mt_misfit.argtypes = [VP, VP, VP, VP, P(D), VP]
@@ -332,6 +337,20 @@ class Context:
         _check(self._lib.ie_set_receivers(self.ctx, int(ix.size), ix.ctypes.data, iy.ctypes.data, float(z_rec)),
                "ie_set_receivers")
         self.n_rec = int(ix.size)
+
+    def set_receivers_xy(self, x, y, z_rec=0.0):
+        """Receivers at arbitrary lateral sites (metres, the grid's frame)."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+        if x.shape != y.shape:
+            raise ValueError("x and y differ in length")
+        _check(self._lib.ie_set_receivers_xy(self.ctx, int(x.size), x.ctypes.data, y.ctypes.data, float(z_rec)),
+               "ie_set_receivers_xy")
+        self.n_rec = int(x.size)
+
+    def mt_apparent(self, inst, z_ptr, n_rec, rho_ptr, phase_ptr):
+        """Apparent resistivity and phase [n_rec][4] (FP64, device) from impedances [n_rec][4]."""
+        _check(self._lib.ie_mt_apparent(self.ctx, inst, z_ptr, n_rec, rho_ptr, phase_ptr), "ie_mt_apparent")
 
     def receiver_fields(self, inst, u_ptr, nrhs, pols, f_ptr):
         pa = np.ascontiguousarray(np.asarray(pols, dtype=np.int32))

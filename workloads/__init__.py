@@ -192,6 +192,46 @@ def config5() -> Model:
                             (0.01, 0.01), (0.01,), ("x", "y"))
 
 
+# The seven blocks of the COMMEMI3D-3 model (Sect. 4, Table (commemi_table)): opposite
+# corners (x1, y1, z1), (x2, y2, z2) in km and conductivity in S/m
+COMMEMI3D3_BLOCKS = (
+    ((0.0, 2.4, 0.05), (3.0, 2.8, 0.30), 0.0033),
+    ((0.0, 1.8, 0.05), (3.0, 2.4, 0.45), 0.033),
+    ((0.0, 1.4, 0.05), (3.0, 1.8, 0.30), 0.1),
+    ((0.0, 0.8, 0.05), (3.0, 1.4, 0.45), 0.033),
+    ((0.0, 0.4, 0.05), (3.0, 0.8, 0.30), 0.0033),
+    ((3.4, 2.8, 0.20), (4.4, 4.8, 1.00), 10.0),
+    ((1.4, 0.0, 1.00), (2.4, 5.6, 3.00), 3.3333),
+)
+# the model's (x, y) origin in the grid's frame (m): the grid spans x in [-1.0, 5.4] km,
+# y in [-0.4, 6.0] km of the model
+COMMEMI3D3_ORIGIN = (1000.0, 400.0)
+
+
+def commemi3d3_like() -> Model:
+    """A COMMEMI3D-3-like synthetic model (Sect. 4): the seven blocks of its table in its
+    layered background (air; 1e-3 S/m to 1 km; 1e-4 S/m to 7.5 km; 0.1 S/m below) on
+    64 x 64 cells of 100 m laterally and 32 cells in z (50 m from 50 to 450 m, 68.75 m to
+    1 km, 125 m to 3 km, so that every block face and the interface at 1 km are cell
+    faces); a cell takes the conductivity of the block holding its centre; period 1 s,
+    both polarisations.  Grid x = model x + 1 km, grid y = model y + 0.4 km."""
+    ze = ([50.0 * k for k in range(1, 10)] + [450.0 + 68.75 * k for k in range(1, 9)] +
+          [1000.0 + 125.0 * k for k in range(1, 17)])
+    grid = Grid(64, 64, 32, 100.0, 100.0, tuple(ze))
+    layers = Layers((0.0, 1000.0, 7500.0), (AIR_SIGMA, 1e-3, 1e-4, 0.1))
+    sb = background_sigma(grid, layers)
+    sa = np.broadcast_to(sb[:, None, None], (grid.nz, grid.ny, grid.nx)).astype(np.complex128).copy()
+    zc = 0.5 * (np.asarray(ze[:-1]) + np.asarray(ze[1:]))
+    xc = (np.arange(grid.nx) + 0.5) * grid.hx - COMMEMI3D3_ORIGIN[0]
+    yc = (np.arange(grid.ny) + 0.5) * grid.hy - COMMEMI3D3_ORIGIN[1]
+    for (x1, y1, z1), (x2, y2, z2), sig in COMMEMI3D3_BLOCKS:
+        kz = (zc > 1000 * z1) & (zc < 1000 * z2)
+        ky = (yc > 1000 * y1) & (yc < 1000 * y2)
+        kx = (xc > 1000 * x1) & (xc < 1000 * x2)
+        sa[np.ix_(kz, ky, kx)] = sig
+    return Model("COMMEMI3D-3-like", grid, layers, sa, (1.0,), ("x", "y"))
+
+
 def small_model(nx=6, ny=5, nz=3, h=100.0, seed=7, freq=1.0, pols=("x",), n_layers=3) -> Model:
     """A small ragged model for tests: Nx != Ny, several layers crossing the cell column."""
     rng = np.random.default_rng(seed)
