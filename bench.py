@@ -796,6 +796,79 @@ def run_maps(args):
     }), flush=True)
 
 
+def run_block_eval(args):
+    """Evaluation of block GMRES across the two polarisations (one Krylov space of block
+    size 2) against two independent GMRES(m), for the decision whether to build it: the
+    same operator (the library's c128 product through ie_matvec on the C2 workload), the
+    Arnoldi steps and least-squares problems in plain torch, and the number of block
+    steps / iterations to ||b - A x|| <= 1e-7 ||b|| counted (one step of either costs one
+    product of two vectors).  Not a solver of the library."""
+    import torch
+    from paper_1512_06126_gb300 import build, ie
+    build.build()
+    m = workload(args.workload)
+    g = m.grid
+    N = 3 * g.nz * g.ny * g.nx
+    ctx = ie.Context(g, m.layers, m.sigma_a, m.freqs[:1], None, max_rhs=2)
+    b = torch.empty((2, N), dtype=torch.complex128, device="cuda")
+    for p in range(2):
+        ctx.rhs_mt(0, p, b[p].data_ptr())
+    torch.cuda.synchronize()
+
+    def A(X):
+        Y = torch.empty_like(X)
+        torch.cuda.synchronize()
+        ctx.matvec(0, X.data_ptr(), Y.data_ptr(), X.shape[0], dtype=ie.IE_C128)
+        if ctx.sync() != ie.IE_OK:
+            raise RuntimeError("a contraction wait ran out")
+        return Y
+
+    def lstsq(H, E):
+        return torch.linalg.lstsq(H.cpu(), E.cpu()).solution.to(H.device)
+
+    def block_gmres(B, mrest, maxit):
+        p = B.shape[0]
+        nbB = B.norm(dim=1)
+        X = torch.zeros_like(B)
+        its = 0
+        while its < maxit:
+            R = B - A(X)
+            if (R.norm(dim=1) <= TOL * nbB).all():
+                return its
+            Q, Rr = torch.linalg.qr(R.T)
+            V = [Q.T.contiguous()]
+            H = torch.zeros(((mrest + 1) * p, mrest * p), dtype=torch.complex128, device="cuda")
+            E = torch.zeros(((mrest + 1) * p, p), dtype=torch.complex128, device="cuda")
+            E[:p, :] = Rr
+            for k in range(mrest):
+                Wk = A(V[k])
+                its += 1
+                Vm = torch.cat(V)
+                h = Vm.conj() @ Wk.T
+                Wk = Wk - (Vm.T @ h).T
+                h2 = Vm.conj() @ Wk.T
+                Wk = Wk - (Vm.T @ h2).T
+                Qk, Rk = torch.linalg.qr(Wk.T)
+                H[:(k + 1) * p, k * p:(k + 1) * p] = h + h2
+                H[(k + 1) * p:(k + 2) * p, k * p:(k + 1) * p] = Rk
+                V.append(Qk.T.contiguous())
+                Hk = H[:(k + 2) * p, :(k + 1) * p]
+                Y = lstsq(Hk, E[:(k + 2) * p])
+                if ((E[:(k + 2) * p] - Hk @ Y).norm(dim=0) <= TOL * nbB).all() or k == mrest - 1:
+                    X = X + (torch.cat(V[:k + 1]).T @ Y).T
+                    break
+        return its
+
+    out = {"mode": "block-eval", "workload": workload_desc(args.workload, m), "tol": TOL, "restarts": {}}
+    for mrest in (45, 20):
+        sep = [block_gmres(b[p:p + 1], mrest, 2000) for p in range(2)]
+        blk = block_gmres(b, mrest, 2000)
+        out["restarts"][str(mrest)] = {"separate_iterations": sep, "lockstep_iterations": max(sep),
+                                       "block_steps": blk}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_gradient(args):
     """MT misfit and its gradient on the 64x64x24 workload: 8 frequencies x 2
     polarisations, 16 x 16 receivers every second cell over the centre, observed
@@ -857,7 +930,8 @@ def main():
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--threads", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--iters", type=int, default=3, help=argparse.SUPPRESS)
-    ap.add_argument("--mode", choices=["solve", "matvec", "batch", "gradient", "maps"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "matvec", "batch", "gradient", "maps", "block-eval"],
+                    default="solve")
     ap.add_argument("--precision", choices=list(PRECISIONS_BY_NAME), default="fp64k",
                     help="batch mode: the precision of the batched and one-at-a-time solves")
     ap.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 comparisons")
@@ -877,6 +951,8 @@ def main():
         run_gradient(args)
     elif args.mode == "maps":
         run_maps(args)
+    elif args.mode == "block-eval":
+        run_block_eval(args)
     elif args.impl == "reference":
         run_reference(args, rank, ws)
     else:
