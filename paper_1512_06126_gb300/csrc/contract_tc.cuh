@@ -232,7 +232,10 @@ struct TcCfg {
   static constexpr int NB0 = 2 + NROW - NROWA;
   static constexpr int NXB = F16 && NB0 < 8 ? 8 - NB0 : 0;  // extra warps 4 + NROW ..
   static constexpr int NB = NB0 + NXB;
-  static constexpr int WARPS = 4 + NROW + NXB;
+  // with two extra warps, the one that would share the MMA-issuing warp's scheduler
+  // (warp index = 1 mod 4) stays idle: warps 4 + NROW and 4 + NROW + 2 stage B
+  static constexpr int SKIP = NXB == 2 && (4 + NROW + 1) % 4 == 1 ? 1 : 0;
+  static constexpr int WARPS = 4 + NROW + NXB + SKIP;
   static constexpr int THREADS = 32 * WARPS;
   static constexpr int NS = 3;                     // shared-memory stages
   static constexpr int KC = 2 * NZ;                // K of a chunk (real)
@@ -648,6 +651,8 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
       if (it >= 1 && !epilogue(it - 1, ea_prev)) { ok = false; break; }
     }
     if (ok && n_it >= 1) ok = epilogue(n_it - 1, ea_cur);
+  } else if (Cfg::SKIP && warp == 4 + Cfg::NROW + 1) {
+    // idle (keeps the MMA-issuing warp's scheduler free of a B warp)
   } else {
     // ---- B warps: warps 2, 3 and the row warps of quadrants without rows ----
     // One complex value x = X[col][beta Nz + b] (mirror signs applied) per thread and
@@ -656,7 +661,7 @@ __global__ void __launch_bounds__(TcCfg<NZ, R, F16>::THREADS, 1)
     // warp take (col, b % 4) of one core-matrix row group, so the stores of a warp fill
     // 128-byte core matrices without bank conflicts.
     const int bw = warp < 4 ? warp - 2
-                 : warp >= 4 + Cfg::NROW ? Cfg::NB0 + (warp - 4 - Cfg::NROW)
+                 : warp >= 4 + Cfg::NROW ? Cfg::NB0 + (warp - 4 - Cfg::NROW) / (1 + Cfg::SKIP)
                                          : 2 + ((warp - 4) >> 2) * (4 - Cfg::NQ) + ((warp & 3) - Cfg::NQ);
     const int bt = bw * 32 + lane, nbt = Cfg::NB * 32;
     for (int it = 0; it < n_it && ok; ++it) {
