@@ -593,6 +593,33 @@ __device__ __forceinline__ void df_warp_sum(Df &a) {
   }
 }
 
+// Warp sums of four double-floats at once by recursive halving: at the first two levels
+// each lane sends the half of its values that its partner keeps, so the four totals
+// cost six double-float additions and twelve shuffles per lane instead of twenty and
+// forty.  Returns, in every lane, the total of a0 (lanes 0-7), a1 (8-15), b0 (16-23)
+// or b1 (24-31).
+__device__ __forceinline__ Df df_warp_sum4(const Df &a0, const Df &a1, const Df &b0, const Df &b1) {
+  const int lane = threadIdx.x & 31;
+  const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0;
+  Df k0 = u16 ? b0 : a0, k1 = u16 ? b1 : a1;
+  const Df s0 = u16 ? a0 : b0, s1 = u16 ? a1 : b1;
+  {
+    const float p0 = __shfl_xor_sync(0xffffffffu, s0.s, 16), q0 = __shfl_xor_sync(0xffffffffu, s0.c, 16);
+    const float p1 = __shfl_xor_sync(0xffffffffu, s1.s, 16), q1 = __shfl_xor_sync(0xffffffffu, s1.c, 16);
+    df_add(k0, p0, q0);
+    df_add(k1, p1, q1);
+  }
+  Df k = u8 ? k1 : k0;
+  const Df sk = u8 ? k0 : k1;
+  df_add(k, __shfl_xor_sync(0xffffffffu, sk.s, 8), __shfl_xor_sync(0xffffffffu, sk.c, 8));
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    const float bs = __shfl_xor_sync(0xffffffffu, k.s, o), bc = __shfl_xor_sync(0xffffffffu, k.c, o);
+    df_add(k, bs, bc);
+  }
+  return k;
+}
+
 // Both double-float passes take chunks of kT * kDfEPT elements, kDfEPT per thread, and
 // walk the basis one vector at a time with the next vector's loads already in flight
 // (the dot pass keeps its chunk of x split in registers).  At 128 x 128 x 32 with two
@@ -636,6 +663,7 @@ __global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const float4 *__restrict
 #pragma unroll
       for (int j = 0; j < EPT; ++j) vn[j] = c0 + j * kT + tid < n ? __ldg(v0 + j * kT) : z4;
     }
+    Df pre = {0.f, 0.f}, pim = {0.f, 0.f};  // an even basis vector's sums, awaiting its partner
 #pragma unroll 1
     for (int i = 0; i < k1; ++i) {
       float4 vc[EPT];
@@ -656,9 +684,19 @@ __global__ void __launch_bounds__(kT) cgs_dot_df_kernel(const float4 *__restrict
         df_fma(aim, vrh, vrl, xs[j][2], xs[j][3]);
         df_fma(aim, -vih, -vil, xs[j][0], xs[j][1]);
       }
-      df_warp_sum(are);
-      df_warp_sum(aim);
-      if (lane == 0) red[wid][i] = make_double2(df_value(are), df_value(aim));
+      if (!(i & 1) && i + 1 < k1) {
+        pre = are;
+        pim = aim;
+        continue;
+      }
+      // the pair (i - 1, i), or the last vector alone
+      const int i0 = (i & 1) ? i - 1 : i;
+      const Df z = {0.f, 0.f};
+      const Df tot = (i & 1) ? df_warp_sum4(pre, pim, are, aim) : df_warp_sum4(are, aim, z, z);
+      if ((lane & 7) == 0 && (i0 + (lane >> 4)) <= i) {
+        double *dst = reinterpret_cast<double *>(&red[wid][i0 + (lane >> 4)]) + ((lane >> 3) & 1);
+        *dst = df_value(tot);
+      }
     }
     __syncthreads();
     if (tid <= k1) {

@@ -22,6 +22,14 @@ namespace fftfast {
 
 constexpr int kTI = 16;
 
+// The exchange between the two steps holds entry (q, k1, t) (q < Q, k1 < 16, t < TI)
+// at q kYQ + k1 kYK + t.  Both strides are odd multiples of one 8-byte word modulo 16,
+// so 16 consecutive t, 16 consecutive k1 or 16 consecutive q (the three thread
+// mappings below) touch 16 distinct 8-byte bank pairs.
+constexpr int kYK = kTI + 1;
+constexpr int kYQ = 16 * kYK + 1;
+__device__ __forceinline__ int yix(int q, int k1, int t) { return q * kYQ + k1 * kYK + t; }
+
 __device__ __forceinline__ float2 fmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -112,8 +120,8 @@ __device__ __forceinline__ void fill_table(float2 *tw, int L) {
   }
 }
 
-// Step 1 for one (sequence t, q): v[bitrev(p)] holds x[q + Q p]; writes
-// Y[(q 16 + k1) TI + t].
+// Step 1 for one (sequence t, q): v[bitrev(p)] holds x[q + Q p]; writes entry
+// (q, k1, t) of the exchange.
 template <int Q, bool INV>
 __device__ __forceinline__ void step1(float2 (&v)[16], const float2 *tw, float2 *Y, int q, int t) {
   constexpr int L = 16 * Q;
@@ -126,7 +134,7 @@ __device__ __forceinline__ void step1(float2 (&v)[16], const float2 *tw, float2 
       if (INV) w.y = -w.y;
       r = fmul(r, w);
     }
-    Y[(q * 16 + k1) * kTI + t] = r;
+    Y[yix(q, k1, t)] = r;
   }
 }
 
@@ -139,7 +147,7 @@ __device__ __forceinline__ void step2(float2 (&w)[Q], const float2 *tw, const fl
   constexpr int L = 16 * Q;
   if constexpr ((Q & (Q - 1)) == 0) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) w[bitrev<Q>(q)] = Y[(q * 16 + k1) * kTI + t];
+    for (int q = 0; q < Q; ++q) w[bitrev<Q>(q)] = Y[yix(q, k1, t)];
     dft_br<Q, INV>(w, tw, L / Q);
   } else {
     constexpr int M = Q / 3;
@@ -148,7 +156,7 @@ __device__ __forceinline__ void step2(float2 (&w)[Q], const float2 *tw, const fl
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
 #pragma unroll
-      for (int m = 0; m < M; ++m) z[r][bitrev<M>(m)] = Y[((r + 3 * m) * 16 + k1) * kTI + t];
+      for (int m = 0; m < M; ++m) z[r][bitrev<M>(m)] = Y[yix(r + 3 * m, k1, t)];
       dft_br<M, INV>(z[r], tw, L / M);
     }
     // sin(2 pi / 3); w_3 = -1/2 -+ i s (forward / inverse)
@@ -212,49 +220,45 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) axis_kernel(const floa
   }
 }
 
-// Forward row pass: x[CZ][Ny][Nx] times in_scale[Nz][Ny][Nx], zero-padded to L = 2 Nx,
-// transformed along x -> T1[Ny][L][CZ].
+// Forward row pass: x[CZ][Ny][Nx] times in_scale[Nz][Ny][Nx], zero-padded to L = 2 Nx
+// (Nx = 8 Q), transformed along x -> T1[Ny][L][CZ].  Step 1 runs with q in the low
+// thread bits, so each thread loads its eight nonzero inputs straight from the rows
+// (Q consecutive elements of a row per warp slice) while the table is being filled;
+// step 2 runs with the sequence in the low bits, so the stores are 16 consecutive
+// elements of the sequence index.
 template <int Q, typename TX>
 __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_fwd_kernel(
     const typename cplx<TX>::type *__restrict__ x, const float2 *__restrict__ in_scale,
     float2 *__restrict__ t1, int CZ, int Nz, int Ny, int Nx) {
-  constexpr int L = 16 * Q;
-  constexpr int LD = kTI + 1;
+  constexpr int L = 16 * Q, NXC = 8 * Q;
   extern __shared__ float2 smf[];
-  float2 *tw = smf, *Y = smf + L;  // Y: input stage [Nx][LD] first, then the exchange
-  const int t = threadIdx.x % kTI, j = threadIdx.x / kTI;
+  float2 *tw = smf, *Y = smf + L;
+  const int tid = threadIdx.x;
   const int cz0 = blockIdx.x * kTI;
   const int y = blockIdx.y;
+  const int q = tid % Q, ts = tid / Q;
+  const bool s1 = tid < Q * kTI;
+  const bool live = s1 && cz0 + ts < CZ;
+  float2 v[16], sc[8];
+  {
+    const int cz = live ? cz0 + ts : 0;
+    const long long row = ((long long)cz * Ny + y) * NXC + q;
+    const long long srow = ((long long)(cz % Nz) * Ny + y) * NXC + q;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      v[bitrev<16>(p)] = live ? to_f32(x[row + Q * p]) : make_float2(0.f, 0.f);
+      sc[p] = (live && in_scale) ? in_scale[srow + Q * p] : make_float2(1.f, 0.f);
+    }
+#pragma unroll
+    for (int p = 8; p < 16; ++p) v[bitrev<16>(p)] = make_float2(0.f, 0.f);
+  }
   fill_table(tw, L);
-  // Nx = L / 2 = 8 Q here, so the staging loop has a compile-time trip count and its
-  // loads are issued together
-  constexpr int NXC = 8 * Q, NT = kTI * (Q > 16 ? Q : 16);
 #pragma unroll
-  for (int it = 0; it < (NXC * kTI + NT - 1) / NT; ++it) {
-    const int e = threadIdx.x + it * NT;
-    if (e < NXC * kTI) {
-      const int tt = e / NXC, xx = e % NXC;
-      const int cz = cz0 + tt;
-      float2 v = make_float2(0.f, 0.f);
-      if (cz < CZ) {
-        v = to_f32(x[((long long)cz * Ny + y) * NXC + xx]);
-        if (in_scale) v = cmul(v, in_scale[((long long)(cz % Nz) * Ny + y) * NXC + xx]);
-      }
-      Y[xx * LD + tt] = v;
-    }
-  }
+  for (int p = 0; p < 8; ++p) v[bitrev<16>(p)] = cmul(v[bitrev<16>(p)], sc[p]);
   __syncthreads();
-  float2 v[16];
-  if (j < Q) {
-#pragma unroll
-    for (int p = 0; p < 16; ++p) {
-      const int l = j + Q * p;
-      v[bitrev<16>(p)] = l < Nx ? Y[l * LD + t] : make_float2(0.f, 0.f);
-    }
-  }
+  if (s1) step1<Q, false>(v, tw, Y, q, ts);
   __syncthreads();
-  if (j < Q) step1<Q, false>(v, tw, Y, j, t);
-  __syncthreads();
+  const int t = tid % kTI, j = tid / kTI;
   if (j < 16) {
     float2 w[Q];
     step2<Q, false>(w, tw, Y, j, t);
@@ -265,60 +269,54 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_fwd_kernel(
   }
 }
 
-// Inverse row pass: T1[Ny][L][CZ] -> inverse along kx, keep x < Nx, and write
-// y[CZ][Ny][Nx] = diag[cell] x[CZ][cell] + out_scale[cell] value.
+// Inverse row pass: T1[Ny][L][CZ] -> inverse along kx, keep x < Nx (= 8 Q), and write
+// y[CZ][Ny][Nx] = diag[cell] x[CZ][cell] + out_scale[cell] value.  Step 1 runs with the
+// sequence in the low thread bits (loads of 16 consecutive sequence elements), step 2
+// with k1 in the low bits, so each output x = k1 + 16 k2 goes straight to its row
+// (16 consecutive elements per half-warp).
 template <int Q, typename TX>
 __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) rows_inv_kernel(
     const float2 *__restrict__ t1, const typename cplx<TX>::type *__restrict__ x,
     const float2 *__restrict__ diag, const float2 *__restrict__ out_scale,
     typename cplx<TX>::type *__restrict__ y_out, int CZ, int Nz, int Ny, int Nx) {
-  constexpr int L = 16 * Q;
-  constexpr int LD = kTI + 1;
+  constexpr int L = 16 * Q, NXC = 8 * Q;
   extern __shared__ float2 smf[];
-  float2 *tw = smf, *Y = smf + L;  // Y: the exchange, then the output stage [Nx][LD]
-  const int t = threadIdx.x % kTI, j = threadIdx.x / kTI;
+  float2 *tw = smf, *Y = smf + L;
+  const int tid = threadIdx.x;
   const int cz0 = blockIdx.x * kTI;
   const int y = blockIdx.y;
-  const bool live = cz0 + t < CZ;
-  fill_table(tw, L);
-  __syncthreads();
-  if (j < Q) {
+  {
+    const int t = tid % kTI, j = tid / kTI;
+    const bool live = cz0 + t < CZ;
     float2 v[16];
+    if (j < Q) {
 #pragma unroll
-    for (int p = 0; p < 16; ++p)
-      v[bitrev<16>(p)] = live ? t1[((long long)y * L + j + Q * p) * CZ + cz0 + t] : make_float2(0.f, 0.f);
-    step1<Q, true>(v, tw, Y, j, t);
-  }
-  __syncthreads();
-  float2 w[Q];
-  if (j < 16) step2<Q, true>(w, tw, Y, j, t);
-  __syncthreads();
-  if (j < 16) {
-#pragma unroll
-    for (int k2 = 0; k2 < Q; ++k2) {
-      const int xx = j + 16 * k2;
-      if (xx < Nx) Y[xx * LD + t] = w[k2];
+      for (int p = 0; p < 16; ++p)
+        v[bitrev<16>(p)] = live ? t1[((long long)y * L + j + Q * p) * CZ + cz0 + t] : make_float2(0.f, 0.f);
     }
+    fill_table(tw, L);
+    __syncthreads();
+    if (j < Q) step1<Q, true>(v, tw, Y, j, t);
   }
   __syncthreads();
-  constexpr int NXC = 8 * Q, NT = kTI * (Q > 16 ? Q : 16);
+  const int k1 = tid % 16, ts = tid / 16;
+  const int cz = cz0 + ts;
+  if (ts < kTI && cz < CZ) {
+    float2 w[Q];
+    step2<Q, true>(w, tw, Y, k1, ts);
+    const long long row = ((long long)cz * Ny + y) * NXC + k1;
+    const long long srow = ((long long)(cz % Nz) * Ny + y) * NXC + k1;
 #pragma unroll
-  for (int it = 0; it < (NXC * kTI + NT - 1) / NT; ++it) {
-    const int e = threadIdx.x + it * NT;
-    const int tt = e / NXC, xx = e % NXC;
-    const int cz = cz0 + tt;
-    if (e < NXC * kTI && cz < CZ) {
-      const long long cell = ((long long)(cz % Nz) * Ny + y) * NXC + xx;
-      const long long gi = ((long long)cz * Ny + y) * NXC + xx;
-      float2 val = cmul(Y[xx * LD + tt], out_scale[cell]);
-      if (diag) cfma(val, diag[cell], to_f32(x[gi]));
-      y_out[gi] = to_prec<TX>(val);
+    for (int k2 = 0; k2 < Q / 2; ++k2) {
+      float2 val = cmul(w[k2], out_scale[srow + 16 * k2]);
+      if (diag) cfma(val, diag[srow + 16 * k2], to_f32(x[row + 16 * k2]));
+      y_out[row + 16 * k2] = to_prec<TX>(val);
     }
   }
 }
 
 // dynamic shared memory of every kernel above: the table and the exchange
-constexpr size_t smem_bytes(int Q) { return sizeof(float2) * (size_t)(16 * Q) * (1 + kTI); }
+constexpr size_t smem_bytes(int Q) { return sizeof(float2) * (size_t)Q * (16 + kYQ); }
 constexpr int threads(int Q) { return kTI * (Q > 16 ? Q : 16); }
 
 }  // namespace fftfast
