@@ -239,7 +239,9 @@ int fast_q(int L) { return (L == 128 || L == 192 || L == 256 || L == 384 || L ==
 template <int Q, bool INV>
 void axis_fast(const float2 *in, float2 *out, int outer, int Lin, int Lout, long long inner, float scale,
                cudaStream_t s) {
-  auto k = fftfast::axis_kernel<Q, INV>;
+  constexpr int L = 16 * Q;
+  const bool half = INV ? (Lin == L && 2 * Lout == L) : (2 * Lin == L && Lout == L);
+  auto k = half ? fftfast::axis_kernel<Q, INV, true> : fftfast::axis_kernel<Q, INV, false>;
   set_smem(k, fftfast::smem_bytes(Q));
   dim3 grid((unsigned)((inner + fftfast::kTI - 1) / fftfast::kTI), (unsigned)outer);
   k<<<grid, fftfast::threads(Q), fftfast::smem_bytes(Q), s>>>(in, out, Lin, Lout, inner, scale);

@@ -185,8 +185,11 @@ __device__ __forceinline__ void step2(float2 (&w)[Q], const float2 *tw, const fl
 }
 
 // Transform along the middle axis of in[outer][Lin][inner] (rows >= Lin are zero) ->
-// out[outer][Lout][inner] (rows >= Lout dropped), times scale.
-template <int Q, bool INV>
+// out[outer][Lout][inner] (rows >= Lout dropped), times scale.  HALF: the zero-padded
+// forward transform (Lin = L / 2, Lout = L) or the cropped inverse (Lin = L, Lout =
+// L / 2), with the zero inputs and the dropped outputs known at compile time.  The
+// loads are issued before the twiddle table is built, so the two overlap.
+template <int Q, bool INV, bool HALF>
 __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) axis_kernel(const float2 *__restrict__ in,
                                                                      float2 *__restrict__ out, int Lin, int Lout,
                                                                      long long inner, float scale) {
@@ -197,17 +200,18 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) axis_kernel(const floa
   const long long i0 = (long long)blockIdx.x * kTI;
   const long long o = blockIdx.y;
   const bool live = i0 + t < inner;
-  fill_table(tw, L);
-  __syncthreads();
+  float2 v[16];
   if (j < Q) {
-    float2 v[16];
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
       const int l = j + Q * p;
-      v[bitrev<16>(p)] = (live && l < Lin) ? in[(o * Lin + l) * inner + i0 + t] : make_float2(0.f, 0.f);
+      const bool have = HALF ? (INV || p < 8) : l < Lin;
+      v[bitrev<16>(p)] = (live && have) ? in[(o * Lin + l) * inner + i0 + t] : make_float2(0.f, 0.f);
     }
-    step1<Q, INV>(v, tw, Y, j, t);
   }
+  fill_table(tw, L);
+  __syncthreads();
+  if (j < Q) step1<Q, INV>(v, tw, Y, j, t);
   __syncthreads();
   if (j < 16) {
     float2 w[Q];
@@ -215,7 +219,8 @@ __global__ void __launch_bounds__(kTI *(Q > 16 ? Q : 16)) axis_kernel(const floa
 #pragma unroll
     for (int k2 = 0; k2 < Q; ++k2) {
       const int l = j + 16 * k2;
-      if (live && l < Lout) out[(o * Lout + l) * inner + i0 + t] = make_float2(w[k2].x * scale, w[k2].y * scale);
+      const bool keep = HALF ? (!INV || k2 < Q / 2) : l < Lout;
+      if (live && keep) out[(o * Lout + l) * inner + i0 + t] = make_float2(w[k2].x * scale, w[k2].y * scale);
     }
   }
 }
