@@ -84,6 +84,11 @@ struct ie_ctx {
   bool gs_df = true;                           // IE_MIXED_FP64K inner Gram-Schmidt in double-float arithmetic
   float4 *Vs = nullptr;                        // split copy of the FP64 basis [restart + 1][R][3N] (gs_df)
   cudaEvent_t pin_ev[4] = {};
+  // the Givens steps of a Krylov iteration run on a second stream, overlapping the next
+  // product: gs_ev (Gram-Schmidt of the iteration done) orders them after their
+  // column, giv_ev (Givens step done) orders the next Gram-Schmidt pass after them
+  cudaStream_t side = nullptr;
+  cudaEvent_t gs_ev = nullptr, giv_ev = nullptr;
   void *jfac = nullptr, *gdiv = nullptr;       // per cell: 2 s gamma; (dgamma/dln sigma_a) / gamma (0 off the anomaly)
   void *efac = nullptr;                        // per cell: 1 / a = 2 s / (sigma_a + conj sigma_b) (E = U / a)
   int n_rec = 0;                               // receivers (ie_set_receivers)
@@ -581,7 +586,13 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
     res->cycles++;
     // the cycle: products, Gram-Schmidt and Givens steps stay on the device; the host
     // learns the number of right-hand sides still iterating from a pinned copy made
-    // kLag iterations earlier, so it never waits for the iteration it just issued
+    // kLag iterations earlier, so it never waits for the iteration it just issued.  The
+    // Givens step of iteration k runs on the side stream, beside the product of
+    // iteration k + 1 (which does not depend on it); the Gram-Schmidt pass of k + 1, which
+    // rewrites the column and norm the step reads, waits for it.  With per-step
+    // profiling everything stays on the main stream.
+    const bool overlap = c->prof < 2;
+    bool giv_pending = false;
     int kmax = 0;
     for (int k = 0; k < m && it < max_iter; ++k) {
       if (k >= kGivensLag) {
@@ -592,21 +603,33 @@ ie_status gmres(ie_ctx *c, const Group &g0, int transpose, ie::C<T> *b, ie::C<T>
       ProfSpan sp_op(c, sizeof(T) == 4 ? IE_PROF_PRODUCT_C64 : IE_PROF_PRODUCT_C128);
       IE_TRY(op(Vb + (long long)k * nR, w, R));
       sp_op.end();
+      if (giv_pending) IE_CUDA(cudaStreamWaitEvent(s, c->giv_ev, 0));
       ProfSpan sp_gs(c, sizeof(T) == 4 ? IE_PROF_GS_C64 : IE_PROF_GS_C128);
       if (ie::gmres_orthogonalize<T>(Vb, w, Vb + (long long)(k + 1) * nR, h1, h2, c->part, c->nrmpart, c->nrm,
                                   c->gsflag, k + 1, R, n, ldh, s, single && c->gs_df, c->Vs,
                                   c->Vs + (long long)(k + 1) * nR) != 0)
         return IE_ERR_ARG;
       sp_gs.end();
+      cudaStream_t sg = s;
+      if (overlap) {
+        IE_CUDA(cudaEventRecord(c->gs_ev, s));
+        IE_CUDA(cudaStreamWaitEvent(c->side, c->gs_ev, 0));
+        sg = c->side;
+      }
       ProfSpan sp_gv(c, IE_PROF_GIVENS);
-      ie::givens_step(st, h1, h2, c->nrm, k, R, m, ldh, sizeof(T) == 4, s);
+      ie::givens_step(st, h1, h2, c->nrm, k, R, m, ldh, sizeof(T) == 4, sg);
       sp_gv.end();
       const int slot = k % kPinSlots;
-      IE_CUDA(cudaMemcpyAsync(c->pin_active + 1 + slot, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-      IE_CUDA(cudaEventRecord(c->pin_ev[slot], s));
+      IE_CUDA(cudaMemcpyAsync(c->pin_active + 1 + slot, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, sg));
+      IE_CUDA(cudaEventRecord(c->pin_ev[slot], sg));
+      if (overlap) {
+        IE_CUDA(cudaEventRecord(c->giv_ev, sg));
+        giv_pending = true;
+      }
       ++it;
       kmax = k + 1;
     }
+    if (giv_pending) IE_CUDA(cudaStreamWaitEvent(s, c->giv_ev, 0));  // the cycle's last Givens step
     // x += V y with y from the rotated least-squares problem (zero beyond each kr); the
     // FP64 vectors of the IE_MIXED_FP64K inner solves in double-float from the split basis
     const bool dfk = sizeof(T) == 8 && single && c->gs_df;
@@ -866,8 +889,12 @@ void ie_destroy(ie_ctx *c) {
   prof_clear(c);
   for (void *p : c->allocs) cudaFree(p);
   if (c->pin_active) cudaFreeHost(c->pin_active);
+  if (c->side) cudaStreamSynchronize(c->side);
   for (auto &e : c->pin_ev)
     if (e) cudaEventDestroy(e);
+  if (c->gs_ev) cudaEventDestroy(c->gs_ev);
+  if (c->giv_ev) cudaEventDestroy(c->giv_ev);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -1164,6 +1191,9 @@ static ie_status setup_impl(const ie_grid *g, const ie_layers *lay, const double
     IE_TRY(dalloc(c, &c->err, sizeof(int)));
     IE_CUDA(cudaMemset(c->err, 0, sizeof(int)));
     for (int k = 0; k < kPinSlots; ++k) IE_CUDA(cudaEventCreateWithFlags(&c->pin_ev[k], cudaEventDisableTiming));
+    IE_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    IE_CUDA(cudaEventCreateWithFlags(&c->gs_ev, cudaEventDisableTiming));
+    IE_CUDA(cudaEventCreateWithFlags(&c->giv_ev, cudaEventDisableTiming));
   }
   IE_CUDA(cudaStreamSynchronize(c->stream));
   if (c->autotune) {
